@@ -1,0 +1,249 @@
+"""Scheme-level pins of the oracle: the paper's own 0+1D algorithm in modal form
+(Sec. 4.4), invariants (static equilibrium, conservation, uniform-grid
+reduction), second-order time accuracy, the conformal free-streaming closed
+form, viscous Bjorken hydrodynamics (Sec. 4.5), and linear sound waves."""
+import math
+
+import numpy as np
+import pytest
+from numpy.polynomial import Polynomial
+from numpy.polynomial import legendre as npleg
+from scipy.integrate import solve_ivp
+from scipy.optimize import curve_fit
+
+H3 = 0.1973269804 ** 3
+
+
+def paper_0p1d(o, eps0, tau0, dtau, nsteps):
+    """Sec. 4.4 literally, in the modal representation of Eq. newfansatz:
+    a^{ml} projections, the s_1^{ml}, s_2^{ml} coefficient sums, the predictor
+    for f and ln M, and the trapezoid corrector.  Readings: T re-matched from the
+    populations at each stage; cosh^2 weight in the d ln M numerator; f_1 = f."""
+    nd, p = o.nodes(), o.params
+    c, s, wxi, mu, wth = nd["c"], nd["s"], nd["wxi"], nd["mu"], nd["wth"]
+    N, Nt, z0, Z = len(c), len(mu), p["z0"], p["Z"]
+    ip = lambda a, b: float(np.sum(wxi * a(c) * b(c)))
+    R = []
+    for l in range(N):  # R_l orthogonal for e^{-z0 cosh} sinh^2 (Gram-Schmidt, exact for l < N)
+        q = Polynomial.basis(l)
+        for r in R:
+            q = q - (ip(q, r) / ip(r, r)) * r
+        R.append(q)
+    I = np.array([ip(r, r) for r in R])
+    Lm = [npleg.Legendre.basis(m) for m in range(Nt)]
+    C, S, MU = c[None, :], s[None, :], mu[:, None]
+    W = np.exp(z0 * C) * wxi[None, :] * wth[:, None] / 2.0
+    th2 = (S / C) ** 2
+    Rv = [r(C) for r in R]
+    Rd = [r.deriv()(C) for r in R]
+    Lv = [L(MU) for L in Lm]
+    Ld = [L.deriv()(MU) for L in Lm]
+
+    def recon(coef):
+        out = np.zeros((Nt, N))
+        for m in range(Nt):
+            for l in range(N):
+                out += coef[m, l] * Lv[m] * Rv[l]
+        return out * np.exp(-z0 * C)
+
+    def S1S2(f):
+        s1, s2 = np.zeros((Nt, N)), np.zeros((Nt, N))
+        for m in range(Nt):
+            for l in range(N):
+                b1 = Lv[m] * (Rd[l] * C - Rv[l]) * MU ** 2 * th2 + Rv[l] * (Lv[m] + Ld[m] * (MU - MU ** 3))
+                b2 = Lv[m] * Rv[l] * (2 + 1 / C ** 2) + Lv[m] * Rd[l] * C * th2
+                s1[m, l] = -(2 * m + 1) / I[l] * np.sum(W * f * b1)
+                s2[m, l] = -(2 * m + 1) / I[l] * np.sum(W * f * b2)
+        return recon(s1), recon(s2)
+
+    def stage(f, lnM, tau):
+        M = math.exp(lnM)
+        eps_kin = M ** 4 / (2 * math.pi ** 2) * np.sum(W * C ** 2 * f)
+        T = o.solve_T(eps_kin, 0)
+        e = o.eos(T)
+        feq = Z * np.exp(-np.sqrt(e["M"] ** 2 + M ** 2 * S ** 2) / T)
+        Sf1, Sf2 = S1S2(f)
+        R0 = Sf1 / tau - (f - feq) / e["tauR"]
+        g = -e["D"] * np.sum(W * C ** 2 * R0) / np.sum(W * f)
+        return R0 + g * Sf2, g, T
+
+    T0 = o.solve_T(eps0 * H3, 1)
+    lnM = math.log(o.eos(T0)["M"])
+    f = Z * np.exp(-math.exp(lnM) * C / T0) * np.ones((Nt, 1))
+    tau = tau0
+    for _ in range(nsteps):
+        r1, g1, _ = stage(f, lnM, tau)
+        fs, ms = f + dtau * r1, lnM + dtau * g1
+        r2, g2, _ = stage(fs, ms, tau + dtau)
+        f, lnM = 0.5 * (f + fs + dtau * r2), 0.5 * (lnM + ms + dtau * g2)
+        tau += dtau
+    M = math.exp(lnM)
+    T = o.solve_T(M ** 4 / (2 * math.pi ** 2) * np.sum(W * C ** 2 * f), 0)
+    return f, lnM, T
+
+
+def test_paper_algorithm_0p1d(oracle_mod):
+    # the paper's run parameters (Sec. 4.5): N_xi = N_theta = 5, dtau = 0.2 fm/c, M0/T0 = 1
+    o = oracle_mod.Oracle(nx=1, ny=1, n_xi=5, n_theta=5, n_phi_half=1, eta_over_s=0.5)
+    fp, lnMp, Tp = paper_0p1d(o, 25.0, 1.0, 0.2, 15)
+    f, lnM = o.init_state(np.array([25.0]))
+    o.step(f, lnM, 1.0, 0.2, 15)
+    m = o.moments(f, lnM)[0]
+    assert m[1] == pytest.approx(Tp, rel=1e-11)
+    assert lnM[0] == pytest.approx(lnMp, rel=1e-11)
+    fo = f.reshape(2, 5, 5)
+    for l in range(2):
+        assert np.allclose(fo[l], fp, rtol=1e-9, atol=1e-12 * fp.max())
+
+
+def test_uniform_grid_is_the_0p1d_algorithm(oracle_mod):
+    kw = dict(n_xi=6, n_theta=4, n_phi_half=3, eta_over_s=0.1)
+    o1 = oracle_mod.Oracle(nx=1, ny=1, **kw)
+    o2 = oracle_mod.Oracle(nx=3, ny=2, **kw)
+    f1, m1 = o1.init_state(np.array([12.0]))
+    f2, m2 = o2.init_state(np.full(6, 12.0))
+    o1.step(f1, m1, 0.4, 0.02, 6)
+    o2.step(f2, m2, 0.4, 0.02, 6)
+    for i in range(6):
+        assert np.array_equal(f2[i], f1[0]) and m2[i] == m1[0]
+
+
+def test_static_equilibrium_stays_fixed(oracle_mod):
+    # Minkowski, u = 0, uniform T_s, z0 = M(T_s)/T_s: the lattice is exact for f_eq's moments
+    probe = oracle_mod.Oracle(nx=1, ny=1)
+    Ts = 0.25
+    z0 = probe.eos(Ts)["x"]
+    o = oracle_mod.Oracle(nx=2, ny=2, metric=0, z0=z0, eta_over_s=0.1)
+    eps = o.eos(Ts)["eps"] / H3
+    f, lnM = o.init_state(np.full(4, eps))
+    f0, m0 = f.copy(), lnM.copy()
+    assert o.moments(f, lnM)[0, 1] == pytest.approx(Ts, rel=1e-14)
+    o.step(f, lnM, 0.5, 0.05, 200)
+    big = f0 > 1e-30
+    assert np.max(np.abs(f[big] / f0[big] - 1)) < 1e-11
+    assert np.max(np.abs(lnM - m0)) < 1e-12
+
+
+def _Ttau(o, f, lnM):
+    nd = o.nodes()
+    p = o.params
+    L, Nt, N = 2 * p["n_phi_half"], p["n_theta"], p["n_xi"]
+    w = o.weights()
+    c = np.tile(nd["c"], L * Nt)
+    s = np.tile(nd["s"], L * Nt)
+    st = np.tile(np.repeat(nd["sth"], N), L)
+    cp = np.repeat(nd["cph"], Nt * N)
+    sp = np.repeat(nd["sph"], Nt * N)
+    M4 = np.exp(4 * lnM)[:, None] / (2 * math.pi ** 2)
+    return np.array([np.sum(M4 * f * w * c * c), np.sum(M4 * f * w * c * s * st * cp),
+                     np.sum(M4 * f * w * c * s * st * sp)])
+
+
+def test_free_streaming_conserves_energy_momentum(oracle_mod):
+    # Minkowski, constant mass, tau_R = inf: sum_x T^{tau nu} is conserved to rounding
+    o = oracle_mod.Oracle(nx=8, ny=6, metric=0, eos_kind=1, eos_m0=0.4, eta_over_s=math.inf,
+                          n_xi=6, n_theta=4, n_phi_half=4)
+    rng = np.random.default_rng(3)
+    f, lnM = o.init_state(0.5 + rng.random(48))
+    f *= 1 + 0.2 * rng.standard_normal(f.shape)  # break isotropy: nonzero momentum
+    P0, lnM0 = _Ttau(o, f, lnM), lnM.copy()
+    o.step(f, lnM, 1.0, 0.05, 40)
+    P1 = _Ttau(o, f, lnM)
+    assert abs(P0[1]) > 1e-6 * P0[0]
+    assert np.allclose(P1, P0, rtol=0, atol=1e-13 * P0[0])
+    assert np.array_equal(lnM, lnM0)
+    assert np.allclose(lnM, math.log(0.4), rtol=1e-15)
+
+
+def test_heun_is_second_order(oracle_mod):
+    o = oracle_mod.Oracle(nx=1, ny=1, n_xi=6, n_theta=6, n_phi_half=1, eta_over_s=0.1)
+    T = []
+    for k in [1, 2, 4]:
+        f, lnM = o.init_state(np.array([20.0]))
+        o.step(f, lnM, 0.4, 0.036 / k, 25 * k)
+        T.append(o.moments(f, lnM)[0, 1])
+    ratio = (T[1] - T[0]) / (T[2] - T[1])
+    assert ratio == pytest.approx(4.0, rel=0.01)
+
+
+def test_conformal_free_streaming_bjorken(oracle_mod):
+    # eps/eps0 = [ (tau0/tau)^2 + arctan(sqrt(r^2-1))/sqrt(r^2-1) ] / 2, r = tau/tau0,
+    # the eta/s = inf limit of Sec. 4.5 for an isotropic massless start
+    errs = []
+    for Nt in [8, 16]:
+        o = oracle_mod.Oracle(nx=1, ny=1, eos_kind=2, family=1, n_theta=Nt, n_phi_half=1,
+                              eta_over_s=math.inf, T0=0.5)
+        f, lnM = o.init_state(np.array([10.0]))
+        e0 = o.moments(f, lnM)[0, 0]
+        o.step(f, lnM, 0.4, 0.004, 300)
+        r = 1.6 / 0.4
+        ex = 0.5 * (1 / r ** 2 + math.atan(math.sqrt(r * r - 1)) / math.sqrt(r * r - 1))
+        errs.append(abs(o.moments(f, lnM)[0, 0] / e0 / ex - 1))
+    assert errs[0] < 3e-4 and errs[1] < 1e-5 and errs[1] < errs[0] / 10
+
+
+def _hydro_T(o, etas, eps0, tau0, tau1):
+    """Second-order Bjorken hydrodynamics of Sec. 4.5 (Eq. hydroeq) with
+    tau_pi = 5 eta/(eps+P), lambda_1 = 5/7 eta tau_pi; GeV units."""
+    hc = 0.1973269804
+
+    def rhs(t, y):
+        eps, Phi = y
+        T = o.solve_T(eps, 1)
+        e = o.eos(T)
+        P, eta = e["p"], etas * e["s"]
+        tp = 5 * eta / (eps + P)
+        lam = 5.0 / 7.0 * eta * tp
+        return [-(eps + P) / t + Phi / t,
+                -Phi / tp + 4 * eta / (3 * tp * t) - 4 * Phi / (3 * t) - lam / (2 * tp * eta ** 2) * Phi ** 2]
+
+    sol = solve_ivp(rhs, [tau0 / hc, tau1 / hc], [eps0 * H3, 0.0], rtol=1e-10, atol=1e-14)
+    return o.solve_T(sol.y[0, -1], 1)
+
+
+@pytest.mark.parametrize("etas,tol", [(0.01, 0.004), (0.08, 0.012), (0.2, 0.025)])
+def test_viscous_bjorken_vs_hydro(oracle_mod, etas, tol):
+    o = oracle_mod.Oracle(nx=1, ny=1, n_phi_half=1, eta_over_s=etas)
+    f, lnM = o.init_state(np.array([30.0]))
+    o.step(f, lnM, 0.4, 0.018, 200)
+    T_lb = o.moments(f, lnM)[0, 1]
+    assert T_lb == pytest.approx(_hydro_T(o, etas, 30.0, 0.4, 4.0), rel=tol)
+
+
+def test_sound_wave_non_ideal_eos(oracle_mod):
+    # Minkowski, T = 0.3 GeV where s/T^3 is flat: c_s^2 = 1/3 although M = 1.83 T
+    # (the bag function makes the difference; an ideal gas of that mass has c_s^2 = 0.272),
+    # shear damping Gamma k^2/2 with Gamma = 4 eta/(3 (eps+P)) and zeta = 0 there (Sec. 4.1).
+    nx, A, T0, etas, dt = 32, 1e-3, 0.3, 0.08, 0.05
+    o = oracle_mod.Oracle(nx=nx, ny=1, metric=0, eta_over_s=etas)
+    e = o.eos(T0)
+    e0 = e["eps"] / H3
+    x = np.arange(nx)
+    cosk = np.cos(2 * np.pi * x / nx)
+    f, lnM = o.init_state(e0 * (1 + A * cosk))
+    amp = lambda: np.sum((o.moments(f, lnM)[:, 0] - e0) * cosk) * 2 / nx / (A * e0)
+    ts, amps = [0.0], [amp()]
+    for i in range(240):
+        o.step(f, lnM, 1.0, dt, 1)
+        ts.append((i + 1) * dt)
+        amps.append(amp())
+    k = 2 * np.pi / (nx * o.params["dx"])
+    cs2 = e["s"] / (T0 * e["sp"])
+    fn = lambda t, a, g, w, ph: a * np.exp(-g * t) * np.cos(w * t + ph)
+    p, _ = curve_fit(fn, np.array(ts), np.array(amps), p0=[1, 0.03, math.sqrt(cs2) * k, 0])
+    assert cs2 == pytest.approx(1 / 3, rel=1e-3)
+    assert p[2] == pytest.approx(math.sqrt(cs2) * k, rel=0.025)
+    gam = 4.0 / 3.0 * etas / T0 * 0.1973269804 * k * k / 2
+    assert p[1] == pytest.approx(gam, rel=0.1)
+
+
+def test_step_sites_matches_full_step(oracle_mod):
+    o = oracle_mod.Oracle(nx=7, ny=5, n_xi=5, n_theta=4, n_phi_half=3, eta_over_s=0.12)
+    rng = np.random.default_rng(9)
+    f, lnM = o.init_state(1.0 + 20 * rng.random(35))
+    o.step(f, lnM, 0.4, 0.02, 3)  # develop flow and mass gradients
+    sites = np.array([0, 6, 17, 34])
+    fo, mo = o.step_sites(f, lnM, 0.46, 0.02, sites)
+    o.step(f, lnM, 0.46, 0.02, 1)
+    assert np.allclose(fo, f[sites], rtol=1e-13, atol=1e-300)
+    assert np.allclose(mo, lnM[sites], rtol=1e-14)
