@@ -1,0 +1,254 @@
+"""Benchmark of the fused stream-collide step (site-population updates/s).
+
+Workload (one "step" = one predictor-corrector time step over the whole grid):
+256 x 256 transverse grid, dx = 0.2 fm, 8 x 8 x 12 = 768-node momentum lattice,
+FP32 populations (FP64 Landau matching / EOS inversion), eta/s = 0.16,
+dtau = 0.0036 fm/c from tau = 0.4 fm/c, 40 seeded Gaussian hotspots.
+The two population arrays (402 MB) exceed the 126 MB L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun) each rank runs an independent replica of the workload
+(the single-grid step has no multi-GPU decomposition here): weak scaling.
+--impl reference times the FP64 CPU oracle on this machine's host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX = NY = 256
+ETA_S, TAU0, DTAU = 0.16, 0.4, 0.0036
+WORKLOAD = "rlb-milne-2+1d 256x256 grid, 768 nodes (8xi x 8theta x 12phi), FP32 populations"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str | None):
+        self.proc = None
+        self.path = None
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if device_id:
+                cmd += ["-i", device_id]
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_rate(eps_window, steps, nthreads):
+    """Oracle (FP64 CPU) updates/s on a window of the workload."""
+    from oracle.oracle import Oracle
+    ny, nx = eps_window.shape
+    o = Oracle(nx=nx, ny=ny, eta_over_s=ETA_S)
+    f, lnM = o.init_state(eps_window, nthreads)
+    t0 = time.perf_counter()
+    o.step(f, lnM, TAU0, DTAU, steps, nthreads)
+    dt = time.perf_counter() - t0
+    return nx * ny * o.nn * steps / dt, dt
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return 0
+    from paper_1108_5561_gb300.inputs import hotspots
+    eps0, _, _ = hotspots(NX, NY, n=40, seed=1108)
+    c = NX // 2
+    win = eps0[c - 8:c + 8, c - 8:c + 8]  # 16 x 16 sample per step
+    cores = os.cpu_count() or 1
+    rate, dt = oracle_rate(win, args.warmup + args.steps, cores)
+    line = {
+        "impl": "reference", "metric": "site-population updates/s", "value": rate,
+        "unit": "updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / (args.warmup + args.steps), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision_of_oracle": "f64", "grid": [NX, NY],
+                   "nodes_per_site": 768},
+        "cpu_baseline": {"value": rate, "unit": "updates/s", "cores": cores, "kind": "oracle",
+                         "sample": "16x16 central window of the 256x256 workload, one oracle "
+                                   "step per benchmark step"},
+        "e2e": {"value": rate, "unit": "updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import torch
+    import paper_1108_5561_gb300 as rlb
+    from paper_1108_5561_gb300.inputs import hotspots
+
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    eps0, _, _ = hotspots(NX, NY, n=40, seed=1108)
+    g = rlb.GridParams(nx=NX, ny=NY, prec=rlb.RLB_F32, eta_over_s=ETA_S, tau0=TAU0, dtau=DTAU)
+    run = rlb.Run(g, device=local)
+    run.init_grid(eps0)
+    stream = torch.cuda.current_stream()
+    run.step(args.warmup)
+    torch.cuda.synchronize()
+    run.check()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    props = torch.cuda.get_device_properties(local)
+    dev_id = str(getattr(props, "uuid", "")) or None
+    if dev_id and not dev_id.startswith("GPU-"):
+        dev_id = "GPU-" + dev_id
+    sampler = ClockSampler(dev_id) if rank == 0 else None
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    run.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t = e0.elapsed_time(e1) / 1e3
+    clocks = sampler.stop() if sampler else None
+    run.check()
+    if dist is not None:
+        tt = torch.tensor([t], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    ns, nn = NX * NY, g.nodes
+    updates = world * ns * nn * args.steps
+    value = updates / t
+    b = 4  # FP32 storage
+    launches = 2 * args.steps
+    alg_bytes_launch = 2.5 * b * ns * nn  # predictor 2b, corrector 3b per population
+    achieved = alg_bytes_launch / (t / launches) / 1e9
+    peak, peak_kind = peaks()
+
+    # end to end through the public API with host buffers: pinned eps0 upload,
+    # initial condition, then every step the step itself and a download of the
+    # per-site observables.
+    host_eps = torch.from_numpy(eps0.reshape(-1).copy()).pin_memory()
+    host_mom = torch.empty((ns, 8), dtype=torch.float64).pin_memory()
+    dev_eps = torch.empty(ns, dtype=torch.float64, device="cuda")
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    dev_eps.copy_(host_eps, non_blocking=True)
+    run.init_grid(dev_eps)
+    for _ in range(args.steps):
+        run.step(1)
+        host_mom.copy_(run.moments(host=False), non_blocking=True)
+    torch.cuda.synchronize()
+    barrier()
+    t_e2e = time.perf_counter() - t0
+    run.check()
+    e2e = {"value": updates / t_e2e, "unit": "updates/s",
+           "h2d_bytes_per_step": ns * 8 / args.steps, "d2h_bytes_per_step": ns * 8 * 8}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        c = NX // 2
+        win = eps0[c - 32:c + 32, c - 32:c + 32]
+        cores = os.cpu_count() or 1
+        rate, dt = oracle_rate(win, 2, cores)
+        cpu = {"value": rate, "unit": "updates/s", "cores": cores, "kind": "oracle",
+               "sample": "64x64 central window of the workload, 2 oracle steps (%.1f s)" % dt}
+
+    if rank == 0:
+        line = {
+            "metric": "site-population updates/s", "value": value, "unit": "updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [NX, NY], "nodes_per_site": nn,
+                       "eta_over_s": ETA_S, "dtau": DTAU, "tau0": TAU0,
+                       "l2": "inputs larger than L2 (two 201 MB population arrays)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_source": peak_kind,
+                         "algorithmic_bytes_per_update": 5 * b},
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

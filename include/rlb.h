@@ -1,0 +1,181 @@
+/*
+ * rlb.h -- C ABI of the GB300 relativistic lattice Boltzmann step with a
+ * quasiparticle (non-ideal) equation of state, after Romatschke,
+ * "Relativistic (Lattice) Boltzmann Equation with Non-Ideal Equation of
+ * State", arXiv:1108.5561.
+ *
+ * The library advances the on-shell distribution f(tau, x, y; v) of one
+ * uncharged quasiparticle species with medium-dependent mass M in the Milne
+ * metric ds^2 = dtau^2 - dx^2 - dy^2 - tau^2 dY^2 (Sec. 3.3, Eq. Bmilne),
+ * boost invariant (no Y dependence), on a periodic transverse grid.  Momenta
+ * are the nodes of the Sec. 4.3 lattice, p~ = M v with
+ * v = sinh(xi) (sin th cos ph, sin th sin ph, cos th); one time step is the
+ * predictor-corrector of Sec. 4.4 applied to (f, ln M).
+ *
+ * Units: T, M in GeV; tau, dtau, dx in fm (fm/c); energy densities returned in
+ * GeV/fm^3.
+ *
+ * Conventions
+ *   - Every function returns rlb_status; nothing throws or exits across the ABI.
+ *     On failure a message is kept in the context (rlb_last_error).
+ *   - Device memory is owned by the caller: the library states how many bytes
+ *     it needs (rlb_workspace_size) and borrows the caller's buffers
+ *     (rlb_bind_buffers).  Host-side tables are owned by the context.
+ *   - Work is enqueued on the caller's cudaStream_t (passed as void*; NULL is
+ *     the legacy default stream).  Launch errors are returned at once; numeric
+ *     failures found on the device (no timelike Landau eigenvector, temperature
+ *     inversion outside the EOS table, non-finite values) set a device error
+ *     word that rlb_check, rlb_moments and rlb_sync_error report as
+ *     RLB_ERR_NUMERIC.
+ *   - A context is not thread safe; use one per host thread.
+ *
+ * State layout (the bound state buffer; offsets from rlb_state_offsets):
+ *   f[site][node] in the storage precision, site = y*nx + x,
+ *   node = (l*n_theta + j)*n_xi + k   (k radial xi_k, j polar th_j, l azimuth ph_l),
+ *   then lnM[site] as double (ln of the dynamical mass M, GeV).
+ */
+#ifndef RLB_H
+#define RLB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rlb_ctx rlb_ctx;
+
+typedef enum {
+  RLB_OK = 0,
+  RLB_ERR_ARG = -1,     /* invalid argument or size                        */
+  RLB_ERR_CUDA = -2,    /* a CUDA runtime call or launch failed            */
+  RLB_ERR_NUMERIC = -3, /* device error word set (see above)              */
+  RLB_ERR_TIMEOUT = -4, /* a bounded device wait expired                  */
+  RLB_ERR_STATE = -5,   /* call out of order (e.g. step before init_grid) */
+  RLB_ERR_NOMEM = -6    /* host allocation failed                         */
+} rlb_status;
+
+typedef enum { RLB_F64 = 0, RLB_F32 = 1, RLB_BF16 = 2 } rlb_prec;
+typedef enum { RLB_EOS_CROSSOVER = 0, RLB_EOS_CONST_MASS = 1, RLB_EOS_CONFORMAL = 2 } rlb_eos_kind;
+typedef enum { RLB_RADIAL_PAPER = 0, RLB_RADIAL_LAGUERRE = 1 } rlb_radial_family;
+typedef enum { RLB_MINKOWSKI = 0, RLB_MILNE = 1 } rlb_metric;
+
+/* Equation of state (Sec. 3.1).  kind CROSSOVER: entropy density
+ * s(T) = T^3 [a (1 + tanh((T - Tc)/w))/2 + b]; the quasiparticle mass M(T)
+ * solves Z M^3 K_3(M/T)/(2 pi^2) = s(T) and the bag function B(T) solves
+ * dB/dT = -Z M^2 T K_1(M/T) dM/dT /(2 pi^2) with B(0) = 0.  CONST_MASS: ideal
+ * Boltzmann gas of mass m0 (B = 0).  CONFORMAL: M = B = 0.
+ * Z is the number of degrees of freedom (Sec. 3.1: pi^4/180 (4(Nc^2-1)+7 Nc Nf)).
+ * The library tabulates the EOS on [T_min, T_max] (GeV, uniform in ln T,
+ * table_points nodes; 0 selects 65536). */
+typedef struct {
+  int kind;
+  int table_points;
+  double a, b, Tc, w;
+  double m0;
+  double Z;
+  double T_min, T_max;
+} rlb_eos_params;
+
+/* Grid, momentum lattice and physics of one run.
+ *   nx, ny, dx            periodic transverse grid, spacing in fm
+ *   metric                RLB_MILNE (expansion term S1/tau) or RLB_MINKOWSKI
+ *   n_xi, n_theta,        lattice of Sec. 4.3: n_xi radial roots, n_theta
+ *   n_phi_half              Gauss-Legendre polar nodes, 2 n_phi_half azimuths.
+ *                         Supported (n_xi, n_theta, 2 n_phi_half): (8, 8, 12),
+ *                         (16, 8, 16), (5, 5, 2), (8, 8, 2), (8, 16, 2).
+ *   family, z0, T0        radial rule: PAPER (weight e^{-z0 cosh xi} sinh^2 xi,
+ *                         z0 = M0/T0 of Eq. fansatz) or LAGUERRE (massless limit,
+ *                         |p~| = T0 x, weight x e^{-x}; needs the conformal EOS)
+ *   prec                  population storage: F64 (all arithmetic FP64), F32 or
+ *                         BF16 (FP32 arithmetic, FP64 Landau matching and EOS
+ *                         inversion)
+ *   eta_over_s            shear viscosity to entropy ratio; tau_R follows from
+ *                         the Chapman-Enskog relation of Sec. 4.1; INFINITY
+ *                         switches collisions off
+ *   tau0, dtau            initial proper time and time step (fm/c) */
+typedef struct {
+  int nx, ny;
+  int metric;
+  int n_xi, n_theta, n_phi_half;
+  int family;
+  int prec;
+  double dx;
+  double z0, T0;
+  double eta_over_s;
+  double tau0, dtau;
+} rlb_grid_params;
+
+/* Create a context bound to CUDA device `cuda_device` (the device is made
+ * current for every later call on this context). */
+rlb_status rlb_create(rlb_ctx** out, int cuda_device);
+void rlb_destroy(rlb_ctx* ctx);
+/* Message of the last failed call; owned by ctx, valid until the next call. */
+const char* rlb_last_error(const rlb_ctx* ctx);
+
+/* Build the host EOS table (Sec. 3.1).  Must precede rlb_bind_buffers. */
+rlb_status rlb_init_eos(rlb_ctx* ctx, const rlb_eos_params* eos);
+
+/* Bytes of device memory a run with grid parameters `g` needs: `state` holds
+ * the populations and ln M (layout above); `scratch` holds the predictor
+ * state, per-site temperatures, the error word and the EOS table.  Pure
+ * function of g and of the EOS table size; may be called before
+ * rlb_init_eos (then 65536 table points are assumed). */
+rlb_status rlb_workspace_size(const rlb_ctx* ctx, const rlb_grid_params* g, size_t* state_bytes,
+                              size_t* scratch_bytes);
+
+/* Configure the grid and momentum lattice (host work only). */
+rlb_status rlb_configure(rlb_ctx* ctx, const rlb_grid_params* g);
+
+/* Borrow caller-owned device buffers of at least the rlb_workspace_size bytes,
+ * 256-byte aligned; the library never frees them.  Uploads the EOS table and
+ * clears the error word on `stream`. */
+rlb_status rlb_bind_buffers(rlb_ctx* ctx, void* state, void* scratch, void* stream);
+
+/* Initial condition: local equilibrium at rest with energy density eps0[site]
+ * (GeV/fm^3, FP64, nx*ny values on the host or, if eps0_on_device, on the
+ * device).  Solves eps_EOS(T) = eps0 for T, sets M = M(T) and
+ * f = Z exp(-E/T) at every node, and tau = tau0.  The host array is copied
+ * before return; a device array must stay valid until `stream` reaches it. */
+rlb_status rlb_init_grid(rlb_ctx* ctx, const double* eps0, int eps0_on_device, void* stream);
+
+/* Advance by `nsteps` predictor-corrector steps of dtau (Sec. 4.4): two fused
+ * stream-collide launches per step.  Asynchronous on `stream`. */
+rlb_status rlb_step(rlb_ctx* ctx, int nsteps, void* stream);
+
+/* Current proper time (host bookkeeping, fm/c). */
+rlb_status rlb_get_tau(const rlb_ctx* ctx, double* tau);
+
+/* Per-site observables of the current state, 8 doubles per site:
+ *   eps [GeV/fm^3] (Landau energy density incl. B), T [GeV], u^tau, u^x, u^y,
+ *   M [GeV] (dynamical mass), P_L [GeV/fm^3] (tau^2 T^{YY}), M(T) [GeV].
+ * `out` is host memory (synchronises `stream`) or device memory
+ * (out_on_device != 0, asynchronous). */
+rlb_status rlb_moments(rlb_ctx* ctx, double* out, int out_on_device, void* stream);
+
+/* Synchronise `stream` and report the device error word (RLB_ERR_NUMERIC if set). */
+rlb_status rlb_check(rlb_ctx* ctx, void* stream);
+
+/* Byte offsets of f and lnM inside the state buffer, and the storage size of
+ * one population in bytes. */
+rlb_status rlb_state_offsets(const rlb_ctx* ctx, size_t* f_offset, size_t* lnM_offset,
+                             size_t* pop_bytes);
+
+/* Host copies of the momentum lattice (for checks): radial c = cosh xi_k
+ * (or x_k), s = sinh xi_k (or x_k), w^xi_k; polar mu_j = cos th_j, w^th_j;
+ * azimuth cos ph_l, sin ph_l.  Arrays of n_xi, n_theta and 2 n_phi_half. */
+rlb_status rlb_lattice(const rlb_ctx* ctx, double* c, double* s, double* wxi, double* mu,
+                       double* wth, double* cph, double* sph);
+
+/* Host copies of the nodal operator matrices (row-major [out][in]): Dr, the
+ * Galerkin representation of v.d/dv on the radial nodes (n_xi^2; the radial
+ * part of S1 and S2 in Sec. 4.4); Dth, the Galerkin representation of
+ * (mu - mu^3) d/dmu on the polar nodes (n_theta^2; the polar part of S1);
+ * Dmu and Dph, collocation derivatives d/dmu (n_theta^2) and d/dphi
+ * ((2 n_phi_half)^2) used by the transverse mass-gradient force. */
+rlb_status rlb_operators(const rlb_ctx* ctx, double* Dr, double* Dth, double* Dmu, double* Dph);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RLB_H */

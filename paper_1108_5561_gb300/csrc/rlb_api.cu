@@ -1,0 +1,416 @@
+// rlb_api.cu -- C ABI (include/rlb.h) of the GB300 lattice Boltzmann step.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/rlb.h"
+#include "rlb_host.hpp"
+#include "rlb_kernels.cuh"
+
+struct rlb_ctx {
+  int device = 0;
+  std::string err;
+  bool eos_ok = false, grid_ok = false, bound = false, inited = false;
+  rlb::EosParams eosp;
+  rlb::EosTable tab;
+  rlb_grid_params gp{};
+  rlb::Lattice lat;
+  size_t ns = 0, nn = 0, pop_bytes = 0;
+  size_t f_off = 0, lnM_off = 0;                               // state
+  size_t fs_off = 0, lnMs_off = 0, T_off = 0, err_off = 0, tab_off = 0, eps_off = 0;  // scratch
+  char* state = nullptr;
+  char* scratch = nullptr;
+  double tau = 0.0;
+};
+
+namespace {
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+rlb_status fail(rlb_ctx* c, rlb_status s, const std::string& m) {
+  if (c) c->err = m;
+  return s;
+}
+
+rlb_status cuda_fail(rlb_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, RLB_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define RLB_CUDA(call, what)                       \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+  } while (0)
+
+size_t pop_size(int prec) { return prec == RLB_F64 ? 8 : (prec == RLB_F32 ? 4 : 2); }
+
+bool supported_shape(int nxi, int nth, int nph) {
+  return (nxi == 8 && nth == 8 && nph == 12) || (nxi == 16 && nth == 8 && nph == 16) ||
+         (nxi == 5 && nth == 5 && nph == 2) || (nxi == 6 && nth == 4 && nph == 6) ||
+         (nxi == 8 && nth == 8 && nph == 2);
+}
+
+void layout(const rlb_grid_params& g, size_t table_points, size_t* state_b, size_t* scratch_b,
+            rlb_ctx* c) {
+  const size_t ns = (size_t)g.nx * g.ny;
+  const size_t nn = (size_t)g.n_xi * g.n_theta * 2 * g.n_phi_half;
+  const size_t fb = align256(ns * nn * pop_size(g.prec));
+  const size_t mb = align256(ns * sizeof(double));
+  size_t off = 0;
+  size_t f_off = off; off += fb;
+  size_t lnM_off = off; off += mb;
+  *state_b = off;
+  off = 0;
+  size_t fs_off = off; off += fb;
+  size_t lnMs_off = off; off += mb;
+  size_t T_off = off; off += mb;
+  size_t eps_off = off; off += mb;
+  size_t err_off = off; off += 256;
+  size_t tab_off = off; off += align256((table_points + 6) * rlb::kFields * sizeof(double));
+  *scratch_b = off;
+  if (c) {
+    c->f_off = f_off; c->lnM_off = lnM_off;
+    c->fs_off = fs_off; c->lnMs_off = lnMs_off; c->T_off = T_off; c->eps_off = eps_off;
+    c->err_off = err_off; c->tab_off = tab_off;
+  }
+}
+
+template <class R, int NXI, int NTH, int NPH>
+rlbk::Ops<R, NXI, NTH, NPH> make_ops(const rlb::Lattice& L) {
+  rlbk::Ops<R, NXI, NTH, NPH> o;
+  for (int i = 0; i < NXI * NXI; ++i) o.Dr[i] = (R)L.Dr[i];
+  for (int i = 0; i < NTH * NTH; ++i) { o.Dth[i] = (R)L.Dth[i]; o.Dmu[i] = (R)L.Dmu[i]; }
+  for (int i = 0; i < NPH * NPH; ++i) o.Dph[i] = (R)L.Dph[i];
+  for (int k = 0; k < NXI; ++k) {
+    const double c = L.c[k], s = L.s[k], e = L.ecw[k];
+    o.c[k] = (R)c; o.s[k] = (R)s; o.c_over_s[k] = (R)(c / s); o.inv_cs[k] = (R)(1.0 / (c * s));
+    o.s2[k] = (R)(s * s); o.inv_c[k] = (R)(1.0 / c);
+    o.w0[k] = (R)e; o.w1[k] = (R)(e * c * s); o.w2[k] = (R)(e * c * c); o.w3[k] = (R)(e * s * s);
+    o.ecw[k] = (R)e;
+  }
+  for (int j = 0; j < NTH; ++j) {
+    o.mu[j] = (R)L.mu[j]; o.mu2[j] = (R)(L.mu[j] * L.mu[j]); o.sth[j] = (R)L.sth[j];
+    o.sth_mu[j] = (R)(L.sth[j] * L.mu[j]); o.wj[j] = (R)(L.wth[j] / (2.0 * NPH));
+  }
+  for (int l = 0; l < NPH; ++l) { o.cph[l] = (R)L.cph[l]; o.sph[l] = (R)L.sph[l]; }
+  return o;
+}
+
+rlbk::EosView eos_view(const rlb_ctx* c) {
+  rlbk::EosView v;
+  v.tab = reinterpret_cast<const double*>(c->scratch + c->tab_off);
+  v.y0 = c->tab.y0;
+  v.inv_h = 1.0 / c->tab.h;
+  v.n = c->tab.n;
+  return v;
+}
+
+template <class S, class R, int NXI, int NTH, int NPH>
+struct Runner {
+  static constexpr int NL = NTH * NPH;
+
+  static rlb_status init(rlb_ctx* ctx, const double* eps_dev, cudaStream_t st) {
+    rlbk::InitArgs<S, R, NXI, NTH, NPH> a;
+    a.eps0 = eps_dev;
+    a.eps_scale = rlb::kHbarc * rlb::kHbarc * rlb::kHbarc;
+    a.f = reinterpret_cast<S*>(ctx->state + ctx->f_off);
+    a.lnM = reinterpret_cast<double*>(ctx->state + ctx->lnM_off);
+    a.Tsite = reinterpret_cast<double*>(ctx->scratch + ctx->T_off);
+    a.err = reinterpret_cast<int*>(ctx->scratch + ctx->err_off);
+    a.eos = eos_view(ctx);
+    a.Z = ctx->eosp.Z;
+    a.family = ctx->gp.family;
+    a.T0 = ctx->gp.T0;
+    a.op = make_ops<R, NXI, NTH, NPH>(ctx->lat);
+    rlbk::init_kernel<S, R, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
+    RLB_CUDA(cudaGetLastError(), "init_kernel launch");
+    return RLB_OK;
+  }
+
+  static rlb_status step(rlb_ctx* ctx, int nsteps, cudaStream_t st) {
+    rlbk::StageArgs<S, R, NXI, NTH, NPH> a;
+    S* f = reinterpret_cast<S*>(ctx->state + ctx->f_off);
+    S* fs = reinterpret_cast<S*>(ctx->scratch + ctx->fs_off);
+    double* m = reinterpret_cast<double*>(ctx->state + ctx->lnM_off);
+    double* ms = reinterpret_cast<double*>(ctx->scratch + ctx->lnMs_off);
+    a.Tsite = reinterpret_cast<double*>(ctx->scratch + ctx->T_off);
+    a.err = reinterpret_cast<int*>(ctx->scratch + ctx->err_off);
+    a.eos = eos_view(ctx);
+    a.nx = ctx->gp.nx;
+    a.ny = ctx->gp.ny;
+    a.metric = ctx->gp.metric;
+    a.dtau = ctx->gp.dtau;
+    a.inv2dx = 1.0 / (2.0 * ctx->gp.dx);
+    a.Z = ctx->eosp.Z;
+    a.eta_over_s = ctx->gp.eta_over_s;
+    a.op = make_ops<R, NXI, NTH, NPH>(ctx->lat);
+    for (int s = 0; s < nsteps; ++s) {
+      // predictor: f* = f + dtau RHS(f) at tau
+      a.f_in = f; a.lnM_in = m; a.f_base = f; a.lnM_base = m;
+      a.f_out = fs; a.lnM_out = ms; a.mode = 0; a.tau = ctx->tau;
+      rlbk::stage_kernel<S, R, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
+      RLB_CUDA(cudaGetLastError(), "stage_kernel (predictor) launch");
+      // corrector: f = (f + f* + dtau RHS(f*))/2 at tau + dtau, in place over f
+      a.f_in = fs; a.lnM_in = ms; a.f_base = f; a.lnM_base = m;
+      a.f_out = f; a.lnM_out = m; a.mode = 1; a.tau = ctx->tau + ctx->gp.dtau;
+      rlbk::stage_kernel<S, R, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
+      RLB_CUDA(cudaGetLastError(), "stage_kernel (corrector) launch");
+      ctx->tau += ctx->gp.dtau;
+    }
+    return RLB_OK;
+  }
+
+  static rlb_status moments(rlb_ctx* ctx, double* out_dev, cudaStream_t st) {
+    rlbk::MomArgs<S, R, NXI, NTH, NPH> a;
+    a.f = reinterpret_cast<const S*>(ctx->state + ctx->f_off);
+    a.lnM = reinterpret_cast<const double*>(ctx->state + ctx->lnM_off);
+    a.Tsite = reinterpret_cast<const double*>(ctx->scratch + ctx->T_off);
+    a.out = out_dev;
+    a.err = reinterpret_cast<int*>(ctx->scratch + ctx->err_off);
+    a.eos = eos_view(ctx);
+    a.eta_over_s = ctx->gp.eta_over_s;
+    a.op = make_ops<R, NXI, NTH, NPH>(ctx->lat);
+    rlbk::moments_kernel<S, R, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
+    RLB_CUDA(cudaGetLastError(), "moments_kernel launch");
+    return RLB_OK;
+  }
+};
+
+enum Op { OP_INIT, OP_STEP, OP_MOMENTS };
+
+template <class S, class R, int NXI, int NTH, int NPH>
+rlb_status run_op(rlb_ctx* c, Op op, int n, double* p, cudaStream_t st) {
+  using Rn = Runner<S, R, NXI, NTH, NPH>;
+  if (op == OP_INIT) return Rn::init(c, p, st);
+  if (op == OP_STEP) return Rn::step(c, n, st);
+  return Rn::moments(c, p, st);
+}
+
+template <int NXI, int NTH, int NPH>
+rlb_status run_prec(rlb_ctx* c, Op op, int n, double* p, cudaStream_t st) {
+  switch (c->gp.prec) {
+    case RLB_F64:
+      if constexpr (NXI * NTH * NPH <= 1024) return run_op<double, double, NXI, NTH, NPH>(c, op, n, p, st);
+      else return fail(c, RLB_ERR_ARG, "FP64 storage supports at most 1024 nodes per site");
+    case RLB_F32: return run_op<float, float, NXI, NTH, NPH>(c, op, n, p, st);
+    case RLB_BF16: return run_op<__nv_bfloat16, float, NXI, NTH, NPH>(c, op, n, p, st);
+  }
+  return fail(c, RLB_ERR_ARG, "unknown precision");
+}
+
+rlb_status dispatch(rlb_ctx* c, Op op, int n, double* p, cudaStream_t st) {
+  const int a = c->gp.n_xi, b = c->gp.n_theta, d = 2 * c->gp.n_phi_half;
+  if (a == 8 && b == 8 && d == 12) return run_prec<8, 8, 12>(c, op, n, p, st);
+  if (a == 16 && b == 8 && d == 16) return run_prec<16, 8, 16>(c, op, n, p, st);
+  if (a == 5 && b == 5 && d == 2) return run_prec<5, 5, 2>(c, op, n, p, st);
+  if (a == 6 && b == 4 && d == 6) return run_prec<6, 4, 6>(c, op, n, p, st);
+  if (a == 8 && b == 8 && d == 2) return run_prec<8, 8, 2>(c, op, n, p, st);
+  return fail(c, RLB_ERR_ARG, "unsupported lattice shape");
+}
+
+rlb_status set_device(rlb_ctx* ctx) {
+  RLB_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+  return RLB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rlb_status rlb_create(rlb_ctx** out, int cuda_device) {
+  if (!out) return RLB_ERR_ARG;
+  *out = nullptr;
+  rlb_ctx* c = new (std::nothrow) rlb_ctx();
+  if (!c) return RLB_ERR_NOMEM;
+  c->device = cuda_device;
+  *out = c;
+  return RLB_OK;
+}
+
+void rlb_destroy(rlb_ctx* ctx) { delete ctx; }
+
+const char* rlb_last_error(const rlb_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+rlb_status rlb_init_eos(rlb_ctx* ctx, const rlb_eos_params* e) {
+  if (!ctx || !e) return RLB_ERR_ARG;
+  if (ctx->bound) return fail(ctx, RLB_ERR_STATE, "EOS must be set before binding buffers");
+  rlb::EosParams p;
+  p.kind = e->kind;
+  p.a = e->a; p.b = e->b; p.Tc = e->Tc; p.w = e->w; p.m0 = e->m0; p.Z = e->Z;
+  p.T_min = e->T_min; p.T_max = e->T_max;
+  p.points = e->table_points > 0 ? e->table_points : 65536;
+  std::string m = rlb::build_eos_table(p, &ctx->tab);
+  if (!m.empty()) return fail(ctx, RLB_ERR_ARG, m);
+  ctx->eosp = p;
+  ctx->eos_ok = true;
+  return RLB_OK;
+}
+
+rlb_status rlb_workspace_size(const rlb_ctx* ctx, const rlb_grid_params* g, size_t* state_bytes,
+                              size_t* scratch_bytes) {
+  if (!g || !state_bytes || !scratch_bytes) return RLB_ERR_ARG;
+  if (g->nx < 1 || g->ny < 1 || g->prec < 0 || g->prec > 2) return RLB_ERR_ARG;
+  size_t pts = (ctx && ctx->eos_ok) ? (size_t)ctx->eosp.points : 65536;
+  layout(*g, pts, state_bytes, scratch_bytes, nullptr);
+  return RLB_OK;
+}
+
+rlb_status rlb_configure(rlb_ctx* ctx, const rlb_grid_params* g) {
+  if (!ctx || !g) return RLB_ERR_ARG;
+  if (!ctx->eos_ok) return fail(ctx, RLB_ERR_STATE, "rlb_init_eos must come first");
+  if (ctx->bound) return fail(ctx, RLB_ERR_STATE, "grid is fixed once buffers are bound");
+  if (g->nx < 1 || g->ny < 1 || !(g->dx > 0) || !(g->dtau > 0) || !(g->tau0 > 0) ||
+      !(g->eta_over_s > 0))
+    return fail(ctx, RLB_ERR_ARG, "invalid grid parameters");
+  if (g->prec < 0 || g->prec > 2) return fail(ctx, RLB_ERR_ARG, "invalid precision");
+  if (!supported_shape(g->n_xi, g->n_theta, 2 * g->n_phi_half))
+    return fail(ctx, RLB_ERR_ARG, "unsupported lattice shape");
+  if (g->family == RLB_RADIAL_LAGUERRE && ctx->eosp.kind != RLB_EOS_CONFORMAL)
+    return fail(ctx, RLB_ERR_ARG, "the Laguerre radial family needs the conformal EOS");
+  if (g->family == RLB_RADIAL_LAGUERRE && !(g->T0 > 0))
+    return fail(ctx, RLB_ERR_ARG, "T0 must be positive");
+  if ((size_t)g->nx * g->ny > 0x7fffffffu) return fail(ctx, RLB_ERR_ARG, "grid too large");
+  std::string m = rlb::build_lattice(g->family, g->n_xi, g->n_theta, g->n_phi_half, g->z0, &ctx->lat);
+  if (!m.empty()) return fail(ctx, RLB_ERR_ARG, m);
+  ctx->gp = *g;
+  ctx->ns = (size_t)g->nx * g->ny;
+  ctx->nn = (size_t)g->n_xi * g->n_theta * 2 * g->n_phi_half;
+  ctx->pop_bytes = pop_size(g->prec);
+  size_t sb, xb;
+  layout(*g, ctx->eosp.points, &sb, &xb, ctx);
+  ctx->grid_ok = true;
+  ctx->tau = g->tau0;
+  return RLB_OK;
+}
+
+rlb_status rlb_bind_buffers(rlb_ctx* ctx, void* state, void* scratch, void* stream) {
+  if (!ctx) return RLB_ERR_ARG;
+  if (!ctx->grid_ok) return fail(ctx, RLB_ERR_STATE, "rlb_configure must come first");
+  if (!state || !scratch || ((uintptr_t)state & 255) || ((uintptr_t)scratch & 255))
+    return fail(ctx, RLB_ERR_ARG, "buffers must be non-null and 256-byte aligned");
+  rlb_status s = set_device(ctx);
+  if (s) return s;
+  ctx->state = static_cast<char*>(state);
+  ctx->scratch = static_cast<char*>(scratch);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  RLB_CUDA(cudaMemcpyAsync(ctx->scratch + ctx->tab_off, ctx->tab.data.data(),
+                           ctx->tab.data.size() * sizeof(double), cudaMemcpyHostToDevice, st),
+           "EOS table upload");
+  RLB_CUDA(cudaMemsetAsync(ctx->scratch + ctx->err_off, 0, 256, st), "error word reset");
+  // the table copy reads pageable host memory owned by ctx: wait for it
+  RLB_CUDA(cudaStreamSynchronize(st), "bind synchronise");
+  ctx->bound = true;
+  return RLB_OK;
+}
+
+rlb_status rlb_init_grid(rlb_ctx* ctx, const double* eps0, int eps0_on_device, void* stream) {
+  if (!ctx || !eps0) return RLB_ERR_ARG;
+  if (!ctx->bound) return fail(ctx, RLB_ERR_STATE, "rlb_bind_buffers must come first");
+  rlb_status s = set_device(ctx);
+  if (s) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double* dev = reinterpret_cast<double*>(ctx->scratch + ctx->eps_off);
+  if (eps0_on_device) {
+    RLB_CUDA(cudaMemcpyAsync(dev, eps0, ctx->ns * sizeof(double), cudaMemcpyDeviceToDevice, st),
+             "eps0 copy");
+  } else {
+    for (size_t i = 0; i < ctx->ns; ++i)
+      if (!(eps0[i] > 0.0) || !std::isfinite(eps0[i]))
+        return fail(ctx, RLB_ERR_ARG, "eps0 must be positive and finite");
+    RLB_CUDA(cudaMemcpyAsync(dev, eps0, ctx->ns * sizeof(double), cudaMemcpyHostToDevice, st),
+             "eps0 upload");
+    RLB_CUDA(cudaStreamSynchronize(st), "eps0 upload synchronise");
+  }
+  s = dispatch(ctx, OP_INIT, 0, dev, st);
+  if (s) return s;
+  ctx->tau = ctx->gp.tau0;
+  ctx->inited = true;
+  return RLB_OK;
+}
+
+rlb_status rlb_step(rlb_ctx* ctx, int nsteps, void* stream) {
+  if (!ctx || nsteps < 0) return RLB_ERR_ARG;
+  if (!ctx->inited) return fail(ctx, RLB_ERR_STATE, "rlb_init_grid must come first");
+  rlb_status s = set_device(ctx);
+  if (s) return s;
+  return dispatch(ctx, OP_STEP, nsteps, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+rlb_status rlb_get_tau(const rlb_ctx* ctx, double* tau) {
+  if (!ctx || !tau) return RLB_ERR_ARG;
+  *tau = ctx->tau;
+  return RLB_OK;
+}
+
+rlb_status rlb_check(rlb_ctx* ctx, void* stream) {
+  if (!ctx) return RLB_ERR_ARG;
+  if (!ctx->bound) return fail(ctx, RLB_ERR_STATE, "no buffers bound");
+  rlb_status s = set_device(ctx);
+  if (s) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int word = 0;
+  RLB_CUDA(cudaMemcpyAsync(&word, ctx->scratch + ctx->err_off, sizeof(int), cudaMemcpyDeviceToHost, st),
+           "error word read");
+  RLB_CUDA(cudaStreamSynchronize(st), "synchronise");
+  if (word) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "device error word 0x%x (1: Landau, 2: EOS inversion, 4: non-finite)", word);
+    return fail(ctx, RLB_ERR_NUMERIC, buf);
+  }
+  return RLB_OK;
+}
+
+rlb_status rlb_moments(rlb_ctx* ctx, double* out, int out_on_device, void* stream) {
+  if (!ctx || !out) return RLB_ERR_ARG;
+  if (!ctx->inited) return fail(ctx, RLB_ERR_STATE, "rlb_init_grid must come first");
+  rlb_status s = set_device(ctx);
+  if (s) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (out_on_device) return dispatch(ctx, OP_MOMENTS, 0, out, st);
+  // host output: stage through the predictor buffer (free between steps)
+  double* dev = reinterpret_cast<double*>(ctx->scratch + ctx->fs_off);
+  if (ctx->ns * 8 * sizeof(double) > ctx->ns * ctx->nn * ctx->pop_bytes)
+    return fail(ctx, RLB_ERR_ARG, "lattice too small to stage host moments");
+  s = dispatch(ctx, OP_MOMENTS, 0, dev, st);
+  if (s) return s;
+  RLB_CUDA(cudaMemcpyAsync(out, dev, ctx->ns * 8 * sizeof(double), cudaMemcpyDeviceToHost, st),
+           "moments download");
+  return rlb_check(ctx, stream);
+}
+
+rlb_status rlb_state_offsets(const rlb_ctx* ctx, size_t* f_offset, size_t* lnM_offset,
+                             size_t* pop_bytes) {
+  if (!ctx || !f_offset || !lnM_offset || !pop_bytes) return RLB_ERR_ARG;
+  if (!ctx->grid_ok) return RLB_ERR_STATE;
+  *f_offset = ctx->f_off;
+  *lnM_offset = ctx->lnM_off;
+  *pop_bytes = ctx->pop_bytes;
+  return RLB_OK;
+}
+
+rlb_status rlb_lattice(const rlb_ctx* ctx, double* c, double* s, double* wxi, double* mu,
+                       double* wth, double* cph, double* sph) {
+  if (!ctx) return RLB_ERR_ARG;
+  if (!ctx->grid_ok) return RLB_ERR_STATE;
+  const rlb::Lattice& L = ctx->lat;
+  for (int k = 0; k < L.nxi; ++k) { c[k] = L.c[k]; s[k] = L.s[k]; wxi[k] = L.wxi[k]; }
+  for (int j = 0; j < L.nth; ++j) { mu[j] = L.mu[j]; wth[j] = L.wth[j]; }
+  for (int l = 0; l < L.nph; ++l) { cph[l] = L.cph[l]; sph[l] = L.sph[l]; }
+  return RLB_OK;
+}
+
+rlb_status rlb_operators(const rlb_ctx* ctx, double* Dr, double* Dth, double* Dmu, double* Dph) {
+  if (!ctx || !Dr || !Dth || !Dmu || !Dph) return RLB_ERR_ARG;
+  if (!ctx->grid_ok) return RLB_ERR_STATE;
+  const rlb::Lattice& L = ctx->lat;
+  std::memcpy(Dr, L.Dr.data(), L.Dr.size() * sizeof(double));
+  std::memcpy(Dth, L.Dth.data(), L.Dth.size() * sizeof(double));
+  std::memcpy(Dmu, L.Dmu.data(), L.Dmu.size() * sizeof(double));
+  std::memcpy(Dph, L.Dph.data(), L.Dph.size() * sizeof(double));
+  return RLB_OK;
+}
+
+}  // extern "C"
