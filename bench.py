@@ -1,9 +1,10 @@
 """Benchmark of the fused stream-collide step (site-population updates/s).
 
 Workload (one "step" = one predictor-corrector time step over the whole grid):
-256 x 256 transverse grid, dx = 0.2 fm, 8 x 8 x 12 = 768-node momentum lattice,
+256 x 256 transverse grid, dx = 0.1 fm, 8 x 8 x 12 = 768-node momentum lattice,
 FP32 populations (FP64 Landau matching / EOS inversion), eta/s = 0.16,
-dtau = 0.0036 fm/c from tau = 0.4 fm/c, 40 seeded Gaussian hotspots.
+dtau = 0.0036 fm/c from tau = 0.4 fm/c, 40 seeded Gaussian hotspots (0.4 fm,
+Exp(20 GeV/fm^3), N(0, 3 fm)) on a 10 GeV/fm^3 background.
 The two population arrays (402 MB) exceed the 126 MB L2, so no flush is needed.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -30,8 +31,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 NX = NY = 256
-ETA_S, TAU0, DTAU = 0.16, 0.4, 0.0036
-WORKLOAD = "rlb-milne-2+1d 256x256 grid, 768 nodes (8xi x 8theta x 12phi), FP32 populations"
+ETA_S, TAU0, DTAU, DX = 0.16, 0.4, 0.0036, 0.1
+WORKLOAD = ("rlb-milne-2+1d 256x256 grid dx 0.1 fm, 768 nodes (8xi x 8theta x 12phi), FP32 "
+            "populations, 40 hotspots on 10 GeV/fm^3")
 
 
 def peaks():
@@ -94,7 +96,7 @@ def oracle_rate(eps_window, steps, nthreads):
     """Oracle (FP64 CPU) updates/s on a window of the workload."""
     from oracle.oracle import Oracle
     ny, nx = eps_window.shape
-    o = Oracle(nx=nx, ny=ny, eta_over_s=ETA_S)
+    o = Oracle(nx=nx, ny=ny, dx=DX, eta_over_s=ETA_S)
     f, lnM = o.init_state(eps_window, nthreads)
     t0 = time.perf_counter()
     o.step(f, lnM, TAU0, DTAU, steps, nthreads)
@@ -135,7 +137,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling)")
+    ap.add_argument("--grid", type=int, default=256,
+                    help="grid side; the benchmark workload is 256 (smaller sides for profiling)")
     args = ap.parse_args()
+    global NX, NY
+    NX = NY = args.grid
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -153,7 +160,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
     eps0, _, _ = hotspots(NX, NY, n=40, seed=1108)
-    g = rlb.GridParams(nx=NX, ny=NY, prec=rlb.RLB_F32, eta_over_s=ETA_S, tau0=TAU0, dtau=DTAU)
+    g = rlb.GridParams(nx=NX, ny=NY, dx=DX, prec=rlb.RLB_F32, eta_over_s=ETA_S, tau0=TAU0,
+                       dtau=DTAU)
     run = rlb.Run(g, device=local)
     run.init_grid(eps0)
     stream = torch.cuda.current_stream()
@@ -180,6 +188,14 @@ def main():
     torch.cuda.synchronize()
     barrier()
     t = e0.elapsed_time(e1) / 1e3
+    # per-kernel launch durations (CUDA events inside the library, same stream),
+    # measured on a separate pass of the same steps so the timed region above
+    # carries no extra events
+    run.set_timing(True)
+    run.step(min(args.steps, 200))
+    torch.cuda.synchronize()
+    stage_ms, stage_n, match_ms, match_n = run.timing()
+    run.set_timing(False)
     clocks = sampler.stop() if sampler else None
     run.check()
     if dist is not None:
@@ -190,14 +206,37 @@ def main():
     updates = world * ns * nn * args.steps
     value = updates / t
     b = 4  # FP32 storage
-    launches = 2 * args.steps
-    alg_bytes_launch = 2.5 * b * ns * nn  # predictor 2b, corrector 3b per population
-    achieved = alg_bytes_launch / (t / launches) / 1e9
+    launches = 4 * args.steps  # per step: (match + stream-collide) x (predictor, corrector)
+    # algorithmic bytes of one stream-collide launch: predictor reads f and writes f*
+    # (2b), corrector reads f* and f and writes f (3b) per population; per site
+    # 2 x 12 doubles of matching results and 8 moments, 2 ln M reads, 1 write
+    alg_bytes_launch = 2.5 * b * ns * nn + ns * (8 * 12 + 8 * 8 + 8 * 3)
+    achieved = alg_bytes_launch / (stage_ms / stage_n / 1e3) / 1e9
     peak, peak_kind = peaks()
 
     # end to end through the public API with host buffers: pinned eps0 upload,
     # initial condition, then every step the step itself and a download of the
     # per-site observables.
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end(run, eps0, args, updates, barrier, torch)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        c = NX // 2
+        win = eps0[c - 32:c + 32, c - 32:c + 32]
+        cores = os.cpu_count() or 1
+        rate, dt = oracle_rate(win, 2, cores)
+        cpu = {"value": rate, "unit": "updates/s", "cores": cores, "kind": "oracle",
+               "sample": "64x64 central window of the workload, 2 oracle steps (%.1f s)" % dt}
+    kern = {"stream_collide_ms_per_launch": stage_ms / stage_n,
+            "match_ms_per_launch": match_ms / match_n, "timed_launches": stage_n + match_n}
+    return finish(args, rank, world, t, value, achieved, peak, peak_kind, b, nn, launches, e2e,
+                  clocks, cpu, dist, kern)
+
+
+def end_to_end(run, eps0, args, updates, barrier, torch):
+    ns = NX * NY
     host_eps = torch.from_numpy(eps0.reshape(-1).copy()).pin_memory()
     host_mom = torch.empty((ns, 8), dtype=torch.float64).pin_memory()
     dev_eps = torch.empty(ns, dtype=torch.float64, device="cuda")
@@ -213,32 +252,26 @@ def main():
     barrier()
     t_e2e = time.perf_counter() - t0
     run.check()
-    e2e = {"value": updates / t_e2e, "unit": "updates/s",
-           "h2d_bytes_per_step": ns * 8 / args.steps, "d2h_bytes_per_step": ns * 8 * 8}
+    return {"value": updates / t_e2e, "unit": "updates/s",
+            "h2d_bytes_per_step": ns * 8 / args.steps, "d2h_bytes_per_step": ns * 8 * 8}
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        c = NX // 2
-        win = eps0[c - 32:c + 32, c - 32:c + 32]
-        cores = os.cpu_count() or 1
-        rate, dt = oracle_rate(win, 2, cores)
-        cpu = {"value": rate, "unit": "updates/s", "cores": cores, "kind": "oracle",
-               "sample": "64x64 central window of the workload, 2 oracle steps (%.1f s)" % dt}
 
+def finish(args, rank, world, t, value, achieved, peak, peak_kind, b, nn, launches, e2e, clocks,
+           cpu, dist, kern):
     if rank == 0:
         line = {
             "metric": "site-population updates/s", "value": value, "unit": "updates/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": [NX, NY], "nodes_per_site": nn,
+            "config": {"workload": WORKLOAD, "grid": [NX, NY], "dx_fm": DX, "nodes_per_site": nn,
                        "eta_over_s": ETA_S, "dtau": DTAU, "tau0": TAU0,
                        "l2": "inputs larger than L2 (two 201 MB population arrays)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
-                         "peak_source": peak_kind,
-                         "algorithmic_bytes_per_update": 5 * b},
+                         "peak_source": peak_kind, "kernel": "stage_kernel (fused stream-collide)",
+                         "algorithmic_bytes_per_update": 5 * b, **kern},
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clocks,

@@ -139,8 +139,10 @@ rlb_status rlb_bind_buffers(rlb_ctx* ctx, void* state, void* scratch, void* stre
  * before return; a device array must stay valid until `stream` reaches it. */
 rlb_status rlb_init_grid(rlb_ctx* ctx, const double* eps0, int eps0_on_device, void* stream);
 
-/* Advance by `nsteps` predictor-corrector steps of dtau (Sec. 4.4): two fused
- * stream-collide launches per step.  Asynchronous on `stream`. */
+/* Advance by `nsteps` predictor-corrector steps of dtau (Sec. 4.4).  Each step
+ * launches, for the predictor and again for the corrector, a per-site
+ * matching kernel (Landau matching and EOS inversion, FP64) and the fused
+ * stream-collide kernel.  Asynchronous on `stream`. */
 rlb_status rlb_step(rlb_ctx* ctx, int nsteps, void* stream);
 
 /* Current proper time (host bookkeeping, fm/c). */
@@ -152,6 +154,15 @@ rlb_status rlb_get_tau(const rlb_ctx* ctx, double* tau);
  * `out` is host memory (synchronises `stream`) or device memory
  * (out_on_device != 0, asynchronous). */
 rlb_status rlb_moments(rlb_ctx* ctx, double* out, int out_on_device, void* stream);
+
+/* Per-kernel device timing.  While enabled, every launch made by this
+ * context is bracketed by CUDA events on its stream; rlb_get_timing waits for
+ * the pending events and returns the accumulated milliseconds and launch
+ * counts of the fused stream-collide kernel (two per step) and of the per-site
+ * matching kernel (two per step).  Enabling resets the counters. */
+rlb_status rlb_set_timing(rlb_ctx* ctx, int enable);
+rlb_status rlb_get_timing(rlb_ctx* ctx, double* stage_ms, long* stage_launches, double* match_ms,
+                          long* match_launches);
 
 /* Synchronise `stream` and report the device error word (RLB_ERR_NUMERIC if set). */
 rlb_status rlb_check(rlb_ctx* ctx, void* stream);
@@ -167,13 +178,11 @@ rlb_status rlb_state_offsets(const rlb_ctx* ctx, size_t* f_offset, size_t* lnM_o
 rlb_status rlb_lattice(const rlb_ctx* ctx, double* c, double* s, double* wxi, double* mu,
                        double* wth, double* cph, double* sph);
 
-/* Host copies of the nodal operator matrices (row-major [out][in]): Dr, the
- * Galerkin representation of v.d/dv on the radial nodes (n_xi^2; the radial
- * part of S1 and S2 in Sec. 4.4); Dth, the Galerkin representation of
- * (mu - mu^3) d/dmu on the polar nodes (n_theta^2; the polar part of S1);
- * Dmu and Dph, collocation derivatives d/dmu (n_theta^2) and d/dphi
- * ((2 n_phi_half)^2) used by the transverse mass-gradient force. */
-rlb_status rlb_operators(const rlb_ctx* ctx, double* Dr, double* Dth, double* Dmu, double* Dph);
+/* Host copies of the nodal operator matrices (row-major [out][in]) of
+ * Sec. 4.4: Dr, the Galerkin representation of v.d/dv on the radial nodes
+ * (n_xi^2; the radial part of S1 and S2), and Dth, the Galerkin representation
+ * of (mu - mu^3) d/dmu on the polar nodes (n_theta^2; the polar part of S1). */
+rlb_status rlb_operators(const rlb_ctx* ctx, double* Dr, double* Dth);
 
 #ifdef __cplusplus
 }

@@ -246,7 +246,6 @@ typedef struct or_ctx {
   double mu[OR_MAXN], sth[OR_MAXN], wth[OR_MAXN];
   double phi[OR_MAXN], cph[OR_MAXN], sph[OR_MAXN];
   double Dr[OR_MAXN * OR_MAXN], Dth[OR_MAXN * OR_MAXN];
-  double Dmu[OR_MAXN * OR_MAXN], Dph[OR_MAXN * OR_MAXN];
   double g16x[16], g16w[16];
 } or_ctx;
 
@@ -453,13 +452,11 @@ static int radial_rule(const or_params* P, int N, double* nodes, double* weights
 /* Dth: Galerkin representation of (mu - mu^3) d/dmu, from the angular part of */
 /*      s_1^{ml}: (1 - 3 mu^2) L_m + (mu - mu^3) L_m'.                          */
 /*      S1 = diag(mu^2) (x) Dr + Dth (x) 1 on each phi slice, S2 = 1 (x) Dr.     */
-/* Dmu: collocation derivative d/dmu on the Gauss-Legendre nodes.               */
-/* Dph: collocation derivative d/dphi of the trigonometric interpolant.        */
 /* Each is built as (reconstruction) x (modal Galerkin/derivative map).         */
 /* ------------------------------------------------------------------------ */
 static int build_operators(or_ctx* C) {
   const or_params* P = &C->P;
-  const int N = C->nxi, Nt = C->nth, L = C->nph;
+  const int N = C->nxi, Nt = C->nth;
   long double al[OR_MAXN + 2], be[OR_MAXN + 2];
   int rc = radial_recurrence(P, N, al, be);
   if (rc) return rc;
@@ -496,29 +493,6 @@ static int build_operators(or_ctx* C) {
         acc += Ljp * (-(2.0L * m + 1.0L) / 2.0L) * C->wth[j] * H;
       }
       C->Dth[jp * Nt + j] = (double)acc;
-    }
-  /* Lagrange collocation derivative on mu nodes: l_j'(mu_i) */
-  for (int i = 0; i < Nt; ++i)
-    for (int j = 0; j < Nt; ++j) {
-      long double den = 1.0L, num = 0.0L;
-      for (int m = 0; m < Nt; ++m)
-        if (m != j) den *= (long double)C->mu[j] - C->mu[m];
-      for (int q = 0; q < Nt; ++q) {
-        if (q == j) continue;
-        long double prod = 1.0L;
-        for (int m = 0; m < Nt; ++m)
-          if (m != j && m != q) prod *= (long double)C->mu[i] - C->mu[m];
-        num += prod;
-      }
-      C->Dmu[i * Nt + j] = (double)(num / den);
-    }
-  /* trigonometric interpolant on L = 2 N_phi equispaced nodes: modes |k| < L/2
-   * plus cos(L phi / 2), whose derivative vanishes on the nodes. */
-  for (int i = 0; i < L; ++i)
-    for (int l = 0; l < L; ++l) {
-      long double acc = 0.0L;
-      for (int k = 1; k < L / 2; ++k) acc += k * sinl(k * ((long double)C->phi[i] - C->phi[l]));
-      C->Dph[i * L + l] = (double)(-2.0L * acc / L);
     }
   return OR_OK;
 }
@@ -612,11 +586,9 @@ int or_nodes(const or_ctx* C, double* c, double* s, double* wxi, double* ecw, do
   return OR_OK;
 }
 
-int or_operators(const or_ctx* C, double* Dr, double* Dth, double* Dmu, double* Dph) {
+int or_operators(const or_ctx* C, double* Dr, double* Dth) {
   memcpy(Dr, C->Dr, sizeof(double) * C->nxi * C->nxi);
   memcpy(Dth, C->Dth, sizeof(double) * C->nth * C->nth);
-  memcpy(Dmu, C->Dmu, sizeof(double) * C->nth * C->nth);
-  memcpy(Dph, C->Dph, sizeof(double) * C->nph * C->nph);
   return OR_OK;
 }
 
@@ -694,24 +666,23 @@ static int match_site(const or_ctx* C, const double* f, double lnM, double T_gue
 }
 
 /* RHS of the kinetic equation at fixed v = p~/M for every node of one site:
- *   rhs = -V.grad f + (1/tau) S1 f + g S2 f + T_M f - (P.U/E)(f - f_eq)/tau_R
+ *   rhs = -V.grad f + (1/tau) S1 f + g S2 f + T_M f_eq - (P.U/E)(f - f_eq)/tau_R
  * with S1 = mu^2 Dr + Dth (Milne term of Eq. newBeq; absent in Minkowski),
- * S2 = Dr, g = d ln M / d tau from the consistency condition (Eq. masschange),
- * and T_M the mass-gradient terms (V.a) S2 f + (a/cosh xi).d_v f with
- * a = grad ln M, written in (xi, theta, phi) with d/dxi = Dr / tanh xi:
- *   T_M = A sin(th) (c/s) Dr f - A sin(th) mu/(c s) Dmu f + A'/(c s sin th) Dph f,
- *   A = a_x cos(phi) + a_y sin(phi), A' = -a_x sin(phi) + a_y cos(phi).
- * Streaming is second-order upwind per axis, periodic.  work: 5 nn doubles. */
-static int stage_site(const or_ctx* C, or_getf gf, or_getm gm, void* ud, int site, double tau,
-                      double T_guess, double* rhs, double* g_out, or_site* info, double* work) {
+ * S2 = Dr, g = d ln M / d tau from the consistency condition (Eq. masschange).
+ * T_M collects the transverse mass-gradient terms at fixed v, a = grad ln M:
+ *   (a.v/cosh xi) v.d_v      nodes move with the local mass,
+ *   (a/cosh xi).d_v          the force 1/2 d_i M^2 d^i_(p) of Eq. Bmilne,
+ * applied to the local equilibrium f_eq, whose v-derivative is known in closed
+ * form (a spectral v-derivative of f itself gives a discrete operator with
+ * eigenvalues of positive real part ~ 9 |a|).  Streaming is second-order upwind
+ * per axis, periodic.  `o` is the site's matching.  work: 3 nn doubles. */
+static int stage_site(const or_ctx* C, or_getf gf, or_getm gm, void* ud, int site,
+                      double tau, const or_site* os, double* rhs, double* g_out, double* work) {
   const or_params* P = &C->P;
   const int Nx = C->nxi, Nt = C->nth, Np = C->nph, nn = C->nn;
   const int x = site % P->nx, y = site / P->nx;
   const double* f = gf(ud, site);
-  double lnM = gm(ud, site);
-  or_site o;
-  int rc = match_site(C, f, lnM, T_guess, &o);
-  if (rc) return rc;
+  const or_site o = *os;
   const double M = o.M, T = o.T, invT = 1.0 / T;
   const double inv_tauR = 1.0 / o.tauR;
   const double ut = o.u[0], ux = o.u[1], uy = o.u[2], uz = o.u[3];
@@ -727,21 +698,15 @@ static int stage_site(const or_ctx* C, or_getf gf, or_getm gm, void* ud, int sit
   const double ay = (gm(ud, site_index(P, x, y + 1)) - gm(ud, site_index(P, x, y - 1))) / (2.0 * P->dx);
   double* Drf = work;
   double* Dthf = work + nn;
-  double* Dmuf = work + 2 * nn;
-  double* Dphf = work + 3 * nn;
-  double* R = work + 4 * nn;
+  double* R = work + 2 * nn;
   for (int l = 0; l < Np; ++l)
     for (int j = 0; j < Nt; ++j)
       for (int k = 0; k < Nx; ++k) {
         int n = (l * Nt + j) * Nx + k;
-        double a = 0.0, b = 0.0, cc = 0.0, d = 0.0;
+        double a = 0.0, b = 0.0;
         for (int q = 0; q < Nx; ++q) a += C->Dr[k * Nx + q] * f[(l * Nt + j) * Nx + q];
-        for (int q = 0; q < Nt; ++q) {
-          b += C->Dth[j * Nt + q] * f[(l * Nt + q) * Nx + k];
-          cc += C->Dmu[j * Nt + q] * f[(l * Nt + q) * Nx + k];
-        }
-        for (int q = 0; q < Np; ++q) d += C->Dph[l * Np + q] * f[(q * Nt + j) * Nx + k];
-        Drf[n] = a; Dthf[n] = b; Dmuf[n] = cc; Dphf[n] = d;
+        for (int q = 0; q < Nt; ++q) b += C->Dth[j * Nt + q] * f[(l * Nt + q) * Nx + k];
+        Drf[n] = a; Dthf[n] = b;
       }
   double K = 0.0, E = 0.0, Q = 0.0, A = 0.0;
   for (int l = 0; l < Np; ++l)
@@ -758,13 +723,15 @@ static int stage_site(const or_ctx* C, or_getf gf, or_getm gm, void* ud, int sit
         else if (Vy < 0) dfy = (-3.0 * f[n] + 4.0 * fyp1[n] - fyp2[n]) / (2.0 * P->dx);
         const double stream = -Vx * dfx - Vy * dfy;
         const double milne = P->metric ? (mu * mu * Drf[n] + Dthf[n]) / tau : 0.0;
-        const double Aph = ax * C->cph[l] + ay * C->sph[l];
-        const double Aphp = -ax * C->sph[l] + ay * C->cph[l];
-        const double TM = Aph * st * (c / s) * Drf[n] - Aph * st * mu / (c * s) * Dmuf[n] +
-                          Aphp / (c * s * st) * Dphf[n];
         const double Eeq = sqrt(o.Meq * o.Meq + M * M * s * s);
         const double PeqU = ut * Eeq - M * (vx * ux + vy * uy + vz * uz);
         const double feq = P->Z * exp(-PeqU * invT);
+        /* d_v f_eq = -(f_eq/T) (u^tau M^2 v/E_eq - M u): node motion (a.v/c) v.d_v and
+         * force (a/c).d_v applied to it */
+        const double av = ax * vx + ay * vy;
+        const double vu3 = vx * ux + vy * uy + vz * uz;
+        const double TM = -feq * invT * ((av / c) * (ut * M * M * s * s / Eeq - M * vu3) +
+                                         (ut * M * M * av / Eeq - M * (ax * ux + ay * uy)) / c);
         const double pu = c * ut - (vx * ux + vy * uy + vz * uz);
         const double coll = -(pu / c) * (f[n] - feq) * inv_tauR;
         R[n] = stream + milne + TM + coll;
@@ -783,7 +750,6 @@ static int stage_site(const or_ctx* C, or_getf gf, or_getm gm, void* ud, int sit
   const double g = -D * A / (K + D * (4.0 * E + Q - K));
   for (int n = 0; n < nn; ++n) rhs[n] = R[n] + g * Drf[n];
   *g_out = g;
-  if (info) *info = o;
   if (!isfinite(g)) return OR_ERR_NUMERIC;
   return OR_OK;
 }
@@ -797,35 +763,51 @@ static const double* grid_f(void* ud, int site) {
 }
 static double grid_m(void* ud, int site) { return ((or_grid*)ud)->lnM[site]; }
 
+/* One stage on the whole grid: match every site, then evaluate the RHS. */
 static int stage_grid(const or_ctx* C, const double* fin, const double* lnMin, double tau,
                       double* rhs, double* g, double* Tcache, int nthreads) {
   const int ns = C->P.nx * C->P.ny, nn = C->nn;
+  or_site* S = (or_site*)malloc(sizeof(or_site) * ns);
+  if (!S) return OR_ERR_NOMEM;
   or_grid G = {fin, lnMin, nn};
   int err = OR_OK;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nthreads > 0 ? nthreads : 1) schedule(static)
+#endif
+  for (int i = 0; i < ns; ++i) {
+    int rc = match_site(C, fin + (size_t)i * nn, lnMin[i], Tcache[i], &S[i]);
+    if (rc) {
+#ifdef _OPENMP
+#pragma omp critical(or_err)
+#endif
+      err = rc;
+    } else {
+      Tcache[i] = S[i].T;
+    }
+  }
+  if (err) { free(S); return err; }
 #ifdef _OPENMP
 #pragma omp parallel num_threads(nthreads > 0 ? nthreads : 1)
 #endif
   {
-    double* work = (double*)malloc(sizeof(double) * 5 * nn);
+    double* work = (double*)malloc(sizeof(double) * 3 * nn);
 #ifdef _OPENMP
 #pragma omp for schedule(static)
 #endif
     for (int i = 0; i < ns; ++i) {
-      or_site o;
-      int rc = work ? stage_site(C, grid_f, grid_m, &G, i, tau, Tcache[i], rhs + (size_t)i * nn,
-                                 g + i, &o, work)
+      int rc = work ? stage_site(C, grid_f, grid_m, &G, i, tau, &S[i], rhs + (size_t)i * nn,
+                                 g + i, work)
                     : OR_ERR_NOMEM;
       if (rc) {
 #ifdef _OPENMP
 #pragma omp critical(or_err)
 #endif
         err = rc;
-      } else {
-        Tcache[i] = o.T;
       }
     }
     free(work);
   }
+  free(S);
   return err;
 }
 
@@ -940,30 +922,32 @@ int or_init_state(const or_ctx* C, const double* eps0, double* f, double* lnM, i
 }
 
 /* One Heun step evaluated only at selected sites (for sampled parity on large
- * grids): the predictor is evaluated on the cross-shaped patch the corrector's
- * stencil reads (offsets up to 2 along x and y), the corrector at the site. */
+ * grids).  The corrector at site s reads predictor populations and ln M at s,
+ * s+-1, s+-2 along x and y; the predictor at those sites reads the input at
+ * their own +-2 neighbours. */
 typedef struct {
-  const double* f; const double* lnM; int nn;
-  int nsel; const int* ids; const double* fs; const double* lnMs;
+  const or_ctx* C; const double* f; const double* lnM;
+  int np; const int* pid; const double* fs; const double* lnMs; /* predictor patch */
+  int use_patch;
 } or_patch;
 static const double* patch_f(void* ud, int site) {
   or_patch* G = (or_patch*)ud;
-  for (int q = 0; q < G->nsel; ++q)
-    if (G->ids[q] == site) return G->fs + (size_t)q * G->nn;
+  if (!G->use_patch) return G->f + (size_t)site * G->C->nn;
+  for (int q = 0; q < G->np; ++q)
+    if (G->pid[q] == site) return G->fs + (size_t)q * G->C->nn;
   return NULL;
 }
 static double patch_m(void* ud, int site) {
   or_patch* G = (or_patch*)ud;
-  for (int q = 0; q < G->nsel; ++q)
-    if (G->ids[q] == site) return G->lnMs[q];
+  if (!G->use_patch) return G->lnM[site];
+  for (int q = 0; q < G->np; ++q)
+    if (G->pid[q] == site) return G->lnMs[q];
   return NAN;
 }
-
 int or_step_sites(const or_ctx* C, const double* f, const double* lnM, double tau, double dtau,
                   const int* sites, int nsel, double* f_out, double* lnM_out, int nthreads) {
   const or_params* P = &C->P;
   const int nn = C->nn;
-  or_grid G = {f, lnM, nn};
   int err = OR_OK;
 #ifdef _OPENMP
 #pragma omp parallel for num_threads(nthreads > 0 ? nthreads : 1) schedule(dynamic)
@@ -977,19 +961,28 @@ int or_step_sites(const or_ctx* C, const double* f, const double* lnM, double ta
       for (int b = 0; b < np; ++b) dup |= (ids[b] == id);
       if (!dup) ids[np++] = id;
     }
-    double* fs = (double*)malloc(sizeof(double) * (size_t)nn * (9 + 6));
+    double* fs = (double*)malloc(sizeof(double) * (size_t)nn * (9 + 4));
     double lnMs[9], g;
     int rc = fs ? OR_OK : OR_ERR_NOMEM;
     double* rhs = fs + (size_t)9 * nn;
     double* work = rhs + nn;
+    or_patch G;
+    memset(&G, 0, sizeof G);
+    G.C = C; G.f = f; G.lnM = lnM;
     for (int a = 0; a < np && !rc; ++a) {
-      rc = stage_site(C, grid_f, grid_m, &G, ids[a], tau, 0.3, rhs, &g, NULL, work);
+      or_site o;
+      rc = match_site(C, f + (size_t)ids[a] * nn, lnM[ids[a]], 0.3, &o);
+      if (!rc) rc = stage_site(C, patch_f, patch_m, &G, ids[a], tau, &o, rhs, &g, work);
       for (int n = 0; n < nn && !rc; ++n) fs[(size_t)a * nn + n] = f[(size_t)ids[a] * nn + n] + dtau * rhs[n];
       lnMs[a] = lnM[ids[a]] + dtau * g;
     }
     if (!rc) {
-      or_patch Pt = {f, lnM, nn, np, ids, fs, lnMs};
-      rc = stage_site(C, patch_f, patch_m, &Pt, s0, tau + dtau, 0.3, rhs, &g, NULL, work);
+      or_patch H;
+      memset(&H, 0, sizeof H);
+      H.C = C; H.f = f; H.lnM = lnM; H.np = np; H.pid = ids; H.fs = fs; H.lnMs = lnMs; H.use_patch = 1;
+      or_site o;
+      rc = match_site(C, fs, lnMs[0], 0.3, &o);
+      if (!rc) rc = stage_site(C, patch_f, patch_m, &H, s0, tau + dtau, &o, rhs, &g, work);
       for (int n = 0; n < nn && !rc; ++n)
         f_out[(size_t)q * nn + n] = 0.5 * (f[(size_t)s0 * nn + n] + fs[n] + dtau * rhs[n]);
       lnM_out[q] = 0.5 * (lnM[s0] + lnMs[0] + dtau * g);

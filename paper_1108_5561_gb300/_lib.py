@@ -15,7 +15,8 @@ RLB_MINKOWSKI, RLB_MILNE = 0, 1
 
 EXPORTS = ["rlb_create", "rlb_destroy", "rlb_last_error", "rlb_init_eos", "rlb_workspace_size",
            "rlb_configure", "rlb_bind_buffers", "rlb_init_grid", "rlb_step", "rlb_get_tau",
-           "rlb_moments", "rlb_check", "rlb_state_offsets", "rlb_lattice", "rlb_operators"]
+           "rlb_moments", "rlb_check", "rlb_state_offsets", "rlb_lattice", "rlb_operators",
+           "rlb_set_timing", "rlb_get_timing"]
 
 
 class EosParamsC(ctypes.Structure):
@@ -76,7 +77,9 @@ def load(build_if_missing: bool = True):
     lib.rlb_check.argtypes = [vp, vp]
     lib.rlb_state_offsets.argtypes = [vp, P(sz), P(sz), P(sz)]
     lib.rlb_lattice.argtypes = [vp] + [dp] * 7
-    lib.rlb_operators.argtypes = [vp, dp, dp, dp, dp]
+    lib.rlb_operators.argtypes = [vp, dp, dp]
+    lib.rlb_set_timing.argtypes = [vp, ctypes.c_int]
+    lib.rlb_get_timing.argtypes = [vp, dp, P(ctypes.c_long), dp, P(ctypes.c_long)]
     for name in EXPORTS:
         if name not in ("rlb_destroy", "rlb_last_error"):
             getattr(lib, name).restype = ctypes.c_int

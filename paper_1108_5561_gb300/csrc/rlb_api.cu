@@ -5,6 +5,8 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "../../include/rlb.h"
 #include "rlb_host.hpp"
@@ -19,11 +21,18 @@ struct rlb_ctx {
   rlb_grid_params gp{};
   rlb::Lattice lat;
   size_t ns = 0, nn = 0, pop_bytes = 0;
-  size_t f_off = 0, lnM_off = 0;                               // state
+  size_t f_off = 0, lnM_off = 0;  // state
   size_t fs_off = 0, lnMs_off = 0, T_off = 0, err_off = 0, tab_off = 0, eps_off = 0;  // scratch
+  size_t mom_off = 0, moms_off = 0, sc_off = 0, tabf_off = 0, scf_off = 0;
   char* state = nullptr;
   char* scratch = nullptr;
   double tau = 0.0;
+  // optional per-kernel timing (CUDA events on the launch stream)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;  // kind, (start, end)
+  double t_ms[3] = {0, 0, 0};
+  long t_n[3] = {0, 0, 0};
 };
 
 namespace {
@@ -68,13 +77,20 @@ void layout(const rlb_grid_params& g, size_t table_points, size_t* state_b, size
   size_t lnMs_off = off; off += mb;
   size_t T_off = off; off += mb;
   size_t eps_off = off; off += mb;
+  size_t mom_off = off; off += align256(ns * rlbk::kMom * sizeof(double));
+  size_t moms_off = off; off += align256(ns * rlbk::kMom * sizeof(double));
+  size_t sc_off = off; off += align256(ns * rlbk::kSc * sizeof(double));
   size_t err_off = off; off += 256;
   size_t tab_off = off; off += align256((table_points + 6) * rlb::kFields * sizeof(double));
+  size_t tabf_off = off; off += align256((table_points + 6) * rlb::kFields * sizeof(float));
+  size_t scf_off = off; off += align256(ns * rlbk::kSc * sizeof(float));
   *scratch_b = off;
   if (c) {
     c->f_off = f_off; c->lnM_off = lnM_off;
     c->fs_off = fs_off; c->lnMs_off = lnMs_off; c->T_off = T_off; c->eps_off = eps_off;
     c->err_off = err_off; c->tab_off = tab_off;
+    c->mom_off = mom_off; c->moms_off = moms_off; c->sc_off = sc_off;
+    c->tabf_off = tabf_off; c->scf_off = scf_off;
   }
 }
 
@@ -82,12 +98,10 @@ template <class R, int NXI, int NTH, int NPH>
 rlbk::Ops<R, NXI, NTH, NPH> make_ops(const rlb::Lattice& L) {
   rlbk::Ops<R, NXI, NTH, NPH> o;
   for (int i = 0; i < NXI * NXI; ++i) o.Dr[i] = (R)L.Dr[i];
-  for (int i = 0; i < NTH * NTH; ++i) { o.Dth[i] = (R)L.Dth[i]; o.Dmu[i] = (R)L.Dmu[i]; }
-  for (int i = 0; i < NPH * NPH; ++i) o.Dph[i] = (R)L.Dph[i];
+  for (int i = 0; i < NTH * NTH; ++i) o.Dth[i] = (R)L.Dth[i];
   for (int k = 0; k < NXI; ++k) {
     const double c = L.c[k], s = L.s[k], e = L.ecw[k];
-    o.c[k] = (R)c; o.s[k] = (R)s; o.c_over_s[k] = (R)(c / s); o.inv_cs[k] = (R)(1.0 / (c * s));
-    o.s2[k] = (R)(s * s); o.inv_c[k] = (R)(1.0 / c);
+    o.c[k] = (R)c; o.s[k] = (R)s; o.s2[k] = (R)(s * s); o.inv_c[k] = (R)(1.0 / c);
     o.w0[k] = (R)e; o.w1[k] = (R)(e * c * s); o.w2[k] = (R)(e * c * c); o.w3[k] = (R)(e * s * s);
     o.ecw[k] = (R)e;
   }
@@ -102,10 +116,64 @@ rlbk::Ops<R, NXI, NTH, NPH> make_ops(const rlb::Lattice& L) {
 rlbk::EosView eos_view(const rlb_ctx* c) {
   rlbk::EosView v;
   v.tab = reinterpret_cast<const double*>(c->scratch + c->tab_off);
+  v.tabf = reinterpret_cast<const float*>(c->scratch + c->tabf_off);
   v.y0 = c->tab.y0;
   v.inv_h = 1.0 / c->tab.h;
   v.n = c->tab.n;
   return v;
+}
+
+enum Kind { K_STAGE = 0, K_MATCH = 1, K_INIT = 2 };
+
+// Event bracket around one launch when timing is enabled.
+struct Timed {
+  rlb_ctx* c;
+  int kind;
+  cudaStream_t st;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  Timed(rlb_ctx* c_, int k, cudaStream_t s) : c(c_), kind(k), st(s) {
+    if (!c->timing) return;
+    e0 = take();
+    e1 = take();
+    if (e0) cudaEventRecord(e0, st);
+  }
+  cudaEvent_t take() {
+    if (c->ev_pool.empty()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      return e;
+    }
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  ~Timed() {
+    if (!c->timing || !e0 || !e1) return;
+    cudaEventRecord(e1, st);
+    c->ev_pending.push_back({kind, {e0, e1}});
+  }
+};
+
+rlb_status match(rlb_ctx* ctx, const double* mom, const double* lnM, double* obs, cudaStream_t st) {
+  rlbk::MatchArgs a;
+  a.mom = mom;
+  a.lnM = lnM;
+  a.Tsite = reinterpret_cast<double*>(ctx->scratch + ctx->T_off);
+  a.sc = reinterpret_cast<double*>(ctx->scratch + ctx->sc_off);
+  a.scf = reinterpret_cast<float*>(ctx->scratch + ctx->scf_off);
+  a.obs = obs;
+  a.err = reinterpret_cast<int*>(ctx->scratch + ctx->err_off);
+  a.eos = eos_view(ctx);
+  a.eta_over_s = ctx->gp.eta_over_s;
+  a.ns = (int)ctx->ns;
+  {
+    Timed tm(ctx, K_MATCH, st);
+    const unsigned nb = (unsigned)((ctx->ns + 127) / 128);
+    if (ctx->gp.prec == RLB_F64) rlbk::match_kernel<false><<<nb, 128, 0, st>>>(a);
+    else rlbk::match_kernel<true><<<nb, 128, 0, st>>>(a);
+  }
+  RLB_CUDA(cudaGetLastError(), "match_kernel launch");
+  return RLB_OK;
 }
 
 template <class S, class R, int NXI, int NTH, int NPH>
@@ -119,62 +187,63 @@ struct Runner {
     a.f = reinterpret_cast<S*>(ctx->state + ctx->f_off);
     a.lnM = reinterpret_cast<double*>(ctx->state + ctx->lnM_off);
     a.Tsite = reinterpret_cast<double*>(ctx->scratch + ctx->T_off);
+    a.mom = reinterpret_cast<double*>(ctx->scratch + ctx->mom_off);
     a.err = reinterpret_cast<int*>(ctx->scratch + ctx->err_off);
     a.eos = eos_view(ctx);
     a.Z = ctx->eosp.Z;
     a.family = ctx->gp.family;
     a.T0 = ctx->gp.T0;
     a.op = make_ops<R, NXI, NTH, NPH>(ctx->lat);
-    rlbk::init_kernel<S, R, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
+    {
+      Timed tm(ctx, K_INIT, st);
+      rlbk::init_kernel<S, R, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
+    }
     RLB_CUDA(cudaGetLastError(), "init_kernel launch");
     return RLB_OK;
   }
 
+  // One predictor-corrector step = match(f) -> stage(f -> f*) -> match(f*) -> stage(f*, f -> f).
   static rlb_status step(rlb_ctx* ctx, int nsteps, cudaStream_t st) {
     rlbk::StageArgs<S, R, NXI, NTH, NPH> a;
     S* f = reinterpret_cast<S*>(ctx->state + ctx->f_off);
     S* fs = reinterpret_cast<S*>(ctx->scratch + ctx->fs_off);
     double* m = reinterpret_cast<double*>(ctx->state + ctx->lnM_off);
     double* ms = reinterpret_cast<double*>(ctx->scratch + ctx->lnMs_off);
-    a.Tsite = reinterpret_cast<double*>(ctx->scratch + ctx->T_off);
+    double* mom = reinterpret_cast<double*>(ctx->scratch + ctx->mom_off);
+    double* moms = reinterpret_cast<double*>(ctx->scratch + ctx->moms_off);
+    a.sc = reinterpret_cast<const double*>(ctx->scratch + ctx->sc_off);
+    a.scf = reinterpret_cast<const float*>(ctx->scratch + ctx->scf_off);
     a.err = reinterpret_cast<int*>(ctx->scratch + ctx->err_off);
-    a.eos = eos_view(ctx);
     a.nx = ctx->gp.nx;
     a.ny = ctx->gp.ny;
     a.metric = ctx->gp.metric;
     a.dtau = ctx->gp.dtau;
     a.inv2dx = 1.0 / (2.0 * ctx->gp.dx);
     a.Z = ctx->eosp.Z;
-    a.eta_over_s = ctx->gp.eta_over_s;
     a.op = make_ops<R, NXI, NTH, NPH>(ctx->lat);
     for (int s = 0; s < nsteps; ++s) {
       // predictor: f* = f + dtau RHS(f) at tau
+      rlb_status r = match(ctx, mom, m, nullptr, st);
+      if (r) return r;
       a.f_in = f; a.lnM_in = m; a.f_base = f; a.lnM_base = m;
-      a.f_out = fs; a.lnM_out = ms; a.mode = 0; a.tau = ctx->tau;
-      rlbk::stage_kernel<S, R, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
+      a.f_out = fs; a.lnM_out = ms; a.mom_out = moms; a.mode = 0; a.tau = ctx->tau;
+      {
+        Timed tm(ctx, K_STAGE, st);
+        rlbk::stage_kernel<S, R, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
+      }
       RLB_CUDA(cudaGetLastError(), "stage_kernel (predictor) launch");
       // corrector: f = (f + f* + dtau RHS(f*))/2 at tau + dtau, in place over f
+      r = match(ctx, moms, ms, nullptr, st);
+      if (r) return r;
       a.f_in = fs; a.lnM_in = ms; a.f_base = f; a.lnM_base = m;
-      a.f_out = f; a.lnM_out = m; a.mode = 1; a.tau = ctx->tau + ctx->gp.dtau;
-      rlbk::stage_kernel<S, R, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
+      a.f_out = f; a.lnM_out = m; a.mom_out = mom; a.mode = 1; a.tau = ctx->tau + ctx->gp.dtau;
+      {
+        Timed tm(ctx, K_STAGE, st);
+        rlbk::stage_kernel<S, R, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
+      }
       RLB_CUDA(cudaGetLastError(), "stage_kernel (corrector) launch");
       ctx->tau += ctx->gp.dtau;
     }
-    return RLB_OK;
-  }
-
-  static rlb_status moments(rlb_ctx* ctx, double* out_dev, cudaStream_t st) {
-    rlbk::MomArgs<S, R, NXI, NTH, NPH> a;
-    a.f = reinterpret_cast<const S*>(ctx->state + ctx->f_off);
-    a.lnM = reinterpret_cast<const double*>(ctx->state + ctx->lnM_off);
-    a.Tsite = reinterpret_cast<const double*>(ctx->scratch + ctx->T_off);
-    a.out = out_dev;
-    a.err = reinterpret_cast<int*>(ctx->scratch + ctx->err_off);
-    a.eos = eos_view(ctx);
-    a.eta_over_s = ctx->gp.eta_over_s;
-    a.op = make_ops<R, NXI, NTH, NPH>(ctx->lat);
-    rlbk::moments_kernel<S, R, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
-    RLB_CUDA(cudaGetLastError(), "moments_kernel launch");
     return RLB_OK;
   }
 };
@@ -186,7 +255,7 @@ rlb_status run_op(rlb_ctx* c, Op op, int n, double* p, cudaStream_t st) {
   using Rn = Runner<S, R, NXI, NTH, NPH>;
   if (op == OP_INIT) return Rn::init(c, p, st);
   if (op == OP_STEP) return Rn::step(c, n, st);
-  return Rn::moments(c, p, st);
+  return RLB_ERR_ARG;
 }
 
 template <int NXI, int NTH, int NPH>
@@ -230,7 +299,12 @@ rlb_status rlb_create(rlb_ctx** out, int cuda_device) {
   return RLB_OK;
 }
 
-void rlb_destroy(rlb_ctx* ctx) { delete ctx; }
+void rlb_destroy(rlb_ctx* ctx) {
+  if (!ctx) return;
+  for (auto& p : ctx->ev_pending) { ctx->ev_pool.push_back(p.second.first); ctx->ev_pool.push_back(p.second.second); }
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  delete ctx;
+}
 
 const char* rlb_last_error(const rlb_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
@@ -299,6 +373,14 @@ rlb_status rlb_bind_buffers(rlb_ctx* ctx, void* state, void* scratch, void* stre
   RLB_CUDA(cudaMemcpyAsync(ctx->scratch + ctx->tab_off, ctx->tab.data.data(),
                            ctx->tab.data.size() * sizeof(double), cudaMemcpyHostToDevice, st),
            "EOS table upload");
+  {
+    std::vector<float> tf(ctx->tab.data.size());
+    for (size_t i = 0; i < tf.size(); ++i) tf[i] = (float)ctx->tab.data[i];
+    RLB_CUDA(cudaMemcpyAsync(ctx->scratch + ctx->tabf_off, tf.data(), tf.size() * sizeof(float),
+                             cudaMemcpyHostToDevice, st),
+             "FP32 EOS table upload");
+    RLB_CUDA(cudaStreamSynchronize(st), "bind synchronise");
+  }
   RLB_CUDA(cudaMemsetAsync(ctx->scratch + ctx->err_off, 0, 256, st), "error word reset");
   // the table copy reads pageable host memory owned by ctx: wait for it
   RLB_CUDA(cudaStreamSynchronize(st), "bind synchronise");
@@ -369,16 +451,48 @@ rlb_status rlb_moments(rlb_ctx* ctx, double* out, int out_on_device, void* strea
   rlb_status s = set_device(ctx);
   if (s) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (out_on_device) return dispatch(ctx, OP_MOMENTS, 0, out, st);
+  const double* mom = reinterpret_cast<const double*>(ctx->scratch + ctx->mom_off);
+  const double* lnM = reinterpret_cast<const double*>(ctx->state + ctx->lnM_off);
+  if (out_on_device) return match(ctx, mom, lnM, out, st);
   // host output: stage through the predictor buffer (free between steps)
   double* dev = reinterpret_cast<double*>(ctx->scratch + ctx->fs_off);
   if (ctx->ns * 8 * sizeof(double) > ctx->ns * ctx->nn * ctx->pop_bytes)
     return fail(ctx, RLB_ERR_ARG, "lattice too small to stage host moments");
-  s = dispatch(ctx, OP_MOMENTS, 0, dev, st);
+  s = match(ctx, mom, lnM, dev, st);
   if (s) return s;
   RLB_CUDA(cudaMemcpyAsync(out, dev, ctx->ns * 8 * sizeof(double), cudaMemcpyDeviceToHost, st),
            "moments download");
   return rlb_check(ctx, stream);
+}
+
+rlb_status rlb_set_timing(rlb_ctx* ctx, int enable) {
+  if (!ctx) return RLB_ERR_ARG;
+  ctx->timing = enable != 0;
+  ctx->t_ms[0] = ctx->t_ms[1] = ctx->t_ms[2] = 0.0;
+  ctx->t_n[0] = ctx->t_n[1] = ctx->t_n[2] = 0;
+  return RLB_OK;
+}
+
+rlb_status rlb_get_timing(rlb_ctx* ctx, double* stage_ms, long* stage_launches, double* match_ms,
+                          long* match_launches) {
+  if (!ctx || !stage_ms || !stage_launches || !match_ms || !match_launches) return RLB_ERR_ARG;
+  rlb_status s = set_device(ctx);
+  if (s) return s;
+  for (auto& p : ctx->ev_pending) {
+    RLB_CUDA(cudaEventSynchronize(p.second.second), "timing event");
+    float ms = 0.0f;
+    RLB_CUDA(cudaEventElapsedTime(&ms, p.second.first, p.second.second), "timing elapsed");
+    ctx->t_ms[p.first] += ms;
+    ctx->t_n[p.first] += 1;
+    ctx->ev_pool.push_back(p.second.first);
+    ctx->ev_pool.push_back(p.second.second);
+  }
+  ctx->ev_pending.clear();
+  *stage_ms = ctx->t_ms[K_STAGE];
+  *stage_launches = ctx->t_n[K_STAGE];
+  *match_ms = ctx->t_ms[K_MATCH];
+  *match_launches = ctx->t_n[K_MATCH];
+  return RLB_OK;
 }
 
 rlb_status rlb_state_offsets(const rlb_ctx* ctx, size_t* f_offset, size_t* lnM_offset,
@@ -402,14 +516,12 @@ rlb_status rlb_lattice(const rlb_ctx* ctx, double* c, double* s, double* wxi, do
   return RLB_OK;
 }
 
-rlb_status rlb_operators(const rlb_ctx* ctx, double* Dr, double* Dth, double* Dmu, double* Dph) {
-  if (!ctx || !Dr || !Dth || !Dmu || !Dph) return RLB_ERR_ARG;
+rlb_status rlb_operators(const rlb_ctx* ctx, double* Dr, double* Dth) {
+  if (!ctx || !Dr || !Dth) return RLB_ERR_ARG;
   if (!ctx->grid_ok) return RLB_ERR_STATE;
   const rlb::Lattice& L = ctx->lat;
   std::memcpy(Dr, L.Dr.data(), L.Dr.size() * sizeof(double));
   std::memcpy(Dth, L.Dth.data(), L.Dth.size() * sizeof(double));
-  std::memcpy(Dmu, L.Dmu.data(), L.Dmu.size() * sizeof(double));
-  std::memcpy(Dph, L.Dph.data(), L.Dph.size() * sizeof(double));
   return RLB_OK;
 }
 

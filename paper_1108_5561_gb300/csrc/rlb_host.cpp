@@ -337,16 +337,14 @@ std::string build_lattice(int family, int nxi, int nth, int nphi_half, double z0
   }
   std::vector<ld> Dm = diff_matrix(mu);
   L->Dth.assign(nth * nth, 0.0);
-  L->Dmu.assign(nth * nth, 0.0);
   for (int jp = 0; jp < nth; ++jp)
     for (int j = 0; j < nth; ++j) {
       ld m = mu[j];
       ld val = -(wt[j] / wt[jp]) * (m - m * m * m) * Dm[j * nth + jp];
       if (j == jp) val -= 1.0L - 3.0L * m * m;
       L->Dth[jp * nth + j] = (double)val;
-      L->Dmu[jp * nth + j] = (double)Dm[jp * nth + j];
     }
-  // azimuths phi_l = l pi / N_phi and the Fourier differentiation matrix
+  // azimuths phi_l = l pi / N_phi (zeros of sin(N_phi phi))
   const int np = L->nph;
   L->cph.resize(np); L->sph.resize(np);
   for (int l = 0; l < np; ++l) {
@@ -355,14 +353,6 @@ std::string build_lattice(int family, int nxi, int nth, int nphi_half, double z0
     L->cph[l] = fabsl(cp) < 1e-12L ? 0.0 : (double)cp;
     L->sph[l] = fabsl(sp) < 1e-12L ? 0.0 : (double)sp;
   }
-  L->Dph.assign(np * np, 0.0);
-  for (int i = 0; i < np; ++i)
-    for (int l = 0; l < np; ++l) {
-      if (i == l) continue;
-      int d = i - l;
-      ld sgn = (((d % 2) + 2) % 2) ? -1.0L : 1.0L;
-      L->Dph[i * np + l] = (double)(0.5L * sgn / tanl((ld)d * kPi / np));
-    }
   return "";
 }
 
@@ -425,16 +415,17 @@ std::string build_eos_table(const EosParams& p, EosTable* out) {
     double B = (p.kind == 0) ? o.pkin - pres : 0.0;
     double eps = T * o.s - pres;
     double* d = &out->data[(size_t)i * kFields];
-    d[0] = std::log(o.e);
+    d[0] = o.e;
     d[1] = o.x;
     d[2] = o.D;
-    d[3] = std::log(o.htau);
+    d[3] = 1.0 / o.htau;
     d[4] = B / (T * T * T * T);
-    d[5] = std::log(eps);
+    d[5] = eps;
     d[6] = 0.0;
     d[7] = 0.0;
     for (int f = 0; f < 6; ++f)
       if (!std::isfinite(d[f])) return "non-finite EOS table entry";
+    if (!(d[0] > 0.0 && d[5] > 0.0)) return "non-positive energy density in the EOS table";
   }
   return "";
 }

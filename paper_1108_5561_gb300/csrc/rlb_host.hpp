@@ -20,7 +20,7 @@ struct Lattice {
   // polar and azimuthal
   std::vector<double> mu, sth, wth, cph, sph;
   // nodal operators, row-major [out][in]
-  std::vector<double> Dr, Dth, Dmu, Dph;
+  std::vector<double> Dr, Dth;
 };
 
 struct EosParams {
@@ -31,12 +31,12 @@ struct EosParams {
 };
 
 // Table of EOS fields on a uniform grid in y = ln T; kFields doubles per node:
-//   0: ln e(T)   (e = eps - B, the kinetic equilibrium energy density, GeV^4)
+//   0: e(T) = eps - B, the kinetic equilibrium energy density [GeV^4]
 //   1: x(T) = M(T)/T
 //   2: D(T) = dB/deps
-//   3: ln h(T),  tau_R = (eta/s) h(T) [fm]  (Chapman-Enskog relation, Sec. 4.1)
+//   3: 1/h(T),  tau_R = (eta/s) h(T) [fm]  (Chapman-Enskog relation, Sec. 4.1)
 //   4: B(T)/T^4
-//   5: ln eps_EOS(T)
+//   5: eps_EOS(T) [GeV^4]
 constexpr int kFields = 8;
 struct EosTable {
   double y0 = 0, h = 0;

@@ -6,9 +6,8 @@
 // n_xi radial nodes at fixed polar index j and azimuth l, contiguous in
 // memory), so a warp's loads of a site are contiguous and vectorised.  The
 // site's populations are staged in shared memory for the polar (theta-line)
-// and azimuthal (phi-line) operators; the per-site FP64 Landau matching and
-// EOS inversion run on lane 0 of warp 0 while the other warps apply the
-// polar/azimuthal operators.
+// operator; the per-site FP64 Landau matching and EOS inversion run on lane 0
+// of warp 0 while the other warps apply the polar operator.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -25,10 +24,8 @@ template <class R, int NXI, int NTH, int NPH>
 struct Ops {
   R Dr[NXI * NXI];    // Galerkin v.d/dv (radial part of S1, S2)
   R Dth[NTH * NTH];   // Galerkin (mu - mu^3) d/dmu (polar part of S1)
-  R Dmu[NTH * NTH];   // collocation d/dmu
-  R Dph[NPH * NPH];   // collocation d/dphi
   // radial node constants
-  R c[NXI], s[NXI], c_over_s[NXI], inv_cs[NXI], s2[NXI], inv_c[NXI];
+  R c[NXI], s[NXI], s2[NXI], inv_c[NXI];
   R w0[NXI], w1[NXI], w2[NXI], w3[NXI];  // ecw * {1, c s, c^2, s^2}
   R ecw[NXI];
   // polar
@@ -38,31 +35,12 @@ struct Ops {
 };
 
 struct EosView {
-  const double* tab;  // n x 8 doubles, uniform in y = ln T
+  const double* tab;   // n x 8 doubles, uniform in y = ln T
+  const float* tabf;   // the same table rounded to FP32
   double y0, inv_h;
   int n;
 };
 
-template <class S, class R, int NXI, int NTH, int NPH>
-struct StageArgs {
-  const S* f_in;          // populations the right-hand side is evaluated on
-  const double* lnM_in;
-  const S* f_base;        // corrector: populations at the start of the step
-  const double* lnM_base;
-  S* f_out;
-  double* lnM_out;
-  double* Tsite;          // per-site temperature: Newton start in, matched T out
-  int* err;
-  EosView eos;
-  int nx, ny;
-  int mode;               // 0 predictor, 1 corrector
-  int metric;             // 1 Milne
-  double tau, dtau;
-  double inv2dx;
-  double Z;
-  double eta_over_s;
-  Ops<R, NXI, NTH, NPH> op;
-};
 
 // ---------------------------------------------------------------------------
 // storage <-> compute conversions
@@ -149,11 +127,27 @@ template <> __device__ __forceinline__ float fsqrt<float>(float x) { return sqrt
 template <> __device__ __forceinline__ double fsqrt<double>(double x) { return sqrt(x); }
 
 // ---------------------------------------------------------------------------
-// EOS table: 6-point Lagrange interpolation in y = ln T (offsets -2..3)
+// EOS table: 6-point Lagrange interpolation in y = ln T (node offsets -2..3).
+// Fields (8 doubles per node): 0 e(T) = eps - B [GeV^4], 1 M(T)/T, 2 dB/deps,
+// 3 1/h with tau_R = (eta/s) h [1/fm], 4 B/T^4, 5 eps(T) [GeV^4].
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void lagrange6(double t, double w[6], double dw[6]) {
+enum : int { EOS_E = 0, EOS_X = 1, EOS_D = 2, EOS_INVH = 3, EOS_B = 4, EOS_EPS = 5 };
+
+__device__ __forceinline__ void lagrange6(double t, double w[6]) {
+  const double a = t + 2.0, b = t + 1.0, c = t, d = t - 1.0, e = t - 2.0, f = t - 3.0;
+  const double ab = a * b, de = d * e, ef = e * f, cd = c * d;
+  w[0] = b * cd * ef * (-1.0 / 120.0);
+  w[1] = a * cd * ef * (1.0 / 24.0);
+  w[2] = ab * de * f * (-1.0 / 12.0);
+  w[3] = ab * c * ef * (1.0 / 12.0);
+  w[4] = ab * cd * f * (-1.0 / 24.0);
+  w[5] = ab * cd * e * (1.0 / 120.0);
+}
+
+// derivative of the six weights with respect to t
+__device__ __forceinline__ void lagrange6_d(double t, double dw[6]) {
   const double fac[6] = {t + 2.0, t + 1.0, t, t - 1.0, t - 2.0, t - 3.0};
-  const double den[6] = {-120.0, 24.0, -12.0, 12.0, -24.0, 120.0};
+  const double inv[6] = {-1.0 / 120.0, 1.0 / 24.0, -1.0 / 12.0, 1.0 / 12.0, -1.0 / 24.0, 1.0 / 120.0};
 #pragma unroll
   for (int m = 0; m < 6; ++m) {
     double prod = 1.0, dprod = 0.0;
@@ -163,8 +157,7 @@ __device__ __forceinline__ void lagrange6(double t, double w[6], double dw[6]) {
       dprod = dprod * fac[q] + prod;
       prod *= fac[q];
     }
-    w[m] = prod / den[m];
-    dw[m] = dprod / den[m];
+    dw[m] = dprod * inv[m];
   }
 }
 
@@ -186,16 +179,20 @@ __device__ __forceinline__ double eos_field(const EosView& E, int i0, const doub
   return v;
 }
 
-// Solve table field `field`(y) = target for y by Newton on the interpolant.
+// Solve table field `field`(y) = target for y (the field increases with y) by
+// Newton on the interpolant, safeguarded by a bisection bracket that starts as
+// the whole tabulated range; a target outside the range is reported as failure.
 __device__ bool eos_invert(const EosView& E, int field, double target, double y, double* y_out) {
-  const double ylo = E.y0 + 2.0 / E.inv_h, yhi = E.y0 + (E.n - 4) / E.inv_h;
-  if (!(y > ylo && y < yhi)) y = 0.5 * (ylo + yhi);
+  double lo = E.y0 + 2.0 / E.inv_h, hi = E.y0 + (E.n - 4) / E.inv_h;
+  const double ymin = lo, ymax = hi;
+  if (!(y > lo && y < hi)) y = 0.5 * (lo + hi);
   int settled = 0;
-  for (int it = 0; it < 60; ++it) {
+  for (int it = 0; it < 200; ++it) {
     int i0;
     double t, w[6], dw[6];
     if (!eos_cell(E, y, &i0, &t)) return false;
-    lagrange6(t, w, dw);
+    lagrange6(t, w);
+    lagrange6_d(t, dw);
     double F = 0.0, dF = 0.0;
 #pragma unroll
     for (int m = 0; m < 6; ++m) {
@@ -204,17 +201,114 @@ __device__ bool eos_invert(const EosView& E, int field, double target, double y,
       dF += dw[m] * v;
     }
     dF *= E.inv_h;
-    if (!(dF > 0.0)) return false;
-    double dy = (F - target) / dF;
-    double yn = y - dy;
-    if (yn < ylo) yn = 0.5 * (y + ylo);
-    if (yn > yhi) yn = 0.5 * (y + yhi);
+    if (F == target) { *y_out = y; return true; }
+    if (F < target) lo = y; else hi = y;
+    double yn = (dF > 0.0) ? y - (F - target) / dF : 0.5 * (lo + hi);
+    if (!(yn >= lo && yn <= hi)) yn = 0.5 * (lo + hi);
+    const double dy = yn - y;
     y = yn;
-    if (fabs(dy) < 1e-13) {
-      if (++settled == 2) { *y_out = y; return true; }
+    if (fabs(dy) < 1e-13 || hi - lo < 1e-14) {
+      if (++settled == 2) {
+        // a target beyond the table drives the bracket onto one of its ends
+        if (y - ymin < 1e-12 || ymax - y < 1e-12) return false;
+        *y_out = y;
+        return true;
+      }
+    } else {
+      settled = 0;
     }
   }
   return false;
+}
+
+// FP32 versions for the FP32-arithmetic kernels (start values and the fields
+// that feed FP32 arithmetic).
+__device__ __forceinline__ void lagrange6f(float t, float w[6]) {
+  const float a = t + 2.f, b = t + 1.f, c = t, d = t - 1.f, e = t - 2.f, f = t - 3.f;
+  const float ab = a * b, de = d * e, ef = e * f, cd = c * d;
+  w[0] = b * cd * ef * (-1.f / 120.f);
+  w[1] = a * cd * ef * (1.f / 24.f);
+  w[2] = ab * de * f * (-1.f / 12.f);
+  w[3] = ab * c * ef * (1.f / 12.f);
+  w[4] = ab * cd * f * (-1.f / 24.f);
+  w[5] = ab * cd * e * (1.f / 120.f);
+}
+__device__ __forceinline__ void lagrange6f_d(float t, float dw[6]) {
+  const float fac[6] = {t + 2.f, t + 1.f, t, t - 1.f, t - 2.f, t - 3.f};
+  const float inv[6] = {-1.f / 120.f, 1.f / 24.f, -1.f / 12.f, 1.f / 12.f, -1.f / 24.f, 1.f / 120.f};
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    float prod = 1.f, dprod = 0.f;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      if (q == m) continue;
+      dprod = dprod * fac[q] + prod;
+      prod *= fac[q];
+    }
+    dw[m] = dprod * inv[m];
+  }
+}
+__device__ __forceinline__ float eos_fieldf(const EosView& E, int i0, const float w[6], int field) {
+  float v = 0.f;
+#pragma unroll
+  for (int m = 0; m < 6; ++m) v += w[m] * __ldg(E.tabf + (size_t)(i0 - 2 + m) * 8 + field);
+  return v;
+}
+
+// Table inversion for the FP32 path: bracketed Newton in FP32 to a start
+// value, then FP64 Newton steps on the FP64 table (the residual in FP64 fixes
+// the root; the slope may be taken from the FP32 table).  Same failure rules as
+// eos_invert.
+__device__ bool eos_invert_mixed(const EosView& E, int field, double target, double y, double* y_out) {
+  float lo = (float)(E.y0 + 2.0 / E.inv_h), hi = (float)(E.y0 + (E.n - 4) / E.inv_h);
+  const float ymin = lo, ymax = hi, tf = (float)target, y0f = (float)E.y0, ihf = (float)E.inv_h;
+  float yf = (y > ymin && y < ymax) ? (float)y : 0.5f * (lo + hi);
+  bool ok = false;
+  for (int it = 0; it < 100; ++it) {
+    const float u = (yf - y0f) * ihf;
+    if (!(u >= 2.f && u <= (float)(E.n - 4))) return false;
+    int i0 = min((int)floorf(u), E.n - 4);
+    const float t = u - (float)i0;
+    float w[6], dw[6];
+    lagrange6f(t, w);
+    lagrange6f_d(t, dw);
+    float F = 0.f, dF = 0.f;
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+      const float v = __ldg(E.tabf + (size_t)(i0 - 2 + m) * 8 + field);
+      F += w[m] * v;
+      dF += dw[m] * v;
+    }
+    dF *= ihf;
+    if (F < tf) lo = yf; else hi = yf;
+    float yn = (dF > 0.f) ? yf - (F - tf) / dF : 0.5f * (lo + hi);
+    if (!(yn >= lo && yn <= hi)) yn = 0.5f * (lo + hi);
+    const float dy = yn - yf;
+    yf = yn;
+    if (fabsf(dy) < 2e-6f || hi - lo < 4e-6f) { ok = true; break; }
+  }
+  if (!ok || yf - ymin < 1e-5f || ymax - yf < 1e-5f) return false;
+  double yd = (double)yf;
+  for (int it = 0; it < 2; ++it) {  // FP64 refinement
+    int i0;
+    double t, w[6];
+    if (!eos_cell(E, yd, &i0, &t)) return false;
+    lagrange6(t, w);
+    float dw[6];
+    lagrange6f_d((float)t, dw);
+    double F = 0.0;
+    float dF = 0.f;
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+      F += w[m] * __ldg(E.tab + (size_t)(i0 - 2 + m) * 8 + field);
+      dF += dw[m] * __ldg(E.tabf + (size_t)(i0 - 2 + m) * 8 + field);
+    }
+    dF *= ihf;
+    if (!(dF > 0.f)) return false;
+    yd -= (F - target) * (double)(1.0f / dF);
+  }
+  *y_out = yd;
+  return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -227,6 +321,7 @@ __device__ bool eos_invert(const EosView& E, int field, double target, double y,
 // space of A - eps (largest cross product of two rows), normalised by the
 // Minkowski norm; eps is then the Rayleigh quotient u_mu u_nu T^{mu nu}.
 // ---------------------------------------------------------------------------
+template <bool FP32_START>
 __device__ bool landau3(const double tm[6], double u[3], double* eps) {
   const double a00 = tm[0], a01 = -tm[1], a02 = -tm[2];
   const double a10 = tm[1], a11 = -tm[3], a12 = -tm[4];
@@ -237,7 +332,26 @@ __device__ bool landau3(const double tm[6], double u[3], double* eps) {
                     a02 * (a10 * a21 - a11 * a20);
   double lam = fmax(fabs(a00) + fabs(a01) + fabs(a02),
                     fmax(fabs(a10) + fabs(a11) + fabs(a12), fabs(a20) + fabs(a21) + fabs(a22)));
-  for (int it = 0; it < 200; ++it) {
+  int iters = 200;
+  if constexpr (FP32_START) {
+    // monotone Newton from above in FP32 (scaled by the bound), then FP64 steps
+    const float sc = (float)lam, isc = 1.f / sc;
+    const float c2f = (float)c2 * isc, c1f = (float)c1 * isc * isc, c0f = (float)c0 * isc * isc * isc;
+    float lf = 1.f;
+    for (int it = 0; it < 60; ++it) {
+      const float p = ((lf - c2f) * lf + c1f) * lf - c0f;
+      const float dp = (3.f * lf - 2.f * c2f) * lf + c1f;
+      if (!(dp > 0.f)) break;
+      const float d = p / dp;
+      if (!(d > 0.f)) break;
+      lf -= d;
+      if (d <= 1e-7f * fabsf(lf)) break;
+    }
+    // stay above the root: back off by a few FP32 ulps before the FP64 steps
+    lam = (double)lf * (1.0 + 4e-7) * (double)sc;
+    iters = 6;
+  }
+  for (int it = 0; it < iters; ++it) {
     double p = ((lam - c2) * lam + c1) * lam - c0;
     double dp = (3.0 * lam - 2.0 * c2) * lam + c1;
     if (!(dp > 0.0)) break;
@@ -246,24 +360,16 @@ __device__ bool landau3(const double tm[6], double u[3], double* eps) {
     lam -= d;
     if (d <= 1e-16 * fabs(lam)) break;
   }
-  const double r0[3] = {a00 - lam, a01, a02};
-  const double r1[3] = {a10, a11 - lam, a12};
-  const double r2[3] = {a20, a21, a22 - lam};
-  double cand[3][3];
-  const double* rows[3][2] = {{r0, r1}, {r0, r2}, {r1, r2}};
-  int best = 0;
-  double bn = -1.0;
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    const double* a = rows[q][0];
-    const double* b = rows[q][1];
-    cand[q][0] = a[1] * b[2] - a[2] * b[1];
-    cand[q][1] = a[2] * b[0] - a[0] * b[2];
-    cand[q][2] = a[0] * b[1] - a[1] * b[0];
-    double nn = cand[q][0] * cand[q][0] + cand[q][1] * cand[q][1] + cand[q][2] * cand[q][2];
-    if (nn > bn) { bn = nn; best = q; }
-  }
-  double v0 = cand[best][0], v1 = cand[best][1], v2 = cand[best][2];
+  // null vector of A - lam: the largest of the three row cross products
+  const double r00 = a00 - lam, r11 = a11 - lam, r22 = a22 - lam;
+  const double p0 = a01 * a12 - a02 * r11, p1 = a02 * a10 - r00 * a12, p2 = r00 * r11 - a01 * a10;  // r0 x r1
+  const double q0 = a01 * r22 - a02 * a21, q1 = a02 * a20 - r00 * r22, q2 = r00 * a21 - a01 * a20;  // r0 x r2
+  const double s0 = r11 * r22 - a12 * a21, s1 = a12 * a20 - a10 * r22, s2 = a10 * a21 - r11 * a20;  // r1 x r2
+  const double np = p0 * p0 + p1 * p1 + p2 * p2, nq = q0 * q0 + q1 * q1 + q2 * q2;
+  const double nsq = s0 * s0 + s1 * s1 + s2 * s2;
+  double v0 = s0, v1 = s1, v2 = s2;
+  if (np >= nq && np >= nsq) { v0 = p0; v1 = p1; v2 = p2; }
+  else if (nq >= nsq) { v0 = q0; v1 = q1; v2 = q2; }
   double mn = v0 * v0 - v1 * v1 - v2 * v2;
   if (!(mn > 0.0)) return false;
   double r = rsqrt(mn);
@@ -274,46 +380,101 @@ __device__ bool landau3(const double tm[6], double u[3], double* eps) {
   return *eps > 0.0;
 }
 
-struct SiteState {
-  double u[3];
-  double T, Meq, D, inv_tauR, eps_kin, B;
+// per-site moments (without the M^4/(2 pi^2) prefactor), 8 doubles per site:
+//   K^ = sum w f, T00, T01, T02, T11, T12, T22 (sum w f P^ P^), Tzz
+constexpr int kMom = 8;
+// per-site matching results consumed by the stage kernel
+constexpr int kSc = 12;
+enum : int {
+  SC_UT = 0, SC_UX, SC_UY, SC_INVT, SC_MEQ, SC_M, SC_ITR, SC_D, SC_B, SC_K, SC_KH, SC_T
 };
 
-// Matching of one site (FP64): Landau (u, eps_kin), T from e(T) = eps_kin,
-// then M(T), dB/deps, tau_R and B(T) from the table.  Returns error bits.
-__device__ int match_site(const EosView& E, const double mom[7], double lnM, double Tguess,
-                          double eta_over_s, bool want_B, SiteState* o) {
+struct MatchArgs {
+  const double* mom;    // kMom per site
+  const double* lnM;
+  double* Tsite;        // Newton start in, T out
+  double* sc;           // kSc per site
+  float* scf;           // FP32 copy of sc (read by the FP32-arithmetic kernels)
+  double* obs;          // 8 observables per site, or nullptr
+  int* err;
+  EosView eos;
+  double eta_over_s;
+  int ns;
+};
+
+// Matching of every site (FP64, one thread per site): Landau (u, eps_kin),
+// T from e(T) = eps_kin (B at its equilibrium value, Eq. sanity), then M(T),
+// dB/deps, tau_R (Sec. 4.1) and B(T) from the table.
+template <bool FAST>
+__global__ void __launch_bounds__(128) match_kernel(const MatchArgs A) {
+  const int site = blockIdx.x * blockDim.x + threadIdx.x;
+  if (site >= A.ns) return;
+  const double* m = A.mom + (size_t)site * kMom;
+  const double lnM = A.lnM[site];
   const double M = exp(lnM);
   const double pref = M * M * M * M * (1.0 / (2.0 * 3.14159265358979323846 * 3.14159265358979323846));
   double tm[6];
 #pragma unroll
-  for (int q = 0; q < 6; ++q) tm[q] = pref * mom[1 + q];
+  for (int q = 0; q < 6; ++q) tm[q] = pref * m[1 + q];
   int err = 0;
-  double eps;
-  if (!landau3(tm, o->u, &eps)) {
+  double u[3], eps;
+  if (!landau3<FAST>(tm, u, &eps)) {
     err |= ERR_LANDAU;
-    o->u[0] = 1.0; o->u[1] = 0.0; o->u[2] = 0.0;
+    u[0] = 1.0; u[1] = 0.0; u[2] = 0.0;
     eps = fmax(tm[0], 1e-300);
   }
-  o->eps_kin = eps;
-  double y;
-  double yg = (Tguess > 0.0) ? log(Tguess) : 0.0;
-  if (!eos_invert(E, 0, log(eps), yg, &y)) {
+  const double Tg = A.Tsite[site];
+  double y, yg = (Tg > 0.0) ? (FAST ? (double)logf((float)Tg) : log(Tg)) : 0.0;
+  const bool inv_ok = FAST ? eos_invert_mixed(A.eos, EOS_E, eps, yg, &y) : eos_invert(A.eos, EOS_E, eps, yg, &y);
+  if (!inv_ok) {
     err |= ERR_EOS;
-    y = fmin(fmax(yg, E.y0 + 2.0 / E.inv_h), E.y0 + (E.n - 4) / E.inv_h);
+    y = fmin(fmax(yg, A.eos.y0 + 2.0 / A.eos.inv_h), A.eos.y0 + (A.eos.n - 4) / A.eos.inv_h);
   }
   int i0;
-  double t, w[6], dw[6];
-  eos_cell(E, y, &i0, &t);
-  lagrange6(t, w, dw);
-  const double T = exp(y);
-  o->T = T;
-  o->Meq = eos_field(E, i0, w, 1) * T;
-  o->D = eos_field(E, i0, w, 2);
-  o->inv_tauR = 1.0 / (eta_over_s * exp(eos_field(E, i0, w, 3)));
-  o->B = want_B ? eos_field(E, i0, w, 4) * T * T * T * T : 0.0;
-  if (!isfinite(o->T) || !isfinite(o->u[1]) || !isfinite(o->u[2])) err |= ERR_NONFINITE;
-  return err;
+  double t, T, Meq, D, itr, B;
+  eos_cell(A.eos, y, &i0, &t);
+  if constexpr (FAST) {  // fields that feed FP32 arithmetic: FP32 interpolation
+    float w[6];
+    lagrange6f((float)t, w);
+    const float Tf = expf((float)y);
+    T = Tf;
+    Meq = eos_fieldf(A.eos, i0, w, EOS_X) * Tf;
+    D = eos_fieldf(A.eos, i0, w, EOS_D);
+    itr = eos_fieldf(A.eos, i0, w, EOS_INVH) / (float)A.eta_over_s;
+    const float T2 = Tf * Tf;
+    B = eos_fieldf(A.eos, i0, w, EOS_B) * T2 * T2;
+  } else {
+    double w[6];
+    lagrange6(t, w);
+    T = exp(y);
+    Meq = eos_field(A.eos, i0, w, EOS_X) * T;
+    D = eos_field(A.eos, i0, w, EOS_D);
+    itr = eos_field(A.eos, i0, w, EOS_INVH) / A.eta_over_s;
+    const double T2 = T * T;
+    B = eos_field(A.eos, i0, w, EOS_B) * T2 * T2;
+  }
+  if (!isfinite(T) || !isfinite(u[1]) || !isfinite(u[2]) || !isfinite(B)) err |= ERR_NONFINITE;
+  if (err) atomicOr(A.err, err);
+  A.Tsite[site] = T;
+  double* o = A.sc + (size_t)site * kSc;
+  o[SC_UT] = u[0]; o[SC_UX] = u[1]; o[SC_UY] = u[2];
+  o[SC_INVT] = 1.0 / T; o[SC_MEQ] = Meq; o[SC_M] = M; o[SC_ITR] = itr; o[SC_D] = D;
+  o[SC_B] = B; o[SC_K] = pref * m[0]; o[SC_KH] = m[0]; o[SC_T] = T;
+  if (A.scf) {
+    float* of = A.scf + (size_t)site * kSc;
+#pragma unroll
+    for (int q = 0; q < kSc; ++q) of[q] = (float)o[q];
+  }
+  if (A.obs) {
+    const double hc = 0.1973269804, h3 = hc * hc * hc;
+    double* r = A.obs + (size_t)site * 8;
+    r[0] = (eps + B) / h3;
+    r[1] = T;
+    r[2] = u[0]; r[3] = u[1]; r[4] = u[2];
+    r[5] = M;
+    r[6] = (pref * m[7] - B) / h3;
+    r[7] = Meq;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -327,8 +488,8 @@ __device__ __forceinline__ void warp_sum(double (&v)[NV]) {
     for (int q = 0; q < NV; ++q) v[q] += __shfl_down_sync(0xffffffffu, v[q], off);
 }
 
-// Sum v over the block into red[0..NV) (valid after the trailing barrier
-// inside); red must hold NV * nwarps doubles.
+// Sum v over the block into red[0..NV) on thread 0 (red must hold NV * nwarps
+// doubles; the caller synchronises before other threads read red).
 template <int NV, int NT>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double* red) {
   constexpr int NW = (NT + 31) / 32;
@@ -348,16 +509,70 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* red) {
   }
 }
 
+// FP32 warp sum with a running compensation (TwoSum at every level of the
+// shuffle tree, Knuth): returns the sum as a float pair (s, c), s + c exact to
+// about the FP32 rounding of the per-lane inputs.
+template <int NV>
+__device__ __forceinline__ void warp_sum_comp(float (&s)[NV], float (&c)[NV]) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const float so = __shfl_down_sync(0xffffffffu, s[q], off);
+      const float co = __shfl_down_sync(0xffffffffu, c[q], off);
+      const float t = s[q] + so;
+      const float bp = t - s[q];
+      const float err = (s[q] - (t - bp)) + (so - bp);
+      s[q] = t;
+      c[q] += co + err;
+    }
+}
+
+// Block sum of NV per-thread values into red[0..NV) (FP64) on thread 0.  FP32
+// values go through the compensated FP32 warp tree; only the per-warp partials
+// are combined in FP64.  The caller synchronises before other threads read red.
+template <int NV, int NT, class R>
+__device__ __forceinline__ void block_reduce(const R (&v)[NV], double* red) {
+  constexpr int NW = (NT + 31) / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if constexpr (sizeof(R) == 4) {
+    float s[NV], c[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) { s[q] = v[q]; c[q] = 0.0f; }
+    warp_sum_comp<NV>(s, c);
+    if (lane == 0)
+#pragma unroll
+      for (int q = 0; q < NV; ++q) red[wid * NV + q] = (double)s[q] + (double)c[q];
+  } else {
+    double d[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) d[q] = (double)v[q];
+    warp_sum<NV>(d);
+    if (lane == 0)
+#pragma unroll
+      for (int q = 0; q < NV; ++q) red[wid * NV + q] = d[q];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double acc = red[q];
+      for (int w = 1; w < NW; ++w) acc += red[w * NV + q];
+      red[q] = acc;
+    }
+  }
+}
+
 __device__ __forceinline__ int wrap(int i, int n) {
   i %= n;
   return i < 0 ? i + n : i;
 }
 
-// Per-thread partial moments of a xi-line: {K, T00, T01, T02, T11, T12, T22}
-// (without the M^4/(2 pi^2) prefactor).
+// Per-thread partial moments of a xi-line (kMom values, no M^4/(2 pi^2)
+// prefactor), in the compute precision R.
 template <class R, int NXI, int NTH, int NPH>
 __device__ __forceinline__ void line_moments(const Ops<R, NXI, NTH, NPH>& op, const R (&f)[NXI],
-                                             int j, int l, double (&mom)[7], double* tzz) {
+                                             int j, int l, R (&mom)[kMom]) {
   R r0 = 0, r1 = 0, r2 = 0, r3 = 0;
 #pragma unroll
   for (int k = 0; k < NXI; ++k) {
@@ -366,73 +581,95 @@ __device__ __forceinline__ void line_moments(const Ops<R, NXI, NTH, NPH>& op, co
     r2 += op.w2[k] * f[k];
     r3 += op.w3[k] * f[k];
   }
-  const double wj = (double)op.wj[j], st = (double)op.sth[j];
-  const double cp = (double)op.cph[l], sp = (double)op.sph[l];
-  mom[0] = wj * (double)r0;
-  mom[1] = wj * (double)r2;
-  mom[2] = wj * (double)r1 * st * cp;
-  mom[3] = wj * (double)r1 * st * sp;
-  mom[4] = wj * (double)r3 * st * st * cp * cp;
-  mom[5] = wj * (double)r3 * st * st * cp * sp;
-  mom[6] = wj * (double)r3 * st * st * sp * sp;
-  if (tzz) {
-    const double mu = (double)op.mu[j];
-    *tzz = wj * (double)r3 * mu * mu;
-  }
+  const R wj = op.wj[j], st = op.sth[j], mu = op.mu[j];
+  const R cp = op.cph[l], sp = op.sph[l];
+  const R a1 = wj * r1 * st, a3 = wj * r3 * st * st;
+  mom[0] = wj * r0;
+  mom[1] = wj * r2;
+  mom[2] = a1 * cp;
+  mom[3] = a1 * sp;
+  mom[4] = a3 * cp * cp;
+  mom[5] = a3 * cp * sp;
+  mom[6] = a3 * sp * sp;
+  mom[7] = wj * r3 * mu * mu;
 }
 
 // ---------------------------------------------------------------------------
 // fused stream-collide stage: evaluates the kinetic right-hand side of one
-// site on f_in and writes the predictor or the trapezoid corrector.
-//   rhs = -V.grad f + (1/tau) [mu^2 Dr f + Dth f] + g Dr f + T_M f
+// site on f_in (with the site scalars of f_in's matching) and writes the
+// predictor or the trapezoid corrector, then the moments of what it wrote.
+//   rhs = -V.grad f + (1/tau) [mu^2 Dr f + Dth f] + g Dr f + T_M f_eq
 //         - ((P.U)/E) (f - f_eq) / tau_R
-//   T_M = A sin(th) (c/s) Dr f - A sin(th) mu/(c s) Dmu f + A'/(c s sin th) Dph f
+//   T_M f_eq = -(f_eq/T) [ (a.v/c)(u^tau M^2 s^2/E_eq - M v.u)
+//                          + (u^tau M^2 (a.v)/E_eq - M a.u)/c ],   a = grad ln M
+//   (node motion with the local mass and the force 1/2 d_i M^2 d^i_(p) of
+//   Eq. Bmilne, applied to the local equilibrium),
 //   g   = -D sum w (P^.U)^2 R / (K + D (4 E + Q - K))   (d ln M / d tau)
 // ---------------------------------------------------------------------------
+template <class S, class R, int NXI, int NTH, int NPH>
+struct StageArgs {
+  const S* f_in;          // populations the right-hand side is evaluated on
+  const double* lnM_in;
+  const double* sc;       // matching of f_in, kSc per site
+  const float* scf;       // FP32 copy of sc
+  const S* f_base;        // corrector: populations at the start of the step
+  const double* lnM_base;
+  S* f_out;
+  double* lnM_out;
+  double* mom_out;        // moments of f_out, kMom per site
+  int* err;
+  int nx, ny;
+  int mode;               // 0 predictor, 1 corrector
+  int metric;             // 1 Milne
+  double tau, dtau;
+  double inv2dx;
+  double Z;
+  Ops<R, NXI, NTH, NPH> op;
+};
+
 template <class S, class R, int NXI, int NTH, int NPH>
 __global__ void __launch_bounds__(NTH* NPH)
     stage_kernel(const __grid_constant__ StageArgs<S, R, NXI, NTH, NPH> A) {
   constexpr int NL = NTH * NPH;
   constexpr int NN = NL * NXI;
   constexpr int NW = (NL + 31) / 32;
-  constexpr int LINE0 = (NL > 32) ? 32 : 0;  // first thread doing polar/azimuthal lines
   const auto& op = A.op;
   const int site = blockIdx.x;
   const int t = threadIdx.x;
   const int j = t % NTH, l = t / NTH;
   const int x = site % A.nx, y = site / A.nx;
-  const int ns = A.nx * A.ny;
 
-  __shared__ R fs[NN];
-  __shared__ R pth[NN];
-  __shared__ R pph[NN];
-  __shared__ double red[8 * NW];
-  __shared__ double sc[12];
+  // populations staged k-major with a padded stride, so that both the xi-line
+  // (consecutive threads) and the polar-line accesses are bank-conflict free
+  constexpr int LD = NL + 1;
+  __shared__ R fs[NXI * LD];
+  __shared__ R pth[NXI * LD];
+  __shared__ double red[kMom * NW];
+  __shared__ double gsh;
+  __shared__ R grad[2];
 
   // 1. own xi-line and the upwind neighbours for streaming
   R f[NXI];
   load_line<S, R, NXI>(A.f_in + (size_t)site * NN + t * NXI, f);
   const R cp = op.cph[l], sp = op.sph[l];
   const int sx = (cp > (R)0) ? -1 : 1, sy = (sp > (R)0) ? -1 : 1;
-  const int sx1 = y * A.nx + wrap(x + sx, A.nx), sx2 = y * A.nx + wrap(x + 2 * sx, A.nx);
-  const int sy1 = wrap(y + sy, A.ny) * A.nx + x, sy2 = wrap(y + 2 * sy, A.ny) * A.nx + x;
+  const int xp = wrap(x + 1, A.nx), xm = wrap(x - 1, A.nx);
+  const int yp = wrap(y + 1, A.ny), ym = wrap(y - 1, A.ny);
+  const int sx1 = y * A.nx + (sx < 0 ? xm : xp), sx2 = y * A.nx + wrap(x + 2 * sx, A.nx);
+  const int sy1 = (sy < 0 ? ym : yp) * A.nx + x, sy2 = wrap(y + 2 * sy, A.ny) * A.nx + x;
   R fx1[NXI], fx2[NXI], fy1[NXI], fy2[NXI];
   load_line<S, R, NXI>(A.f_in + (size_t)sx1 * NN + t * NXI, fx1);
   load_line<S, R, NXI>(A.f_in + (size_t)sx2 * NN + t * NXI, fx2);
   load_line<S, R, NXI>(A.f_in + (size_t)sy1 * NN + t * NXI, fy1);
   load_line<S, R, NXI>(A.f_in + (size_t)sy2 * NN + t * NXI, fy2);
-  const double lnM = __ldg(A.lnM_in + site);
-  const double ax = (__ldg(A.lnM_in + y * A.nx + wrap(x + 1, A.nx)) -
-                     __ldg(A.lnM_in + y * A.nx + wrap(x - 1, A.nx))) * A.inv2dx;
-  const double ay = (__ldg(A.lnM_in + wrap(y + 1, A.ny) * A.nx + x) -
-                     __ldg(A.lnM_in + wrap(y - 1, A.ny) * A.nx + x)) * A.inv2dx;
-  (void)ns;
+  if (t == 0) {  // a = grad ln M, central differences in FP64
+    grad[0] = (R)((__ldg(A.lnM_in + y * A.nx + xp) - __ldg(A.lnM_in + y * A.nx + xm)) * A.inv2dx);
+    grad[1] = (R)((__ldg(A.lnM_in + yp * A.nx + x) - __ldg(A.lnM_in + ym * A.nx + x)) * A.inv2dx);
+  }
 
-  // 2. moments of the site
-  double mom[7];
-  line_moments<R, NXI, NTH, NPH>(op, f, j, l, mom, nullptr);
+  // 2. radial operator on the own line; stage the site for the polar operator
 #pragma unroll
-  for (int k = 0; k < NXI; ++k) fs[t * NXI + k] = f[k];
+  for (int k = 0; k < NXI; ++k) fs[k * LD + t] = f[k];
   R Drf[NXI];
 #pragma unroll
   for (int kp = 0; kp < NXI; ++kp) {
@@ -441,113 +678,82 @@ __global__ void __launch_bounds__(NTH* NPH)
     for (int k = 0; k < NXI; ++k) acc += op.Dr[kp * NXI + k] * f[k];
     Drf[kp] = acc;
   }
-  block_sum<7, NL>(mom, red);  // contains __syncthreads: fs visible after it
-
-  // 3. FP64 matching on thread 0 while the other warps do the line operators
+  __syncthreads();
   const R milne = A.metric ? (R)(1.0 / A.tau) : (R)0;
-  auto line_work = [&](int first, int stride) {
-    // polar lines (k', l'): Dth and Dmu along j
-    for (int it = t - first; it < NXI * NPH; it += stride) {
-      const int kq = it % NXI, lq = it / NXI;
-      R g[NTH];
+  for (int it = t; it < NXI * NPH; it += NL) {  // polar lines (k', l'): (1/tau) Dth along j
+    const int kq = it % NXI, lq = it / NXI;
+    R g[NTH];
 #pragma unroll
-      for (int jj = 0; jj < NTH; ++jj) g[jj] = fs[(lq * NTH + jj) * NXI + kq];
-      const R Aph = (R)ax * op.cph[lq] + (R)ay * op.sph[lq];
-      const R bcoef = -Aph * op.inv_cs[kq];
+    for (int jj = 0; jj < NTH; ++jj) g[jj] = fs[kq * LD + lq * NTH + jj];
 #pragma unroll
-      for (int jp = 0; jp < NTH; ++jp) {
-        R dth = 0, dmu = 0;
+    for (int jp = 0; jp < NTH; ++jp) {
+      R dth = 0;
 #pragma unroll
-        for (int jj = 0; jj < NTH; ++jj) {
-          dth += op.Dth[jp * NTH + jj] * g[jj];
-          dmu += op.Dmu[jp * NTH + jj] * g[jj];
-        }
-        pth[(lq * NTH + jp) * NXI + kq] = milne * dth + bcoef * op.sth_mu[jp] * dmu;
-      }
+      for (int jj = 0; jj < NTH; ++jj) dth += op.Dth[jp * NTH + jj] * g[jj];
+      pth[kq * LD + lq * NTH + jp] = milne * dth;
     }
-    // azimuthal lines (k'', j''): Dph along l
-    for (int it = t - first; it < NXI * NTH; it += stride) {
-      const int kq = it % NXI, jq = it / NXI;
-      R h[NPH];
-#pragma unroll
-      for (int ll = 0; ll < NPH; ++ll) h[ll] = fs[(ll * NTH + jq) * NXI + kq];
-      const R gcoef = op.inv_cs[kq] / op.sth[jq];
-#pragma unroll
-      for (int lp = 0; lp < NPH; ++lp) {
-        R d = 0;
-#pragma unroll
-        for (int ll = 0; ll < NPH; ++ll) d += op.Dph[lp * NPH + ll] * h[ll];
-        const R Aphp = -(R)ax * op.sph[lp] + (R)ay * op.cph[lp];
-        pph[(lp * NTH + jq) * NXI + kq] = gcoef * Aphp * d;
-      }
-    }
-  };
-  if (t == 0) {
-    SiteState ss;
-    int e = match_site(A.eos, red, lnM, A.Tsite[site], A.eta_over_s, false, &ss);
-    if (e) atomicOr(A.err, e);
-    A.Tsite[site] = ss.T;
-    sc[0] = ss.u[0]; sc[1] = ss.u[1]; sc[2] = ss.u[2];
-    sc[3] = 1.0 / ss.T;
-    sc[4] = ss.Meq;
-    sc[5] = exp(lnM);
-    sc[6] = ss.inv_tauR;
-    sc[7] = ss.D;
-    sc[8] = red[0];  // K (no prefactor)
-  }
-  if (LINE0 > 0) {
-    if (t >= LINE0) line_work(LINE0, NL - LINE0);
-  } else {
-    __syncthreads();
-    line_work(0, NL);
   }
   __syncthreads();
 
-  // 4. right-hand side on the own xi-line
-  const R ut = (R)sc[0], ux = (R)sc[1], uy = (R)sc[2], invT = (R)sc[3];
-  const R Meq = (R)sc[4], M = (R)sc[5], itr = (R)sc[6];
+  // 3. right-hand side on the own xi-line
+  R scl[kSc];
+  if constexpr (sizeof(R) == 4) {
+    const float* q = A.scf + (size_t)site * kSc;
+#pragma unroll
+    for (int i = 0; i < kSc; ++i) scl[i] = __ldg(q + i);
+  } else {
+    const double* q = A.sc + (size_t)site * kSc;
+#pragma unroll
+    for (int i = 0; i < kSc; ++i) scl[i] = __ldg(q + i);
+  }
+  const R ut = scl[SC_UT], ux = scl[SC_UX], uy = scl[SC_UY];
+  const R invT = scl[SC_INVT], Meq = scl[SC_MEQ], M = scl[SC_M], itr = scl[SC_ITR];
+  const R ax = grad[0], ay = grad[1];
   const R st = op.sth[j], mu2 = op.mu2[j];
-  const R vu = st * (cp * ux + sp * uy);               // v_perp . u_perp / sinh(xi)
-  const R Aph = (R)ax * cp + (R)ay * sp;
+  const R vu = st * (cp * ux + sp * uy);              // (v_perp . u_perp) / sinh(xi)
+  const R av1 = st * (ax * cp + ay * sp);              // (a . v) / sinh(xi)
+  const R au = ax * ux + ay * uy;
   const R ax_abs = st * (cp < 0 ? -cp : cp) * (R)A.inv2dx;
   const R ay_abs = st * (sp < 0 ? -sp : sp) * (R)A.inv2dx;
   const R wj = op.wj[j];
   const R Z = (R)A.Z;
+  const R M2 = M * M;
   R Rn[NXI];
   R sA = 0, sQ = 0, sE = 0;
 #pragma unroll
   for (int k = 0; k < NXI; ++k) {
-    const int n = t * NXI + k;
-    const R s = op.s[k], c = op.c[k];
-    const R tv = s * op.inv_c[k];  // tanh(xi)
+    const R s = op.s[k], c = op.c[k], ic = op.inv_c[k], s2 = op.s2[k];
+    const R tv = s * ic;  // tanh(xi)
     const R stream = -tv * (ax_abs * ((R)3 * f[k] - (R)4 * fx1[k] + fx2[k]) +
                             ay_abs * ((R)3 * f[k] - (R)4 * fy1[k] + fy2[k]));
-    const R radial = (milne * mu2 + Aph * st * op.c_over_s[k]) * Drf[k];
-    const R Eeq = fsqrt<R>(Meq * Meq + M * M * op.s2[k]);
+    const R Eeq = fsqrt<R>(Meq * Meq + M2 * s2);
+    const R iE = (R)1 / Eeq;
     const R PeqU = ut * Eeq - M * s * vu;
     const R feq = Z * fexp<R>(-PeqU * invT);
+    const R force = -feq * invT *
+                    (s * av1 * ic * (ut * M2 * s2 * iE - M * s * vu) + (ut * M2 * s * av1 * iE - M * au) * ic);
     const R pu = c * ut - s * vu;
-    const R coll = -(pu * op.inv_c[k]) * (f[k] - feq) * itr;
-    const R r = stream + radial + pth[n] + pph[n] + coll;
+    const R coll = -(pu * ic) * (f[k] - feq) * itr;
+    const R r = stream + milne * mu2 * Drf[k] + pth[k * LD + t] + force + coll;
     Rn[k] = r;
     const R wpu2 = wj * op.ecw[k] * pu * pu;
     sA += wpu2 * r;
     sQ += wpu2 * Drf[k];
     sE += wpu2 * f[k];
   }
-  double v3[3] = {(double)sA, (double)sQ, (double)sE};
-  __syncthreads();  // red reuse
-  block_sum<3, NL>(v3, red);
+  const R v3[3] = {sA, sQ, sE};
+  block_reduce<3, NL, R>(v3, red);
   if (t == 0) {
-    const double D = sc[7], K = sc[8];
-    const double g = -D * red[0] / (K + D * (4.0 * red[2] + red[1] - K));
+    const double* scs = A.sc + (size_t)site * kSc;
+    const double D = __ldg(scs + SC_D), Kh = __ldg(scs + SC_KH);
+    const double g = (D == 0.0) ? 0.0 : -D * red[0] / (Kh + D * (4.0 * red[2] + red[1] - Kh));
     if (!isfinite(g)) atomicOr(A.err, (int)ERR_NONFINITE);
-    sc[9] = g;
-    const double dt = A.dtau;
-    A.lnM_out[site] = A.mode == 0 ? lnM + dt * g : 0.5 * (__ldg(A.lnM_base + site) + lnM + dt * g);
+    gsh = g;
+    const double lnM = __ldg(A.lnM_in + site);
+    A.lnM_out[site] = A.mode == 0 ? lnM + A.dtau * g : 0.5 * (__ldg(A.lnM_base + site) + lnM + A.dtau * g);
   }
   __syncthreads();
-  const R g = (R)sc[9];
+  const R g = (R)gsh;
   const R dt = (R)A.dtau;
   R out[NXI];
   if (A.mode == 0) {
@@ -559,11 +765,21 @@ __global__ void __launch_bounds__(NTH* NPH)
 #pragma unroll
     for (int k = 0; k < NXI; ++k) out[k] = (R)0.5 * (fb[k] + f[k] + dt * (Rn[k] + g * Drf[k]));
   }
+  // the moments describe exactly what is stored (after rounding to S)
+#pragma unroll
+  for (int k = 0; k < NXI; ++k) out[k] = ld1<S, R>(st1<S, R>(out[k]));
   store_line<S, R, NXI>(A.f_out + (size_t)site * NN + t * NXI, out);
+  R mom[kMom];
+  line_moments<R, NXI, NTH, NPH>(op, out, j, l, mom);
+  block_reduce<kMom, NL, R>(mom, red);
+  if (t == 0)
+#pragma unroll
+    for (int q = 0; q < kMom; ++q) A.mom_out[(size_t)site * kMom + q] = red[q];
 }
 
 // ---------------------------------------------------------------------------
-// initial condition and observables
+// initial condition: local equilibrium at rest with energy density eps0
+// (eps_EOS(T) = eps0, M = M(T), f = Z exp(-E/T)), and its moments
 // ---------------------------------------------------------------------------
 template <class S, class R, int NXI, int NTH, int NPH>
 struct InitArgs {
@@ -572,6 +788,7 @@ struct InitArgs {
   S* f;
   double* lnM;
   double* Tsite;
+  double* mom;
   int* err;
   EosView eos;
   double Z;
@@ -585,20 +802,23 @@ __global__ void __launch_bounds__(NTH* NPH)
     init_kernel(const __grid_constant__ InitArgs<S, R, NXI, NTH, NPH> A) {
   constexpr int NL = NTH * NPH;
   constexpr int NN = NL * NXI;
+  constexpr int NW = (NL + 31) / 32;
   const int site = blockIdx.x, t = threadIdx.x;
+  const int j = t % NTH, l = t / NTH;
   __shared__ double sc[3];
+  __shared__ double red[kMom * NW];
   if (t == 0) {
-    double y = 0.0, target = log(__ldg(A.eps0 + site) * A.eps_scale);
-    if (!eos_invert(A.eos, 5, target, log(0.3), &y)) {
+    double y = 0.0;
+    if (!eos_invert(A.eos, EOS_EPS, __ldg(A.eps0 + site) * A.eps_scale, log(0.3), &y)) {
       atomicOr(A.err, (int)ERR_EOS);
       y = log(0.3);
     }
     int i0;
-    double tt, w[6], dw[6];
+    double tt, w[6];
     eos_cell(A.eos, y, &i0, &tt);
-    lagrange6(tt, w, dw);
+    lagrange6(tt, w);
     const double T = exp(y);
-    const double Meq = eos_field(A.eos, i0, w, 1) * T;
+    const double Meq = eos_field(A.eos, i0, w, EOS_X) * T;
     const double M = A.family == 1 ? A.T0 : Meq;
     A.Tsite[site] = T;
     A.lnM[site] = log(M);
@@ -610,59 +830,15 @@ __global__ void __launch_bounds__(NTH* NPH)
 #pragma unroll
   for (int k = 0; k < NXI; ++k) {
     const double s = (double)A.op.s[k];
-    out[k] = (R)(A.Z * exp(-sqrt(Meq * Meq + M * M * s * s) / T));
+    out[k] = ld1<S, R>(st1<S, R>((R)(A.Z * exp(-sqrt(Meq * Meq + M * M * s * s) / T))));
   }
   store_line<S, R, NXI>(A.f + (size_t)site * NN + t * NXI, out);
-}
-
-template <class S, class R, int NXI, int NTH, int NPH>
-struct MomArgs {
-  const S* f;
-  const double* lnM;
-  const double* Tsite;
-  double* out;  // 8 per site
-  int* err;
-  EosView eos;
-  double eta_over_s;
-  Ops<R, NXI, NTH, NPH> op;
-};
-
-template <class S, class R, int NXI, int NTH, int NPH>
-__global__ void __launch_bounds__(NTH* NPH)
-    moments_kernel(const __grid_constant__ MomArgs<S, R, NXI, NTH, NPH> A) {
-  constexpr int NL = NTH * NPH;
-  constexpr int NN = NL * NXI;
-  constexpr int NW = (NL + 31) / 32;
-  __shared__ double red[8 * NW];
-  const int site = blockIdx.x, t = threadIdx.x;
-  const int j = t % NTH, l = t / NTH;
-  R f[NXI];
-  load_line<S, R, NXI>(A.f + (size_t)site * NN + t * NXI, f);
-  double mom[8], tzz;
-  double m7[7];
-  line_moments<R, NXI, NTH, NPH>(A.op, f, j, l, m7, &tzz);
+  R mom[kMom];
+  line_moments<R, NXI, NTH, NPH>(A.op, out, j, l, mom);
+  block_reduce<kMom, NL, R>(mom, red);
+  if (t == 0)
 #pragma unroll
-  for (int q = 0; q < 7; ++q) mom[q] = m7[q];
-  mom[7] = tzz;
-  block_sum<8, NL>(mom, red);
-  if (t == 0) {
-    const double lnM = A.lnM[site];
-    SiteState ss;
-    int e = match_site(A.eos, red, lnM, A.Tsite[site], A.eta_over_s, true, &ss);
-    if (e) atomicOr(A.err, e);
-    const double M = exp(lnM);
-    const double pref = M * M * M * M * (1.0 / (2.0 * 3.14159265358979323846 * 3.14159265358979323846));
-    const double hc = 0.1973269804, h3 = hc * hc * hc;
-    double* o = A.out + (size_t)site * 8;
-    o[0] = (ss.eps_kin + ss.B) / h3;
-    o[1] = ss.T;
-    o[2] = ss.u[0];
-    o[3] = ss.u[1];
-    o[4] = ss.u[2];
-    o[5] = M;
-    o[6] = (pref * red[7] - ss.B) / h3;
-    o[7] = ss.Meq;
-  }
+    for (int q = 0; q < kMom; ++q) A.mom[(size_t)site * kMom + q] = red[q];
 }
 
 }  // namespace rlbk

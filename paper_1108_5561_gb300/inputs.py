@@ -3,10 +3,11 @@ Boltzmann runs.  Holds no arithmetic of the method: it only draws hotspot
 positions and amplitudes and sums Gaussians on the grid.
 
 Recipe (both the CUDA path and the oracle receive these arrays):
-  - smooth:  eps = eps0 exp(-r^2 / (2 sigma^2)) + floor, r from the grid centre
+  - smooth:  eps = eps0 exp(-r^2 / (2 sigma^2)) + floor, r from the grid centre,
+    floor = 0.005 GeV/fm^3 (about eps(T = 0.1 GeV) for the crossover EOS)
   - hotspots: n Gaussians of width 0.4 fm, amplitudes ~ Exp(mean 20 GeV/fm^3),
-    centres ~ N(0, 3 fm) per coordinate, plus floor
-  - floor = 0.005 GeV/fm^3 (about eps(T = 0.1 GeV) for the crossover EOS)
+    centres ~ N(0, 3 fm) per coordinate, on a uniform background of
+    10 GeV/fm^3 (T about 0.3 GeV), sampled on a 0.1 fm grid
 Random numbers come from splitmix64 with a Box-Muller transform so the draws
 are identical on every machine.
 """
@@ -17,6 +18,7 @@ import math
 import numpy as np
 
 EPS_FLOOR = 0.005
+HOTSPOT_BACKGROUND = 10.0
 MASK = (1 << 64) - 1
 
 
@@ -54,8 +56,8 @@ def smooth_gaussian(nx: int, ny: int, dx: float = 0.2, eps0: float = 30.0, sigma
     return eps0 * np.exp(-(X * X + Y * Y) / (2 * sigma * sigma)) + floor
 
 
-def hotspots(nx: int, ny: int, dx: float = 0.2, n: int = 40, seed: int = 1108, width: float = 0.4,
-             mean_amp: float = 20.0, spread: float = 3.0, floor: float = EPS_FLOOR):
+def hotspots(nx: int, ny: int, dx: float = 0.1, n: int = 40, seed: int = 1108, width: float = 0.4,
+             mean_amp: float = 20.0, spread: float = 3.0, floor: float = HOTSPOT_BACKGROUND):
     """Returns (eps, amplitudes, centres)."""
     rng = SplitMix64(seed)
     amps = np.array([rng.exponential(mean_amp) for _ in range(n)])

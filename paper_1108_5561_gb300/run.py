@@ -177,6 +177,16 @@ class Run:
     def lnM(self):
         return self.state[self._m_off:self._m_off + 8 * self.ns].view(self.torch.float64)
 
+    def set_timing(self, enable: bool = True):
+        self._chk(self.lib.rlb_set_timing(self._h, int(enable)), "rlb_set_timing")
+
+    def timing(self):
+        """(stage ms, stage launches, match ms, match launches) since timing was enabled."""
+        a, b, c, d = ctypes.c_double(), ctypes.c_long(), ctypes.c_double(), ctypes.c_long()
+        self._chk(self.lib.rlb_get_timing(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                          ctypes.byref(d)), "rlb_get_timing")
+        return a.value, b.value, c.value, d.value
+
     def lattice(self):
         g = self.grid
         n1, n2, n3 = g.n_xi, g.n_theta, 2 * g.n_phi_half

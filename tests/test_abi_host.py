@@ -58,9 +58,8 @@ def test_lattice_and_operators_match_oracle(lib, oracle_mod, shape, z0, fam):
     mu, wt = np.zeros(nth), np.zeros(nth)
     cp, sp = np.zeros(2 * nph), np.zeros(2 * nph)
     assert lib.rlb_lattice(h, dp(c), dp(s), dp(w), dp(mu), dp(wt), dp(cp), dp(sp)) == 0
-    Dr, Dth, Dmu, Dph = (np.zeros((nxi, nxi)), np.zeros((nth, nth)), np.zeros((nth, nth)),
-                         np.zeros((2 * nph, 2 * nph)))
-    assert lib.rlb_operators(h, dp(Dr), dp(Dth), dp(Dmu), dp(Dph)) == 0
+    Dr, Dth = np.zeros((nxi, nxi)), np.zeros((nth, nth))
+    assert lib.rlb_operators(h, dp(Dr), dp(Dth)) == 0
     lib.rlb_destroy(h)
     o = oracle_mod.Oracle(nx=1, ny=1, n_xi=nxi, n_theta=nth, n_phi_half=nph, z0=z0, family=fam,
                           eos_kind=2 if fam else 0)
@@ -75,8 +74,6 @@ def test_lattice_and_operators_match_oracle(lib, oracle_mod, shape, z0, fam):
     scale = lambda A: max(np.abs(A).max(), 1.0)
     assert np.allclose(Dr, ops["Dr"], rtol=0, atol=1e-12 * scale(Dr))
     assert np.allclose(Dth, ops["Dth"], rtol=0, atol=1e-13 * scale(Dth))
-    assert np.allclose(Dmu, ops["Dmu"], rtol=0, atol=1e-13 * scale(Dmu))
-    assert np.allclose(Dph, ops["Dph"], rtol=0, atol=1e-13 * scale(Dph))
 
 
 def test_invalid_arguments_are_rejected(lib):

@@ -155,30 +155,6 @@ def test_galerkin_integration_by_parts(oracle_mod, fam):
         assert lhs == pytest.approx(rhs, abs=1e-13 * scale)
 
 
-def test_mu_collocation_derivative(oracle_mod):
-    o = oracle_mod.Oracle(nx=1, ny=1, n_theta=8)
-    mu = o.nodes()["mu"]
-    D = o.operators()["Dmu"]
-    for deg in range(8):
-        assert np.allclose(D @ mu ** deg, deg * mu ** max(deg - 1, 0) * (deg > 0), atol=1e-12)
-
-
-def test_phi_collocation_derivative(oracle_mod):
-    o = oracle_mod.Oracle(nx=1, ny=1, n_phi_half=6)
-    L = 12
-    phi = np.arange(L) * math.pi / 6
-    D = o.operators()["Dph"]
-    for k in range(6):
-        assert np.allclose(D @ np.cos(k * phi), -k * np.sin(k * phi), atol=1e-13)
-        assert np.allclose(D @ np.sin(k * phi), k * np.cos(k * phi), atol=1e-13)
-    # closed form of the Fourier differentiation matrix for an even number of nodes
-    i, l = np.meshgrid(np.arange(L), np.arange(L), indexing="ij")
-    d = i - l
-    with np.errstate(divide="ignore"):
-        ref = np.where(d == 0, 0.0, 0.5 * (-1.0) ** d / np.tan(d * math.pi / L))
-    assert np.allclose(D, ref, atol=1e-13)
-
-
 def _landau_case(rng):
     # T = Lambda diag(eps, p1, p2, p3) Lambda^T (anisotropic, boosted in x-y)
     eps = 2.0 + rng.random()
