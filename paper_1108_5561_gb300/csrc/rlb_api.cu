@@ -125,6 +125,8 @@ rlbk::EosView eos_view(const rlb_ctx* c) {
 
 enum Kind { K_STAGE = 0, K_MATCH = 1, K_INIT = 2 };
 
+dim3 grid2d(const rlb_ctx* c) { return dim3((unsigned)c->gp.nx, (unsigned)c->gp.ny, 1); }
+
 // Event bracket around one launch when timing is enabled.
 struct Timed {
   rlb_ctx* c;
@@ -157,6 +159,10 @@ struct Timed {
 rlb_status match(rlb_ctx* ctx, const double* mom, const double* lnM, double* obs, cudaStream_t st) {
   rlbk::MatchArgs a;
   a.mom = mom;
+  a.momf = reinterpret_cast<const float*>(mom);  // FP32 storage keeps (hi, lo) float pairs here
+  a.inv2dx = 1.0 / (2.0 * ctx->gp.dx);
+  a.nx = ctx->gp.nx;
+  a.ny = ctx->gp.ny;
   a.lnM = lnM;
   a.Tsite = reinterpret_cast<double*>(ctx->scratch + ctx->T_off);
   a.sc = reinterpret_cast<double*>(ctx->scratch + ctx->sc_off);
@@ -188,6 +194,7 @@ struct Runner {
     a.lnM = reinterpret_cast<double*>(ctx->state + ctx->lnM_off);
     a.Tsite = reinterpret_cast<double*>(ctx->scratch + ctx->T_off);
     a.mom = reinterpret_cast<double*>(ctx->scratch + ctx->mom_off);
+    a.momf = reinterpret_cast<float*>(ctx->scratch + ctx->mom_off);
     a.err = reinterpret_cast<int*>(ctx->scratch + ctx->err_off);
     a.eos = eos_view(ctx);
     a.Z = ctx->eosp.Z;
@@ -216,30 +223,35 @@ struct Runner {
     a.err = reinterpret_cast<int*>(ctx->scratch + ctx->err_off);
     a.nx = ctx->gp.nx;
     a.ny = ctx->gp.ny;
-    a.metric = ctx->gp.metric;
     a.dtau = ctx->gp.dtau;
     a.inv2dx = 1.0 / (2.0 * ctx->gp.dx);
-    a.Z = ctx->eosp.Z;
+    a.dtau_r = (R)a.dtau;
+    a.inv2dx_r = (R)a.inv2dx;
+    a.Z = (R)ctx->eosp.Z;
     a.op = make_ops<R, NXI, NTH, NPH>(ctx->lat);
     for (int s = 0; s < nsteps; ++s) {
       // predictor: f* = f + dtau RHS(f) at tau
       rlb_status r = match(ctx, mom, m, nullptr, st);
       if (r) return r;
       a.f_in = f; a.lnM_in = m; a.f_base = f; a.lnM_base = m;
-      a.f_out = fs; a.lnM_out = ms; a.mom_out = moms; a.mode = 0; a.tau = ctx->tau;
+      a.f_out = fs; a.lnM_out = ms; a.mom_out = moms; a.momf_out = reinterpret_cast<float*>(moms);
+      a.mode = 0;
+      a.milne = ctx->gp.metric ? (R)(1.0 / ctx->tau) : (R)0;
       {
         Timed tm(ctx, K_STAGE, st);
-        rlbk::stage_kernel<S, R, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
+        rlbk::stage_kernel<S, R, NXI, NTH, NPH><<<grid2d(ctx), NL, 0, st>>>(a);
       }
       RLB_CUDA(cudaGetLastError(), "stage_kernel (predictor) launch");
       // corrector: f = (f + f* + dtau RHS(f*))/2 at tau + dtau, in place over f
       r = match(ctx, moms, ms, nullptr, st);
       if (r) return r;
       a.f_in = fs; a.lnM_in = ms; a.f_base = f; a.lnM_base = m;
-      a.f_out = f; a.lnM_out = m; a.mom_out = mom; a.mode = 1; a.tau = ctx->tau + ctx->gp.dtau;
+      a.f_out = f; a.lnM_out = m; a.mom_out = mom; a.momf_out = reinterpret_cast<float*>(mom);
+      a.mode = 1;
+      a.milne = ctx->gp.metric ? (R)(1.0 / (ctx->tau + ctx->gp.dtau)) : (R)0;
       {
         Timed tm(ctx, K_STAGE, st);
-        rlbk::stage_kernel<S, R, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
+        rlbk::stage_kernel<S, R, NXI, NTH, NPH><<<grid2d(ctx), NL, 0, st>>>(a);
       }
       RLB_CUDA(cudaGetLastError(), "stage_kernel (corrector) launch");
       ctx->tau += ctx->gp.dtau;
@@ -346,7 +358,8 @@ rlb_status rlb_configure(rlb_ctx* ctx, const rlb_grid_params* g) {
     return fail(ctx, RLB_ERR_ARG, "the Laguerre radial family needs the conformal EOS");
   if (g->family == RLB_RADIAL_LAGUERRE && !(g->T0 > 0))
     return fail(ctx, RLB_ERR_ARG, "T0 must be positive");
-  if ((size_t)g->nx * g->ny > 0x7fffffffu) return fail(ctx, RLB_ERR_ARG, "grid too large");
+  if ((size_t)g->nx * g->ny > 0x7fffffffu || g->ny > 65535)
+    return fail(ctx, RLB_ERR_ARG, "grid too large (ny <= 65535, nx * ny < 2^31)");
   std::string m = rlb::build_lattice(g->family, g->n_xi, g->n_theta, g->n_phi_half, g->z0, &ctx->lat);
   if (!m.empty()) return fail(ctx, RLB_ERR_ARG, m);
   ctx->gp = *g;

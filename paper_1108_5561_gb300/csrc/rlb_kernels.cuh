@@ -384,13 +384,15 @@ __device__ bool landau3(const double tm[6], double u[3], double* eps) {
 //   K^ = sum w f, T00, T01, T02, T11, T12, T22 (sum w f P^ P^), Tzz
 constexpr int kMom = 8;
 // per-site matching results consumed by the stage kernel
-constexpr int kSc = 12;
+constexpr int kSc = 14;
 enum : int {
-  SC_UT = 0, SC_UX, SC_UY, SC_INVT, SC_MEQ, SC_M, SC_ITR, SC_D, SC_B, SC_K, SC_KH, SC_T
+  SC_UT = 0, SC_UX, SC_UY, SC_INVT, SC_MEQ, SC_M, SC_ITR, SC_D, SC_B, SC_K, SC_KH, SC_T,
+  SC_AX, SC_AY  // grad ln M (central differences, 1/fm)
 };
 
 struct MatchArgs {
-  const double* mom;    // kMom per site
+  const double* mom;    // kMom per site (FP64 storage)
+  const float* momf;    // 2 kMom per site, (hi, lo) pairs (FP32 storage)
   const double* lnM;
   double* Tsite;        // Newton start in, T out
   double* sc;           // kSc per site
@@ -399,7 +401,8 @@ struct MatchArgs {
   int* err;
   EosView eos;
   double eta_over_s;
-  int ns;
+  double inv2dx;
+  int nx, ny, ns;
 };
 
 // Matching of every site (FP64, one thread per site): Landau (u, eps_kin),
@@ -409,7 +412,16 @@ template <bool FAST>
 __global__ void __launch_bounds__(128) match_kernel(const MatchArgs A) {
   const int site = blockIdx.x * blockDim.x + threadIdx.x;
   if (site >= A.ns) return;
-  const double* m = A.mom + (size_t)site * kMom;
+  double m[kMom];
+  if constexpr (FAST) {
+    const float* q = A.momf + (size_t)site * 2 * kMom;
+#pragma unroll
+    for (int i = 0; i < kMom; ++i) m[i] = (double)q[2 * i] + (double)q[2 * i + 1];
+  } else {
+    const double* q = A.mom + (size_t)site * kMom;
+#pragma unroll
+    for (int i = 0; i < kMom; ++i) m[i] = q[i];
+  }
   const double lnM = A.lnM[site];
   const double M = exp(lnM);
   const double pref = M * M * M * M * (1.0 / (2.0 * 3.14159265358979323846 * 3.14159265358979323846));
@@ -460,6 +472,13 @@ __global__ void __launch_bounds__(128) match_kernel(const MatchArgs A) {
   o[SC_UT] = u[0]; o[SC_UX] = u[1]; o[SC_UY] = u[2];
   o[SC_INVT] = 1.0 / T; o[SC_MEQ] = Meq; o[SC_M] = M; o[SC_ITR] = itr; o[SC_D] = D;
   o[SC_B] = B; o[SC_K] = pref * m[0]; o[SC_KH] = m[0]; o[SC_T] = T;
+  {
+    const int x = site % A.nx, y = site / A.nx;
+    const int xp = x + 1 == A.nx ? 0 : x + 1, xm = x == 0 ? A.nx - 1 : x - 1;
+    const int yp = y + 1 == A.ny ? 0 : y + 1, ym = y == 0 ? A.ny - 1 : y - 1;
+    o[SC_AX] = (A.lnM[y * A.nx + xp] - A.lnM[y * A.nx + xm]) * A.inv2dx;
+    o[SC_AY] = (A.lnM[yp * A.nx + x] - A.lnM[ym * A.nx + x]) * A.inv2dx;
+  }
   if (A.scf) {
     float* of = A.scf + (size_t)site * kSc;
 #pragma unroll
@@ -488,61 +507,69 @@ __device__ __forceinline__ void warp_sum(double (&v)[NV]) {
     for (int q = 0; q < NV; ++q) v[q] += __shfl_down_sync(0xffffffffu, v[q], off);
 }
 
-// Sum v over the block into red[0..NV) on thread 0 (red must hold NV * nwarps
-// doubles; the caller synchronises before other threads read red).
-template <int NV, int NT>
-__device__ __forceinline__ void block_sum(double (&v)[NV], double* red) {
-  constexpr int NW = (NT + 31) / 32;
-  warp_sum<NV>(v);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0)
+
+// Warp sums of NV values (NV a power of two <= 32) by recursive halving: each
+// exchange level hands half of the remaining values to the partner lane, so 8
+// values take 9 shuffles instead of 40.  On return v[0] of lane l holds the
+// warp sum of value (l >> (5 - log2 NV)).
+template <int NV>
+__device__ __forceinline__ void warp_reduce_halving(float (&v)[NV], int lane) {
+  constexpr int L = NV >= 32 ? 5 : NV >= 16 ? 4 : NV >= 8 ? 3 : NV >= 4 ? 2 : NV >= 2 ? 1 : 0;
+  static_assert((1 << L) == NV, "power of two");
 #pragma unroll
-    for (int q = 0; q < NV; ++q) red[wid * NV + q] = v[q];
-  __syncthreads();
-  if (threadIdx.x == 0) {
+  for (int lev = 0; lev < L; ++lev) {
+    const int h = NV >> (lev + 1), off = 16 >> lev;
+    const bool upper = (lane & off) != 0;
 #pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      double s = red[q];
-      for (int w = 1; w < NW; ++w) s += red[w * NV + q];
-      red[q] = s;
+    for (int q = 0; q < h; ++q) {
+      const float keep = upper ? v[q + h] : v[q];
+      const float send = upper ? v[q] : v[q + h];
+      v[q] = keep + __shfl_xor_sync(0xffffffffu, send, off);
     }
   }
+#pragma unroll
+  for (int off = 16 >> L; off > 0; off >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
 }
 
-// FP32 warp sum with a running compensation (TwoSum at every level of the
-// shuffle tree, Knuth): returns the sum as a float pair (s, c), s + c exact to
-// about the FP32 rounding of the per-lane inputs.
-template <int NV>
-__device__ __forceinline__ void warp_sum_comp(float (&s)[NV], float (&c)[NV]) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      const float so = __shfl_down_sync(0xffffffffu, s[q], off);
-      const float co = __shfl_down_sync(0xffffffffu, c[q], off);
-      const float t = s[q] + so;
-      const float bp = t - s[q];
-      const float err = (s[q] - (t - bp)) + (so - bp);
-      s[q] = t;
-      c[q] += co + err;
-    }
-}
-
-// Block sum of NV per-thread values into red[0..NV) (FP64) on thread 0.  FP32
-// values go through the compensated FP32 warp tree; only the per-warp partials
-// are combined in FP64.  The caller synchronises before other threads read red.
+// Block sum of NV per-thread values on thread 0.  FP32: compensated FP32 warp
+// trees, then the per-warp (s, c) pairs combined with TwoSum by thread 0; the
+// result is left in redf[2q] + redf[2q+1].  FP64: plain warp trees, result in
+// redd[q].  The caller synchronises before other threads read the result.
 template <int NV, int NT, class R>
-__device__ __forceinline__ void block_reduce(const R (&v)[NV], double* red) {
+__device__ __forceinline__ void block_reduce(const R (&v)[NV], float* redf, double* redd) {
   constexpr int NW = (NT + 31) / 32;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if constexpr (sizeof(R) == 4) {
-    float s[NV], c[NV];
+    // pairwise sums inside each warp (recursive halving over the NV values,
+    // padded to a power of two); the warp partials are combined with TwoSum so
+    // the block total keeps a compensation term
+    constexpr int NP = NV <= 1 ? 1 : NV <= 2 ? 2 : NV <= 4 ? 4 : NV <= 8 ? 8 : 16;
+    constexpr int L = NP == 1 ? 0 : NP == 2 ? 1 : NP == 4 ? 2 : NP == 8 ? 3 : 4;
+    float s[NP];
 #pragma unroll
-    for (int q = 0; q < NV; ++q) { s[q] = v[q]; c[q] = 0.0f; }
-    warp_sum_comp<NV>(s, c);
-    if (lane == 0)
+    for (int q = 0; q < NP; ++q) s[q] = q < NV ? (float)v[q] : 0.0f;
+    warp_reduce_halving<NP>(s, lane);
+    const int q = lane >> (5 - L);
+    if ((lane & ((1 << (5 - L)) - 1)) == 0 && q < NV) {
+      redf[(wid * NV + q) * 2] = s[0];
+      redf[(wid * NV + q) * 2 + 1] = 0.0f;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
 #pragma unroll
-      for (int q = 0; q < NV; ++q) red[wid * NV + q] = (double)s[q] + (double)c[q];
+      for (int q = 0; q < NV; ++q) {
+        float a = redf[2 * q], ca = redf[2 * q + 1];
+        for (int w = 1; w < NW; ++w) {
+          const float b = redf[(w * NV + q) * 2], cb = redf[(w * NV + q) * 2 + 1];
+          const float t = a + b, bp = t - a;
+          ca += cb + ((a - (t - bp)) + (b - bp));
+          a = t;
+        }
+        const float t = a + ca;  // renormalise the pair
+        redf[2 * q + 1] = ca - (t - a);
+        redf[2 * q] = t;
+      }
+    }
   } else {
     double d[NV];
 #pragma unroll
@@ -550,15 +577,15 @@ __device__ __forceinline__ void block_reduce(const R (&v)[NV], double* red) {
     warp_sum<NV>(d);
     if (lane == 0)
 #pragma unroll
-      for (int q = 0; q < NV; ++q) red[wid * NV + q] = d[q];
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
+      for (int q = 0; q < NV; ++q) redd[wid * NV + q] = d[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
 #pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      double acc = red[q];
-      for (int w = 1; w < NW; ++w) acc += red[w * NV + q];
-      red[q] = acc;
+      for (int q = 0; q < NV; ++q) {
+        double acc = redd[q];
+        for (int w = 1; w < NW; ++w) acc += redd[w * NV + q];
+        redd[q] = acc;
+      }
     }
   }
 }
@@ -616,14 +643,14 @@ struct StageArgs {
   const double* lnM_base;
   S* f_out;
   double* lnM_out;
-  double* mom_out;        // moments of f_out, kMom per site
+  double* mom_out;        // moments of f_out, kMom per site (FP64 storage)
+  float* momf_out;        // moments of f_out, (hi, lo) pairs (FP32 storage)
   int* err;
   int nx, ny;
   int mode;               // 0 predictor, 1 corrector
-  int metric;             // 1 Milne
-  double tau, dtau;
-  double inv2dx;
-  double Z;
+  double dtau, inv2dx;    // FP64 copies for the per-site (thread 0) arithmetic
+  R milne;                // 1/tau in the Milne metric, 0 in Minkowski
+  R dtau_r, inv2dx_r, Z;  // the same constants in the compute precision
   Ops<R, NXI, NTH, NPH> op;
 };
 
@@ -634,40 +661,62 @@ __global__ void __launch_bounds__(NTH* NPH)
   constexpr int NN = NL * NXI;
   constexpr int NW = (NL + 31) / 32;
   const auto& op = A.op;
-  const int site = blockIdx.x;
+  const int x = blockIdx.x, y = blockIdx.y;
+  const int site = y * A.nx + x;
   const int t = threadIdx.x;
   const int j = t % NTH, l = t / NTH;
-  const int x = site % A.nx, y = site / A.nx;
 
   // populations staged k-major with a padded stride, so that both the xi-line
   // (consecutive threads) and the polar-line accesses are bank-conflict free
   constexpr int LD = NL + 1;
   __shared__ R fs[NXI * LD];
   __shared__ R pth[NXI * LD];
-  __shared__ double red[kMom * NW];
-  __shared__ double gsh;
-  __shared__ R grad[2];
+  __shared__ double redd[kMom * NW];
+  __shared__ float redf[2 * kMom * NW];
+  __shared__ R gsh;
+  __shared__ R Etab[NXI], iEtab[NXI];
 
   // 1. own xi-line and the upwind neighbours for streaming
   R f[NXI];
   load_line<S, R, NXI>(A.f_in + (size_t)site * NN + t * NXI, f);
   const R cp = op.cph[l], sp = op.sph[l];
+  // upwind neighbours (periodic): x -/+ 1, 2 when cos(phi) >/<= 0, likewise y
   const int sx = (cp > (R)0) ? -1 : 1, sy = (sp > (R)0) ? -1 : 1;
-  const int xp = wrap(x + 1, A.nx), xm = wrap(x - 1, A.nx);
-  const int yp = wrap(y + 1, A.ny), ym = wrap(y - 1, A.ny);
-  const int sx1 = y * A.nx + (sx < 0 ? xm : xp), sx2 = y * A.nx + wrap(x + 2 * sx, A.nx);
-  const int sy1 = (sy < 0 ? ym : yp) * A.nx + x, sy2 = wrap(y + 2 * sy, A.ny) * A.nx + x;
+  int x1 = x + sx, x2 = x + 2 * sx, y1 = y + sy, y2 = y + 2 * sy;
+  x1 += (x1 < 0) ? A.nx : (x1 >= A.nx ? -A.nx : 0);
+  x2 += (x2 < 0) ? A.nx : (x2 >= A.nx ? -A.nx : 0);
+  x2 += (x2 < 0) ? A.nx : (x2 >= A.nx ? -A.nx : 0);  // grids of one site
+  y1 += (y1 < 0) ? A.ny : (y1 >= A.ny ? -A.ny : 0);
+  y2 += (y2 < 0) ? A.ny : (y2 >= A.ny ? -A.ny : 0);
+  y2 += (y2 < 0) ? A.ny : (y2 >= A.ny ? -A.ny : 0);
+  const int sx1 = y * A.nx + x1, sx2 = y * A.nx + x2;
+  const int sy1 = y1 * A.nx + x, sy2 = y2 * A.nx + x;
   R fx1[NXI], fx2[NXI], fy1[NXI], fy2[NXI];
   load_line<S, R, NXI>(A.f_in + (size_t)sx1 * NN + t * NXI, fx1);
   load_line<S, R, NXI>(A.f_in + (size_t)sx2 * NN + t * NXI, fx2);
   load_line<S, R, NXI>(A.f_in + (size_t)sy1 * NN + t * NXI, fy1);
   load_line<S, R, NXI>(A.f_in + (size_t)sy2 * NN + t * NXI, fy2);
-  if (t == 0) {  // a = grad ln M, central differences in FP64
-    grad[0] = (R)((__ldg(A.lnM_in + y * A.nx + xp) - __ldg(A.lnM_in + y * A.nx + xm)) * A.inv2dx);
-    grad[1] = (R)((__ldg(A.lnM_in + yp * A.nx + x) - __ldg(A.lnM_in + ym * A.nx + x)) * A.inv2dx);
-  }
 
-  // 2. radial operator on the own line; stage the site for the polar operator
+  // 2. radial operator on the own line; stage the site for the polar operator;
+  //    per-site radial tables E_eq(k) = sqrt(M_eq^2 + M^2 sinh^2 xi_k) and 1/E_eq
+  R scl[kSc];
+  if constexpr (sizeof(R) == 4) {
+    const float* q = A.scf + (size_t)site * kSc;
+#pragma unroll
+    for (int i = 0; i < kSc; ++i) scl[i] = __ldg(q + i);
+  } else {
+    const double* q = A.sc + (size_t)site * kSc;
+#pragma unroll
+    for (int i = 0; i < kSc; ++i) scl[i] = __ldg(q + i);
+  }
+  const R ut = scl[SC_UT], ux = scl[SC_UX], uy = scl[SC_UY];
+  const R invT = scl[SC_INVT], Meq = scl[SC_MEQ], M = scl[SC_M], itr = scl[SC_ITR];
+  const R M2 = M * M;
+  if (t < NXI) {
+    const R e = fsqrt<R>(Meq * Meq + M2 * op.s2[t]);
+    Etab[t] = e;
+    iEtab[t] = (R)1 / e;
+  }
 #pragma unroll
   for (int k = 0; k < NXI; ++k) fs[k * LD + t] = f[k];
   R Drf[NXI];
@@ -679,7 +728,7 @@ __global__ void __launch_bounds__(NTH* NPH)
     Drf[kp] = acc;
   }
   __syncthreads();
-  const R milne = A.metric ? (R)(1.0 / A.tau) : (R)0;
+  const R milne = A.milne;
   for (int it = t; it < NXI * NPH; it += NL) {  // polar lines (k', l'): (1/tau) Dth along j
     const int kq = it % NXI, lq = it / NXI;
     R g[NTH];
@@ -695,66 +744,69 @@ __global__ void __launch_bounds__(NTH* NPH)
   }
   __syncthreads();
 
-  // 3. right-hand side on the own xi-line
-  R scl[kSc];
-  if constexpr (sizeof(R) == 4) {
-    const float* q = A.scf + (size_t)site * kSc;
-#pragma unroll
-    for (int i = 0; i < kSc; ++i) scl[i] = __ldg(q + i);
-  } else {
-    const double* q = A.sc + (size_t)site * kSc;
-#pragma unroll
-    for (int i = 0; i < kSc; ++i) scl[i] = __ldg(q + i);
-  }
-  const R ut = scl[SC_UT], ux = scl[SC_UX], uy = scl[SC_UY];
-  const R invT = scl[SC_INVT], Meq = scl[SC_MEQ], M = scl[SC_M], itr = scl[SC_ITR];
-  const R ax = grad[0], ay = grad[1];
+  // 3. right-hand side on the own xi-line.  With vu = (v.u)/sinh, A1 = (a.v)/sinh:
+  //    f_eq  = Z exp((M vu sinh - u^tau E_eq)/T)
+  //    force = -(f_eq/(T cosh)) [A1 u^tau M^2 sinh (sinh^2+1)/E_eq - A1 M vu sinh^2 - M a.u]
+  //    coll  = -(f - f_eq) (u^tau - tanh vu)/tau_R,    pu = cosh u^tau - sinh vu
+  const R ax = scl[SC_AX], ay = scl[SC_AY];
   const R st = op.sth[j], mu2 = op.mu2[j];
-  const R vu = st * (cp * ux + sp * uy);              // (v_perp . u_perp) / sinh(xi)
-  const R av1 = st * (ax * cp + ay * sp);              // (a . v) / sinh(xi)
+  const R vu = st * (cp * ux + sp * uy);
+  const R A1 = st * (ax * cp + ay * sp);
   const R au = ax * ux + ay * uy;
-  const R ax_abs = st * (cp < 0 ? -cp : cp) * (R)A.inv2dx;
-  const R ay_abs = st * (sp < 0 ? -sp : sp) * (R)A.inv2dx;
+  const R ax_abs = st * (cp < 0 ? -cp : cp) * A.inv2dx_r;
+  const R ay_abs = st * (sp < 0 ? -sp : sp) * A.inv2dx_r;
   const R wj = op.wj[j];
-  const R Z = (R)A.Z;
-  const R M2 = M * M;
+  const R milne_mu2 = milne * mu2;
+  // exponent of f_eq (natural log for FP64, log2 for the FP32 ex2 path)
+  constexpr bool kF = sizeof(R) == 4;
+  const R lsc = kF ? (R)1.4426950408889634 : (R)1;
+  const R c1 = -lsc * invT * ut, c2 = lsc * invT * M * vu;
+  const R lZ = kF ? (R)log2f((float)A.Z) : (R)0;
+  const R G = A1 * ut * M2, H = A1 * M * vu, J = M * au;
+  const R nutr = -ut * itr, vtr = vu * itr;
   R Rn[NXI];
   R sA = 0, sQ = 0, sE = 0;
 #pragma unroll
   for (int k = 0; k < NXI; ++k) {
     const R s = op.s[k], c = op.c[k], ic = op.inv_c[k], s2 = op.s2[k];
     const R tv = s * ic;  // tanh(xi)
+    const R E = Etab[k], iE = iEtab[k];
     const R stream = -tv * (ax_abs * ((R)3 * f[k] - (R)4 * fx1[k] + fx2[k]) +
                             ay_abs * ((R)3 * f[k] - (R)4 * fy1[k] + fy2[k]));
-    const R Eeq = fsqrt<R>(Meq * Meq + M2 * s2);
-    const R iE = (R)1 / Eeq;
-    const R PeqU = ut * Eeq - M * s * vu;
-    const R feq = Z * fexp<R>(-PeqU * invT);
-    const R force = -feq * invT *
-                    (s * av1 * ic * (ut * M2 * s2 * iE - M * s * vu) + (ut * M2 * s * av1 * iE - M * au) * ic);
-    const R pu = c * ut - s * vu;
-    const R coll = -(pu * ic) * (f[k] - feq) * itr;
-    const R r = stream + milne * mu2 * Drf[k] + pth[k * LD + t] + force + coll;
+    R feq;
+    if constexpr (kF) feq = exp2f(c1 * E + (c2 * s + lZ));
+    else feq = A.Z * exp(c1 * E + c2 * s);
+    const R bracket = G * (s * (s2 + (R)1)) * iE - H * s2 - J;
+    const R force = -(feq * invT * ic) * bracket;
+    const R coll = (feq - f[k]) * (-(nutr + tv * vtr));
+    const R r = stream + milne_mu2 * Drf[k] + pth[k * LD + t] + force + coll;
     Rn[k] = r;
-    const R wpu2 = wj * op.ecw[k] * pu * pu;
+    const R pu = c * ut - s * vu;
+    const R wpu2 = (wj * op.ecw[k]) * (pu * pu);
     sA += wpu2 * r;
     sQ += wpu2 * Drf[k];
     sE += wpu2 * f[k];
   }
   const R v3[3] = {sA, sQ, sE};
-  block_reduce<3, NL, R>(v3, red);
+  block_reduce<3, NL, R>(v3, redf, redd);
   if (t == 0) {
-    const double* scs = A.sc + (size_t)site * kSc;
-    const double D = __ldg(scs + SC_D), Kh = __ldg(scs + SC_KH);
-    const double g = (D == 0.0) ? 0.0 : -D * red[0] / (Kh + D * (4.0 * red[2] + red[1] - Kh));
-    if (!isfinite(g)) atomicOr(A.err, (int)ERR_NONFINITE);
+    // d ln M / d tau from the consistency condition, in the compute precision
+    R g;
+    const R D = scl[SC_D], Kh = scl[SC_KH];
+    if constexpr (sizeof(R) == 4) {
+      const float Af = redf[0] + redf[1], Qf = redf[2] + redf[3], Ef = redf[4] + redf[5];
+      g = (D == 0.f) ? 0.f : -D * Af / (Kh + D * (4.f * Ef + Qf - Kh));
+    } else {
+      g = (D == 0.0) ? 0.0 : -D * redd[0] / (Kh + D * (4.0 * redd[2] + redd[1] - Kh));
+    }
+    if (!isfinite((double)g)) atomicOr(A.err, (int)ERR_NONFINITE);
     gsh = g;
-    const double lnM = __ldg(A.lnM_in + site);
-    A.lnM_out[site] = A.mode == 0 ? lnM + A.dtau * g : 0.5 * (__ldg(A.lnM_base + site) + lnM + A.dtau * g);
+    const double lnM = __ldg(A.lnM_in + site), gd = (double)g;
+    A.lnM_out[site] = A.mode == 0 ? lnM + A.dtau * gd : 0.5 * (__ldg(A.lnM_base + site) + lnM + A.dtau * gd);
   }
   __syncthreads();
-  const R g = (R)gsh;
-  const R dt = (R)A.dtau;
+  const R g = gsh;
+  const R dt = A.dtau_r;
   R out[NXI];
   if (A.mode == 0) {
 #pragma unroll
@@ -771,10 +823,16 @@ __global__ void __launch_bounds__(NTH* NPH)
   store_line<S, R, NXI>(A.f_out + (size_t)site * NN + t * NXI, out);
   R mom[kMom];
   line_moments<R, NXI, NTH, NPH>(op, out, j, l, mom);
-  block_reduce<kMom, NL, R>(mom, red);
-  if (t == 0)
+  block_reduce<kMom, NL, R>(mom, redf, redd);
+  if (t == 0) {
+    if constexpr (sizeof(R) == 4) {
 #pragma unroll
-    for (int q = 0; q < kMom; ++q) A.mom_out[(size_t)site * kMom + q] = red[q];
+      for (int q = 0; q < 2 * kMom; ++q) A.momf_out[(size_t)site * 2 * kMom + q] = redf[q];
+    } else {
+#pragma unroll
+      for (int q = 0; q < kMom; ++q) A.mom_out[(size_t)site * kMom + q] = redd[q];
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -789,6 +847,7 @@ struct InitArgs {
   double* lnM;
   double* Tsite;
   double* mom;
+  float* momf;
   int* err;
   EosView eos;
   double Z;
@@ -806,7 +865,8 @@ __global__ void __launch_bounds__(NTH* NPH)
   const int site = blockIdx.x, t = threadIdx.x;
   const int j = t % NTH, l = t / NTH;
   __shared__ double sc[3];
-  __shared__ double red[kMom * NW];
+  __shared__ double redd[kMom * NW];
+  __shared__ float redf[2 * kMom * NW];
   if (t == 0) {
     double y = 0.0;
     if (!eos_invert(A.eos, EOS_EPS, __ldg(A.eps0 + site) * A.eps_scale, log(0.3), &y)) {
@@ -825,20 +885,24 @@ __global__ void __launch_bounds__(NTH* NPH)
     sc[0] = T; sc[1] = Meq; sc[2] = M;
   }
   __syncthreads();
-  const double T = sc[0], Meq = sc[1], M = sc[2];
+  const R invT = (R)(1.0 / sc[0]), Meq = (R)sc[1], M = (R)sc[2], Z = (R)A.Z;
   R out[NXI];
 #pragma unroll
-  for (int k = 0; k < NXI; ++k) {
-    const double s = (double)A.op.s[k];
-    out[k] = ld1<S, R>(st1<S, R>((R)(A.Z * exp(-sqrt(Meq * Meq + M * M * s * s) / T))));
-  }
+  for (int k = 0; k < NXI; ++k)
+    out[k] = ld1<S, R>(st1<S, R>(Z * fexp<R>(-fsqrt<R>(Meq * Meq + M * M * A.op.s2[k]) * invT)));
   store_line<S, R, NXI>(A.f + (size_t)site * NN + t * NXI, out);
   R mom[kMom];
   line_moments<R, NXI, NTH, NPH>(A.op, out, j, l, mom);
-  block_reduce<kMom, NL, R>(mom, red);
-  if (t == 0)
+  block_reduce<kMom, NL, R>(mom, redf, redd);
+  if (t == 0) {
+    if constexpr (sizeof(R) == 4) {
 #pragma unroll
-    for (int q = 0; q < kMom; ++q) A.mom[(size_t)site * kMom + q] = red[q];
+      for (int q = 0; q < 2 * kMom; ++q) A.momf[(size_t)site * 2 * kMom + q] = redf[q];
+    } else {
+#pragma unroll
+      for (int q = 0; q < kMom; ++q) A.mom[(size_t)site * kMom + q] = redd[q];
+    }
+  }
 }
 
 }  // namespace rlbk
