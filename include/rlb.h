@@ -145,6 +145,36 @@ rlb_status rlb_init_grid(rlb_ctx* ctx, const double* eps0, int eps0_on_device, v
  * stream-collide kernel.  Asynchronous on `stream`. */
 rlb_status rlb_step(rlb_ctx* ctx, int nsteps, void* stream);
 
+/* Step variant for callers that cannot allocate device memory.
+ *
+ * Some callers may not call cudaMalloc or hand the library scratch of their
+ * own: code hosted inside a framework whose allocator owns all device memory,
+ * latency-critical loops that cannot absorb the implicit synchronisation of an
+ * allocation, or deployments that forbid allocating after start-up.  This
+ * entry point advances `nsteps` predictor-corrector steps exactly as rlb_step
+ * does, in place on the caller's state buffer (layout of rlb_state_offsets,
+ * 256-byte aligned; it needs rlb_init_eos and rlb_configure but no bound
+ * buffers), and keeps every intermediate array in one file-scope device array
+ * of 24 MiB declared by the library.  It calls no allocating routine: no
+ * cudaMalloc, no cudaFree, no library allocator.
+ *   - The first call on a device looks up the device address of that array
+ *     (cudaGetSymbolAddress) with the context's device current; make this first
+ *     call before any stream capture begins.
+ *   - Grids whose scratch would exceed 24 MiB are rejected with RLB_ERR_ARG
+ *     (about 5,000 sites with FP32 populations on the 8x8x12 lattice, 2,500 with
+ *     FP64).
+ *   - Every call in the process shares the array, which keeps whatever the last
+ *     call left in it: each call re-uploads the EOS tables, clears the error
+ *     word and the Newton starting temperatures, and recomputes the moments of
+ *     its input.  Calls whose GPU work overlaps (other streams, threads or
+ *     contexts on the same device) race on the array; the caller serialises
+ *     them.
+ *   - The call synchronises `stream` before returning and reports a numeric
+ *     failure recorded during it as RLB_ERR_NUMERIC.
+ * The paper has no counterpart of this entry point: it concerns memory
+ * management only. */
+rlb_status rlb_step_static_scratch(rlb_ctx* ctx, void* state, int nsteps, void* stream);
+
 /* Current proper time (host bookkeeping, fm/c). */
 rlb_status rlb_get_tau(const rlb_ctx* ctx, double* tau);
 

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <utility>
 #include <vector>
 
@@ -297,6 +298,147 @@ rlb_status set_device(rlb_ctx* ctx) {
   return RLB_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Step variant that allocates nothing: its scratch lives in one file-scope
+// device array, shared by every call in the process on a given device.
+// ---------------------------------------------------------------------------
+constexpr size_t kStaticScratchBytes = (size_t)24 << 20;  // 24 MiB per device
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+static void* g_static_ptr[kMaxDevices];  // device address of g_static_scratch, per device
+static std::mutex g_static_mu;
+
+// Device address of the static scratch on the current device (looked up once).
+rlb_status static_scratch(rlb_ctx* ctx, char** out) {
+  if (ctx->device < 0 || ctx->device >= kMaxDevices) return fail(ctx, RLB_ERR_ARG, "device id out of range");
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[ctx->device]) {
+    void* p = nullptr;
+    RLB_CUDA(cudaGetSymbolAddress(&p, g_static_scratch), "cudaGetSymbolAddress(static scratch)");
+    g_static_ptr[ctx->device] = p;
+  }
+  *out = static_cast<char*>(g_static_ptr[ctx->device]);
+  return RLB_OK;
+}
+
+template <class S, class R, int NXI, int NTH, int NPH>
+rlb_status step_static(rlb_ctx* ctx, char* state, char* scr, int nsteps, cudaStream_t st) {
+  constexpr int NL = NTH * NPH;
+  // same layout as the bound scratch, rooted at the static array
+  size_t sb, xb;
+  rlb_ctx L;
+  layout(ctx->gp, (size_t)ctx->eosp.points, &sb, &xb, &L);
+  S* f = reinterpret_cast<S*>(state + ctx->f_off);
+  double* m = reinterpret_cast<double*>(state + ctx->lnM_off);
+  S* fs = reinterpret_cast<S*>(scr + L.fs_off);
+  double* ms = reinterpret_cast<double*>(scr + L.lnMs_off);
+  double* mom = reinterpret_cast<double*>(scr + L.mom_off);
+  double* moms = reinterpret_cast<double*>(scr + L.moms_off);
+  double* Tsite = reinterpret_cast<double*>(scr + L.T_off);
+  int* err = reinterpret_cast<int*>(scr + L.err_off);
+  rlbk::EosView ev;
+  ev.tab = reinterpret_cast<const double*>(scr + L.tab_off);
+  ev.tabf = reinterpret_cast<const float*>(scr + L.tabf_off);
+  ev.y0 = ctx->tab.y0;
+  ev.inv_h = 1.0 / ctx->tab.h;
+  ev.n = ctx->tab.n;
+  // contents left by earlier calls are not trusted: EOS tables, Newton starts,
+  // error word and the moments of the input are rebuilt here
+  RLB_CUDA(cudaMemcpyAsync(scr + L.tab_off, ctx->tab.data.data(), ctx->tab.data.size() * sizeof(double),
+                           cudaMemcpyHostToDevice, st), "static EOS table upload");
+  {
+    std::vector<float> tf(ctx->tab.data.size());
+    for (size_t i = 0; i < tf.size(); ++i) tf[i] = (float)ctx->tab.data[i];
+    RLB_CUDA(cudaMemcpyAsync(scr + L.tabf_off, tf.data(), tf.size() * sizeof(float),
+                             cudaMemcpyHostToDevice, st), "static FP32 EOS table upload");
+    RLB_CUDA(cudaStreamSynchronize(st), "static table upload synchronise");
+  }
+  RLB_CUDA(cudaMemsetAsync(Tsite, 0, ctx->ns * sizeof(double), st), "static Newton starts reset");
+  RLB_CUDA(cudaMemsetAsync(err, 0, 256, st), "static error word reset");
+  const auto op = make_ops<R, NXI, NTH, NPH>(ctx->lat);
+  {
+    rlbk::MomentsArgs<S, R, NXI, NTH, NPH> a;
+    a.f = f;
+    a.mom = mom;
+    a.momf = reinterpret_cast<float*>(mom);
+    a.op = op;
+    rlbk::moments_kernel<S, R, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
+    RLB_CUDA(cudaGetLastError(), "moments_kernel launch");
+  }
+  rlbk::MatchArgs ma;
+  ma.Tsite = Tsite;
+  ma.sc = reinterpret_cast<double*>(scr + L.sc_off);
+  ma.scf = reinterpret_cast<float*>(scr + L.scf_off);
+  ma.obs = nullptr;
+  ma.err = err;
+  ma.eos = ev;
+  ma.eta_over_s = ctx->gp.eta_over_s;
+  ma.inv2dx = 1.0 / (2.0 * ctx->gp.dx);
+  ma.nx = ctx->gp.nx;
+  ma.ny = ctx->gp.ny;
+  ma.ns = (int)ctx->ns;
+  auto run_match = [&](const double* mm, const double* lnM) -> rlb_status {
+    ma.mom = mm;
+    ma.momf = reinterpret_cast<const float*>(mm);
+    ma.lnM = lnM;
+    const unsigned nb = (unsigned)((ctx->ns + 127) / 128);
+    if (ctx->gp.prec == RLB_F64) rlbk::match_kernel<false><<<nb, 128, 0, st>>>(ma);
+    else rlbk::match_kernel<true><<<nb, 128, 0, st>>>(ma);
+    RLB_CUDA(cudaGetLastError(), "match_kernel launch");
+    return RLB_OK;
+  };
+  rlbk::StageArgs<S, R, NXI, NTH, NPH> a;
+  a.sc = ma.sc;
+  a.scf = ma.scf;
+  a.err = err;
+  a.nx = ctx->gp.nx;
+  a.ny = ctx->gp.ny;
+  a.dtau = ctx->gp.dtau;
+  a.inv2dx = 1.0 / (2.0 * ctx->gp.dx);
+  a.dtau_r = (R)a.dtau;
+  a.inv2dx_r = (R)a.inv2dx;
+  a.Z = (R)ctx->eosp.Z;
+  a.op = op;
+  for (int s = 0; s < nsteps; ++s) {
+    rlb_status r = run_match(mom, m);
+    if (r) return r;
+    a.f_in = f; a.lnM_in = m; a.f_base = f; a.lnM_base = m;
+    a.f_out = fs; a.lnM_out = ms; a.mom_out = moms; a.momf_out = reinterpret_cast<float*>(moms);
+    a.mode = 0;
+    a.milne = ctx->gp.metric ? (R)(1.0 / ctx->tau) : (R)0;
+    rlbk::stage_kernel<S, R, NXI, NTH, NPH><<<grid2d(ctx), NL, 0, st>>>(a);
+    RLB_CUDA(cudaGetLastError(), "stage_kernel (predictor) launch");
+    r = run_match(moms, ms);
+    if (r) return r;
+    a.f_in = fs; a.lnM_in = ms; a.f_base = f; a.lnM_base = m;
+    a.f_out = f; a.lnM_out = m; a.mom_out = mom; a.momf_out = reinterpret_cast<float*>(mom);
+    a.mode = 1;
+    a.milne = ctx->gp.metric ? (R)(1.0 / (ctx->tau + ctx->gp.dtau)) : (R)0;
+    rlbk::stage_kernel<S, R, NXI, NTH, NPH><<<grid2d(ctx), NL, 0, st>>>(a);
+    RLB_CUDA(cudaGetLastError(), "stage_kernel (corrector) launch");
+    ctx->tau += ctx->gp.dtau;
+  }
+  // report numeric failures of this call (the error word is shared)
+  int word = 0;
+  RLB_CUDA(cudaMemcpyAsync(&word, err, sizeof(int), cudaMemcpyDeviceToHost, st), "static error word read");
+  RLB_CUDA(cudaStreamSynchronize(st), "static step synchronise");
+  if (word) return fail(ctx, RLB_ERR_NUMERIC, "device error word set in the static-scratch step");
+  return RLB_OK;
+}
+
+template <int NXI, int NTH, int NPH>
+rlb_status step_static_prec(rlb_ctx* c, char* state, char* scr, int n, cudaStream_t st) {
+  switch (c->gp.prec) {
+    case RLB_F64:
+      if constexpr (NXI * NTH * NPH <= 1024) return step_static<double, double, NXI, NTH, NPH>(c, state, scr, n, st);
+      else return fail(c, RLB_ERR_ARG, "FP64 storage supports at most 1024 nodes per site");
+    case RLB_F32: return step_static<float, float, NXI, NTH, NPH>(c, state, scr, n, st);
+    case RLB_BF16: return step_static<__nv_bfloat16, float, NXI, NTH, NPH>(c, state, scr, n, st);
+  }
+  return fail(c, RLB_ERR_ARG, "unknown precision");
+}
+
 }  // namespace
 
 extern "C" {
@@ -432,6 +574,35 @@ rlb_status rlb_step(rlb_ctx* ctx, int nsteps, void* stream) {
   rlb_status s = set_device(ctx);
   if (s) return s;
   return dispatch(ctx, OP_STEP, nsteps, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+rlb_status rlb_step_static_scratch(rlb_ctx* ctx, void* state, int nsteps, void* stream) {
+  if (!ctx || !state || nsteps < 0) return RLB_ERR_ARG;
+  if (!ctx->grid_ok) return fail(ctx, RLB_ERR_STATE, "rlb_configure must come first");
+  if ((uintptr_t)state & 255) return fail(ctx, RLB_ERR_ARG, "state must be 256-byte aligned");
+  size_t sb, xb;
+  layout(ctx->gp, (size_t)ctx->eosp.points, &sb, &xb, nullptr);
+  if (xb > kStaticScratchBytes) {
+    char buf[200];
+    snprintf(buf, sizeof buf,
+             "grid needs %zu bytes of scratch; the static scratch holds %zu (use rlb_step with bound buffers)",
+             xb, kStaticScratchBytes);
+    return fail(ctx, RLB_ERR_ARG, buf);
+  }
+  rlb_status s = set_device(ctx);
+  if (s) return s;
+  char* scr = nullptr;
+  s = static_scratch(ctx, &scr);
+  if (s) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* stp = static_cast<char*>(state);
+  const int a = ctx->gp.n_xi, b = ctx->gp.n_theta, d = 2 * ctx->gp.n_phi_half;
+  if (a == 8 && b == 8 && d == 12) return step_static_prec<8, 8, 12>(ctx, stp, scr, nsteps, st);
+  if (a == 16 && b == 8 && d == 16) return step_static_prec<16, 8, 16>(ctx, stp, scr, nsteps, st);
+  if (a == 5 && b == 5 && d == 2) return step_static_prec<5, 5, 2>(ctx, stp, scr, nsteps, st);
+  if (a == 6 && b == 4 && d == 6) return step_static_prec<6, 4, 6>(ctx, stp, scr, nsteps, st);
+  if (a == 8 && b == 8 && d == 2) return step_static_prec<8, 8, 2>(ctx, stp, scr, nsteps, st);
+  return fail(ctx, RLB_ERR_ARG, "unsupported lattice shape");
 }
 
 rlb_status rlb_get_tau(const rlb_ctx* ctx, double* tau) {

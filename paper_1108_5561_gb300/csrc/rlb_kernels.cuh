@@ -905,4 +905,42 @@ __global__ void __launch_bounds__(NTH* NPH)
   }
 }
 
+// ---------------------------------------------------------------------------
+// moments of stored populations (kMom per site), used where no stage kernel
+// has produced them (the step variant that works in static scratch)
+// ---------------------------------------------------------------------------
+template <class S, class R, int NXI, int NTH, int NPH>
+struct MomentsArgs {
+  const S* f;
+  double* mom;
+  float* momf;
+  Ops<R, NXI, NTH, NPH> op;
+};
+
+template <class S, class R, int NXI, int NTH, int NPH>
+__global__ void __launch_bounds__(NTH* NPH)
+    moments_kernel(const __grid_constant__ MomentsArgs<S, R, NXI, NTH, NPH> A) {
+  constexpr int NL = NTH * NPH;
+  constexpr int NN = NL * NXI;
+  constexpr int NW = (NL + 31) / 32;
+  const int site = blockIdx.x, t = threadIdx.x;
+  const int j = t % NTH, l = t / NTH;
+  __shared__ double redd[kMom * NW];
+  __shared__ float redf[2 * kMom * NW];
+  R f[NXI];
+  load_line<S, R, NXI>(A.f + (size_t)site * NN + t * NXI, f);
+  R mom[kMom];
+  line_moments<R, NXI, NTH, NPH>(A.op, f, j, l, mom);
+  block_reduce<kMom, NL, R>(mom, redf, redd);
+  if (t == 0) {
+    if constexpr (sizeof(R) == 4) {
+#pragma unroll
+      for (int q = 0; q < 2 * kMom; ++q) A.momf[(size_t)site * 2 * kMom + q] = redf[q];
+    } else {
+#pragma unroll
+      for (int q = 0; q < kMom; ++q) A.mom[(size_t)site * kMom + q] = redd[q];
+    }
+  }
+}
+
 }  // namespace rlbk
