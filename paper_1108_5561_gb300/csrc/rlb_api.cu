@@ -103,6 +103,7 @@ rlbk::Ops<R, NXI, NTH, NPH> make_ops(const rlb::Lattice& L) {
   for (int k = 0; k < NXI; ++k) {
     const double c = L.c[k], s = L.s[k], e = L.ecw[k];
     o.c[k] = (R)c; o.s[k] = (R)s; o.s2[k] = (R)(s * s); o.inv_c[k] = (R)(1.0 / c);
+    o.tv[k] = (R)(s / c); o.q1[k] = (R)(s * (s * s + 1.0) / c); o.q2[k] = (R)(s * s / c);
     o.w0[k] = (R)e; o.w1[k] = (R)(e * c * s); o.w2[k] = (R)(e * c * c); o.w3[k] = (R)(e * s * s);
     o.ecw[k] = (R)e;
   }
@@ -114,19 +115,38 @@ rlbk::Ops<R, NXI, NTH, NPH> make_ops(const rlb::Lattice& L) {
   return o;
 }
 
+// Table geometry of an EosView, including the split constants of the FP32 cell
+// location (see EosView).
+void eos_geometry(const rlb::EosTable& tab, rlbk::EosView* v) {
+  v->y0 = tab.y0;
+  v->inv_h = 1.0 / tab.h;
+  v->n = tab.n;
+  v->ih_hi = (float)v->inv_h;
+  v->ih_lo = (float)(v->inv_h - (double)v->ih_hi);
+  const double c = tab.y0 * v->inv_h;
+  v->c_hi = (float)std::nearbyint(c);
+  v->c_lo = (float)(c - (double)v->c_hi);
+}
+
 rlbk::EosView eos_view(const rlb_ctx* c) {
   rlbk::EosView v;
   v.tab = reinterpret_cast<const double*>(c->scratch + c->tab_off);
   v.tabf = reinterpret_cast<const float*>(c->scratch + c->tabf_off);
-  v.y0 = c->tab.y0;
-  v.inv_h = 1.0 / c->tab.h;
-  v.n = c->tab.n;
+  eos_geometry(c->tab, &v);
   return v;
 }
 
 enum Kind { K_STAGE = 0, K_MATCH = 1, K_INIT = 2 };
 
 dim3 grid2d(const rlb_ctx* c) { return dim3((unsigned)c->gp.nx, (unsigned)c->gp.ny, 1); }
+
+// Set the Milne factor 1/tau of one launch and fold it into the polar operator.
+template <class R, int NXI, int NTH, int NPH>
+void set_milne(rlbk::Ops<R, NXI, NTH, NPH>& op, const rlb::Lattice& L, int metric, double tau, R* milne) {
+  const double inv = metric ? 1.0 / tau : 0.0;
+  *milne = (R)inv;
+  for (int i = 0; i < NTH * NTH; ++i) op.Dth[i] = (R)(L.Dth[i] * inv);
+}
 
 // Event bracket around one launch when timing is enabled.
 struct Timed {
@@ -157,7 +177,7 @@ struct Timed {
   }
 };
 
-rlb_status match(rlb_ctx* ctx, const double* mom, const double* lnM, double* obs, cudaStream_t st) {
+rlbk::MatchArgs match_args(rlb_ctx* ctx, const double* mom, const double* lnM, double* obs) {
   rlbk::MatchArgs a;
   a.mom = mom;
   a.momf = reinterpret_cast<const float*>(mom);  // FP32 storage keeps (hi, lo) float pairs here
@@ -173,6 +193,11 @@ rlb_status match(rlb_ctx* ctx, const double* mom, const double* lnM, double* obs
   a.eos = eos_view(ctx);
   a.eta_over_s = ctx->gp.eta_over_s;
   a.ns = (int)ctx->ns;
+  return a;
+}
+
+rlb_status match(rlb_ctx* ctx, const double* mom, const double* lnM, double* obs, cudaStream_t st) {
+  const rlbk::MatchArgs a = match_args(ctx, mom, lnM, obs);
   {
     Timed tm(ctx, K_MATCH, st);
     const unsigned nb = (unsigned)((ctx->ns + 127) / 128);
@@ -237,7 +262,7 @@ struct Runner {
       a.f_in = f; a.lnM_in = m; a.f_base = f; a.lnM_base = m;
       a.f_out = fs; a.lnM_out = ms; a.mom_out = moms; a.momf_out = reinterpret_cast<float*>(moms);
       a.mode = 0;
-      a.milne = ctx->gp.metric ? (R)(1.0 / ctx->tau) : (R)0;
+      set_milne<R, NXI, NTH, NPH>(a.op, ctx->lat, ctx->gp.metric, ctx->tau, &a.milne);
       {
         Timed tm(ctx, K_STAGE, st);
         rlbk::stage_kernel<S, R, NXI, NTH, NPH><<<grid2d(ctx), NL, 0, st>>>(a);
@@ -249,7 +274,7 @@ struct Runner {
       a.f_in = fs; a.lnM_in = ms; a.f_base = f; a.lnM_base = m;
       a.f_out = f; a.lnM_out = m; a.mom_out = mom; a.momf_out = reinterpret_cast<float*>(mom);
       a.mode = 1;
-      a.milne = ctx->gp.metric ? (R)(1.0 / (ctx->tau + ctx->gp.dtau)) : (R)0;
+      set_milne<R, NXI, NTH, NPH>(a.op, ctx->lat, ctx->gp.metric, ctx->tau + ctx->gp.dtau, &a.milne);
       {
         Timed tm(ctx, K_STAGE, st);
         rlbk::stage_kernel<S, R, NXI, NTH, NPH><<<grid2d(ctx), NL, 0, st>>>(a);
@@ -340,9 +365,7 @@ rlb_status step_static(rlb_ctx* ctx, char* state, char* scr, int nsteps, cudaStr
   rlbk::EosView ev;
   ev.tab = reinterpret_cast<const double*>(scr + L.tab_off);
   ev.tabf = reinterpret_cast<const float*>(scr + L.tabf_off);
-  ev.y0 = ctx->tab.y0;
-  ev.inv_h = 1.0 / ctx->tab.h;
-  ev.n = ctx->tab.n;
+  eos_geometry(ctx->tab, &ev);
   // contents left by earlier calls are not trusted: EOS tables, Newton starts,
   // error word and the moments of the input are rebuilt here
   RLB_CUDA(cudaMemcpyAsync(scr + L.tab_off, ctx->tab.data.data(), ctx->tab.data.size() * sizeof(double),
@@ -406,7 +429,7 @@ rlb_status step_static(rlb_ctx* ctx, char* state, char* scr, int nsteps, cudaStr
     a.f_in = f; a.lnM_in = m; a.f_base = f; a.lnM_base = m;
     a.f_out = fs; a.lnM_out = ms; a.mom_out = moms; a.momf_out = reinterpret_cast<float*>(moms);
     a.mode = 0;
-    a.milne = ctx->gp.metric ? (R)(1.0 / ctx->tau) : (R)0;
+    set_milne<R, NXI, NTH, NPH>(a.op, ctx->lat, ctx->gp.metric, ctx->tau, &a.milne);
     rlbk::stage_kernel<S, R, NXI, NTH, NPH><<<grid2d(ctx), NL, 0, st>>>(a);
     RLB_CUDA(cudaGetLastError(), "stage_kernel (predictor) launch");
     r = run_match(moms, ms);
@@ -414,7 +437,7 @@ rlb_status step_static(rlb_ctx* ctx, char* state, char* scr, int nsteps, cudaStr
     a.f_in = fs; a.lnM_in = ms; a.f_base = f; a.lnM_base = m;
     a.f_out = f; a.lnM_out = m; a.mom_out = mom; a.momf_out = reinterpret_cast<float*>(mom);
     a.mode = 1;
-    a.milne = ctx->gp.metric ? (R)(1.0 / (ctx->tau + ctx->gp.dtau)) : (R)0;
+    set_milne<R, NXI, NTH, NPH>(a.op, ctx->lat, ctx->gp.metric, ctx->tau + ctx->gp.dtau, &a.milne);
     rlbk::stage_kernel<S, R, NXI, NTH, NPH><<<grid2d(ctx), NL, 0, st>>>(a);
     RLB_CUDA(cudaGetLastError(), "stage_kernel (corrector) launch");
     ctx->tau += ctx->gp.dtau;

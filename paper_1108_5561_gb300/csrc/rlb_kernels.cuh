@@ -25,7 +25,8 @@ struct Ops {
   R Dr[NXI * NXI];    // Galerkin v.d/dv (radial part of S1, S2)
   R Dth[NTH * NTH];   // Galerkin (mu - mu^3) d/dmu (polar part of S1)
   // radial node constants
-  R c[NXI], s[NXI], s2[NXI], inv_c[NXI];
+  R c[NXI], s[NXI], s2[NXI], inv_c[NXI], tv[NXI];  // cosh, sinh, sinh^2, 1/cosh, tanh
+  R q1[NXI], q2[NXI];  // sinh (sinh^2 + 1)/cosh, sinh^2/cosh
   R w0[NXI], w1[NXI], w2[NXI], w3[NXI];  // ecw * {1, c s, c^2, s^2}
   R ecw[NXI];
   // polar
@@ -39,6 +40,10 @@ struct EosView {
   const float* tabf;   // the same table rounded to FP32
   double y0, inv_h;
   int n;
+  // FP32 cell location: u = (y - y0)/h = y (ih_hi + ih_lo) - (c_hi + c_lo), with
+  // c = y0/h split into an integer c_hi and a remainder, so that the offset in
+  // the cell keeps FP32 relative precision (u itself reaches n ~ 6.5e4)
+  float ih_hi, ih_lo, c_hi, c_lo;
 };
 
 
@@ -122,6 +127,11 @@ __device__ __forceinline__ void store_line(S* __restrict__ p, const R (&v)[N]) {
 template <class R> __device__ __forceinline__ R fexp(R x);
 template <> __device__ __forceinline__ float fexp<float>(float x) { return __expf(x); }
 template <> __device__ __forceinline__ double fexp<double>(double x) { return exp(x); }
+__device__ __forceinline__ float ex2_ftz(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 template <class R> __device__ __forceinline__ R fsqrt(R x);
 template <> __device__ __forceinline__ float fsqrt<float>(float x) { return sqrtf(x); }
 template <> __device__ __forceinline__ double fsqrt<double>(double x) { return sqrt(x); }
@@ -255,20 +265,31 @@ __device__ __forceinline__ float eos_fieldf(const EosView& E, int i0, const floa
   return v;
 }
 
-// Table inversion for the FP32 path: bracketed Newton in FP32 to a start
-// value, then FP64 Newton steps on the FP64 table (the residual in FP64 fixes
-// the root; the slope may be taken from the FP32 table).  Same failure rules as
-// eos_invert.
-__device__ bool eos_invert_mixed(const EosView& E, int field, double target, double y, double* y_out) {
+// FP32 cell location of y: i0 (clamped to the interior) and the offset t in the
+// cell; false outside the tabulated range.
+__device__ __forceinline__ bool eos_cellf(const EosView& E, float y, int* i0, float* t) {
+  const float u = fmaf(y, E.ih_hi, -E.c_hi);
+  if (!(u >= 2.f && u <= (float)(E.n - 4))) return false;
+  const int i = min((int)floorf(u), E.n - 4);
+  *i0 = i;
+  *t = fmaf(y, E.ih_hi, -(E.c_hi + (float)i)) + fmaf(y, E.ih_lo, -E.c_lo);
+  return true;
+}
+
+// Table inversion in FP32 (FP32 storage path): Newton on the interpolant of the
+// FP32 table, safeguarded by a bisection bracket; same failure rules as
+// eos_invert.  The result carries FP32 precision, which is what the FP32
+// kernels consume.
+__device__ bool eos_invert_f(const EosView& E, int field, float target, float y, float* y_out) {
+  const float ih = E.ih_hi + E.ih_lo;
   float lo = (float)(E.y0 + 2.0 / E.inv_h), hi = (float)(E.y0 + (E.n - 4) / E.inv_h);
-  const float ymin = lo, ymax = hi, tf = (float)target, y0f = (float)E.y0, ihf = (float)E.inv_h;
-  float yf = (y > ymin && y < ymax) ? (float)y : 0.5f * (lo + hi);
+  const float ymin = lo, ymax = hi;
+  float yf = (y > ymin && y < ymax) ? y : 0.5f * (lo + hi);
   bool ok = false;
   for (int it = 0; it < 100; ++it) {
-    const float u = (yf - y0f) * ihf;
-    if (!(u >= 2.f && u <= (float)(E.n - 4))) return false;
-    int i0 = min((int)floorf(u), E.n - 4);
-    const float t = u - (float)i0;
+    int i0;
+    float t;
+    if (!eos_cellf(E, yf, &i0, &t)) return false;
     float w[6], dw[6];
     lagrange6f(t, w);
     lagrange6f_d(t, dw);
@@ -279,35 +300,17 @@ __device__ bool eos_invert_mixed(const EosView& E, int field, double target, dou
       F += w[m] * v;
       dF += dw[m] * v;
     }
-    dF *= ihf;
-    if (F < tf) lo = yf; else hi = yf;
-    float yn = (dF > 0.f) ? yf - (F - tf) / dF : 0.5f * (lo + hi);
+    dF *= ih;
+    if (F == target) { ok = true; break; }
+    if (F < target) lo = yf; else hi = yf;
+    float yn = (dF > 0.f) ? yf - (F - target) / dF : 0.5f * (lo + hi);
     if (!(yn >= lo && yn <= hi)) yn = 0.5f * (lo + hi);
     const float dy = yn - yf;
     yf = yn;
     if (fabsf(dy) < 2e-6f || hi - lo < 4e-6f) { ok = true; break; }
   }
   if (!ok || yf - ymin < 1e-5f || ymax - yf < 1e-5f) return false;
-  double yd = (double)yf;
-  for (int it = 0; it < 2; ++it) {  // FP64 refinement
-    int i0;
-    double t, w[6];
-    if (!eos_cell(E, yd, &i0, &t)) return false;
-    lagrange6(t, w);
-    float dw[6];
-    lagrange6f_d((float)t, dw);
-    double F = 0.0;
-    float dF = 0.f;
-#pragma unroll
-    for (int m = 0; m < 6; ++m) {
-      F += w[m] * __ldg(E.tab + (size_t)(i0 - 2 + m) * 8 + field);
-      dF += dw[m] * __ldg(E.tabf + (size_t)(i0 - 2 + m) * 8 + field);
-    }
-    dF *= ihf;
-    if (!(dF > 0.f)) return false;
-    yd -= (F - target) * (double)(1.0f / dF);
-  }
-  *y_out = yd;
+  *y_out = yf;
   return true;
 }
 
@@ -321,7 +324,50 @@ __device__ bool eos_invert_mixed(const EosView& E, int field, double target, dou
 // space of A - eps (largest cross product of two rows), normalised by the
 // Minkowski norm; eps is then the Rayleigh quotient u_mu u_nu T^{mu nu}.
 // ---------------------------------------------------------------------------
-template <bool FP32_START>
+// FP32 version for the FP32 storage path: the same steps on the matrix scaled
+// by its infinity norm, eps as the Rayleigh quotient of the unscaled T.
+__device__ bool landau3f(const float tm[6], float u[3], float* eps) {
+  const float sc = fmaxf(fabsf(tm[0]) + fabsf(tm[1]) + fabsf(tm[2]),
+                         fmaxf(fabsf(tm[1]) + fabsf(tm[3]) + fabsf(tm[4]),
+                               fabsf(tm[2]) + fabsf(tm[4]) + fabsf(tm[5])));
+  if (!(sc > 0.f) || !isfinite(sc)) return false;
+  const float is = 1.f / sc;
+  const float a00 = tm[0] * is, a01 = -tm[1] * is, a02 = -tm[2] * is;
+  const float a10 = -a01, a11 = -tm[3] * is, a12 = -tm[4] * is;
+  const float a20 = -a02, a21 = a12, a22 = -tm[5] * is;
+  const float c2 = a00 + a11 + a22;
+  const float c1 = a00 * a11 - a01 * a10 + a00 * a22 - a02 * a20 + a11 * a22 - a12 * a21;
+  const float c0 = a00 * (a11 * a22 - a12 * a21) - a01 * (a10 * a22 - a12 * a20) +
+                   a02 * (a10 * a21 - a11 * a20);
+  float lam = 1.f;  // the infinity norm bounds every eigenvalue
+  for (int it = 0; it < 60; ++it) {
+    const float p = ((lam - c2) * lam + c1) * lam - c0;
+    const float dp = (3.f * lam - 2.f * c2) * lam + c1;
+    if (!(dp > 0.f)) break;
+    const float d = p / dp;
+    if (!(d > 0.f)) break;
+    lam -= d;
+    if (d <= 1e-7f * lam) break;
+  }
+  const float r00 = a00 - lam, r11 = a11 - lam, r22 = a22 - lam;
+  const float p0 = a01 * a12 - a02 * r11, p1 = a02 * a10 - r00 * a12, p2 = r00 * r11 - a01 * a10;
+  const float q0 = a01 * r22 - a02 * a21, q1 = a02 * a20 - r00 * r22, q2 = r00 * a21 - a01 * a20;
+  const float s0 = r11 * r22 - a12 * a21, s1 = a12 * a20 - a10 * r22, s2 = a10 * a21 - r11 * a20;
+  const float np = p0 * p0 + p1 * p1 + p2 * p2, nq = q0 * q0 + q1 * q1 + q2 * q2;
+  const float nsq = s0 * s0 + s1 * s1 + s2 * s2;
+  float v0 = s0, v1 = s1, v2 = s2;
+  if (np >= nq && np >= nsq) { v0 = p0; v1 = p1; v2 = p2; }
+  else if (nq >= nsq) { v0 = q0; v1 = q1; v2 = q2; }
+  const float mn = v0 * v0 - v1 * v1 - v2 * v2;
+  if (!(mn > 0.f)) return false;
+  float r = rsqrtf(mn);
+  if (v0 < 0.f) r = -r;
+  u[0] = v0 * r; u[1] = v1 * r; u[2] = v2 * r;
+  *eps = u[0] * u[0] * tm[0] - 2.f * u[0] * (u[1] * tm[1] + u[2] * tm[2]) +
+         u[1] * u[1] * tm[3] + 2.f * u[1] * u[2] * tm[4] + u[2] * u[2] * tm[5];
+  return *eps > 0.f;
+}
+
 __device__ bool landau3(const double tm[6], double u[3], double* eps) {
   const double a00 = tm[0], a01 = -tm[1], a02 = -tm[2];
   const double a10 = tm[1], a11 = -tm[3], a12 = -tm[4];
@@ -332,25 +378,7 @@ __device__ bool landau3(const double tm[6], double u[3], double* eps) {
                     a02 * (a10 * a21 - a11 * a20);
   double lam = fmax(fabs(a00) + fabs(a01) + fabs(a02),
                     fmax(fabs(a10) + fabs(a11) + fabs(a12), fabs(a20) + fabs(a21) + fabs(a22)));
-  int iters = 200;
-  if constexpr (FP32_START) {
-    // monotone Newton from above in FP32 (scaled by the bound), then FP64 steps
-    const float sc = (float)lam, isc = 1.f / sc;
-    const float c2f = (float)c2 * isc, c1f = (float)c1 * isc * isc, c0f = (float)c0 * isc * isc * isc;
-    float lf = 1.f;
-    for (int it = 0; it < 60; ++it) {
-      const float p = ((lf - c2f) * lf + c1f) * lf - c0f;
-      const float dp = (3.f * lf - 2.f * c2f) * lf + c1f;
-      if (!(dp > 0.f)) break;
-      const float d = p / dp;
-      if (!(d > 0.f)) break;
-      lf -= d;
-      if (d <= 1e-7f * fabsf(lf)) break;
-    }
-    // stay above the root: back off by a few FP32 ulps before the FP64 steps
-    lam = (double)lf * (1.0 + 4e-7) * (double)sc;
-    iters = 6;
-  }
+  const int iters = 200;
   for (int it = 0; it < iters; ++it) {
     double p = ((lam - c2) * lam + c1) * lam - c0;
     double dp = (3.0 * lam - 2.0 * c2) * lam + c1;
@@ -405,84 +433,56 @@ struct MatchArgs {
   int nx, ny, ns;
 };
 
-// Matching of every site (FP64, one thread per site): Landau (u, eps_kin),
-// T from e(T) = eps_kin (B at its equilibrium value, Eq. sanity), then M(T),
-// dB/deps, tau_R (Sec. 4.1) and B(T) from the table.
-template <bool FAST>
-__global__ void __launch_bounds__(128) match_kernel(const MatchArgs A) {
-  const int site = blockIdx.x * blockDim.x + threadIdx.x;
-  if (site >= A.ns) return;
+// Matching of one site in FP64 (FP64 storage path): Landau (u, eps_kin), T from
+// e(T) = eps_kin (B at its equilibrium value, Eq. sanity), then M(T), dB/deps,
+// tau_R (Sec. 4.1) and B(T) from the table.  Writes the kSc site scalars to o,
+// the temperature to Tsite (the next Newton start) and the observables when
+// A.obs is set; returns the error bits.
+__device__ __forceinline__ int match_site_d(const MatchArgs& A, int site, double (&o)[kSc]) {
   double m[kMom];
-  if constexpr (FAST) {
-    const float* q = A.momf + (size_t)site * 2 * kMom;
+  const double* q = A.mom + (size_t)site * kMom;
 #pragma unroll
-    for (int i = 0; i < kMom; ++i) m[i] = (double)q[2 * i] + (double)q[2 * i + 1];
-  } else {
-    const double* q = A.mom + (size_t)site * kMom;
-#pragma unroll
-    for (int i = 0; i < kMom; ++i) m[i] = q[i];
-  }
+  for (int i = 0; i < kMom; ++i) m[i] = q[i];
   const double lnM = A.lnM[site];
   const double M = exp(lnM);
   const double pref = M * M * M * M * (1.0 / (2.0 * 3.14159265358979323846 * 3.14159265358979323846));
   double tm[6];
 #pragma unroll
-  for (int q = 0; q < 6; ++q) tm[q] = pref * m[1 + q];
+  for (int i = 0; i < 6; ++i) tm[i] = pref * m[1 + i];
   int err = 0;
   double u[3], eps;
-  if (!landau3<FAST>(tm, u, &eps)) {
+  if (!landau3(tm, u, &eps)) {
     err |= ERR_LANDAU;
     u[0] = 1.0; u[1] = 0.0; u[2] = 0.0;
     eps = fmax(tm[0], 1e-300);
   }
   const double Tg = A.Tsite[site];
-  double y, yg = (Tg > 0.0) ? (FAST ? (double)logf((float)Tg) : log(Tg)) : 0.0;
-  const bool inv_ok = FAST ? eos_invert_mixed(A.eos, EOS_E, eps, yg, &y) : eos_invert(A.eos, EOS_E, eps, yg, &y);
-  if (!inv_ok) {
+  double y, yg = (Tg > 0.0) ? log(Tg) : 0.0;
+  if (!eos_invert(A.eos, EOS_E, eps, yg, &y)) {
     err |= ERR_EOS;
     y = fmin(fmax(yg, A.eos.y0 + 2.0 / A.eos.inv_h), A.eos.y0 + (A.eos.n - 4) / A.eos.inv_h);
   }
   int i0;
-  double t, T, Meq, D, itr, B;
+  double t, w[6];
   eos_cell(A.eos, y, &i0, &t);
-  if constexpr (FAST) {  // fields that feed FP32 arithmetic: FP32 interpolation
-    float w[6];
-    lagrange6f((float)t, w);
-    const float Tf = expf((float)y);
-    T = Tf;
-    Meq = eos_fieldf(A.eos, i0, w, EOS_X) * Tf;
-    D = eos_fieldf(A.eos, i0, w, EOS_D);
-    itr = eos_fieldf(A.eos, i0, w, EOS_INVH) / (float)A.eta_over_s;
-    const float T2 = Tf * Tf;
-    B = eos_fieldf(A.eos, i0, w, EOS_B) * T2 * T2;
-  } else {
-    double w[6];
-    lagrange6(t, w);
-    T = exp(y);
-    Meq = eos_field(A.eos, i0, w, EOS_X) * T;
-    D = eos_field(A.eos, i0, w, EOS_D);
-    itr = eos_field(A.eos, i0, w, EOS_INVH) / A.eta_over_s;
-    const double T2 = T * T;
-    B = eos_field(A.eos, i0, w, EOS_B) * T2 * T2;
-  }
+  lagrange6(t, w);
+  const double T = exp(y);
+  const double Meq = eos_field(A.eos, i0, w, EOS_X) * T;
+  const double D = eos_field(A.eos, i0, w, EOS_D);
+  const double itr = eos_field(A.eos, i0, w, EOS_INVH) / A.eta_over_s;
+  const double T2 = T * T;
+  const double B = eos_field(A.eos, i0, w, EOS_B) * T2 * T2;
   if (!isfinite(T) || !isfinite(u[1]) || !isfinite(u[2]) || !isfinite(B)) err |= ERR_NONFINITE;
-  if (err) atomicOr(A.err, err);
   A.Tsite[site] = T;
-  double* o = A.sc + (size_t)site * kSc;
   o[SC_UT] = u[0]; o[SC_UX] = u[1]; o[SC_UY] = u[2];
   o[SC_INVT] = 1.0 / T; o[SC_MEQ] = Meq; o[SC_M] = M; o[SC_ITR] = itr; o[SC_D] = D;
   o[SC_B] = B; o[SC_K] = pref * m[0]; o[SC_KH] = m[0]; o[SC_T] = T;
   {
-    const int x = site % A.nx, y = site / A.nx;
+    const int x = site % A.nx, yy = site / A.nx;
     const int xp = x + 1 == A.nx ? 0 : x + 1, xm = x == 0 ? A.nx - 1 : x - 1;
-    const int yp = y + 1 == A.ny ? 0 : y + 1, ym = y == 0 ? A.ny - 1 : y - 1;
-    o[SC_AX] = (A.lnM[y * A.nx + xp] - A.lnM[y * A.nx + xm]) * A.inv2dx;
+    const int yp = yy + 1 == A.ny ? 0 : yy + 1, ym = yy == 0 ? A.ny - 1 : yy - 1;
+    o[SC_AX] = (A.lnM[yy * A.nx + xp] - A.lnM[yy * A.nx + xm]) * A.inv2dx;
     o[SC_AY] = (A.lnM[yp * A.nx + x] - A.lnM[ym * A.nx + x]) * A.inv2dx;
-  }
-  if (A.scf) {
-    float* of = A.scf + (size_t)site * kSc;
-#pragma unroll
-    for (int q = 0; q < kSc; ++q) of[q] = (float)o[q];
   }
   if (A.obs) {
     const double hc = 0.1973269804, h3 = hc * hc * hc;
@@ -493,6 +493,105 @@ __global__ void __launch_bounds__(128) match_kernel(const MatchArgs A) {
     r[5] = M;
     r[6] = (pref * m[7] - B) / h3;
     r[7] = Meq;
+  }
+  return err;
+}
+
+// The same matching in FP32 arithmetic (FP32 and BF16 storage paths, whose
+// kernels consume the site scalars in FP32).  On GB300 an FP64 warp
+// instruction occupies the pipe for 64 cycles, so the matching keeps FP64 only
+// for the differences of ln M (central differences of nearly equal values).
+__device__ __forceinline__ int match_site_f(const MatchArgs& A, int site, float (&o)[kSc]) {
+  float m[kMom];
+  const float4* q = reinterpret_cast<const float4*>(A.momf + (size_t)site * 2 * kMom);
+#pragma unroll
+  for (int i = 0; i < kMom / 2; ++i) {
+    const float4 v = __ldg(q + i);  // (hi, lo) pairs of two moments
+    m[2 * i] = v.x + v.y;
+    m[2 * i + 1] = v.z + v.w;
+  }
+  const double lnMd = A.lnM[site];
+  const float M = expf((float)lnMd);
+  const float M2 = M * M;
+  const float pref = M2 * M2 * (float)(1.0 / (2.0 * 3.14159265358979323846 * 3.14159265358979323846));
+  float tm[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) tm[i] = pref * m[1 + i];
+  int err = 0;
+  float u[3], eps;
+  if (!landau3f(tm, u, &eps)) {
+    err |= ERR_LANDAU;
+    u[0] = 1.f; u[1] = 0.f; u[2] = 0.f;
+    eps = fmaxf(tm[0], 1e-30f);
+  }
+  const float Tg = (float)A.Tsite[site];
+  const float yg = (Tg > 0.f) ? logf(Tg) : 0.f;
+  float y;
+  if (!eos_invert_f(A.eos, EOS_E, eps, yg, &y)) {
+    err |= ERR_EOS;
+    y = fminf(fmaxf(yg, (float)(A.eos.y0 + 2.0 / A.eos.inv_h)), (float)(A.eos.y0 + (A.eos.n - 4) / A.eos.inv_h));
+  }
+  int i0;
+  float t, w[6];
+  eos_cellf(A.eos, y, &i0, &t);
+  lagrange6f(t, w);
+  const float T = expf(y);
+  const float Meq = eos_fieldf(A.eos, i0, w, EOS_X) * T;
+  const float D = eos_fieldf(A.eos, i0, w, EOS_D);
+  const float itr = eos_fieldf(A.eos, i0, w, EOS_INVH) / (float)A.eta_over_s;
+  const float T2 = T * T;
+  const float B = eos_fieldf(A.eos, i0, w, EOS_B) * T2 * T2;
+  if (!isfinite(T) || !isfinite(u[1]) || !isfinite(u[2]) || !isfinite(B)) err |= ERR_NONFINITE;
+  A.Tsite[site] = (double)T;
+  o[SC_UT] = u[0]; o[SC_UX] = u[1]; o[SC_UY] = u[2];
+  o[SC_INVT] = 1.f / T; o[SC_MEQ] = Meq; o[SC_M] = M; o[SC_ITR] = itr; o[SC_D] = D;
+  o[SC_B] = B; o[SC_K] = pref * m[0]; o[SC_KH] = m[0]; o[SC_T] = T;
+  {
+    const int x = site % A.nx, yy = site / A.nx;
+    const int xp = x + 1 == A.nx ? 0 : x + 1, xm = x == 0 ? A.nx - 1 : x - 1;
+    const int yp = yy + 1 == A.ny ? 0 : yy + 1, ym = yy == 0 ? A.ny - 1 : yy - 1;
+    const float i2dx = (float)A.inv2dx;
+    o[SC_AX] = (float)(A.lnM[yy * A.nx + xp] - A.lnM[yy * A.nx + xm]) * i2dx;
+    o[SC_AY] = (float)(A.lnM[yp * A.nx + x] - A.lnM[ym * A.nx + x]) * i2dx;
+  }
+  if (A.obs) {
+    const double hc = 0.1973269804, h3 = hc * hc * hc;
+    double* r = A.obs + (size_t)site * 8;
+    r[0] = ((double)eps + (double)B) / h3;
+    r[1] = T;
+    r[2] = u[0]; r[3] = u[1]; r[4] = u[2];
+    r[5] = M;
+    r[6] = ((double)pref * (double)m[7] - (double)B) / h3;
+    r[7] = Meq;
+  }
+  return err;
+}
+
+// Matching of every site, one thread per site.  FAST: FP32 arithmetic, results
+// to scf only; otherwise FP64, results to sc (and scf when set).
+template <bool FAST>
+__global__ void __launch_bounds__(128) match_kernel(const MatchArgs A) {
+  const int site = blockIdx.x * blockDim.x + threadIdx.x;
+  if (site >= A.ns) return;
+  if constexpr (FAST) {
+    float o[kSc];
+    const int err = match_site_f(A, site, o);
+    if (err) atomicOr(A.err, err);
+    float* of = A.scf + (size_t)site * kSc;
+#pragma unroll
+    for (int q = 0; q < kSc; ++q) of[q] = o[q];
+  } else {
+    double o[kSc];
+    const int err = match_site_d(A, site, o);
+    if (err) atomicOr(A.err, err);
+    double* od = A.sc + (size_t)site * kSc;
+#pragma unroll
+    for (int q = 0; q < kSc; ++q) od[q] = o[q];
+    if (A.scf) {
+      float* of = A.scf + (size_t)site * kSc;
+#pragma unroll
+      for (int q = 0; q < kSc; ++q) of[q] = (float)o[q];
+    }
   }
 }
 
@@ -649,7 +748,7 @@ struct StageArgs {
   int nx, ny;
   int mode;               // 0 predictor, 1 corrector
   double dtau, inv2dx;    // FP64 copies for the per-site (thread 0) arithmetic
-  R milne;                // 1/tau in the Milne metric, 0 in Minkowski
+  R milne;                // 1/tau in the Milne metric, 0 in Minkowski (op.Dth is pre-scaled by it)
   R dtau_r, inv2dx_r, Z;  // the same constants in the compute precision
   Ops<R, NXI, NTH, NPH> op;
 };
@@ -674,7 +773,7 @@ __global__ void __launch_bounds__(NTH* NPH)
   __shared__ double redd[kMom * NW];
   __shared__ float redf[2 * kMom * NW];
   __shared__ R gsh;
-  __shared__ R Etab[NXI], iEtab[NXI];
+  __shared__ __align__(16) R Etab[2 * NXI];  // (E_eq, 1/E_eq) per radial node
 
   // 1. own xi-line and the upwind neighbours for streaming
   R f[NXI];
@@ -714,8 +813,8 @@ __global__ void __launch_bounds__(NTH* NPH)
   const R M2 = M * M;
   if (t < NXI) {
     const R e = fsqrt<R>(Meq * Meq + M2 * op.s2[t]);
-    Etab[t] = e;
-    iEtab[t] = (R)1 / e;
+    Etab[2 * t] = e;
+    Etab[2 * t + 1] = (R)1 / e;
   }
 #pragma unroll
   for (int k = 0; k < NXI; ++k) fs[k * LD + t] = f[k];
@@ -729,17 +828,19 @@ __global__ void __launch_bounds__(NTH* NPH)
   }
   __syncthreads();
   const R milne = A.milne;
-  for (int it = t; it < NXI * NPH; it += NL) {  // polar lines (k', l'): (1/tau) Dth along j
-    const int kq = it % NXI, lq = it / NXI;
-    R g[NTH];
+  if (milne != (R)0) {
+    for (int it = t; it < NXI * NPH; it += NL) {  // polar lines (k', l'): (1/tau) Dth along j
+      const int kq = it % NXI, lq = it / NXI;
+      R g[NTH];
 #pragma unroll
-    for (int jj = 0; jj < NTH; ++jj) g[jj] = fs[kq * LD + lq * NTH + jj];
+      for (int jj = 0; jj < NTH; ++jj) g[jj] = fs[kq * LD + lq * NTH + jj];
 #pragma unroll
-    for (int jp = 0; jp < NTH; ++jp) {
-      R dth = 0;
+      for (int jp = 0; jp < NTH; ++jp) {
+        R dth = 0;
 #pragma unroll
-      for (int jj = 0; jj < NTH; ++jj) dth += op.Dth[jp * NTH + jj] * g[jj];
-      pth[kq * LD + lq * NTH + jp] = milne * dth;
+        for (int jj = 0; jj < NTH; ++jj) dth += op.Dth[jp * NTH + jj] * g[jj];
+        pth[kq * LD + lq * NTH + jp] = dth;
+      }
     }
   }
   __syncthreads();
@@ -747,41 +848,41 @@ __global__ void __launch_bounds__(NTH* NPH)
   // 3. right-hand side on the own xi-line.  With vu = (v.u)/sinh, A1 = (a.v)/sinh:
   //    f_eq  = Z exp((M vu sinh - u^tau E_eq)/T)
   //    force = -(f_eq/(T cosh)) [A1 u^tau M^2 sinh (sinh^2+1)/E_eq - A1 M vu sinh^2 - M a.u]
+  //          = f_eq [Gp q1/E_eq + Hp q2 + Jp/cosh]
   //    coll  = -(f - f_eq) (u^tau - tanh vu)/tau_R,    pu = cosh u^tau - sinh vu
   const R ax = scl[SC_AX], ay = scl[SC_AY];
   const R st = op.sth[j], mu2 = op.mu2[j];
   const R vu = st * (cp * ux + sp * uy);
   const R A1 = st * (ax * cp + ay * sp);
   const R au = ax * ux + ay * uy;
-  const R ax_abs = st * (cp < 0 ? -cp : cp) * A.inv2dx_r;
-  const R ay_abs = st * (sp < 0 ? -sp : sp) * A.inv2dx_r;
+  const R nsx = -st * (cp < 0 ? -cp : cp) * A.inv2dx_r;
+  const R nsy = -st * (sp < 0 ? -sp : sp) * A.inv2dx_r;
   const R wj = op.wj[j];
   const R milne_mu2 = milne * mu2;
-  // exponent of f_eq (natural log for FP64, log2 for the FP32 ex2 path)
   constexpr bool kF = sizeof(R) == 4;
-  const R lsc = kF ? (R)1.4426950408889634 : (R)1;
+  const R lsc = kF ? (R)1.4426950408889634 : (R)1;  // exp2 in FP32, exp in FP64
   const R c1 = -lsc * invT * ut, c2 = lsc * invT * M * vu;
   const R lZ = kF ? (R)log2f((float)A.Z) : (R)0;
-  const R G = A1 * ut * M2, H = A1 * M * vu, J = M * au;
-  const R nutr = -ut * itr, vtr = vu * itr;
+  const R Gp = -invT * A1 * ut * M2, Hp = invT * A1 * M * vu, Jp = invT * M * au;
+  const R cc0 = ut * itr, cc1 = -vu * itr;
+  const bool pol = milne != (R)0;
   R Rn[NXI];
   R sA = 0, sQ = 0, sE = 0;
 #pragma unroll
   for (int k = 0; k < NXI; ++k) {
-    const R s = op.s[k], c = op.c[k], ic = op.inv_c[k], s2 = op.s2[k];
-    const R tv = s * ic;  // tanh(xi)
-    const R E = Etab[k], iE = iEtab[k];
-    const R stream = -tv * (ax_abs * ((R)3 * f[k] - (R)4 * fx1[k] + fx2[k]) +
-                            ay_abs * ((R)3 * f[k] - (R)4 * fy1[k] + fy2[k]));
+    const R E = Etab[2 * k], iE = Etab[2 * k + 1];
+    const R Sx = (R)3 * f[k] - (R)4 * fx1[k] + fx2[k];
+    const R Sy = (R)3 * f[k] - (R)4 * fy1[k] + fy2[k];
+    R r = op.tv[k] * (nsx * Sx + nsy * Sy) + milne_mu2 * Drf[k];
+    if (pol) r += pth[k * LD + t];
     R feq;
-    if constexpr (kF) feq = exp2f(c1 * E + (c2 * s + lZ));
-    else feq = A.Z * exp(c1 * E + c2 * s);
-    const R bracket = G * (s * (s2 + (R)1)) * iE - H * s2 - J;
-    const R force = -(feq * invT * ic) * bracket;
-    const R coll = (feq - f[k]) * (-(nutr + tv * vtr));
-    const R r = stream + milne_mu2 * Drf[k] + pth[k * LD + t] + force + coll;
+    if constexpr (kF) feq = ex2_ftz(c1 * E + (c2 * op.s[k] + lZ));
+    else feq = A.Z * exp(c1 * E + c2 * op.s[k]);
+    const R fc = (Gp * op.q1[k]) * iE + (Hp * op.q2[k] + Jp * op.inv_c[k]);
+    const R cc = cc0 + cc1 * op.tv[k];
+    r += feq * (fc + cc) - f[k] * cc;
     Rn[k] = r;
-    const R pu = c * ut - s * vu;
+    const R pu = op.c[k] * ut - op.s[k] * vu;
     const R wpu2 = (wj * op.ecw[k]) * (pu * pu);
     sA += wpu2 * r;
     sQ += wpu2 * Drf[k];
