@@ -271,7 +271,7 @@ def finish(args, rank, world, t, value, achieved, peak, peak_kind, b, nn, launch
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
-                         "peak_source": peak_kind, "kernel": "stage_kernel (fused stream-collide)",
+                         "peak_source": peak_kind, "kernel": "stage_kernel_x2 (fused stream-collide, packed FP32 pairs)",
                          "algorithmic_bytes_per_update": 5 * b, **kern},
             "e2e": e2e,
             "gpu_launches": launches,

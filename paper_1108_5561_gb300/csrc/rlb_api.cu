@@ -1,17 +1,21 @@
 // rlb_api.cu -- C ABI (include/rlb.h) of the GB300 lattice Boltzmann step.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <string>
 #include <mutex>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
 #include "../../include/rlb.h"
 #include "rlb_host.hpp"
 #include "rlb_kernels.cuh"
+#include "rlb_stage_x2.cuh"
 
 struct rlb_ctx {
   int device = 0;
@@ -78,8 +82,10 @@ void layout(const rlb_grid_params& g, size_t table_points, size_t* state_b, size
   size_t lnMs_off = off; off += mb;
   size_t T_off = off; off += mb;
   size_t eps_off = off; off += mb;
-  size_t mom_off = off; off += align256(ns * rlbk::kMom * sizeof(double));
-  size_t moms_off = off; off += align256(ns * rlbk::kMom * sizeof(double));
+  // moments: kMom doubles per site (FP64 storage) or kMom x kMomParts floats
+  const size_t momb = align256(ns * std::max(rlbk::kMom * sizeof(double), rlbk::kMom * rlbk::kMomParts * sizeof(float)));
+  size_t mom_off = off; off += momb;
+  size_t moms_off = off; off += momb;
   size_t sc_off = off; off += align256(ns * rlbk::kSc * sizeof(double));
   size_t err_off = off; off += 256;
   size_t tab_off = off; off += align256((table_points + 6) * rlb::kFields * sizeof(double));
@@ -115,6 +121,41 @@ rlbk::Ops<R, NXI, NTH, NPH> make_ops(const rlb::Lattice& L) {
   return o;
 }
 
+template <int NXI, int NTH, int NPH>
+rlbk::OpsX2<NXI, NTH, NPH> make_ops_x2(const rlb::Lattice& L) {
+  rlbk::OpsX2<NXI, NTH, NPH> o;
+  constexpr int NP = NXI / 2;
+  auto pr = [](double a, double b) { return make_float2((float)a, (float)b); };
+  for (int k = 0; k < NXI; ++k)
+    for (int p = 0; p < NP; ++p) o.Drb[k * NP + p] = pr(L.Dr[(2 * p) * NXI + k], L.Dr[(2 * p + 1) * NXI + k]);
+  for (int i = 0; i < NTH * NTH; ++i) o.Dthb[i] = pr(L.Dth[i], L.Dth[i]);
+  for (int p = 0; p < NP; ++p) {
+    double c[2], s[2], e[2];
+    for (int h = 0; h < 2; ++h) { c[h] = L.c[2 * p + h]; s[h] = L.s[2 * p + h]; e[h] = L.ecw[2 * p + h]; }
+    o.tv[p] = pr(s[0] / c[0], s[1] / c[1]);
+    o.s[p] = pr(s[0], s[1]);
+    o.q2[p] = pr(s[0] * s[0] / c[0], s[1] * s[1] / c[1]);
+    o.ic[p] = pr(1.0 / c[0], 1.0 / c[1]);
+    o.Cw[p] = pr(c[0] * std::sqrt(e[0]), c[1] * std::sqrt(e[1]));
+    o.Sw[p] = pr(s[0] * std::sqrt(e[0]), s[1] * std::sqrt(e[1]));
+    o.w0[p] = pr(e[0], e[1]);
+    o.w1[p] = pr(e[0] * c[0] * s[0], e[1] * c[1] * s[1]);
+    o.w2[p] = pr(e[0] * c[0] * c[0], e[1] * c[1] * c[1]);
+    o.w3[p] = pr(e[0] * s[0] * s[0], e[1] * s[1] * s[1]);
+  }
+  for (int k = 0; k < NXI; ++k) {
+    const double c = L.c[k], s = L.s[k];
+    o.s2[k] = (float)(s * s);
+    o.q1[k] = (float)(s * (s * s + 1.0) / c);
+  }
+  for (int j = 0; j < NTH; ++j) {
+    o.sth[j] = (float)L.sth[j]; o.mu[j] = (float)L.mu[j]; o.mu2[j] = (float)(L.mu[j] * L.mu[j]);
+    o.wj[j] = (float)(L.wth[j] / (2.0 * NPH));
+  }
+  for (int l = 0; l < NPH; ++l) { o.cph[l] = (float)L.cph[l]; o.sph[l] = (float)L.sph[l]; }
+  return o;
+}
+
 // Table geometry of an EosView, including the split constants of the FP32 cell
 // location (see EosView).
 void eos_geometry(const rlb::EosTable& tab, rlbk::EosView* v) {
@@ -137,8 +178,6 @@ rlbk::EosView eos_view(const rlb_ctx* c) {
 }
 
 enum Kind { K_STAGE = 0, K_MATCH = 1, K_INIT = 2 };
-
-dim3 grid2d(const rlb_ctx* c) { return dim3((unsigned)c->gp.nx, (unsigned)c->gp.ny, 1); }
 
 // Set the Milne factor 1/tau of one launch and fold it into the polar operator.
 template <class R, int NXI, int NTH, int NPH>
@@ -180,7 +219,7 @@ struct Timed {
 rlbk::MatchArgs match_args(rlb_ctx* ctx, const double* mom, const double* lnM, double* obs) {
   rlbk::MatchArgs a;
   a.mom = mom;
-  a.momf = reinterpret_cast<const float*>(mom);  // FP32 storage keeps (hi, lo) float pairs here
+  a.momf = reinterpret_cast<const float*>(mom);  // FP32 storage keeps kMomParts partial sums here
   a.inv2dx = 1.0 / (2.0 * ctx->gp.dx);
   a.nx = ctx->gp.nx;
   a.ny = ctx->gp.ny;
@@ -195,6 +234,75 @@ rlbk::MatchArgs match_args(rlb_ctx* ctx, const double* mom, const double* lnM, d
   a.ns = (int)ctx->ns;
   return a;
 }
+
+// One stage-kernel launch per call: the paired FP32 kernel where the lattice
+// allows it (FP32 arithmetic, even N_xi and N_theta, whole warps per site), the
+// generic one otherwise.
+template <class S, class R, int NXI, int NTH, int NPH>
+struct Stager {
+  static constexpr bool kX2 =
+      std::is_same<R, float>::value && NXI % 2 == 0 && NTH % 2 == 0 && (NTH * NPH) % 32 == 0;
+  static constexpr int NL = NTH * NPH;
+  rlbk::StageArgs<S, R, NXI, NTH, NPH> a;
+  rlbk::StageArgsX2<S, NXI, NTH, NPH> b;
+  const rlb::Lattice* lat = nullptr;
+  int metric = 0;
+  dim3 grid;
+
+  Stager(const rlb_ctx* ctx, const double* sc, const float* scf, int* err) {
+    lat = &ctx->lat;
+    metric = ctx->gp.metric;
+    grid = dim3((unsigned)ctx->gp.nx, (unsigned)ctx->gp.ny, 1);
+    const double dtau = ctx->gp.dtau, inv2dx = 1.0 / (2.0 * ctx->gp.dx);
+    if constexpr (kX2) {
+      b.scf = scf;
+      b.err = err;
+      b.nx = ctx->gp.nx;
+      b.ny = ctx->gp.ny;
+      b.dtau = dtau;
+      b.dtau_r = (float)dtau;
+      b.inv2dx_r = (float)inv2dx;
+      b.log2Z = (float)std::log2(ctx->eosp.Z);
+      b.op = make_ops_x2<NXI, NTH, NPH>(ctx->lat);
+    } else {
+      a.sc = sc;
+      a.scf = scf;
+      a.err = err;
+      a.nx = ctx->gp.nx;
+      a.ny = ctx->gp.ny;
+      a.dtau = dtau;
+      a.inv2dx = inv2dx;
+      a.dtau_r = (R)dtau;
+      a.inv2dx_r = (R)inv2dx;
+      a.Z = (R)ctx->eosp.Z;
+      a.op = make_ops<R, NXI, NTH, NPH>(ctx->lat);
+    }
+  }
+
+  // mode 0: predictor f_out = f_in + dtau rhs(f_in); mode 1: corrector
+  // f_out = (f_base + f_in + dtau rhs(f_in)) / 2; tau is the time of f_in.
+  void launch(const S* f_in, const double* lnM_in, const S* f_base, const double* lnM_base, S* f_out,
+              double* lnM_out, double* mom_out, int mode, double tau, cudaStream_t st) {
+    const double inv = metric ? 1.0 / tau : 0.0;
+    if constexpr (kX2) {
+      b.f_in = f_in; b.lnM_in = lnM_in; b.f_base = f_base; b.lnM_base = lnM_base;
+      b.f_out = f_out; b.lnM_out = lnM_out; b.momf_out = reinterpret_cast<float*>(mom_out);
+      b.mode = mode;
+      b.milne = (float)inv;
+      for (int i = 0; i < NTH * NTH; ++i) {
+        const float v = (float)(lat->Dth[i] * inv);
+        b.op.Dthb[i] = make_float2(v, v);
+      }
+      rlbk::stage_kernel_x2<S, NXI, NTH, NPH><<<grid, NL, 0, st>>>(b);
+    } else {
+      a.f_in = f_in; a.lnM_in = lnM_in; a.f_base = f_base; a.lnM_base = lnM_base;
+      a.f_out = f_out; a.lnM_out = lnM_out; a.mom_out = mom_out; a.momf_out = reinterpret_cast<float*>(mom_out);
+      a.mode = mode;
+      set_milne<R, NXI, NTH, NPH>(a.op, *lat, metric, tau, &a.milne);
+      rlbk::stage_kernel<S, R, NXI, NTH, NPH><<<grid, NL, 0, st>>>(a);
+    }
+  }
+};
 
 rlb_status match(rlb_ctx* ctx, const double* mom, const double* lnM, double* obs, cudaStream_t st) {
   const rlbk::MatchArgs a = match_args(ctx, mom, lnM, obs);
@@ -237,49 +345,32 @@ struct Runner {
 
   // One predictor-corrector step = match(f) -> stage(f -> f*) -> match(f*) -> stage(f*, f -> f).
   static rlb_status step(rlb_ctx* ctx, int nsteps, cudaStream_t st) {
-    rlbk::StageArgs<S, R, NXI, NTH, NPH> a;
     S* f = reinterpret_cast<S*>(ctx->state + ctx->f_off);
     S* fs = reinterpret_cast<S*>(ctx->scratch + ctx->fs_off);
     double* m = reinterpret_cast<double*>(ctx->state + ctx->lnM_off);
     double* ms = reinterpret_cast<double*>(ctx->scratch + ctx->lnMs_off);
     double* mom = reinterpret_cast<double*>(ctx->scratch + ctx->mom_off);
     double* moms = reinterpret_cast<double*>(ctx->scratch + ctx->moms_off);
-    a.sc = reinterpret_cast<const double*>(ctx->scratch + ctx->sc_off);
-    a.scf = reinterpret_cast<const float*>(ctx->scratch + ctx->scf_off);
-    a.err = reinterpret_cast<int*>(ctx->scratch + ctx->err_off);
-    a.nx = ctx->gp.nx;
-    a.ny = ctx->gp.ny;
-    a.dtau = ctx->gp.dtau;
-    a.inv2dx = 1.0 / (2.0 * ctx->gp.dx);
-    a.dtau_r = (R)a.dtau;
-    a.inv2dx_r = (R)a.inv2dx;
-    a.Z = (R)ctx->eosp.Z;
-    a.op = make_ops<R, NXI, NTH, NPH>(ctx->lat);
+    Stager<S, R, NXI, NTH, NPH> sg(ctx, reinterpret_cast<const double*>(ctx->scratch + ctx->sc_off),
+                                   reinterpret_cast<const float*>(ctx->scratch + ctx->scf_off),
+                                   reinterpret_cast<int*>(ctx->scratch + ctx->err_off));
     for (int s = 0; s < nsteps; ++s) {
       // predictor: f* = f + dtau RHS(f) at tau
       rlb_status r = match(ctx, mom, m, nullptr, st);
       if (r) return r;
-      a.f_in = f; a.lnM_in = m; a.f_base = f; a.lnM_base = m;
-      a.f_out = fs; a.lnM_out = ms; a.mom_out = moms; a.momf_out = reinterpret_cast<float*>(moms);
-      a.mode = 0;
-      set_milne<R, NXI, NTH, NPH>(a.op, ctx->lat, ctx->gp.metric, ctx->tau, &a.milne);
       {
         Timed tm(ctx, K_STAGE, st);
-        rlbk::stage_kernel<S, R, NXI, NTH, NPH><<<grid2d(ctx), NL, 0, st>>>(a);
+        sg.launch(f, m, f, m, fs, ms, moms, 0, ctx->tau, st);
       }
-      RLB_CUDA(cudaGetLastError(), "stage_kernel (predictor) launch");
+      RLB_CUDA(cudaGetLastError(), "stage kernel (predictor) launch");
       // corrector: f = (f + f* + dtau RHS(f*))/2 at tau + dtau, in place over f
       r = match(ctx, moms, ms, nullptr, st);
       if (r) return r;
-      a.f_in = fs; a.lnM_in = ms; a.f_base = f; a.lnM_base = m;
-      a.f_out = f; a.lnM_out = m; a.mom_out = mom; a.momf_out = reinterpret_cast<float*>(mom);
-      a.mode = 1;
-      set_milne<R, NXI, NTH, NPH>(a.op, ctx->lat, ctx->gp.metric, ctx->tau + ctx->gp.dtau, &a.milne);
       {
         Timed tm(ctx, K_STAGE, st);
-        rlbk::stage_kernel<S, R, NXI, NTH, NPH><<<grid2d(ctx), NL, 0, st>>>(a);
+        sg.launch(fs, ms, f, m, f, m, mom, 1, ctx->tau + ctx->gp.dtau, st);
       }
-      RLB_CUDA(cudaGetLastError(), "stage_kernel (corrector) launch");
+      RLB_CUDA(cudaGetLastError(), "stage kernel (corrector) launch");
       ctx->tau += ctx->gp.dtau;
     }
     return RLB_OK;
@@ -411,35 +502,16 @@ rlb_status step_static(rlb_ctx* ctx, char* state, char* scr, int nsteps, cudaStr
     RLB_CUDA(cudaGetLastError(), "match_kernel launch");
     return RLB_OK;
   };
-  rlbk::StageArgs<S, R, NXI, NTH, NPH> a;
-  a.sc = ma.sc;
-  a.scf = ma.scf;
-  a.err = err;
-  a.nx = ctx->gp.nx;
-  a.ny = ctx->gp.ny;
-  a.dtau = ctx->gp.dtau;
-  a.inv2dx = 1.0 / (2.0 * ctx->gp.dx);
-  a.dtau_r = (R)a.dtau;
-  a.inv2dx_r = (R)a.inv2dx;
-  a.Z = (R)ctx->eosp.Z;
-  a.op = op;
+  Stager<S, R, NXI, NTH, NPH> sg(ctx, ma.sc, ma.scf, err);
   for (int s = 0; s < nsteps; ++s) {
     rlb_status r = run_match(mom, m);
     if (r) return r;
-    a.f_in = f; a.lnM_in = m; a.f_base = f; a.lnM_base = m;
-    a.f_out = fs; a.lnM_out = ms; a.mom_out = moms; a.momf_out = reinterpret_cast<float*>(moms);
-    a.mode = 0;
-    set_milne<R, NXI, NTH, NPH>(a.op, ctx->lat, ctx->gp.metric, ctx->tau, &a.milne);
-    rlbk::stage_kernel<S, R, NXI, NTH, NPH><<<grid2d(ctx), NL, 0, st>>>(a);
-    RLB_CUDA(cudaGetLastError(), "stage_kernel (predictor) launch");
+    sg.launch(f, m, f, m, fs, ms, moms, 0, ctx->tau, st);
+    RLB_CUDA(cudaGetLastError(), "stage kernel (predictor) launch");
     r = run_match(moms, ms);
     if (r) return r;
-    a.f_in = fs; a.lnM_in = ms; a.f_base = f; a.lnM_base = m;
-    a.f_out = f; a.lnM_out = m; a.mom_out = mom; a.momf_out = reinterpret_cast<float*>(mom);
-    a.mode = 1;
-    set_milne<R, NXI, NTH, NPH>(a.op, ctx->lat, ctx->gp.metric, ctx->tau + ctx->gp.dtau, &a.milne);
-    rlbk::stage_kernel<S, R, NXI, NTH, NPH><<<grid2d(ctx), NL, 0, st>>>(a);
-    RLB_CUDA(cudaGetLastError(), "stage_kernel (corrector) launch");
+    sg.launch(fs, ms, f, m, f, m, mom, 1, ctx->tau + ctx->gp.dtau, st);
+    RLB_CUDA(cudaGetLastError(), "stage kernel (corrector) launch");
     ctx->tau += ctx->gp.dtau;
   }
   // report numeric failures of this call (the error word is shared)

@@ -410,7 +410,17 @@ __device__ bool landau3(const double tm[6], double u[3], double* eps) {
 
 // per-site moments (without the M^4/(2 pi^2) prefactor), 8 doubles per site:
 //   K^ = sum w f, T00, T01, T02, T11, T12, T22 (sum w f P^ P^), Tzz
+// FP32 storage keeps kMomParts float partial sums per moment instead
+// ([site][moment][part]); the moment is their sum.
 constexpr int kMom = 8;
+constexpr int kMomParts = 4;
+
+// (hi, lo) pairs of a compensated block sum -> the kMomParts layout
+__device__ __forceinline__ void store_mom_parts(float* dst, const float* pairs) {
+  float4* d = reinterpret_cast<float4*>(dst);
+#pragma unroll
+  for (int q = 0; q < kMom; ++q) d[q] = make_float4(pairs[2 * q], pairs[2 * q + 1], 0.f, 0.f);
+}
 // per-site matching results consumed by the stage kernel
 constexpr int kSc = 14;
 enum : int {
@@ -420,7 +430,7 @@ enum : int {
 
 struct MatchArgs {
   const double* mom;    // kMom per site (FP64 storage)
-  const float* momf;    // 2 kMom per site, (hi, lo) pairs (FP32 storage)
+  const float* momf;    // kMom x kMomParts partial sums per site (FP32 storage)
   const double* lnM;
   double* Tsite;        // Newton start in, T out
   double* sc;           // kSc per site
@@ -503,12 +513,11 @@ __device__ __forceinline__ int match_site_d(const MatchArgs& A, int site, double
 // for the differences of ln M (central differences of nearly equal values).
 __device__ __forceinline__ int match_site_f(const MatchArgs& A, int site, float (&o)[kSc]) {
   float m[kMom];
-  const float4* q = reinterpret_cast<const float4*>(A.momf + (size_t)site * 2 * kMom);
+  const float4* q = reinterpret_cast<const float4*>(A.momf + (size_t)site * kMom * kMomParts);
 #pragma unroll
-  for (int i = 0; i < kMom / 2; ++i) {
-    const float4 v = __ldg(q + i);  // (hi, lo) pairs of two moments
-    m[2 * i] = v.x + v.y;
-    m[2 * i + 1] = v.z + v.w;
+  for (int i = 0; i < kMom; ++i) {
+    const float4 v = __ldg(q + i);  // the partial sums of moment i
+    m[i] = (v.x + v.y) + (v.z + v.w);
   }
   const double lnMd = A.lnM[site];
   const float M = expf((float)lnMd);
@@ -637,8 +646,30 @@ __device__ __forceinline__ void warp_reduce_halving(float (&v)[NV], int lane) {
 template <int NV, int NT, class R>
 __device__ __forceinline__ void block_reduce(const R (&v)[NV], float* redf, double* redd) {
   constexpr int NW = (NT + 31) / 32;
+  static_assert(NT < 32 || NT % 32 == 0, "one partial warp or whole warps");
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if constexpr (sizeof(R) == 4) {
+  if constexpr (NT < 32) {
+    // a block of one partial warp: no shuffles (lanes >= NT do not exist);
+    // thread 0 sums the staged values in FP64
+    __shared__ double buf[NT * NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) buf[threadIdx.x * NV + q] = (double)v[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        double acc = 0.0;
+        for (int i = 0; i < NT; ++i) acc += buf[i * NV + q];
+        if constexpr (sizeof(R) == 4) {
+          const float hi = (float)acc;
+          redf[2 * q] = hi;
+          redf[2 * q + 1] = (float)(acc - (double)hi);
+        } else {
+          redd[q] = acc;
+        }
+      }
+    }
+  } else if constexpr (sizeof(R) == 4) {
     // pairwise sums inside each warp (recursive halving over the NV values,
     // padded to a power of two); the warp partials are combined with TwoSum so
     // the block total keeps a compensation term
@@ -743,7 +774,7 @@ struct StageArgs {
   S* f_out;
   double* lnM_out;
   double* mom_out;        // moments of f_out, kMom per site (FP64 storage)
-  float* momf_out;        // moments of f_out, (hi, lo) pairs (FP32 storage)
+  float* momf_out;        // moments of f_out, kMomParts partial sums (FP32 storage)
   int* err;
   int nx, ny;
   int mode;               // 0 predictor, 1 corrector
@@ -927,8 +958,7 @@ __global__ void __launch_bounds__(NTH* NPH)
   block_reduce<kMom, NL, R>(mom, redf, redd);
   if (t == 0) {
     if constexpr (sizeof(R) == 4) {
-#pragma unroll
-      for (int q = 0; q < 2 * kMom; ++q) A.momf_out[(size_t)site * 2 * kMom + q] = redf[q];
+      store_mom_parts(A.momf_out + (size_t)site * kMom * kMomParts, redf);
     } else {
 #pragma unroll
       for (int q = 0; q < kMom; ++q) A.mom_out[(size_t)site * kMom + q] = redd[q];
@@ -997,8 +1027,7 @@ __global__ void __launch_bounds__(NTH* NPH)
   block_reduce<kMom, NL, R>(mom, redf, redd);
   if (t == 0) {
     if constexpr (sizeof(R) == 4) {
-#pragma unroll
-      for (int q = 0; q < 2 * kMom; ++q) A.momf[(size_t)site * 2 * kMom + q] = redf[q];
+      store_mom_parts(A.momf + (size_t)site * kMom * kMomParts, redf);
     } else {
 #pragma unroll
       for (int q = 0; q < kMom; ++q) A.mom[(size_t)site * kMom + q] = redd[q];
@@ -1035,8 +1064,7 @@ __global__ void __launch_bounds__(NTH* NPH)
   block_reduce<kMom, NL, R>(mom, redf, redd);
   if (t == 0) {
     if constexpr (sizeof(R) == 4) {
-#pragma unroll
-      for (int q = 0; q < 2 * kMom; ++q) A.momf[(size_t)site * 2 * kMom + q] = redf[q];
+      store_mom_parts(A.momf + (size_t)site * kMom * kMomParts, redf);
     } else {
 #pragma unroll
       for (int q = 0; q < kMom; ++q) A.mom[(size_t)site * kMom + q] = redd[q];

@@ -1,0 +1,319 @@
+// rlb_stage_x2.cuh -- the fused stream-collide stage in FP32 arithmetic with
+// packed pairs of radial nodes (FFMA2 / FADD2 / FMUL2, sm_100 and later).
+//
+// Same right-hand side as stage_kernel (Romatschke, arXiv:1108.5561, Sec. 4.3,
+// Eq. Bmilne with the BGK term of Sec. 4.1, Heun stages of Sec. 4.4):
+//   rhs = -V.grad f + (1/tau) [mu^2 Dr f + Dth f] + g Dr f + T_M f_eq
+//         - ((P.U)/E) (f - f_eq) / tau_R
+// Each thread owns one (theta_j, phi_l) line of radial nodes and holds it as
+// NXI/2 float2 pairs (xi_2p, xi_2p+1), so every per-node operation acts on two
+// nodes per instruction.  The per-node constants are stored as the matching
+// pairs in parameter space; the per-line scalars are broadcast to pairs once.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "rlb_kernels.cuh"
+
+namespace rlbk {
+
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// Per-run constants of the paired kernel (parameter space).
+template <int NXI, int NTH, int NPH>
+struct OpsX2 {
+  static constexpr int NP = NXI / 2;
+  float2 Drb[NXI * NP];    // [k * NP + p] = (Dr[2p][k], Dr[2p+1][k])
+  float2 Dthb[NTH * NTH];  // [jp * NTH + jj] = (1/tau) Dth[jp][jj] in both halves
+  float2 tv[NP], s[NP], q2[NP], ic[NP];  // tanh, sinh, sinh^2/cosh, 1/cosh
+  float2 Cw[NP], Sw[NP];                 // cosh sqrt(ecw), sinh sqrt(ecw)
+  float2 w0[NP], w1[NP], w2[NP], w3[NP];  // ecw * {1, c s, c^2, s^2}
+  float s2[NXI], q1[NXI];                 // sinh^2, sinh (sinh^2 + 1)/cosh
+  float sth[NTH], mu[NTH], mu2[NTH], wj[NTH];
+  float cph[NPH], sph[NPH];
+};
+
+template <class S, int NXI, int NTH, int NPH>
+struct StageArgsX2 {
+  const S* f_in;
+  const double* lnM_in;
+  const float* scf;       // FP32 matching of f_in, kSc per site
+  const S* f_base;        // corrector: populations at the start of the step
+  const double* lnM_base;
+  S* f_out;
+  double* lnM_out;
+  float* momf_out;        // moments of f_out: one partial sum per warp (kMomParts slots)
+  int* err;
+  int nx, ny;
+  int mode;               // 0 predictor, 1 corrector
+  double dtau;
+  float milne;            // 1/tau in the Milne metric (0: Minkowski); Dthb carries it
+  float dtau_r, inv2dx_r, log2Z;
+  OpsX2<NXI, NTH, NPH> op;
+};
+
+// line of NXI stored values -> NXI/2 FP32 pairs (vector loads where aligned)
+template <class S, int NP>
+__device__ __forceinline__ void load_pairs(const S* __restrict__ p, float2 (&v)[NP]) {
+  if constexpr (sizeof(S) == 4) {
+    if constexpr (NP % 2 == 0) {
+      const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+      for (int i = 0; i < NP / 2; ++i) {
+        const float4 a = __ldg(q + i);
+        v[2 * i] = make_float2(a.x, a.y);
+        v[2 * i + 1] = make_float2(a.z, a.w);
+      }
+    } else {
+      const float2* q = reinterpret_cast<const float2*>(p);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) v[i] = __ldg(q + i);
+    }
+  } else {
+    static_assert(sizeof(S) == 2, "FP32 or BF16 storage");
+    if constexpr (NP % 4 == 0) {
+      const uint4* q = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+      for (int i = 0; i < NP / 4; ++i) {
+        uint4 a = __ldg(q + i);
+        const __nv_bfloat162* b = reinterpret_cast<const __nv_bfloat162*>(&a);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) v[4 * i + h] = __bfloat1622float2(b[h]);
+      }
+    } else {
+      const __nv_bfloat162* q = reinterpret_cast<const __nv_bfloat162*>(p);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) v[i] = __bfloat1622float2(q[i]);
+    }
+  }
+}
+
+// FP32 pairs -> storage; returns in v what was stored (rounded to S)
+template <class S, int NP>
+__device__ __forceinline__ void store_pairs(S* __restrict__ p, float2 (&v)[NP]) {
+  if constexpr (sizeof(S) == 4) {
+    if constexpr (NP % 2 == 0) {
+      float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+      for (int i = 0; i < NP / 2; ++i) q[i] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
+    } else {
+      float2* q = reinterpret_cast<float2*>(p);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) q[i] = v[i];
+    }
+  } else {
+    __nv_bfloat162 b[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      b[i] = __float22bfloat162_rn(v[i]);
+      v[i] = __bfloat1622float2(b[i]);
+    }
+    if constexpr (NP % 4 == 0) {
+      uint4* q = reinterpret_cast<uint4*>(p);
+#pragma unroll
+      for (int i = 0; i < NP / 4; ++i) q[i] = *reinterpret_cast<const uint4*>(&b[4 * i]);
+    } else {
+      __nv_bfloat162* q = reinterpret_cast<__nv_bfloat162*>(p);
+#pragma unroll
+      for (int i = 0; i < NP; ++i) q[i] = b[i];
+    }
+  }
+}
+
+// 8 resident blocks of 96 threads cap the registers at 80: measured faster than
+// the uncapped 88 (fewer warps left waiting on memory)
+template <class S, int NXI, int NTH, int NPH>
+__global__ void __launch_bounds__(NTH* NPH, (NTH * NPH <= 96 ? 8 : 3))
+    stage_kernel_x2(const __grid_constant__ StageArgsX2<S, NXI, NTH, NPH> A) {
+  static_assert(NXI % 2 == 0 && NTH % 2 == 0, "paired radial nodes, half polar lines");
+  constexpr int NL = NTH * NPH;
+  constexpr int NN = NL * NXI;
+  constexpr int NP = NXI / 2;
+  constexpr int NW = (NL + 31) / 32;
+  static_assert(NL % 32 == 0, "whole warps (the warp reductions use every lane)");
+  static_assert(NW <= kMomParts, "one moment slot per warp");
+  constexpr int H = NTH / 2;
+  // staged site: pair p of line (l, j) at p * LDK + l * LDL + j (float2 units).
+  // LDL odd and LDK = 12 (mod 16) keep both the line-wise writes and the
+  // polar-line reads (consecutive l, then the next pair) nearly conflict free.
+  constexpr int LDL = NTH + 1;
+  constexpr int LDK = NPH * LDL + (((12 - NPH * LDL) % 16) + 16) % 16;
+  const auto& op = A.op;
+  const int x = blockIdx.x, y = blockIdx.y;
+  const int site = y * A.nx + x;
+  const int t = threadIdx.x;
+  const int j = t % NTH, l = t / NTH;
+
+  __shared__ float2 fs[NP * LDK];
+  __shared__ float2 pth[NP * LDK];
+  __shared__ float4 tab[NP];  // (E_eq at 2p, 2p+1;  q1/E_eq at 2p, 2p+1)
+  __shared__ float4 red[NW];  // per-warp partial sums for d ln M / d tau
+
+  // 1. own line and the upwind neighbours (periodic)
+  float2 f[NP];
+  load_pairs<S, NP>(A.f_in + (size_t)site * NN + t * NXI, f);
+  const float cp = op.cph[l], sp = op.sph[l];
+  const int sx = (cp > 0.f) ? -1 : 1, sy = (sp > 0.f) ? -1 : 1;
+  int x1 = x + sx, x2 = x + 2 * sx, y1 = y + sy, y2 = y + 2 * sy;
+  x1 += (x1 < 0) ? A.nx : (x1 >= A.nx ? -A.nx : 0);
+  x2 += (x2 < 0) ? A.nx : (x2 >= A.nx ? -A.nx : 0);
+  x2 += (x2 < 0) ? A.nx : (x2 >= A.nx ? -A.nx : 0);  // grids of one site
+  y1 += (y1 < 0) ? A.ny : (y1 >= A.ny ? -A.ny : 0);
+  y2 += (y2 < 0) ? A.ny : (y2 >= A.ny ? -A.ny : 0);
+  y2 += (y2 < 0) ? A.ny : (y2 >= A.ny ? -A.ny : 0);
+  float2 fx1[NP], fx2[NP], fy1[NP], fy2[NP];
+  load_pairs<S, NP>(A.f_in + (size_t)(y * A.nx + x1) * NN + t * NXI, fx1);
+  load_pairs<S, NP>(A.f_in + (size_t)(y * A.nx + x2) * NN + t * NXI, fx2);
+  load_pairs<S, NP>(A.f_in + (size_t)(y1 * A.nx + x) * NN + t * NXI, fy1);
+  load_pairs<S, NP>(A.f_in + (size_t)(y2 * A.nx + x) * NN + t * NXI, fy2);
+
+  // site scalars of the matching of f_in
+  const float* q = A.scf + (size_t)site * kSc;
+  const float ut = __ldg(q + SC_UT), ux = __ldg(q + SC_UX), uy = __ldg(q + SC_UY);
+  const float invT = __ldg(q + SC_INVT), Meq = __ldg(q + SC_MEQ), M = __ldg(q + SC_M);
+  const float itr = __ldg(q + SC_ITR), ax = __ldg(q + SC_AX), ay = __ldg(q + SC_AY);
+  const float M2 = M * M;
+  if (t < NP) {  // per-site radial table
+    const float e0 = sqrtf(Meq * Meq + M2 * op.s2[2 * t]), e1 = sqrtf(Meq * Meq + M2 * op.s2[2 * t + 1]);
+    tab[t] = make_float4(e0, e1, op.q1[2 * t] / e0, op.q1[2 * t + 1] / e1);
+  }
+
+  // 2. stage the site for the polar operator; radial operator on the own line
+#pragma unroll
+  for (int p = 0; p < NP; ++p) fs[p * LDK + l * LDL + j] = f[p];
+  float2 Drf[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) Drf[p] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < NXI; ++k) {
+    const float2 fk = bc2((k & 1) ? f[k >> 1].y : f[k >> 1].x);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) Drf[p] = fma2(op.Drb[k * NP + p], fk, Drf[p]);
+  }
+  __syncthreads();
+  const bool pol = A.milne != 0.f;
+  if (pol) {  // polar lines (pair, l), one half of the outputs per item
+    for (int it = t; it < NXI * NPH; it += NL) {
+      const int lq = it % NPH, r = it / NPH, kp = r % NP, half = r / NP;
+      const int base = kp * LDK + lq * LDL;
+      float2 g[NTH];
+#pragma unroll
+      for (int jj = 0; jj < NTH; ++jj) g[jj] = fs[base + jj];
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        if (half != hh) continue;
+#pragma unroll
+        for (int qq = 0; qq < H; ++qq) {
+          const int jp = hh * H + qq;
+          float2 acc = mul2(op.Dthb[jp * NTH], g[0]);
+#pragma unroll
+          for (int jj = 1; jj < NTH; ++jj) acc = fma2(op.Dthb[jp * NTH + jj], g[jj], acc);
+          pth[base + jp] = acc;
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  // 3. right-hand side on the own line (same algebra as stage_kernel):
+  //    f_eq = Z 2^(c1 E_eq + c2 sinh),  force = f_eq [Gp q1/E_eq + Hp q2 + Jp/cosh],
+  //    collision = -(f - f_eq) cc,  cc = (u^tau - tanh vu)/tau_R
+  const float st = op.sth[j];
+  const float vu = st * (cp * ux + sp * uy);
+  const float A1 = st * (ax * cp + ay * sp);
+  const float au = ax * ux + ay * uy;
+  const float2 nsx = bc2(-st * fabsf(cp) * A.inv2dx_r), nsy = bc2(-st * fabsf(sp) * A.inv2dx_r);
+  const float2 mmu2 = bc2(A.milne * op.mu2[j]);
+  constexpr float kLog2e = 1.4426950408889634f;
+  const float2 c1 = bc2(-kLog2e * invT * ut), c2 = bc2(kLog2e * invT * M * vu), lZ = bc2(A.log2Z);
+  const float2 Gp = bc2(-invT * A1 * ut * M2), Hp = bc2(invT * A1 * M * vu), Jp = bc2(invT * M * au);
+  const float2 cc0 = bc2(ut * itr), cc1 = bc2(-vu * itr);
+  const float2 ncc0 = bc2(-ut * itr), ncc1 = bc2(vu * itr);
+  const float2 utb = bc2(ut), nvub = bc2(-vu);
+  const float2 three = bc2(3.f), mfour = bc2(-4.f);
+  float2 Rn[NP];
+  float2 sA = make_float2(0.f, 0.f), sQ = sA, sE = sA;
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const float4 tb = tab[p];
+    const float2 E = make_float2(tb.x, tb.y), QE = make_float2(tb.z, tb.w);
+    const float2 Sx = fma2(mfour, fx1[p], fma2(three, f[p], fx2[p]));
+    const float2 Sy = fma2(mfour, fy1[p], fma2(three, f[p], fy2[p]));
+    float2 r = fma2(mmu2, Drf[p], mul2(op.tv[p], fma2(nsy, Sy, mul2(nsx, Sx))));
+    if (pol) r = add2(r, pth[p * LDK + l * LDL + j]);
+    const float2 ex = fma2(c1, E, fma2(c2, op.s[p], lZ));
+    const float2 feq = make_float2(ex2_ftz(ex.x), ex2_ftz(ex.y));
+    const float2 cc = fma2(cc1, op.tv[p], cc0), ncc = fma2(ncc1, op.tv[p], ncc0);
+    const float2 fcc = fma2(Gp, QE, fma2(Hp, op.q2[p], fma2(Jp, op.ic[p], cc)));
+    r = fma2(f[p], ncc, fma2(feq, fcc, r));
+    Rn[p] = r;
+    const float2 pu = fma2(op.Sw[p], nvub, mul2(op.Cw[p], utb));
+    const float2 w = mul2(pu, pu);
+    sA = fma2(w, r, sA);
+    sQ = fma2(w, Drf[p], sQ);
+    sE = fma2(w, f[p], sE);
+  }
+  const float wj = op.wj[j];
+  // warp partial sums, then every thread combines the NW partials itself
+  const int lane = t & 31, wid = t >> 5;
+  {
+    float v4[4] = {wj * (sA.x + sA.y), wj * (sQ.x + sQ.y), wj * (sE.x + sE.y), 0.f};
+    warp_reduce_halving<4>(v4, lane);  // lane 8 qq holds value qq
+    const float s1 = __shfl_sync(0xffffffffu, v4[0], 8), s2 = __shfl_sync(0xffffffffu, v4[0], 16);
+    if (lane == 0) red[wid] = make_float4(v4[0], s1, s2, 0.f);
+  }
+  __syncthreads();
+  float Af = 0.f, Qf = 0.f, Ef = 0.f;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) {
+    const float4 rw = red[w];
+    Af += rw.x; Qf += rw.y; Ef += rw.z;
+  }
+  // d ln M / d tau from the consistency condition
+  const float D = __ldg(q + SC_D), Kh = __ldg(q + SC_KH);
+  const float g = (D == 0.f) ? 0.f : -D * Af / (Kh + D * (4.f * Ef + Qf - Kh));
+  if (t == 0) {
+    if (!isfinite(g)) atomicOr(A.err, (int)ERR_NONFINITE);
+    const double lnM = __ldg(A.lnM_in + site), gd = (double)g;
+    A.lnM_out[site] = A.mode == 0 ? lnM + A.dtau * gd : 0.5 * (__ldg(A.lnM_base + site) + lnM + A.dtau * gd);
+  }
+  const float2 gb = bc2(g), dt = bc2(A.dtau_r);
+  float2 out[NP];
+  if (A.mode == 0) {
+#pragma unroll
+    for (int p = 0; p < NP; ++p) out[p] = fma2(dt, fma2(gb, Drf[p], Rn[p]), f[p]);
+  } else {
+    float2 fb[NP];
+    load_pairs<S, NP>(A.f_base + (size_t)site * NN + t * NXI, fb);
+    const float2 half = bc2(0.5f), hdt = bc2(0.5f * A.dtau_r);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) out[p] = fma2(hdt, fma2(gb, Drf[p], Rn[p]), mul2(half, add2(fb[p], f[p])));
+  }
+  store_pairs<S, NP>(A.f_out + (size_t)site * NN + t * NXI, out);  // out now holds the stored values
+
+  // 4. moments of what was stored
+  float2 r0 = make_float2(0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    r0 = fma2(op.w0[p], out[p], r0);
+    r1 = fma2(op.w1[p], out[p], r1);
+    r2 = fma2(op.w2[p], out[p], r2);
+    r3 = fma2(op.w3[p], out[p], r3);
+  }
+  const float mu = op.mu[j];
+  const float a1 = wj * (r1.x + r1.y) * st, a3 = wj * (r3.x + r3.y) * st * st;
+  float mom[kMom] = {wj * (r0.x + r0.y), wj * (r2.x + r2.y), a1 * cp, a1 * sp,
+                     a3 * cp * cp, a3 * cp * sp, a3 * sp * sp, wj * (r3.x + r3.y) * mu * mu};
+  warp_reduce_halving<kMom>(mom, lane);  // lanes 4 qq .. 4 qq + 3 hold moment qq
+  // slot wid of moment qq; warp 0 also clears the slots no warp owns
+  float* dst = A.momf_out + (size_t)site * kMom * kMomParts + (lane >> 2) * kMomParts;
+  const int r = lane & 3;
+  if (r == 0) dst[wid] = mom[0];
+  else if (wid == 0 && r >= NW) dst[r] = 0.f;
+}
+
+}  // namespace rlbk
