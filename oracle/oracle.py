@@ -95,6 +95,7 @@ def _load():
         lib.or_step.argtypes = [vp, dp, dp, d, d, ctypes.c_int, ctypes.c_int]
         lib.or_rhs.argtypes = [vp, dp, dp, d, dp, dp, ctypes.c_int]
         lib.or_moments.argtypes = [vp, dp, dp, dp, ctypes.c_int]
+        lib.or_observables.argtypes = [vp, dp, dp, dp, ctypes.c_int]
         lib.or_init_state.argtypes = [vp, dp, dp, dp, ctypes.c_int]
         lib.or_step_sites.argtypes = [vp, dp, dp, d, d, ip, ctypes.c_int, dp, dp, ctypes.c_int]
         _lib = lib
@@ -223,6 +224,14 @@ class Oracle:
         out = np.zeros((self.ns, 8))
         _check(self._lib.or_moments(self._h, _dp(f), _dp(lnM), _dp(out), _nt(nthreads)), "moments")
         return out
+
+    def observables(self, f, lnM, nthreads: int = 0):
+        """(eps_p, v2 weighted by p_perp) of the whole grid."""
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        lnM = np.ascontiguousarray(lnM, dtype=np.float64)
+        out = np.zeros(2)
+        _check(self._lib.or_observables(self._h, _dp(f), _dp(lnM), _dp(out), _nt(nthreads)), "observables")
+        return float(out[0]), float(out[1])
 
     def step_sites(self, f, lnM, tau, dtau, sites, nthreads: int = 0):
         """One Heun step evaluated only at `sites` of a (possibly huge) grid."""

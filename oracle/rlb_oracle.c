@@ -890,6 +890,67 @@ int or_moments(const or_ctx* C, const double* f, const double* lnM, double* out,
   return err;
 }
 
+/* Observables of the whole grid.  The paper defines none; these are the
+ * usual heavy-ion ones, built from the paper's moments (Eq. emtnew) and its
+ * momentum weights (Sec. 4.3):
+ *   eps_p = sum_x (T^xx - T^yy) / sum_x (T^xx + T^yy),
+ *           T^{mu nu} = T_kin^{mu nu} + B(T) g^{mu nu}  (g^xx = g^yy = -1),
+ *   v2    = sum_{x,n} W_n p_perp,n cos(2 phi_n) f_n / sum_{x,n} W_n p_perp,n f_n,
+ *           W_n = M^2 w_n / (2 pi^2),  p_perp,n = M sinh xi_k sin theta_j.
+ * B(T) comes from matching each site.  out[0] = eps_p, out[1] = v2.  The sums
+ * over sites run in site order. */
+int or_observables(const or_ctx* C, const double* f, const double* lnM, double* out, int nthreads) {
+  const int ns = C->P.nx * C->P.ny, nn = C->nn;
+  double* part = (double*)malloc(sizeof(double) * 4 * (size_t)ns);
+  if (!part) return OR_ERR_NUMERIC;
+  int err = OR_OK;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(nthreads > 0 ? nthreads : 1) schedule(static)
+#endif
+  for (int i = 0; i < ns; ++i) {
+    or_site o;
+    const double* fi = f + (size_t)i * nn;
+    int rc = match_site(C, fi, lnM[i], 0.3, &o);
+    if (rc) {
+#ifdef _OPENMP
+#pragma omp critical(or_err3)
+#endif
+      err = rc;
+      continue;
+    }
+    double txx = 0.0, tyy = 0.0, num = 0.0, den = 0.0;
+    for (int l = 0; l < C->nph; ++l)
+      for (int j = 0; j < C->nth; ++j)
+        for (int k = 0; k < C->nxi; ++k) {
+          const double w = C->ecw[k] * C->wth[j] / (2.0 * C->nph);
+          const double fn = fi[(l * C->nth + j) * C->nxi + k];
+          const double vx = C->s[k] * C->sth[j] * C->cph[l], vy = C->s[k] * C->sth[j] * C->sph[l];
+          const double vperp = C->s[k] * C->sth[j];
+          const double cos2phi = C->cph[l] * C->cph[l] - C->sph[l] * C->sph[l];
+          txx += w * fn * vx * vx;
+          tyy += w * fn * vy * vy;
+          num += w * fn * vperp * cos2phi;
+          den += w * fn * vperp;
+        }
+    const double M = o.M, m4 = M * M * M * M / (2.0 * OR_PI * OR_PI), m3 = M * M * M / (2.0 * OR_PI * OR_PI);
+    part[4 * (size_t)i + 0] = m4 * txx - o.B;
+    part[4 * (size_t)i + 1] = m4 * tyy - o.B;
+    part[4 * (size_t)i + 2] = m3 * num;
+    part[4 * (size_t)i + 3] = m3 * den;
+  }
+  double sxx = 0.0, syy = 0.0, sn = 0.0, sd = 0.0;
+  for (int i = 0; i < ns; ++i) {
+    sxx += part[4 * (size_t)i + 0];
+    syy += part[4 * (size_t)i + 1];
+    sn += part[4 * (size_t)i + 2];
+    sd += part[4 * (size_t)i + 3];
+  }
+  free(part);
+  out[0] = (sxx - syy) / (sxx + syy);
+  out[1] = sn / sd;
+  return err;
+}
+
 /* initial state: T from eps_EOS(T) = eps0, M = M(T), u = 0, f = f_eq */
 int or_init_state(const or_ctx* C, const double* eps0, double* f, double* lnM, int nthreads) {
   const int ns = C->P.nx * C->P.ny, nn = C->nn;
