@@ -175,6 +175,21 @@ rlb_status rlb_step(rlb_ctx* ctx, int nsteps, void* stream);
  * management only. */
 rlb_status rlb_step_static_scratch(rlb_ctx* ctx, void* state, int nsteps, void* stream);
 
+/* Checkpoint and restart.  A state blob holds a header (grid, lattice and
+ * precision it belongs to, and tau), the populations f, ln M, the per-site
+ * Newton starting temperatures and the stored moments of f, so that a run
+ * restarted from a blob continues bit for bit like the uninterrupted run (same
+ * library build, same GPU).  rlb_state_blob_size gives the bytes (configured
+ * context).  rlb_save_state copies the current state into `host_buf` (host
+ * memory of at least that size; synchronises `stream`); rlb_load_state checks
+ * the header against the configured grid (RLB_ERR_ARG on a mismatch or a short
+ * buffer, the message says which) and replaces the state, tau included; eta/s,
+ * dtau and the EOS are taken from the context, not from the blob.  The paper's
+ * scheme needs exactly this state to continue (Sec. 4.4: f, M and T at tau). */
+rlb_status rlb_state_blob_size(const rlb_ctx* ctx, size_t* bytes);
+rlb_status rlb_save_state(rlb_ctx* ctx, void* host_buf, size_t bytes, void* stream);
+rlb_status rlb_load_state(rlb_ctx* ctx, const void* host_buf, size_t bytes, void* stream);
+
 /* Current proper time (host bookkeeping, fm/c). */
 rlb_status rlb_get_tau(const rlb_ctx* ctx, double* tau);
 
@@ -184,6 +199,19 @@ rlb_status rlb_get_tau(const rlb_ctx* ctx, double* tau);
  * `out` is host memory (synchronises `stream`) or device memory
  * (out_on_device != 0, asynchronous). */
 rlb_status rlb_moments(rlb_ctx* ctx, double* out, int out_on_device, void* stream);
+
+/* Grid observables of the current state (two host doubles; synchronises
+ * `stream`):
+ *   eps_p = sum_x (T^xx - T^yy) / sum_x (T^xx + T^yy)  (momentum anisotropy,
+ *           T^{mu nu} = T_kin^{mu nu} + B(T) g^{mu nu}, lab-frame components),
+ *   v2_pt = sum_{x,n} W_n p_perp,n cos(2 phi_n) f_n / sum_{x,n} W_n p_perp,n f_n
+ *           (elliptic flow weighted by transverse momentum, W_n = M^2 w_n/(2 pi^2),
+ *           p_perp,n = M sinh(xi_k) sin(theta_j)).
+ * Built on the moments of Eq. emtnew and the weights of Sec. 4.3; the paper
+ * itself defines no observables (these are the usual heavy-ion ones).  The
+ * matching needed for B(T) runs on the stored moments; a numeric failure there
+ * returns RLB_ERR_NUMERIC.  Sums over sites run in a fixed order in FP64. */
+rlb_status rlb_observables(rlb_ctx* ctx, double* eps_p, double* v2_pt, void* stream);
 
 /* Per-kernel device timing.  While enabled, every launch made by this
  * context is bracketed by CUDA events on its stream; rlb_get_timing waits for

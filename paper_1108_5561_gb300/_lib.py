@@ -16,7 +16,8 @@ RLB_MINKOWSKI, RLB_MILNE = 0, 1
 EXPORTS = ["rlb_create", "rlb_destroy", "rlb_last_error", "rlb_init_eos", "rlb_workspace_size",
            "rlb_configure", "rlb_bind_buffers", "rlb_init_grid", "rlb_step", "rlb_get_tau",
            "rlb_moments", "rlb_check", "rlb_state_offsets", "rlb_lattice", "rlb_operators",
-           "rlb_set_timing", "rlb_get_timing", "rlb_step_static_scratch"]
+           "rlb_set_timing", "rlb_get_timing", "rlb_step_static_scratch", "rlb_observables",
+           "rlb_state_blob_size", "rlb_save_state", "rlb_load_state"]
 
 
 class EosParamsC(ctypes.Structure):
@@ -81,6 +82,10 @@ def load(build_if_missing: bool = True):
     lib.rlb_set_timing.argtypes = [vp, ctypes.c_int]
     lib.rlb_step_static_scratch.argtypes = [vp, vp, ctypes.c_int, vp]
     lib.rlb_get_timing.argtypes = [vp, dp, P(ctypes.c_long), dp, P(ctypes.c_long)]
+    lib.rlb_observables.argtypes = [vp, dp, dp, vp]
+    lib.rlb_state_blob_size.argtypes = [vp, P(sz)]
+    lib.rlb_save_state.argtypes = [vp, vp, sz, vp]
+    lib.rlb_load_state.argtypes = [vp, vp, sz, vp]
     for name in EXPORTS:
         if name not in ("rlb_destroy", "rlb_last_error"):
             getattr(lib, name).restype = ctypes.c_int

@@ -377,13 +377,37 @@ struct Runner {
   }
 };
 
-enum Op { OP_INIT, OP_STEP, OP_MOMENTS };
+// Grid observables of the current state into out_dev[2] (device): matching of
+// the stored moments (for B), per-site partial sums, one fixed-order reduction.
+template <class S, class R, int NXI, int NTH, int NPH>
+rlb_status observables(rlb_ctx* ctx, double* out_dev, cudaStream_t st) {
+  constexpr int NL = NTH * NPH;
+  const double* mom = reinterpret_cast<const double*>(ctx->scratch + ctx->mom_off);
+  const double* lnM = reinterpret_cast<const double*>(ctx->state + ctx->lnM_off);
+  rlb_status r = match(ctx, mom, lnM, nullptr, st);
+  if (r) return r;
+  rlbk::ObsArgs<S, R, NXI, NTH, NPH> a;
+  a.f = reinterpret_cast<const S*>(ctx->state + ctx->f_off);
+  a.lnM = lnM;
+  a.sc = ctx->gp.prec == RLB_F64 ? reinterpret_cast<const double*>(ctx->scratch + ctx->sc_off) : nullptr;
+  a.scf = reinterpret_cast<const float*>(ctx->scratch + ctx->scf_off);
+  a.part = reinterpret_cast<double*>(ctx->scratch + ctx->moms_off);  // free between steps
+  a.op = make_ops<R, NXI, NTH, NPH>(ctx->lat);
+  rlbk::observables_kernel<S, R, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
+  RLB_CUDA(cudaGetLastError(), "observables_kernel launch");
+  rlbk::observables_reduce_kernel<<<1, 1024, 0, st>>>(a.part, (int)ctx->ns, out_dev);
+  RLB_CUDA(cudaGetLastError(), "observables_reduce_kernel launch");
+  return RLB_OK;
+}
+
+enum Op { OP_INIT, OP_STEP, OP_MOMENTS, OP_OBS };
 
 template <class S, class R, int NXI, int NTH, int NPH>
 rlb_status run_op(rlb_ctx* c, Op op, int n, double* p, cudaStream_t st) {
   using Rn = Runner<S, R, NXI, NTH, NPH>;
   if (op == OP_INIT) return Rn::init(c, p, st);
   if (op == OP_STEP) return Rn::step(c, n, st);
+  if (op == OP_OBS) return observables<S, R, NXI, NTH, NPH>(c, p, st);
   return RLB_ERR_ARG;
 }
 
@@ -742,6 +766,126 @@ rlb_status rlb_moments(rlb_ctx* ctx, double* out, int out_on_device, void* strea
   RLB_CUDA(cudaMemcpyAsync(out, dev, ctx->ns * 8 * sizeof(double), cudaMemcpyDeviceToHost, st),
            "moments download");
   return rlb_check(ctx, stream);
+}
+
+rlb_status rlb_observables(rlb_ctx* ctx, double* eps_p, double* v2_pt, void* stream) {
+  if (!ctx || !eps_p || !v2_pt) return RLB_ERR_ARG;
+  if (!ctx->inited) return fail(ctx, RLB_ERR_STATE, "rlb_init_grid must come first");
+  rlb_status s = set_device(ctx);
+  if (s) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double* dev = reinterpret_cast<double*>(ctx->scratch + ctx->eps_off);  // free between steps
+  s = dispatch(ctx, OP_OBS, 0, dev, st);
+  if (s) return s;
+  double h[2];
+  RLB_CUDA(cudaMemcpyAsync(h, dev, sizeof(h), cudaMemcpyDeviceToHost, st), "observables download");
+  s = rlb_check(ctx, stream);  // synchronises the stream
+  if (s) return s;
+  *eps_p = h[0];
+  *v2_pt = h[1];
+  return RLB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// checkpoint blob: header, f, ln M, Newton starting temperatures, stored moments
+// ---------------------------------------------------------------------------
+namespace {
+
+struct BlobHeader {
+  char magic[8];  // "RLBSTAT1"
+  uint32_t version;
+  int32_t prec, nx, ny, n_xi, n_theta, n_phi_half, family, metric;
+  double dx, z0, T0;
+  double tau;
+  uint64_t f_bytes, lnM_bytes, T_bytes, mom_bytes;
+};
+
+void blob_parts(const rlb_ctx* c, BlobHeader* h) {
+  std::memset(h, 0, sizeof(*h));
+  std::memcpy(h->magic, "RLBSTAT1", 8);
+  h->version = 1;
+  h->prec = c->gp.prec; h->nx = c->gp.nx; h->ny = c->gp.ny;
+  h->n_xi = c->gp.n_xi; h->n_theta = c->gp.n_theta; h->n_phi_half = c->gp.n_phi_half;
+  h->family = c->gp.family; h->metric = c->gp.metric;
+  h->dx = c->gp.dx; h->z0 = c->gp.z0; h->T0 = c->gp.T0;
+  h->tau = c->tau;
+  h->f_bytes = (uint64_t)c->ns * c->nn * c->pop_bytes;
+  h->lnM_bytes = (uint64_t)c->ns * sizeof(double);
+  h->T_bytes = (uint64_t)c->ns * sizeof(double);
+  h->mom_bytes = (uint64_t)c->ns * std::max(rlbk::kMom * sizeof(double), rlbk::kMom * rlbk::kMomParts * sizeof(float));
+}
+
+size_t blob_size(const BlobHeader& h) {
+  return sizeof(BlobHeader) + h.f_bytes + h.lnM_bytes + h.T_bytes + h.mom_bytes;
+}
+
+}  // namespace
+
+rlb_status rlb_state_blob_size(const rlb_ctx* ctx, size_t* bytes) {
+  if (!ctx || !bytes || !ctx->grid_ok) return RLB_ERR_ARG;
+  BlobHeader h;
+  blob_parts(ctx, &h);
+  *bytes = blob_size(h);
+  return RLB_OK;
+}
+
+rlb_status rlb_save_state(rlb_ctx* ctx, void* host_buf, size_t bytes, void* stream) {
+  if (!ctx || !host_buf) return RLB_ERR_ARG;
+  if (!ctx->inited) return fail(ctx, RLB_ERR_STATE, "nothing to save: rlb_init_grid or rlb_load_state first");
+  BlobHeader h;
+  blob_parts(ctx, &h);
+  if (bytes < blob_size(h)) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "state blob needs %zu bytes, buffer has %zu", blob_size(h), bytes);
+    return fail(ctx, RLB_ERR_ARG, buf);
+  }
+  rlb_status s = set_device(ctx);
+  if (s) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* p = static_cast<char*>(host_buf);
+  std::memcpy(p, &h, sizeof h);
+  p += sizeof h;
+  const struct { const char* src; uint64_t n; } parts[4] = {
+      {ctx->state + ctx->f_off, h.f_bytes}, {ctx->state + ctx->lnM_off, h.lnM_bytes},
+      {ctx->scratch + ctx->T_off, h.T_bytes}, {ctx->scratch + ctx->mom_off, h.mom_bytes}};
+  for (const auto& q : parts) {
+    RLB_CUDA(cudaMemcpyAsync(p, q.src, q.n, cudaMemcpyDeviceToHost, st), "state download");
+    p += q.n;
+  }
+  RLB_CUDA(cudaStreamSynchronize(st), "state download synchronise");
+  return RLB_OK;
+}
+
+rlb_status rlb_load_state(rlb_ctx* ctx, const void* host_buf, size_t bytes, void* stream) {
+  if (!ctx || !host_buf) return RLB_ERR_ARG;
+  if (!ctx->bound) return fail(ctx, RLB_ERR_STATE, "rlb_bind_buffers must come first");
+  BlobHeader want, got;
+  blob_parts(ctx, &want);
+  if (bytes < sizeof got) return fail(ctx, RLB_ERR_ARG, "state blob shorter than its header");
+  std::memcpy(&got, host_buf, sizeof got);
+  if (std::memcmp(got.magic, want.magic, 8) != 0 || got.version != want.version)
+    return fail(ctx, RLB_ERR_ARG, "not a state blob of this library version");
+  if (got.prec != want.prec || got.nx != want.nx || got.ny != want.ny || got.n_xi != want.n_xi ||
+      got.n_theta != want.n_theta || got.n_phi_half != want.n_phi_half || got.family != want.family ||
+      got.metric != want.metric || got.dx != want.dx || got.z0 != want.z0 || got.T0 != want.T0 ||
+      got.f_bytes != want.f_bytes || got.mom_bytes != want.mom_bytes)
+    return fail(ctx, RLB_ERR_ARG, "state blob was saved with another grid, lattice or precision");
+  if (bytes < blob_size(got)) return fail(ctx, RLB_ERR_ARG, "state blob is truncated");
+  rlb_status s = set_device(ctx);
+  if (s) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const char* p = static_cast<const char*>(host_buf) + sizeof got;
+  const struct { char* dst; uint64_t n; } parts[4] = {
+      {ctx->state + ctx->f_off, got.f_bytes}, {ctx->state + ctx->lnM_off, got.lnM_bytes},
+      {ctx->scratch + ctx->T_off, got.T_bytes}, {ctx->scratch + ctx->mom_off, got.mom_bytes}};
+  for (const auto& q : parts) {
+    RLB_CUDA(cudaMemcpyAsync(q.dst, p, q.n, cudaMemcpyHostToDevice, st), "state upload");
+    p += q.n;
+  }
+  RLB_CUDA(cudaStreamSynchronize(st), "state upload synchronise");
+  ctx->tau = got.tau;
+  ctx->inited = true;
+  return RLB_OK;
 }
 
 rlb_status rlb_set_timing(rlb_ctx* ctx, int enable) {

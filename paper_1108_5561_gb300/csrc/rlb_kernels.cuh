@@ -1072,4 +1072,81 @@ __global__ void __launch_bounds__(NTH* NPH)
   }
 }
 
+// ---------------------------------------------------------------------------
+// grid observables (no counterpart in the paper; the usual heavy-ion forms on
+// the paper's moments, Eq. emtnew, and momentum weights, Sec. 4.3):
+//   eps_p = sum_x (T^xx - T^yy) / sum_x (T^xx + T^yy),  T = T_kin + B g
+//   v2    = sum_{x,n} W_n p_perp,n cos 2phi_n f_n / sum_{x,n} W_n p_perp,n f_n,
+//           W_n = M^2 w_n / (2 pi^2), p_perp = M sinh xi sin theta
+// Pass 1 (one CTA per site) writes four FP64 partial sums per site; pass 2 (one
+// CTA) adds them in a fixed order.
+// ---------------------------------------------------------------------------
+template <class S, class R, int NXI, int NTH, int NPH>
+struct ObsArgs {
+  const S* f;
+  const double* lnM;
+  const double* sc;   // site scalars (FP64 matching) or nullptr
+  const float* scf;   // site scalars (FP32 matching) when sc is nullptr
+  double* part;       // 4 per site: T^xx, T^yy (with B), num, den of v2
+  Ops<R, NXI, NTH, NPH> op;
+};
+
+template <class S, class R, int NXI, int NTH, int NPH>
+__global__ void __launch_bounds__(NTH* NPH)
+    observables_kernel(const __grid_constant__ ObsArgs<S, R, NXI, NTH, NPH> A) {
+  constexpr int NL = NTH * NPH;
+  constexpr int NN = NL * NXI;
+  constexpr int NW = (NL + 31) / 32;
+  const int site = blockIdx.x, t = threadIdx.x;
+  const int j = t % NTH, l = t / NTH;
+  __shared__ double redd[4 * NW];
+  __shared__ float redf[8 * NW];
+  R f[NXI];
+  load_line<S, R, NXI>(A.f + (size_t)site * NN + t * NXI, f);
+  double r3 = 0.0, rs = 0.0;
+#pragma unroll
+  for (int k = 0; k < NXI; ++k) {
+    r3 += (double)A.op.w3[k] * (double)f[k];
+    rs += (double)A.op.ecw[k] * (double)A.op.s[k] * (double)f[k];
+  }
+  const double wj = A.op.wj[j], st = A.op.sth[j], cp = A.op.cph[l], sp = A.op.sph[l];
+  const double den = wj * rs * st;
+  const double v[4] = {wj * r3 * st * st * cp * cp, wj * r3 * st * st * sp * sp, den * (cp * cp - sp * sp), den};
+  block_reduce<4, NL, double>(v, redf, redd);
+  if (t == 0) {
+    const double M = exp(__ldg(A.lnM + site));
+    const double pi2 = 2.0 * 3.14159265358979323846 * 3.14159265358979323846;
+    const double p3 = M * M * M / pi2, p4 = p3 * M;
+    const double B = A.sc ? A.sc[(size_t)site * kSc + SC_B] : (double)A.scf[(size_t)site * kSc + SC_B];
+    double* o = A.part + (size_t)site * 4;
+    o[0] = p4 * redd[0] - B;
+    o[1] = p4 * redd[1] - B;
+    o[2] = p3 * redd[2];
+    o[3] = p3 * redd[3];
+  }
+}
+
+// out[0] = eps_p, out[1] = v2; one block of 1024 threads, fixed summation order
+__global__ void __launch_bounds__(1024) observables_reduce_kernel(const double* part, int ns, double* out) {
+  __shared__ double red[4 * 32];
+  double a[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int i = threadIdx.x; i < ns; i += 1024)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) a[q] += part[(size_t)i * 4 + q];
+  warp_sum<4>(a);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) red[wid * 4 + q] = a[q];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int w = 0; w < 32; ++w)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) s[q] += red[w * 4 + q];
+    out[0] = (s[0] - s[1]) / (s[0] + s[1]);
+    out[1] = s[2] / s[3];
+  }
+}
+
 }  // namespace rlbk

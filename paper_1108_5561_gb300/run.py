@@ -167,6 +167,26 @@ class Run:
         self._chk(self.lib.rlb_moments(self._h, ptr, 1, self._stream()), "rlb_moments")
         return t
 
+    def observables(self):
+        """(eps_p, v2 weighted by p_perp) of the current state (synchronises)."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        self._chk(self.lib.rlb_observables(self._h, ctypes.byref(a), ctypes.byref(b), self._stream()),
+                  "rlb_observables")
+        return a.value, b.value
+
+    def save_state(self) -> bytes:
+        """Checkpoint blob of the current state (host bytes)."""
+        n = ctypes.c_size_t()
+        self._chk(self.lib.rlb_state_blob_size(self._h, ctypes.byref(n)), "rlb_state_blob_size")
+        buf = ctypes.create_string_buffer(n.value)
+        self._chk(self.lib.rlb_save_state(self._h, buf, n, self._stream()), "rlb_save_state")
+        return buf.raw
+
+    def load_state(self, blob: bytes):
+        """Replace the state (and tau) by a blob from save_state of the same grid."""
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        self._chk(self.lib.rlb_load_state(self._h, buf, len(blob), self._stream()), "rlb_load_state")
+
     def populations(self):
         """Device view (ns, nodes) of f in the storage precision (aliases the state buffer)."""
         torch = self.torch

@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle on
 the same seeded inputs.  Tolerances: 1e-12 relative for the FP64 path, 1e-5 for
-FP32 populations (FP64 Landau/EOS), BF16 reported with a loose bound.
+FP32 populations (FP32 Landau/EOS), BF16 reported with a loose bound.
 
 Norms (per site, maximum over the grid): eps and T relative; u the relative
 error of the 4-vector, max_mu |du^mu| / max_mu |u^mu| (u^tau >= 1); u^tau
