@@ -88,7 +88,7 @@ typedef struct {
  *                         z0 = M0/T0 of Eq. fansatz) or LAGUERRE (massless limit,
  *                         |p~| = T0 x, weight x e^{-x}; needs the conformal EOS)
  *   prec                  population storage: F64 (all arithmetic FP64), F32 or
- *                         BF16 (FP32 arithmetic, FP64 Landau matching and EOS
+ *                         BF16 (FP32 arithmetic, FP32 Landau matching and EOS
  *                         inversion)
  *   eta_over_s            shear viscosity to entropy ratio; tau_R follows from
  *                         the Chapman-Enskog relation of Sec. 4.1; INFINITY
@@ -120,12 +120,30 @@ rlb_status rlb_init_eos(rlb_ctx* ctx, const rlb_eos_params* eos);
  * the populations and ln M (layout above); `scratch` holds the predictor
  * state, per-site temperatures, the error word and the EOS table.  Pure
  * function of g and of the EOS table size; may be called before
- * rlb_init_eos (then 65536 table points are assumed). */
+ * rlb_init_eos (then 65536 table points are assumed).  With g == NULL: the
+ * sizes for the grid or batch configured in ctx. */
 rlb_status rlb_workspace_size(const rlb_ctx* ctx, const rlb_grid_params* g, size_t* state_bytes,
                               size_t* scratch_bytes);
 
 /* Configure the grid and momentum lattice (host work only). */
 rlb_status rlb_configure(rlb_ctx* ctx, const rlb_grid_params* g);
+
+/* One event of a batch: its own periodic nx x ny grid and eta/s. */
+typedef struct {
+  int nx, ny;
+  double eta_over_s;
+} rlb_event_desc;
+
+/* Configure a batch of independent events instead of one grid: every event
+ * evolves with the scheme of the paper (Sec. 4.4) on its own periodic grid,
+ * with its own eta/s; all events share the lattice, precision, dx, tau0, dtau,
+ * metric and EOS of `base` (its nx, ny and eta_over_s are ignored).  Sites are
+ * stored event after event, row-major inside an event, so the state layout is
+ * that of one grid of sum(nx * ny) sites; each rlb_step advances all events
+ * with one launch per kernel.  Size the buffers with rlb_workspace_size(ctx,
+ * NULL, ...).  Limits: nx <= 65535, fewer than 2^31 sites in total. */
+rlb_status rlb_configure_batch(rlb_ctx* ctx, const rlb_grid_params* base, int n_events,
+                               const rlb_event_desc* events);
 
 /* Borrow caller-owned device buffers of at least the rlb_workspace_size bytes,
  * 256-byte aligned; the library never frees them.  Uploads the EOS table and
@@ -138,6 +156,11 @@ rlb_status rlb_bind_buffers(rlb_ctx* ctx, void* state, void* scratch, void* stre
  * f = Z exp(-E/T) at every node, and tau = tau0.  The host array is copied
  * before return; a device array must stay valid until `stream` reaches it. */
 rlb_status rlb_init_grid(rlb_ctx* ctx, const double* eps0, int eps0_on_device, void* stream);
+
+/* Initial state of a batch: eps0_concat holds the energy densities of all
+ * events' sites in storage order (event after event, row-major); otherwise as
+ * rlb_init_grid. */
+rlb_status rlb_init_batch(rlb_ctx* ctx, const double* eps0_concat, int eps0_on_device, void* stream);
 
 /* Advance by `nsteps` predictor-corrector steps of dtau (Sec. 4.4).  Each step
  * launches, for the predictor and again for the corrector, a per-site

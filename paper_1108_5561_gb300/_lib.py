@@ -17,7 +17,8 @@ EXPORTS = ["rlb_create", "rlb_destroy", "rlb_last_error", "rlb_init_eos", "rlb_w
            "rlb_configure", "rlb_bind_buffers", "rlb_init_grid", "rlb_step", "rlb_get_tau",
            "rlb_moments", "rlb_check", "rlb_state_offsets", "rlb_lattice", "rlb_operators",
            "rlb_set_timing", "rlb_get_timing", "rlb_step_static_scratch", "rlb_observables",
-           "rlb_state_blob_size", "rlb_save_state", "rlb_load_state"]
+           "rlb_state_blob_size", "rlb_save_state", "rlb_load_state", "rlb_configure_batch",
+           "rlb_init_batch"]
 
 
 class EosParamsC(ctypes.Structure):
@@ -34,6 +35,10 @@ class GridParamsC(ctypes.Structure):
                 ("dx", ctypes.c_double), ("z0", ctypes.c_double), ("T0", ctypes.c_double),
                 ("eta_over_s", ctypes.c_double), ("tau0", ctypes.c_double),
                 ("dtau", ctypes.c_double)]
+
+
+class EventDescC(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("eta_over_s", ctypes.c_double)]
 
 
 class RLBError(RuntimeError):
@@ -86,6 +91,8 @@ def load(build_if_missing: bool = True):
     lib.rlb_state_blob_size.argtypes = [vp, P(sz)]
     lib.rlb_save_state.argtypes = [vp, vp, sz, vp]
     lib.rlb_load_state.argtypes = [vp, vp, sz, vp]
+    lib.rlb_configure_batch.argtypes = [vp, P(GridParamsC), ctypes.c_int, P(EventDescC)]
+    lib.rlb_init_batch.argtypes = [vp, dp, ctypes.c_int, vp]
     for name in EXPORTS:
         if name not in ("rlb_destroy", "rlb_last_error"):
             getattr(lib, name).restype = ctypes.c_int

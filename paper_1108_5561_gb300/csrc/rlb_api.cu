@@ -29,6 +29,11 @@ struct rlb_ctx {
   size_t f_off = 0, lnM_off = 0;  // state
   size_t fs_off = 0, lnMs_off = 0, T_off = 0, err_off = 0, tab_off = 0, eps_off = 0;  // scratch
   size_t mom_off = 0, moms_off = 0, sc_off = 0, tabf_off = 0, scf_off = 0;
+  size_t ev_off = 0, rowev_off = 0, rowy_off = 0, clock_off = 0;
+  // events: one for a single grid, n for a batch; rows of all events in order
+  std::vector<rlbk::EventInfo> events;
+  std::vector<int> row_event, row_y;
+  size_t rows = 0, max_nx = 0;
   char* state = nullptr;
   char* scratch = nullptr;
   double tau = 0.0;
@@ -67,9 +72,15 @@ bool supported_shape(int nxi, int nth, int nph) {
          (nxi == 8 && nth == 8 && nph == 2);
 }
 
-void layout(const rlb_grid_params& g, size_t table_points, size_t* state_b, size_t* scratch_b,
-            rlb_ctx* c) {
-  const size_t ns = (size_t)g.nx * g.ny;
+// sites, rows and events of a configuration (one grid or a batch of events)
+struct Shape {
+  size_t ns, rows, events;
+};
+Shape grid_shape(const rlb_grid_params& g) { return {(size_t)g.nx * g.ny, (size_t)g.ny, 1}; }
+
+void layout(const rlb_grid_params& g, const Shape& sh, size_t table_points, size_t* state_b,
+            size_t* scratch_b, rlb_ctx* c) {
+  const size_t ns = sh.ns;
   const size_t nn = (size_t)g.n_xi * g.n_theta * 2 * g.n_phi_half;
   const size_t fb = align256(ns * nn * pop_size(g.prec));
   const size_t mb = align256(ns * sizeof(double));
@@ -91,8 +102,13 @@ void layout(const rlb_grid_params& g, size_t table_points, size_t* state_b, size
   size_t tab_off = off; off += align256((table_points + 6) * rlb::kFields * sizeof(double));
   size_t tabf_off = off; off += align256((table_points + 6) * rlb::kFields * sizeof(float));
   size_t scf_off = off; off += align256(ns * rlbk::kSc * sizeof(float));
+  size_t ev_off = off; off += align256(sh.events * sizeof(rlbk::EventInfo));
+  size_t rowev_off = off; off += align256(sh.rows * sizeof(int));
+  size_t rowy_off = off; off += align256(sh.rows * sizeof(int));
+  size_t clock_off = off; off += 256;
   *scratch_b = off;
   if (c) {
+    c->ev_off = ev_off; c->rowev_off = rowev_off; c->rowy_off = rowy_off; c->clock_off = clock_off;
     c->f_off = f_off; c->lnM_off = lnM_off;
     c->fs_off = fs_off; c->lnMs_off = lnMs_off; c->T_off = T_off; c->eps_off = eps_off;
     c->err_off = err_off; c->tab_off = tab_off;
@@ -177,15 +193,55 @@ rlbk::EosView eos_view(const rlb_ctx* c) {
   return v;
 }
 
+Shape ctx_shape(const rlb_ctx* c) { return {c->ns, c->rows, c->events.size()}; }
+
+rlbk::GridMap grid_map(const rlb_ctx* c, char* scr) {
+  rlbk::GridMap g;
+  g.ev = reinterpret_cast<const rlbk::EventInfo*>(scr + c->ev_off);
+  g.row_event = reinterpret_cast<const int*>(scr + c->rowev_off);
+  g.row_y = reinterpret_cast<const int*>(scr + c->rowy_off);
+  g.n_events = (int)c->events.size();
+  return g;
+}
+
+// event, row and clock tables into a scratch block (host memory of the context)
+rlb_status upload_tables(rlb_ctx* ctx, char* scr, cudaStream_t st) {
+  RLB_CUDA(cudaMemcpyAsync(scr + ctx->ev_off, ctx->events.data(), ctx->events.size() * sizeof(rlbk::EventInfo),
+                           cudaMemcpyHostToDevice, st), "event table upload");
+  RLB_CUDA(cudaMemcpyAsync(scr + ctx->rowev_off, ctx->row_event.data(), ctx->rows * sizeof(int),
+                           cudaMemcpyHostToDevice, st), "row table upload");
+  RLB_CUDA(cudaMemcpyAsync(scr + ctx->rowy_off, ctx->row_y.data(), ctx->rows * sizeof(int),
+                           cudaMemcpyHostToDevice, st), "row table upload");
+  return RLB_OK;
+}
+
+rlb_status set_clock(rlb_ctx* ctx, char* scr, double tau, cudaStream_t st) {
+  const rlbk::Clock c{tau, 1.0 / tau, (float)(1.0 / tau), 0.f};  // pageable: copied before return
+  RLB_CUDA(cudaMemcpyAsync(scr + ctx->clock_off, &c, sizeof c, cudaMemcpyHostToDevice, st), "clock upload");
+  return RLB_OK;
+}
+
+// events and rows of a configuration (ctx->gp holds the shared parameters)
+void set_events(rlb_ctx* ctx, const std::vector<rlbk::EventInfo>& ev) {
+  ctx->events = ev;
+  ctx->row_event.clear();
+  ctx->row_y.clear();
+  ctx->max_nx = 0;
+  size_t ns = 0;
+  for (size_t e = 0; e < ev.size(); ++e) {
+    for (int y = 0; y < ev[e].ny; ++y) {
+      ctx->row_event.push_back((int)e);
+      ctx->row_y.push_back(y);
+    }
+    ctx->max_nx = std::max(ctx->max_nx, (size_t)ev[e].nx);
+    ns += (size_t)ev[e].nx * ev[e].ny;
+  }
+  ctx->ns = ns;
+  ctx->rows = ctx->row_event.size();
+}
+
 enum Kind { K_STAGE = 0, K_MATCH = 1, K_INIT = 2 };
 
-// Set the Milne factor 1/tau of one launch and fold it into the polar operator.
-template <class R, int NXI, int NTH, int NPH>
-void set_milne(rlbk::Ops<R, NXI, NTH, NPH>& op, const rlb::Lattice& L, int metric, double tau, R* milne) {
-  const double inv = metric ? 1.0 / tau : 0.0;
-  *milne = (R)inv;
-  for (int i = 0; i < NTH * NTH; ++i) op.Dth[i] = (R)(L.Dth[i] * inv);
-}
 
 // Event bracket around one launch when timing is enabled.
 struct Timed {
@@ -221,8 +277,9 @@ rlbk::MatchArgs match_args(rlb_ctx* ctx, const double* mom, const double* lnM, d
   a.mom = mom;
   a.momf = reinterpret_cast<const float*>(mom);  // FP32 storage keeps kMomParts partial sums here
   a.inv2dx = 1.0 / (2.0 * ctx->gp.dx);
-  a.nx = ctx->gp.nx;
-  a.ny = ctx->gp.ny;
+  a.grid = grid_map(ctx, ctx->scratch);
+  a.clock = nullptr;
+  a.dtau = ctx->gp.dtau;
   a.lnM = lnM;
   a.Tsite = reinterpret_cast<double*>(ctx->scratch + ctx->T_off);
   a.sc = reinterpret_cast<double*>(ctx->scratch + ctx->sc_off);
@@ -230,7 +287,6 @@ rlbk::MatchArgs match_args(rlb_ctx* ctx, const double* mom, const double* lnM, d
   a.obs = obs;
   a.err = reinterpret_cast<int*>(ctx->scratch + ctx->err_off);
   a.eos = eos_view(ctx);
-  a.eta_over_s = ctx->gp.eta_over_s;
   a.ns = (int)ctx->ns;
   return a;
 }
@@ -245,20 +301,20 @@ struct Stager {
   static constexpr int NL = NTH * NPH;
   rlbk::StageArgs<S, R, NXI, NTH, NPH> a;
   rlbk::StageArgsX2<S, NXI, NTH, NPH> b;
-  const rlb::Lattice* lat = nullptr;
-  int metric = 0;
   dim3 grid;
 
-  Stager(const rlb_ctx* ctx, const double* sc, const float* scf, int* err) {
-    lat = &ctx->lat;
-    metric = ctx->gp.metric;
-    grid = dim3((unsigned)ctx->gp.nx, (unsigned)ctx->gp.ny, 1);
+  // scr: the scratch block holding the event tables and the clock
+  Stager(const rlb_ctx* ctx, char* scr, const double* sc, const float* scf, int* err) {
+    grid = dim3((unsigned)ctx->rows, (unsigned)ctx->max_nx, 1);
     const double dtau = ctx->gp.dtau, inv2dx = 1.0 / (2.0 * ctx->gp.dx);
+    const rlbk::GridMap gm = grid_map(ctx, scr);
+    const rlbk::Clock* clock = reinterpret_cast<const rlbk::Clock*>(scr + ctx->clock_off);
     if constexpr (kX2) {
       b.scf = scf;
       b.err = err;
-      b.nx = ctx->gp.nx;
-      b.ny = ctx->gp.ny;
+      b.grid = gm;
+      b.clock = clock;
+      b.milne_on = ctx->gp.metric == RLB_MILNE;
       b.dtau = dtau;
       b.dtau_r = (float)dtau;
       b.inv2dx_r = (float)inv2dx;
@@ -268,8 +324,9 @@ struct Stager {
       a.sc = sc;
       a.scf = scf;
       a.err = err;
-      a.nx = ctx->gp.nx;
-      a.ny = ctx->gp.ny;
+      a.grid = gm;
+      a.clock = clock;
+      a.milne_on = ctx->gp.metric == RLB_MILNE;
       a.dtau = dtau;
       a.inv2dx = inv2dx;
       a.dtau_r = (R)dtau;
@@ -280,32 +337,29 @@ struct Stager {
   }
 
   // mode 0: predictor f_out = f_in + dtau rhs(f_in); mode 1: corrector
-  // f_out = (f_base + f_in + dtau rhs(f_in)) / 2; tau is the time of f_in.
+  // f_out = (f_base + f_in + dtau rhs(f_in)) / 2.  The time of f_in is the
+  // device clock's.
   void launch(const S* f_in, const double* lnM_in, const S* f_base, const double* lnM_base, S* f_out,
-              double* lnM_out, double* mom_out, int mode, double tau, cudaStream_t st) {
-    const double inv = metric ? 1.0 / tau : 0.0;
+              double* lnM_out, double* mom_out, int mode, cudaStream_t st) {
     if constexpr (kX2) {
       b.f_in = f_in; b.lnM_in = lnM_in; b.f_base = f_base; b.lnM_base = lnM_base;
       b.f_out = f_out; b.lnM_out = lnM_out; b.momf_out = reinterpret_cast<float*>(mom_out);
       b.mode = mode;
-      b.milne = (float)inv;
-      for (int i = 0; i < NTH * NTH; ++i) {
-        const float v = (float)(lat->Dth[i] * inv);
-        b.op.Dthb[i] = make_float2(v, v);
-      }
       rlbk::stage_kernel_x2<S, NXI, NTH, NPH><<<grid, NL, 0, st>>>(b);
     } else {
       a.f_in = f_in; a.lnM_in = lnM_in; a.f_base = f_base; a.lnM_base = lnM_base;
       a.f_out = f_out; a.lnM_out = lnM_out; a.mom_out = mom_out; a.momf_out = reinterpret_cast<float*>(mom_out);
       a.mode = mode;
-      set_milne<R, NXI, NTH, NPH>(a.op, *lat, metric, tau, &a.milne);
       rlbk::stage_kernel<S, R, NXI, NTH, NPH><<<grid, NL, 0, st>>>(a);
     }
   }
 };
 
-rlb_status match(rlb_ctx* ctx, const double* mom, const double* lnM, double* obs, cudaStream_t st) {
-  const rlbk::MatchArgs a = match_args(ctx, mom, lnM, obs);
+// clock: advanced by dtau in the launch (corrector matching) when non-null
+rlb_status match(rlb_ctx* ctx, const double* mom, const double* lnM, double* obs, cudaStream_t st,
+                 rlbk::Clock* clock = nullptr) {
+  rlbk::MatchArgs a = match_args(ctx, mom, lnM, obs);
+  a.clock = clock;
   {
     Timed tm(ctx, K_MATCH, st);
     const unsigned nb = (unsigned)((ctx->ns + 127) / 128);
@@ -351,24 +405,26 @@ struct Runner {
     double* ms = reinterpret_cast<double*>(ctx->scratch + ctx->lnMs_off);
     double* mom = reinterpret_cast<double*>(ctx->scratch + ctx->mom_off);
     double* moms = reinterpret_cast<double*>(ctx->scratch + ctx->moms_off);
-    Stager<S, R, NXI, NTH, NPH> sg(ctx, reinterpret_cast<const double*>(ctx->scratch + ctx->sc_off),
+    Stager<S, R, NXI, NTH, NPH> sg(ctx, ctx->scratch, reinterpret_cast<const double*>(ctx->scratch + ctx->sc_off),
                                    reinterpret_cast<const float*>(ctx->scratch + ctx->scf_off),
                                    reinterpret_cast<int*>(ctx->scratch + ctx->err_off));
+    rlbk::Clock* clock = reinterpret_cast<rlbk::Clock*>(ctx->scratch + ctx->clock_off);
     for (int s = 0; s < nsteps; ++s) {
       // predictor: f* = f + dtau RHS(f) at tau
       rlb_status r = match(ctx, mom, m, nullptr, st);
       if (r) return r;
       {
         Timed tm(ctx, K_STAGE, st);
-        sg.launch(f, m, f, m, fs, ms, moms, 0, ctx->tau, st);
+        sg.launch(f, m, f, m, fs, ms, moms, 0, st);
       }
       RLB_CUDA(cudaGetLastError(), "stage kernel (predictor) launch");
-      // corrector: f = (f + f* + dtau RHS(f*))/2 at tau + dtau, in place over f
-      r = match(ctx, moms, ms, nullptr, st);
+      // corrector: f = (f + f* + dtau RHS(f*))/2 at tau + dtau, in place over f;
+      // its matching moves the device clock to tau + dtau
+      r = match(ctx, moms, ms, nullptr, st, clock);
       if (r) return r;
       {
         Timed tm(ctx, K_STAGE, st);
-        sg.launch(fs, ms, f, m, f, m, mom, 1, ctx->tau + ctx->gp.dtau, st);
+        sg.launch(fs, ms, f, m, f, m, mom, 1, st);
       }
       RLB_CUDA(cudaGetLastError(), "stage kernel (corrector) launch");
       ctx->tau += ctx->gp.dtau;
@@ -468,7 +524,7 @@ rlb_status step_static(rlb_ctx* ctx, char* state, char* scr, int nsteps, cudaStr
   // same layout as the bound scratch, rooted at the static array
   size_t sb, xb;
   rlb_ctx L;
-  layout(ctx->gp, (size_t)ctx->eosp.points, &sb, &xb, &L);
+  layout(ctx->gp, ctx_shape(ctx), (size_t)ctx->eosp.points, &sb, &xb, &L);
   S* f = reinterpret_cast<S*>(state + ctx->f_off);
   double* m = reinterpret_cast<double*>(state + ctx->lnM_off);
   S* fs = reinterpret_cast<S*>(scr + L.fs_off);
@@ -494,6 +550,11 @@ rlb_status step_static(rlb_ctx* ctx, char* state, char* scr, int nsteps, cudaStr
   }
   RLB_CUDA(cudaMemsetAsync(Tsite, 0, ctx->ns * sizeof(double), st), "static Newton starts reset");
   RLB_CUDA(cudaMemsetAsync(err, 0, 256, st), "static error word reset");
+  rlb_status r0 = upload_tables(ctx, scr, st);
+  if (r0) return r0;
+  r0 = set_clock(ctx, scr, ctx->tau, st);
+  if (r0) return r0;
+  RLB_CUDA(cudaStreamSynchronize(st), "static table upload synchronise");
   const auto op = make_ops<R, NXI, NTH, NPH>(ctx->lat);
   {
     rlbk::MomentsArgs<S, R, NXI, NTH, NPH> a;
@@ -511,30 +572,31 @@ rlb_status step_static(rlb_ctx* ctx, char* state, char* scr, int nsteps, cudaStr
   ma.obs = nullptr;
   ma.err = err;
   ma.eos = ev;
-  ma.eta_over_s = ctx->gp.eta_over_s;
+  ma.grid = grid_map(ctx, scr);
   ma.inv2dx = 1.0 / (2.0 * ctx->gp.dx);
-  ma.nx = ctx->gp.nx;
-  ma.ny = ctx->gp.ny;
   ma.ns = (int)ctx->ns;
-  auto run_match = [&](const double* mm, const double* lnM) -> rlb_status {
+  ma.dtau = ctx->gp.dtau;
+  rlbk::Clock* clock = reinterpret_cast<rlbk::Clock*>(scr + L.clock_off);
+  auto run_match = [&](const double* mm, const double* lnM, rlbk::Clock* adv) -> rlb_status {
     ma.mom = mm;
     ma.momf = reinterpret_cast<const float*>(mm);
     ma.lnM = lnM;
+    ma.clock = adv;
     const unsigned nb = (unsigned)((ctx->ns + 127) / 128);
     if (ctx->gp.prec == RLB_F64) rlbk::match_kernel<false><<<nb, 128, 0, st>>>(ma);
     else rlbk::match_kernel<true><<<nb, 128, 0, st>>>(ma);
     RLB_CUDA(cudaGetLastError(), "match_kernel launch");
     return RLB_OK;
   };
-  Stager<S, R, NXI, NTH, NPH> sg(ctx, ma.sc, ma.scf, err);
+  Stager<S, R, NXI, NTH, NPH> sg(ctx, scr, ma.sc, ma.scf, err);
   for (int s = 0; s < nsteps; ++s) {
-    rlb_status r = run_match(mom, m);
+    rlb_status r = run_match(mom, m, nullptr);
     if (r) return r;
-    sg.launch(f, m, f, m, fs, ms, moms, 0, ctx->tau, st);
+    sg.launch(f, m, f, m, fs, ms, moms, 0, st);
     RLB_CUDA(cudaGetLastError(), "stage kernel (predictor) launch");
-    r = run_match(moms, ms);
+    r = run_match(moms, ms, clock);
     if (r) return r;
-    sg.launch(fs, ms, f, m, f, m, mom, 1, ctx->tau + ctx->gp.dtau, st);
+    sg.launch(fs, ms, f, m, f, m, mom, 1, st);
     RLB_CUDA(cudaGetLastError(), "stage kernel (corrector) launch");
     ctx->tau += ctx->gp.dtau;
   }
@@ -598,10 +660,15 @@ rlb_status rlb_init_eos(rlb_ctx* ctx, const rlb_eos_params* e) {
 
 rlb_status rlb_workspace_size(const rlb_ctx* ctx, const rlb_grid_params* g, size_t* state_bytes,
                               size_t* scratch_bytes) {
-  if (!g || !state_bytes || !scratch_bytes) return RLB_ERR_ARG;
+  if (!state_bytes || !scratch_bytes) return RLB_ERR_ARG;
+  if (!g) {  // the configured grid or batch
+    if (!ctx || !ctx->grid_ok) return RLB_ERR_ARG;
+    layout(ctx->gp, ctx_shape(ctx), (size_t)ctx->eosp.points, state_bytes, scratch_bytes, nullptr);
+    return RLB_OK;
+  }
   if (g->nx < 1 || g->ny < 1 || g->prec < 0 || g->prec > 2) return RLB_ERR_ARG;
   size_t pts = (ctx && ctx->eos_ok) ? (size_t)ctx->eosp.points : 65536;
-  layout(*g, pts, state_bytes, scratch_bytes, nullptr);
+  layout(*g, grid_shape(*g), pts, state_bytes, scratch_bytes, nullptr);
   return RLB_OK;
 }
 
@@ -619,18 +686,46 @@ rlb_status rlb_configure(rlb_ctx* ctx, const rlb_grid_params* g) {
     return fail(ctx, RLB_ERR_ARG, "the Laguerre radial family needs the conformal EOS");
   if (g->family == RLB_RADIAL_LAGUERRE && !(g->T0 > 0))
     return fail(ctx, RLB_ERR_ARG, "T0 must be positive");
-  if ((size_t)g->nx * g->ny > 0x7fffffffu || g->ny > 65535)
-    return fail(ctx, RLB_ERR_ARG, "grid too large (ny <= 65535, nx * ny < 2^31)");
+  if ((size_t)g->nx * g->ny > 0x7fffffffu || g->nx > 65535)
+    return fail(ctx, RLB_ERR_ARG, "grid too large (nx <= 65535, nx * ny < 2^31)");
   std::string m = rlb::build_lattice(g->family, g->n_xi, g->n_theta, g->n_phi_half, g->z0, &ctx->lat);
   if (!m.empty()) return fail(ctx, RLB_ERR_ARG, m);
   ctx->gp = *g;
-  ctx->ns = (size_t)g->nx * g->ny;
+  set_events(ctx, {rlbk::EventInfo{0, g->nx, g->ny, 0, g->eta_over_s, 0.0}});
   ctx->nn = (size_t)g->n_xi * g->n_theta * 2 * g->n_phi_half;
   ctx->pop_bytes = pop_size(g->prec);
   size_t sb, xb;
-  layout(*g, ctx->eosp.points, &sb, &xb, ctx);
+  layout(*g, ctx_shape(ctx), ctx->eosp.points, &sb, &xb, ctx);
   ctx->grid_ok = true;
   ctx->tau = g->tau0;
+  return RLB_OK;
+}
+
+rlb_status rlb_configure_batch(rlb_ctx* ctx, const rlb_grid_params* base, int n_events,
+                               const rlb_event_desc* events) {
+  if (!ctx || !base || !events || n_events < 1) return RLB_ERR_ARG;
+  std::vector<rlbk::EventInfo> ev((size_t)n_events);
+  size_t ns = 0, rows = 0;
+  int max_nx = 0;
+  for (int e = 0; e < n_events; ++e) {
+    const rlb_event_desc& d = events[e];
+    if (d.nx < 1 || d.ny < 1 || d.nx > 65535 || !(d.eta_over_s > 0))
+      return fail(ctx, RLB_ERR_ARG, "invalid event (nx in [1, 65535], ny >= 1, eta/s > 0)");
+    ev[e] = rlbk::EventInfo{(int)ns, d.nx, d.ny, 0, d.eta_over_s, 0.0};
+    ns += (size_t)d.nx * d.ny;
+    rows += (size_t)d.ny;
+    max_nx = std::max(max_nx, d.nx);
+    if (ns > 0x7fffffffu) return fail(ctx, RLB_ERR_ARG, "batch too large (fewer than 2^31 sites)");
+  }
+  rlb_grid_params g = *base;  // shared lattice, precision, dx, tau0, dtau, metric
+  g.nx = max_nx;
+  g.ny = (int)rows;
+  g.eta_over_s = events[0].eta_over_s;
+  rlb_status s = rlb_configure(ctx, &g);  // validates the shared parameters, builds the lattice
+  if (s) return s;
+  set_events(ctx, ev);
+  size_t sb, xb;
+  layout(ctx->gp, ctx_shape(ctx), ctx->eosp.points, &sb, &xb, ctx);
   return RLB_OK;
 }
 
@@ -656,7 +751,11 @@ rlb_status rlb_bind_buffers(rlb_ctx* ctx, void* state, void* scratch, void* stre
     RLB_CUDA(cudaStreamSynchronize(st), "bind synchronise");
   }
   RLB_CUDA(cudaMemsetAsync(ctx->scratch + ctx->err_off, 0, 256, st), "error word reset");
-  // the table copy reads pageable host memory owned by ctx: wait for it
+  s = upload_tables(ctx, ctx->scratch, st);
+  if (s) return s;
+  s = set_clock(ctx, ctx->scratch, ctx->tau, st);
+  if (s) return s;
+  // the table copies read pageable host memory owned by ctx: wait for them
   RLB_CUDA(cudaStreamSynchronize(st), "bind synchronise");
   ctx->bound = true;
   return RLB_OK;
@@ -683,8 +782,14 @@ rlb_status rlb_init_grid(rlb_ctx* ctx, const double* eps0, int eps0_on_device, v
   s = dispatch(ctx, OP_INIT, 0, dev, st);
   if (s) return s;
   ctx->tau = ctx->gp.tau0;
+  s = set_clock(ctx, ctx->scratch, ctx->tau, st);
+  if (s) return s;
   ctx->inited = true;
   return RLB_OK;
+}
+
+rlb_status rlb_init_batch(rlb_ctx* ctx, const double* eps0_concat, int eps0_on_device, void* stream) {
+  return rlb_init_grid(ctx, eps0_concat, eps0_on_device, stream);
 }
 
 rlb_status rlb_step(rlb_ctx* ctx, int nsteps, void* stream) {
@@ -700,7 +805,7 @@ rlb_status rlb_step_static_scratch(rlb_ctx* ctx, void* state, int nsteps, void* 
   if (!ctx->grid_ok) return fail(ctx, RLB_ERR_STATE, "rlb_configure must come first");
   if ((uintptr_t)state & 255) return fail(ctx, RLB_ERR_ARG, "state must be 256-byte aligned");
   size_t sb, xb;
-  layout(ctx->gp, (size_t)ctx->eosp.points, &sb, &xb, nullptr);
+  layout(ctx->gp, ctx_shape(ctx), (size_t)ctx->eosp.points, &sb, &xb, nullptr);
   if (xb > kStaticScratchBytes) {
     char buf[200];
     snprintf(buf, sizeof buf,
@@ -882,8 +987,10 @@ rlb_status rlb_load_state(rlb_ctx* ctx, const void* host_buf, size_t bytes, void
     RLB_CUDA(cudaMemcpyAsync(q.dst, p, q.n, cudaMemcpyHostToDevice, st), "state upload");
     p += q.n;
   }
-  RLB_CUDA(cudaStreamSynchronize(st), "state upload synchronise");
   ctx->tau = got.tau;
+  s = set_clock(ctx, ctx->scratch, ctx->tau, st);
+  if (s) return s;
+  RLB_CUDA(cudaStreamSynchronize(st), "state upload synchronise");
   ctx->inited = true;
   return RLB_OK;
 }

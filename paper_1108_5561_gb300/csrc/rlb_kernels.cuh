@@ -428,6 +428,58 @@ enum : int {
   SC_AX, SC_AY  // grad ln M (central differences, 1/fm)
 };
 
+// Grid of one or more independent events: periodic transverse grids of their
+// own size and eta/s, stored event after event, row-major inside an event.
+// 32 bytes, 16-byte aligned: the first four ints are read as one int4
+struct alignas(16) EventInfo {
+  int site_off, nx, ny, pad;
+  double eta_over_s, pad2;
+};
+static_assert(sizeof(EventInfo) == 32 && alignof(EventInfo) == 16, "EventInfo layout");
+struct GridMap {
+  const EventInfo* ev;   // n_events entries (device)
+  const int* row_event;  // event of every global row (device)
+  const int* row_y;      // y of every global row inside its event (device)
+  int n_events;
+};
+
+// Position of the site of CTA (row, x) of a stage launch (grid = global rows x
+// widest row); false for the padding CTAs beyond a narrower event's row.
+struct SiteLoc {
+  int site, x, y, nx, ny, base;
+};
+__device__ __forceinline__ bool locate_site(const GridMap& G, int row, int x, SiteLoc* L) {
+  const int e = __ldg(G.row_event + row);
+  const int4 v = __ldg(reinterpret_cast<const int4*>(G.ev + e));  // site_off, nx, ny, pad
+  if (x >= v.y) return false;
+  L->base = v.x;
+  L->nx = v.y;
+  L->ny = v.z;
+  L->x = x;
+  L->y = __ldg(G.row_y + row);
+  L->site = v.x + L->y * v.y + x;
+  return true;
+}
+
+// Event holding `site` (binary search over the event offsets, log2 n_events steps).
+__device__ __forceinline__ int event_of_site(const GridMap& G, int site) {
+  int lo = 0, hi = G.n_events - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (G.ev[mid].site_off <= site) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Proper time of the state being advanced, in device memory: the matching
+// launch of the corrector stage advances it, so every launch of a step has the
+// same parameters from step to step (a step can be replayed as a CUDA graph).
+struct Clock {
+  double tau, inv_tau;
+  float inv_tau_f, pad;
+};
+
 struct MatchArgs {
   const double* mom;    // kMom per site (FP64 storage)
   const float* momf;    // kMom x kMomParts partial sums per site (FP32 storage)
@@ -438,10 +490,21 @@ struct MatchArgs {
   double* obs;          // 8 observables per site, or nullptr
   int* err;
   EosView eos;
-  double eta_over_s;
+  GridMap grid;         // events (eta/s per event) and their sizes
   double inv2dx;
-  int nx, ny, ns;
+  int ns;
+  Clock* clock;         // advanced by dtau when non-null (corrector matching)
+  double dtau;
 };
+
+// Position of a site inside its event (matching: one thread per site).
+__device__ __forceinline__ void site_xy(const GridMap& G, int site, int* e, int* x, int* y) {
+  *e = event_of_site(G, site);
+  const EventInfo& v = G.ev[*e];
+  const int loc = site - v.site_off;
+  *y = loc / v.nx;
+  *x = loc - *y * v.nx;
+}
 
 // Matching of one site in FP64 (FP64 storage path): Landau (u, eps_kin), T from
 // e(T) = eps_kin (B at its equilibrium value, Eq. sanity), then M(T), dB/deps,
@@ -476,10 +539,13 @@ __device__ __forceinline__ int match_site_d(const MatchArgs& A, int site, double
   double t, w[6];
   eos_cell(A.eos, y, &i0, &t);
   lagrange6(t, w);
+  int ev, sxi, syi;
+  site_xy(A.grid, site, &ev, &sxi, &syi);
+  const EventInfo& evi = A.grid.ev[ev];
   const double T = exp(y);
   const double Meq = eos_field(A.eos, i0, w, EOS_X) * T;
   const double D = eos_field(A.eos, i0, w, EOS_D);
-  const double itr = eos_field(A.eos, i0, w, EOS_INVH) / A.eta_over_s;
+  const double itr = eos_field(A.eos, i0, w, EOS_INVH) / evi.eta_over_s;
   const double T2 = T * T;
   const double B = eos_field(A.eos, i0, w, EOS_B) * T2 * T2;
   if (!isfinite(T) || !isfinite(u[1]) || !isfinite(u[2]) || !isfinite(B)) err |= ERR_NONFINITE;
@@ -488,11 +554,12 @@ __device__ __forceinline__ int match_site_d(const MatchArgs& A, int site, double
   o[SC_INVT] = 1.0 / T; o[SC_MEQ] = Meq; o[SC_M] = M; o[SC_ITR] = itr; o[SC_D] = D;
   o[SC_B] = B; o[SC_K] = pref * m[0]; o[SC_KH] = m[0]; o[SC_T] = T;
   {
-    const int x = site % A.nx, yy = site / A.nx;
-    const int xp = x + 1 == A.nx ? 0 : x + 1, xm = x == 0 ? A.nx - 1 : x - 1;
-    const int yp = yy + 1 == A.ny ? 0 : yy + 1, ym = yy == 0 ? A.ny - 1 : yy - 1;
-    o[SC_AX] = (A.lnM[yy * A.nx + xp] - A.lnM[yy * A.nx + xm]) * A.inv2dx;
-    o[SC_AY] = (A.lnM[yp * A.nx + x] - A.lnM[ym * A.nx + x]) * A.inv2dx;
+    const int nx = evi.nx, ny = evi.ny, x = sxi, yy = syi;
+    const double* m = A.lnM + evi.site_off;
+    const int xp = x + 1 == nx ? 0 : x + 1, xm = x == 0 ? nx - 1 : x - 1;
+    const int yp = yy + 1 == ny ? 0 : yy + 1, ym = yy == 0 ? ny - 1 : yy - 1;
+    o[SC_AX] = (m[yy * nx + xp] - m[yy * nx + xm]) * A.inv2dx;
+    o[SC_AY] = (m[yp * nx + x] - m[ym * nx + x]) * A.inv2dx;
   }
   if (A.obs) {
     const double hc = 0.1973269804, h3 = hc * hc * hc;
@@ -544,10 +611,13 @@ __device__ __forceinline__ int match_site_f(const MatchArgs& A, int site, float 
   float t, w[6];
   eos_cellf(A.eos, y, &i0, &t);
   lagrange6f(t, w);
+  int ev, sxi, syi;
+  site_xy(A.grid, site, &ev, &sxi, &syi);
+  const EventInfo& evi = A.grid.ev[ev];
   const float T = expf(y);
   const float Meq = eos_fieldf(A.eos, i0, w, EOS_X) * T;
   const float D = eos_fieldf(A.eos, i0, w, EOS_D);
-  const float itr = eos_fieldf(A.eos, i0, w, EOS_INVH) / (float)A.eta_over_s;
+  const float itr = eos_fieldf(A.eos, i0, w, EOS_INVH) / (float)evi.eta_over_s;
   const float T2 = T * T;
   const float B = eos_fieldf(A.eos, i0, w, EOS_B) * T2 * T2;
   if (!isfinite(T) || !isfinite(u[1]) || !isfinite(u[2]) || !isfinite(B)) err |= ERR_NONFINITE;
@@ -556,12 +626,13 @@ __device__ __forceinline__ int match_site_f(const MatchArgs& A, int site, float 
   o[SC_INVT] = 1.f / T; o[SC_MEQ] = Meq; o[SC_M] = M; o[SC_ITR] = itr; o[SC_D] = D;
   o[SC_B] = B; o[SC_K] = pref * m[0]; o[SC_KH] = m[0]; o[SC_T] = T;
   {
-    const int x = site % A.nx, yy = site / A.nx;
-    const int xp = x + 1 == A.nx ? 0 : x + 1, xm = x == 0 ? A.nx - 1 : x - 1;
-    const int yp = yy + 1 == A.ny ? 0 : yy + 1, ym = yy == 0 ? A.ny - 1 : yy - 1;
+    const int nx = evi.nx, ny = evi.ny, x = sxi, yy = syi;
+    const double* m = A.lnM + evi.site_off;
+    const int xp = x + 1 == nx ? 0 : x + 1, xm = x == 0 ? nx - 1 : x - 1;
+    const int yp = yy + 1 == ny ? 0 : yy + 1, ym = yy == 0 ? ny - 1 : yy - 1;
     const float i2dx = (float)A.inv2dx;
-    o[SC_AX] = (float)(A.lnM[yy * A.nx + xp] - A.lnM[yy * A.nx + xm]) * i2dx;
-    o[SC_AY] = (float)(A.lnM[yp * A.nx + x] - A.lnM[ym * A.nx + x]) * i2dx;
+    o[SC_AX] = (float)(m[yy * nx + xp] - m[yy * nx + xm]) * i2dx;
+    o[SC_AY] = (float)(m[yp * nx + x] - m[ym * nx + x]) * i2dx;
   }
   if (A.obs) {
     const double hc = 0.1973269804, h3 = hc * hc * hc;
@@ -581,6 +652,12 @@ __device__ __forceinline__ int match_site_f(const MatchArgs& A, int site, float 
 template <bool FAST>
 __global__ void __launch_bounds__(128) match_kernel(const MatchArgs A) {
   const int site = blockIdx.x * blockDim.x + threadIdx.x;
+  if (A.clock && site == 0) {  // the state being matched is at tau + dtau
+    const double tau = A.clock->tau + A.dtau, inv = 1.0 / tau;
+    A.clock->tau = tau;
+    A.clock->inv_tau = inv;
+    A.clock->inv_tau_f = (float)inv;
+  }
   if (site >= A.ns) return;
   if constexpr (FAST) {
     float o[kSc];
@@ -776,10 +853,11 @@ struct StageArgs {
   double* mom_out;        // moments of f_out, kMom per site (FP64 storage)
   float* momf_out;        // moments of f_out, kMomParts partial sums (FP32 storage)
   int* err;
-  int nx, ny;
+  GridMap grid;
+  const Clock* clock;     // proper time of f_in
+  int milne_on;           // Milne metric (1/tau terms) or Minkowski
   int mode;               // 0 predictor, 1 corrector
   double dtau, inv2dx;    // FP64 copies for the per-site (thread 0) arithmetic
-  R milne;                // 1/tau in the Milne metric, 0 in Minkowski (op.Dth is pre-scaled by it)
   R dtau_r, inv2dx_r, Z;  // the same constants in the compute precision
   Ops<R, NXI, NTH, NPH> op;
 };
@@ -791,8 +869,9 @@ __global__ void __launch_bounds__(NTH* NPH)
   constexpr int NN = NL * NXI;
   constexpr int NW = (NL + 31) / 32;
   const auto& op = A.op;
-  const int x = blockIdx.x, y = blockIdx.y;
-  const int site = y * A.nx + x;
+  SiteLoc L;
+  if (!locate_site(A.grid, blockIdx.x, blockIdx.y, &L)) return;  // padding CTA: whole block
+  const int x = L.x, y = L.y, site = L.site, nx = L.nx, ny = L.ny;
   const int t = threadIdx.x;
   const int j = t % NTH, l = t / NTH;
 
@@ -813,14 +892,14 @@ __global__ void __launch_bounds__(NTH* NPH)
   // upwind neighbours (periodic): x -/+ 1, 2 when cos(phi) >/<= 0, likewise y
   const int sx = (cp > (R)0) ? -1 : 1, sy = (sp > (R)0) ? -1 : 1;
   int x1 = x + sx, x2 = x + 2 * sx, y1 = y + sy, y2 = y + 2 * sy;
-  x1 += (x1 < 0) ? A.nx : (x1 >= A.nx ? -A.nx : 0);
-  x2 += (x2 < 0) ? A.nx : (x2 >= A.nx ? -A.nx : 0);
-  x2 += (x2 < 0) ? A.nx : (x2 >= A.nx ? -A.nx : 0);  // grids of one site
-  y1 += (y1 < 0) ? A.ny : (y1 >= A.ny ? -A.ny : 0);
-  y2 += (y2 < 0) ? A.ny : (y2 >= A.ny ? -A.ny : 0);
-  y2 += (y2 < 0) ? A.ny : (y2 >= A.ny ? -A.ny : 0);
-  const int sx1 = y * A.nx + x1, sx2 = y * A.nx + x2;
-  const int sy1 = y1 * A.nx + x, sy2 = y2 * A.nx + x;
+  x1 += (x1 < 0) ? nx : (x1 >= nx ? -nx : 0);
+  x2 += (x2 < 0) ? nx : (x2 >= nx ? -nx : 0);
+  x2 += (x2 < 0) ? nx : (x2 >= nx ? -nx : 0);  // grids of one site
+  y1 += (y1 < 0) ? ny : (y1 >= ny ? -ny : 0);
+  y2 += (y2 < 0) ? ny : (y2 >= ny ? -ny : 0);
+  y2 += (y2 < 0) ? ny : (y2 >= ny ? -ny : 0);
+  const int sx1 = L.base + y * nx + x1, sx2 = L.base + y * nx + x2;
+  const int sy1 = L.base + y1 * nx + x, sy2 = L.base + y2 * nx + x;
   R fx1[NXI], fx2[NXI], fy1[NXI], fy2[NXI];
   load_line<S, R, NXI>(A.f_in + (size_t)sx1 * NN + t * NXI, fx1);
   load_line<S, R, NXI>(A.f_in + (size_t)sx2 * NN + t * NXI, fx2);
@@ -858,7 +937,11 @@ __global__ void __launch_bounds__(NTH* NPH)
     Drf[kp] = acc;
   }
   __syncthreads();
-  const R milne = A.milne;
+  R milne = 0;
+  if (A.milne_on) {
+    if constexpr (sizeof(R) == 8) milne = (R)A.clock->inv_tau;
+    else milne = (R)A.clock->inv_tau_f;
+  }
   if (milne != (R)0) {
     for (int it = t; it < NXI * NPH; it += NL) {  // polar lines (k', l'): (1/tau) Dth along j
       const int kq = it % NXI, lq = it / NXI;
@@ -905,7 +988,7 @@ __global__ void __launch_bounds__(NTH* NPH)
     const R Sx = (R)3 * f[k] - (R)4 * fx1[k] + fx2[k];
     const R Sy = (R)3 * f[k] - (R)4 * fy1[k] + fy2[k];
     R r = op.tv[k] * (nsx * Sx + nsy * Sy) + milne_mu2 * Drf[k];
-    if (pol) r += pth[k * LD + t];
+    if (pol) r += milne * pth[k * LD + t];
     R feq;
     if constexpr (kF) feq = ex2_ftz(c1 * E + (c2 * op.s[k] + lZ));
     else feq = A.Z * exp(c1 * E + c2 * op.s[k]);

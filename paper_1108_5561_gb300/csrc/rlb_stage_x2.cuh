@@ -28,7 +28,7 @@ template <int NXI, int NTH, int NPH>
 struct OpsX2 {
   static constexpr int NP = NXI / 2;
   float2 Drb[NXI * NP];    // [k * NP + p] = (Dr[2p][k], Dr[2p+1][k])
-  float2 Dthb[NTH * NTH];  // [jp * NTH + jj] = (1/tau) Dth[jp][jj] in both halves
+  float2 Dthb[NTH * NTH];  // [jp * NTH + jj] = Dth[jp][jj] in both halves
   float2 tv[NP], s[NP], q2[NP], ic[NP];  // tanh, sinh, sinh^2/cosh, 1/cosh
   float2 Cw[NP], Sw[NP];                 // cosh sqrt(ecw), sinh sqrt(ecw)
   float2 w0[NP], w1[NP], w2[NP], w3[NP];  // ecw * {1, c s, c^2, s^2}
@@ -48,10 +48,11 @@ struct StageArgsX2 {
   double* lnM_out;
   float* momf_out;        // moments of f_out: one partial sum per warp (kMomParts slots)
   int* err;
-  int nx, ny;
+  GridMap grid;
+  const Clock* clock;     // proper time of f_in
+  int milne_on;           // Milne metric (1/tau terms) or Minkowski
   int mode;               // 0 predictor, 1 corrector
   double dtau;
-  float milne;            // 1/tau in the Milne metric (0: Minkowski); Dthb carries it
   float dtau_r, inv2dx_r, log2Z;
   OpsX2<NXI, NTH, NPH> op;
 };
@@ -115,7 +116,14 @@ __device__ __forceinline__ void store_pairs(S* __restrict__ p, float2 (&v)[NP]) 
     if constexpr (NP % 4 == 0) {
       uint4* q = reinterpret_cast<uint4*>(p);
 #pragma unroll
-      for (int i = 0; i < NP / 4; ++i) q[i] = *reinterpret_cast<const uint4*>(&b[4 * i]);
+      for (int i = 0; i < NP / 4; ++i) {
+        uint4 u;
+        u.x = *reinterpret_cast<const unsigned*>(&b[4 * i]);
+        u.y = *reinterpret_cast<const unsigned*>(&b[4 * i + 1]);
+        u.z = *reinterpret_cast<const unsigned*>(&b[4 * i + 2]);
+        u.w = *reinterpret_cast<const unsigned*>(&b[4 * i + 3]);
+        q[i] = u;
+      }
     } else {
       __nv_bfloat162* q = reinterpret_cast<__nv_bfloat162*>(p);
 #pragma unroll
@@ -143,8 +151,9 @@ __global__ void __launch_bounds__(NTH* NPH, (NTH * NPH <= 96 ? 8 : 3))
   constexpr int LDL = NTH + 1;
   constexpr int LDK = NPH * LDL + (((12 - NPH * LDL) % 16) + 16) % 16;
   const auto& op = A.op;
-  const int x = blockIdx.x, y = blockIdx.y;
-  const int site = y * A.nx + x;
+  SiteLoc L;
+  if (!locate_site(A.grid, blockIdx.x, blockIdx.y, &L)) return;  // padding CTA: whole block
+  const int x = L.x, y = L.y, site = L.site, nx = L.nx, ny = L.ny;
   const int t = threadIdx.x;
   const int j = t % NTH, l = t / NTH;
 
@@ -159,17 +168,18 @@ __global__ void __launch_bounds__(NTH* NPH, (NTH * NPH <= 96 ? 8 : 3))
   const float cp = op.cph[l], sp = op.sph[l];
   const int sx = (cp > 0.f) ? -1 : 1, sy = (sp > 0.f) ? -1 : 1;
   int x1 = x + sx, x2 = x + 2 * sx, y1 = y + sy, y2 = y + 2 * sy;
-  x1 += (x1 < 0) ? A.nx : (x1 >= A.nx ? -A.nx : 0);
-  x2 += (x2 < 0) ? A.nx : (x2 >= A.nx ? -A.nx : 0);
-  x2 += (x2 < 0) ? A.nx : (x2 >= A.nx ? -A.nx : 0);  // grids of one site
-  y1 += (y1 < 0) ? A.ny : (y1 >= A.ny ? -A.ny : 0);
-  y2 += (y2 < 0) ? A.ny : (y2 >= A.ny ? -A.ny : 0);
-  y2 += (y2 < 0) ? A.ny : (y2 >= A.ny ? -A.ny : 0);
+  x1 += (x1 < 0) ? nx : (x1 >= nx ? -nx : 0);
+  x2 += (x2 < 0) ? nx : (x2 >= nx ? -nx : 0);
+  x2 += (x2 < 0) ? nx : (x2 >= nx ? -nx : 0);  // grids of one site
+  y1 += (y1 < 0) ? ny : (y1 >= ny ? -ny : 0);
+  y2 += (y2 < 0) ? ny : (y2 >= ny ? -ny : 0);
+  y2 += (y2 < 0) ? ny : (y2 >= ny ? -ny : 0);
   float2 fx1[NP], fx2[NP], fy1[NP], fy2[NP];
-  load_pairs<S, NP>(A.f_in + (size_t)(y * A.nx + x1) * NN + t * NXI, fx1);
-  load_pairs<S, NP>(A.f_in + (size_t)(y * A.nx + x2) * NN + t * NXI, fx2);
-  load_pairs<S, NP>(A.f_in + (size_t)(y1 * A.nx + x) * NN + t * NXI, fy1);
-  load_pairs<S, NP>(A.f_in + (size_t)(y2 * A.nx + x) * NN + t * NXI, fy2);
+  const S* fev = A.f_in + (size_t)L.base * NN + t * NXI;
+  load_pairs<S, NP>(fev + (size_t)(y * nx + x1) * NN, fx1);
+  load_pairs<S, NP>(fev + (size_t)(y * nx + x2) * NN, fx2);
+  load_pairs<S, NP>(fev + (size_t)(y1 * nx + x) * NN, fy1);
+  load_pairs<S, NP>(fev + (size_t)(y2 * nx + x) * NN, fy2);
 
   // site scalars of the matching of f_in
   const float* q = A.scf + (size_t)site * kSc;
@@ -195,7 +205,8 @@ __global__ void __launch_bounds__(NTH* NPH, (NTH * NPH <= 96 ? 8 : 3))
     for (int p = 0; p < NP; ++p) Drf[p] = fma2(op.Drb[k * NP + p], fk, Drf[p]);
   }
   __syncthreads();
-  const bool pol = A.milne != 0.f;
+  const float milne = A.milne_on ? A.clock->inv_tau_f : 0.f;
+  const bool pol = milne != 0.f;
   if (pol) {  // polar lines (pair, l), one half of the outputs per item
     for (int it = t; it < NXI * NPH; it += NL) {
       const int lq = it % NPH, r = it / NPH, kp = r % NP, half = r / NP;
@@ -227,7 +238,7 @@ __global__ void __launch_bounds__(NTH* NPH, (NTH * NPH <= 96 ? 8 : 3))
   const float A1 = st * (ax * cp + ay * sp);
   const float au = ax * ux + ay * uy;
   const float2 nsx = bc2(-st * fabsf(cp) * A.inv2dx_r), nsy = bc2(-st * fabsf(sp) * A.inv2dx_r);
-  const float2 mmu2 = bc2(A.milne * op.mu2[j]);
+  const float2 mmu2 = bc2(milne * op.mu2[j]), milne2 = bc2(milne);
   constexpr float kLog2e = 1.4426950408889634f;
   const float2 c1 = bc2(-kLog2e * invT * ut), c2 = bc2(kLog2e * invT * M * vu), lZ = bc2(A.log2Z);
   const float2 Gp = bc2(-invT * A1 * ut * M2), Hp = bc2(invT * A1 * M * vu), Jp = bc2(invT * M * au);
@@ -244,7 +255,7 @@ __global__ void __launch_bounds__(NTH* NPH, (NTH * NPH <= 96 ? 8 : 3))
     const float2 Sx = fma2(mfour, fx1[p], fma2(three, f[p], fx2[p]));
     const float2 Sy = fma2(mfour, fy1[p], fma2(three, f[p], fy2[p]));
     float2 r = fma2(mmu2, Drf[p], mul2(op.tv[p], fma2(nsy, Sy, mul2(nsx, Sx))));
-    if (pol) r = add2(r, pth[p * LDK + l * LDL + j]);
+    if (pol) r = fma2(milne2, pth[p * LDK + l * LDL + j], r);
     const float2 ex = fma2(c1, E, fma2(c2, op.s[p], lZ));
     const float2 feq = make_float2(ex2_ftz(ex.x), ex2_ftz(ex.y));
     const float2 cc = fma2(cc1, op.tv[p], cc0), ncc = fma2(ncc1, op.tv[p], ncc0);

@@ -68,10 +68,21 @@ class GridParams:
 _TORCH_DT = {L.RLB_F64: "float64", L.RLB_F32: "float32", L.RLB_BF16: "bfloat16"}
 
 
-class Run:
-    """One simulation on one GPU: EOS table, grid, device buffers, state."""
+@dataclass
+class Event:
+    """One event of a batch: its own periodic nx x ny grid and eta/s."""
+    nx: int
+    ny: int
+    eta_over_s: float
 
-    def __init__(self, grid: GridParams, eos: EosParams | None = None, device: int = 0):
+
+class Run:
+    """One simulation on one GPU: EOS table, grid (or batch of events), device
+    buffers, state.  With `events`, the grid's lattice, precision, dx, tau0,
+    dtau and metric are shared by all events and its nx, ny, eta/s are unused."""
+
+    def __init__(self, grid: GridParams, eos: EosParams | None = None, device: int = 0,
+                 events: list[Event] | None = None):
         import torch
 
         if not torch.cuda.is_available():
@@ -87,10 +98,17 @@ class Run:
         gs, es = grid.c_struct(), self.eos.c_struct()
         self._gs = gs
         self._chk(self.lib.rlb_init_eos(self._h, ctypes.byref(es)), "rlb_init_eos")
-        self._chk(self.lib.rlb_configure(self._h, ctypes.byref(gs)), "rlb_configure")
+        self.events = list(events) if events else None
+        if self.events:
+            arr = (L.EventDescC * len(self.events))(*[L.EventDescC(e.nx, e.ny, e.eta_over_s)
+                                                       for e in self.events])
+            self._chk(self.lib.rlb_configure_batch(self._h, ctypes.byref(gs), len(self.events), arr),
+                      "rlb_configure_batch")
+        else:
+            self._chk(self.lib.rlb_configure(self._h, ctypes.byref(gs)), "rlb_configure")
         sb, xb = ctypes.c_size_t(), ctypes.c_size_t()
-        self._chk(self.lib.rlb_workspace_size(self._h, ctypes.byref(gs), ctypes.byref(sb),
-                                              ctypes.byref(xb)), "rlb_workspace_size")
+        self._chk(self.lib.rlb_workspace_size(self._h, None, ctypes.byref(sb), ctypes.byref(xb)),
+                  "rlb_workspace_size")
         self.state = torch.empty(sb.value, dtype=torch.uint8, device=self.device)
         self.scratch = torch.empty(xb.value, dtype=torch.uint8, device=self.device)
         self._chk(self.lib.rlb_bind_buffers(self._h, ctypes.c_void_p(self.state.data_ptr()),
@@ -100,8 +118,13 @@ class Run:
         self._chk(self.lib.rlb_state_offsets(self._h, ctypes.byref(fo), ctypes.byref(mo),
                                              ctypes.byref(pb)), "rlb_state_offsets")
         self._f_off, self._m_off, self.pop_bytes = fo.value, mo.value, pb.value
-        self.ns = grid.nx * grid.ny
+        self.ns = sum(e.nx * e.ny for e in self.events) if self.events else grid.nx * grid.ny
         self.nn = grid.nodes
+        # first site of every event (batch) or [0]
+        offs = [0]
+        for e in (self.events or []):
+            offs.append(offs[-1] + e.nx * e.ny)
+        self.event_offsets = offs[:-1] if self.events else [0]
 
     # -- helpers --------------------------------------------------------------
     def _stream(self):
