@@ -201,6 +201,8 @@ rlbk::GridMap grid_map(const rlb_ctx* c, char* scr) {
   g.row_event = reinterpret_cast<const int*>(scr + c->rowev_off);
   g.row_y = reinterpret_cast<const int*>(scr + c->rowy_off);
   g.n_events = (int)c->events.size();
+  g.nx0 = c->events[0].nx;
+  g.ny0 = c->events[0].ny;
   return g;
 }
 

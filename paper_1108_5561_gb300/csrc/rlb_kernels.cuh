@@ -314,6 +314,35 @@ __device__ bool eos_invert_f(const EosView& E, int field, float target, float y,
   return true;
 }
 
+// One FP64 Newton step of e(y) = target on the FP64 table from an FP32 root
+// (slope from the FP32 table): the EOS inversion of the FP32 storage path.
+__device__ __forceinline__ double eos_refine(const EosView& E, int field, double target, float y) {
+  double yd = (double)y;
+  int i0;
+  double t, w[6];
+  if (!eos_cell(E, yd, &i0, &t)) return yd;
+  lagrange6(t, w);
+  float dw[6];
+  lagrange6f_d((float)t, dw);
+  double F = 0.0;
+  float dF = 0.f;
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    F += w[m] * __ldg(E.tab + (size_t)(i0 - 2 + m) * 8 + field);
+    dF += dw[m] * __ldg(E.tabf + (size_t)(i0 - 2 + m) * 8 + field);
+  }
+  dF *= E.ih_hi + E.ih_lo;
+  if (!(dF > 0.f)) return yd;
+  return yd - (F - target) * (double)(1.f / dF);
+}
+
+// a + b = s + e exactly (Knuth's TwoSum)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
 // ---------------------------------------------------------------------------
 // Landau matching on the (tau, x, y) block (Eq. sanity).  Boost invariance and
 // the eta_s -> -eta_s reflection of the lattice make the Y row and column of
@@ -324,9 +353,14 @@ __device__ bool eos_invert_f(const EosView& E, int field, float target, float y,
 // space of A - eps (largest cross product of two rows), normalised by the
 // Minkowski norm; eps is then the Rayleigh quotient u_mu u_nu T^{mu nu}.
 // ---------------------------------------------------------------------------
-// FP32 version for the FP32 storage path: the same steps on the matrix scaled
-// by its infinity norm, eps as the Rayleigh quotient of the unscaled T.
-__device__ bool landau3f(const float tm[6], float u[3], float* eps) {
+// Mixed version for the FP32 storage path: Newton from the infinity-norm bound
+// in FP32 on the scaled matrix, then one FP64 Newton step on the FP64 cubic for
+// the eigenvalue (eps = lambda); the eigenvector by the same cross products in
+// FP32 (it is consumed in FP32).
+__device__ bool landau3_mixed(const double tmd[6], float u[3], double* eps) {
+  float tm[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) tm[i] = (float)tmd[i];
   const float sc = fmaxf(fabsf(tm[0]) + fabsf(tm[1]) + fabsf(tm[2]),
                          fmaxf(fabsf(tm[1]) + fabsf(tm[3]) + fabsf(tm[4]),
                                fabsf(tm[2]) + fabsf(tm[4]) + fabsf(tm[5])));
@@ -335,37 +369,52 @@ __device__ bool landau3f(const float tm[6], float u[3], float* eps) {
   const float a00 = tm[0] * is, a01 = -tm[1] * is, a02 = -tm[2] * is;
   const float a10 = -a01, a11 = -tm[3] * is, a12 = -tm[4] * is;
   const float a20 = -a02, a21 = a12, a22 = -tm[5] * is;
-  const float c2 = a00 + a11 + a22;
-  const float c1 = a00 * a11 - a01 * a10 + a00 * a22 - a02 * a20 + a11 * a22 - a12 * a21;
-  const float c0 = a00 * (a11 * a22 - a12 * a21) - a01 * (a10 * a22 - a12 * a20) +
-                   a02 * (a10 * a21 - a11 * a20);
-  float lam = 1.f;  // the infinity norm bounds every eigenvalue
-  for (int it = 0; it < 60; ++it) {
-    const float p = ((lam - c2) * lam + c1) * lam - c0;
-    const float dp = (3.f * lam - 2.f * c2) * lam + c1;
-    if (!(dp > 0.f)) break;
-    const float d = p / dp;
-    if (!(d > 0.f)) break;
-    lam -= d;
-    if (d <= 1e-7f * lam) break;
+  {
+    const float c2 = a00 + a11 + a22;
+    const float c1 = a00 * a11 - a01 * a10 + a00 * a22 - a02 * a20 + a11 * a22 - a12 * a21;
+    const float c0 = a00 * (a11 * a22 - a12 * a21) - a01 * (a10 * a22 - a12 * a20) +
+                     a02 * (a10 * a21 - a11 * a20);
+    float lam = 1.f;  // the infinity norm bounds every eigenvalue
+    for (int it = 0; it < 60; ++it) {
+      const float p = ((lam - c2) * lam + c1) * lam - c0;
+      const float dp = (3.f * lam - 2.f * c2) * lam + c1;
+      if (!(dp > 0.f)) break;
+      const float d = p / dp;
+      if (!(d > 0.f)) break;
+      lam -= d;
+      if (d <= 1e-7f * lam) break;
+    }
+    // FP64 Newton step on the unscaled cubic (slope from FP32)
+    const double b00 = tmd[0], b01 = -tmd[1], b02 = -tmd[2];
+    const double b10 = tmd[1], b11 = -tmd[3], b12 = -tmd[4];
+    const double b20 = tmd[2], b21 = -tmd[4], b22 = -tmd[5];
+    const double d2 = b00 + b11 + b22;
+    const double d1 = b00 * b11 - b01 * b10 + b00 * b22 - b02 * b20 + b11 * b22 - b12 * b21;
+    const double d0 = b00 * (b11 * b22 - b12 * b21) - b01 * (b10 * b22 - b12 * b20) +
+                      b02 * (b10 * b21 - b11 * b20);
+    double L = (double)lam * (double)sc;
+    const double pL = ((L - d2) * L + d1) * L - d0;
+    const float dpf = ((3.f * lam - 2.f * c2) * lam + c1) * sc * sc;
+    if (!(dpf > 0.f)) return false;
+    L -= pL * (double)(1.f / dpf);
+    *eps = L;
+    lam = (float)(L * (double)is);
+    const float r00 = a00 - lam, r11 = a11 - lam, r22 = a22 - lam;
+    const float p0 = a01 * a12 - a02 * r11, p1 = a02 * a10 - r00 * a12, p2 = r00 * r11 - a01 * a10;
+    const float q0 = a01 * r22 - a02 * a21, q1 = a02 * a20 - r00 * r22, q2 = r00 * a21 - a01 * a20;
+    const float s0 = r11 * r22 - a12 * a21, s1 = a12 * a20 - a10 * r22, s2 = a10 * a21 - r11 * a20;
+    const float np = p0 * p0 + p1 * p1 + p2 * p2, nq = q0 * q0 + q1 * q1 + q2 * q2;
+    const float nsq = s0 * s0 + s1 * s1 + s2 * s2;
+    float v0 = s0, v1 = s1, v2 = s2;
+    if (np >= nq && np >= nsq) { v0 = p0; v1 = p1; v2 = p2; }
+    else if (nq >= nsq) { v0 = q0; v1 = q1; v2 = q2; }
+    const float mn = v0 * v0 - v1 * v1 - v2 * v2;
+    if (!(mn > 0.f)) return false;
+    float r = rsqrtf(mn);
+    if (v0 < 0.f) r = -r;
+    u[0] = v0 * r; u[1] = v1 * r; u[2] = v2 * r;
   }
-  const float r00 = a00 - lam, r11 = a11 - lam, r22 = a22 - lam;
-  const float p0 = a01 * a12 - a02 * r11, p1 = a02 * a10 - r00 * a12, p2 = r00 * r11 - a01 * a10;
-  const float q0 = a01 * r22 - a02 * a21, q1 = a02 * a20 - r00 * r22, q2 = r00 * a21 - a01 * a20;
-  const float s0 = r11 * r22 - a12 * a21, s1 = a12 * a20 - a10 * r22, s2 = a10 * a21 - r11 * a20;
-  const float np = p0 * p0 + p1 * p1 + p2 * p2, nq = q0 * q0 + q1 * q1 + q2 * q2;
-  const float nsq = s0 * s0 + s1 * s1 + s2 * s2;
-  float v0 = s0, v1 = s1, v2 = s2;
-  if (np >= nq && np >= nsq) { v0 = p0; v1 = p1; v2 = p2; }
-  else if (nq >= nsq) { v0 = q0; v1 = q1; v2 = q2; }
-  const float mn = v0 * v0 - v1 * v1 - v2 * v2;
-  if (!(mn > 0.f)) return false;
-  float r = rsqrtf(mn);
-  if (v0 < 0.f) r = -r;
-  u[0] = v0 * r; u[1] = v1 * r; u[2] = v2 * r;
-  *eps = u[0] * u[0] * tm[0] - 2.f * u[0] * (u[1] * tm[1] + u[2] * tm[2]) +
-         u[1] * u[1] * tm[3] + 2.f * u[1] * u[2] * tm[4] + u[2] * u[2] * tm[5];
-  return *eps > 0.f;
+  return *eps > 0.0;
 }
 
 __device__ bool landau3(const double tm[6], double u[3], double* eps) {
@@ -441,6 +490,7 @@ struct GridMap {
   const int* row_event;  // event of every global row (device)
   const int* row_y;      // y of every global row inside its event (device)
   int n_events;
+  int nx0, ny0;          // the grid when n_events == 1 (no table reads)
 };
 
 // Position of the site of CTA (row, x) of a stage launch (grid = global rows x
@@ -449,6 +499,16 @@ struct SiteLoc {
   int site, x, y, nx, ny, base;
 };
 __device__ __forceinline__ bool locate_site(const GridMap& G, int row, int x, SiteLoc* L) {
+  if (G.n_events == 1) {
+    if (x >= G.nx0) return false;
+    L->base = 0;
+    L->nx = G.nx0;
+    L->ny = G.ny0;
+    L->x = x;
+    L->y = row;
+    L->site = row * G.nx0 + x;
+    return true;
+  }
   const int e = __ldg(G.row_event + row);
   const int4 v = __ldg(reinterpret_cast<const int4*>(G.ev + e));  // site_off, nx, ny, pad
   if (x >= v.y) return false;
@@ -555,11 +615,11 @@ __device__ __forceinline__ int match_site_d(const MatchArgs& A, int site, double
   o[SC_B] = B; o[SC_K] = pref * m[0]; o[SC_KH] = m[0]; o[SC_T] = T;
   {
     const int nx = evi.nx, ny = evi.ny, x = sxi, yy = syi;
-    const double* m = A.lnM + evi.site_off;
+    const double* lm = A.lnM + evi.site_off;
     const int xp = x + 1 == nx ? 0 : x + 1, xm = x == 0 ? nx - 1 : x - 1;
     const int yp = yy + 1 == ny ? 0 : yy + 1, ym = yy == 0 ? ny - 1 : yy - 1;
-    o[SC_AX] = (m[yy * nx + xp] - m[yy * nx + xm]) * A.inv2dx;
-    o[SC_AY] = (m[yp * nx + x] - m[ym * nx + x]) * A.inv2dx;
+    o[SC_AX] = (lm[yy * nx + xp] - lm[yy * nx + xm]) * A.inv2dx;
+    o[SC_AY] = (lm[yp * nx + x] - lm[ym * nx + x]) * A.inv2dx;
   }
   if (A.obs) {
     const double hc = 0.1973269804, h3 = hc * hc * hc;
@@ -579,33 +639,44 @@ __device__ __forceinline__ int match_site_d(const MatchArgs& A, int site, double
 // instruction occupies the pipe for 64 cycles, so the matching keeps FP64 only
 // for the differences of ln M (central differences of nearly equal values).
 __device__ __forceinline__ int match_site_f(const MatchArgs& A, int site, float (&o)[kSc]) {
-  float m[kMom];
+  // moments: the kMomParts FP32 partial sums combined with TwoSum, then FP64
+  // (FP64 only for T^{mu nu}, the Landau eigenvalue and the EOS Newton step)
+  float m[kMom], mlo[kMom];
   const float4* q = reinterpret_cast<const float4*>(A.momf + (size_t)site * kMom * kMomParts);
 #pragma unroll
   for (int i = 0; i < kMom; ++i) {
-    const float4 v = __ldg(q + i);  // the partial sums of moment i
-    m[i] = (v.x + v.y) + (v.z + v.w);
+    const float4 v = __ldg(q + i);
+    float s1, e1, s2, e2, s, e;
+    two_sum(v.x, v.y, s1, e1);
+    two_sum(v.z, v.w, s2, e2);
+    two_sum(s1, s2, s, e);
+    e += e1 + e2;
+    two_sum(s, e, m[i], mlo[i]);  // m + mlo = the compensated sum
   }
   const double lnMd = A.lnM[site];
-  const float M = expf((float)lnMd);
-  const float M2 = M * M;
-  const float pref = M2 * M2 * (float)(1.0 / (2.0 * 3.14159265358979323846 * 3.14159265358979323846));
-  float tm[6];
+  const double Md = exp(lnMd);
+  const double prefd = Md * Md * Md * Md * (1.0 / (2.0 * 3.14159265358979323846 * 3.14159265358979323846));
+  const float M = (float)Md, pref = (float)prefd;
+  double tmd[6];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) tm[i] = pref * m[1 + i];
+  for (int i = 0; i < 6; ++i) tmd[i] = prefd * ((double)m[1 + i] + (double)mlo[1 + i]);
   int err = 0;
-  float u[3], eps;
-  if (!landau3f(tm, u, &eps)) {
+  float u[3];
+  double epsd;
+  if (!landau3_mixed(tmd, u, &epsd)) {
     err |= ERR_LANDAU;
     u[0] = 1.f; u[1] = 0.f; u[2] = 0.f;
-    eps = fmaxf(tm[0], 1e-30f);
+    epsd = fmax(tmd[0], 1e-300);
   }
+  const float eps = (float)epsd;
   const float Tg = (float)A.Tsite[site];
   const float yg = (Tg > 0.f) ? logf(Tg) : 0.f;
   float y;
   if (!eos_invert_f(A.eos, EOS_E, eps, yg, &y)) {
     err |= ERR_EOS;
     y = fminf(fmaxf(yg, (float)(A.eos.y0 + 2.0 / A.eos.inv_h)), (float)(A.eos.y0 + (A.eos.n - 4) / A.eos.inv_h));
+  } else {
+    y = (float)eos_refine(A.eos, EOS_E, epsd, y);
   }
   int i0;
   float t, w[6];
@@ -627,21 +698,21 @@ __device__ __forceinline__ int match_site_f(const MatchArgs& A, int site, float 
   o[SC_B] = B; o[SC_K] = pref * m[0]; o[SC_KH] = m[0]; o[SC_T] = T;
   {
     const int nx = evi.nx, ny = evi.ny, x = sxi, yy = syi;
-    const double* m = A.lnM + evi.site_off;
+    const double* lm = A.lnM + evi.site_off;
     const int xp = x + 1 == nx ? 0 : x + 1, xm = x == 0 ? nx - 1 : x - 1;
     const int yp = yy + 1 == ny ? 0 : yy + 1, ym = yy == 0 ? ny - 1 : yy - 1;
     const float i2dx = (float)A.inv2dx;
-    o[SC_AX] = (float)(m[yy * nx + xp] - m[yy * nx + xm]) * i2dx;
-    o[SC_AY] = (float)(m[yp * nx + x] - m[ym * nx + x]) * i2dx;
+    o[SC_AX] = (float)(lm[yy * nx + xp] - lm[yy * nx + xm]) * i2dx;
+    o[SC_AY] = (float)(lm[yp * nx + x] - lm[ym * nx + x]) * i2dx;
   }
   if (A.obs) {
     const double hc = 0.1973269804, h3 = hc * hc * hc;
     double* r = A.obs + (size_t)site * 8;
-    r[0] = ((double)eps + (double)B) / h3;
+    r[0] = (epsd + (double)B) / h3;
     r[1] = T;
     r[2] = u[0]; r[3] = u[1]; r[4] = u[2];
     r[5] = M;
-    r[6] = ((double)pref * (double)m[7] - (double)B) / h3;
+    r[6] = (prefd * ((double)m[7] + (double)mlo[7]) - (double)B) / h3;
     r[7] = Meq;
   }
   return err;
