@@ -213,6 +213,26 @@ rlb_status rlb_state_blob_size(const rlb_ctx* ctx, size_t* bytes);
 rlb_status rlb_save_state(rlb_ctx* ctx, void* host_buf, size_t bytes, void* stream);
 rlb_status rlb_load_state(rlb_ctx* ctx, const void* host_buf, size_t bytes, void* stream);
 
+/* Launch tuning.  rlb_step records one time step (match, predictor stage,
+ * match, corrector stage) as a CUDA graph on the context's own stream the first
+ * time it runs and replays it for every step; the caller's stream is ordered
+ * before and after the replays with events, so the call stays asynchronous on
+ * `stream`.  The launch parameters are the same for every step because the
+ * proper time lives in a device clock.  rlb_set_graphs(ctx, 0) switches back
+ * to plain launches (per-kernel timing does so by itself).  The graph is
+ * recaptured after rlb_bind_buffers or rlb_autotune.
+ *
+ * rlb_autotune times every compiled variant of the stage kernel for the
+ * configured lattice and precision (packed FP32 kernel with and without its
+ * register cap, generic kernel; one variant for lattices only the generic
+ * kernel takes) on three predictor launches over the current state, and keeps
+ * the fastest for later steps.  The state (f, ln M, tau) is unchanged.  Outputs:
+ * the chosen variant, optionally the milliseconds per launch of each variant
+ * (variant_ms holds at least 3 doubles) and their number.  Synchronises
+ * `stream`.  Implementation choices, not part of the paper's scheme. */
+rlb_status rlb_autotune(rlb_ctx* ctx, void* stream, int* chosen, double* variant_ms, int* n_variants);
+rlb_status rlb_set_graphs(rlb_ctx* ctx, int enable);
+
 /* Current proper time (host bookkeeping, fm/c). */
 rlb_status rlb_get_tau(const rlb_ctx* ctx, double* tau);
 

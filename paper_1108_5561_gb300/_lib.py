@@ -18,7 +18,7 @@ EXPORTS = ["rlb_create", "rlb_destroy", "rlb_last_error", "rlb_init_eos", "rlb_w
            "rlb_moments", "rlb_check", "rlb_state_offsets", "rlb_lattice", "rlb_operators",
            "rlb_set_timing", "rlb_get_timing", "rlb_step_static_scratch", "rlb_observables",
            "rlb_state_blob_size", "rlb_save_state", "rlb_load_state", "rlb_configure_batch",
-           "rlb_init_batch"]
+           "rlb_init_batch", "rlb_autotune", "rlb_set_graphs"]
 
 
 class EosParamsC(ctypes.Structure):
@@ -93,6 +93,8 @@ def load(build_if_missing: bool = True):
     lib.rlb_load_state.argtypes = [vp, vp, sz, vp]
     lib.rlb_configure_batch.argtypes = [vp, P(GridParamsC), ctypes.c_int, P(EventDescC)]
     lib.rlb_init_batch.argtypes = [vp, dp, ctypes.c_int, vp]
+    lib.rlb_autotune.argtypes = [vp, vp, P(ctypes.c_int), dp, P(ctypes.c_int)]
+    lib.rlb_set_graphs.argtypes = [vp, ctypes.c_int]
     for name in EXPORTS:
         if name not in ("rlb_destroy", "rlb_last_error"):
             getattr(lib, name).restype = ctypes.c_int

@@ -29,14 +29,19 @@ struct rlb_ctx {
   size_t f_off = 0, lnM_off = 0;  // state
   size_t fs_off = 0, lnMs_off = 0, T_off = 0, err_off = 0, tab_off = 0, eps_off = 0;  // scratch
   size_t mom_off = 0, moms_off = 0, sc_off = 0, tabf_off = 0, scf_off = 0;
-  size_t ev_off = 0, rowev_off = 0, rowy_off = 0, clock_off = 0;
-  // events: one for a single grid, n for a batch; rows of all events in order
+  size_t ev_off = 0, loc_off = 0, clock_off = 0;
+  // events: one for a single grid, n for a batch (with a per-site locator)
   std::vector<rlbk::EventInfo> events;
-  std::vector<int> row_event, row_y;
-  size_t rows = 0, max_nx = 0;
+  std::vector<int2> loc;
   char* state = nullptr;
   char* scratch = nullptr;
   double tau = 0.0;
+  // one step captured as a CUDA graph (on the first rlb_step), replayed after
+  bool graphs = true;
+  cudaStream_t gstream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaEvent_t gev[2] = {nullptr, nullptr};
+  int stage_variant = 0;  // rlb_autotune's choice (see Stager)
   // optional per-kernel timing (CUDA events on the launch stream)
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -72,11 +77,11 @@ bool supported_shape(int nxi, int nth, int nph) {
          (nxi == 8 && nth == 8 && nph == 2);
 }
 
-// sites, rows and events of a configuration (one grid or a batch of events)
+// sites and events of a configuration (one grid or a batch of events)
 struct Shape {
-  size_t ns, rows, events;
+  size_t ns, events;
 };
-Shape grid_shape(const rlb_grid_params& g) { return {(size_t)g.nx * g.ny, (size_t)g.ny, 1}; }
+Shape grid_shape(const rlb_grid_params& g) { return {(size_t)g.nx * g.ny, 1}; }
 
 void layout(const rlb_grid_params& g, const Shape& sh, size_t table_points, size_t* state_b,
             size_t* scratch_b, rlb_ctx* c) {
@@ -103,12 +108,11 @@ void layout(const rlb_grid_params& g, const Shape& sh, size_t table_points, size
   size_t tabf_off = off; off += align256((table_points + 6) * rlb::kFields * sizeof(float));
   size_t scf_off = off; off += align256(ns * rlbk::kSc * sizeof(float));
   size_t ev_off = off; off += align256(sh.events * sizeof(rlbk::EventInfo));
-  size_t rowev_off = off; off += align256(sh.rows * sizeof(int));
-  size_t rowy_off = off; off += align256(sh.rows * sizeof(int));
+  size_t loc_off = off; off += sh.events > 1 ? align256(ns * sizeof(int2)) : 0;
   size_t clock_off = off; off += 256;
   *scratch_b = off;
   if (c) {
-    c->ev_off = ev_off; c->rowev_off = rowev_off; c->rowy_off = rowy_off; c->clock_off = clock_off;
+    c->ev_off = ev_off; c->loc_off = loc_off; c->clock_off = clock_off;
     c->f_off = f_off; c->lnM_off = lnM_off;
     c->fs_off = fs_off; c->lnMs_off = lnMs_off; c->T_off = T_off; c->eps_off = eps_off;
     c->err_off = err_off; c->tab_off = tab_off;
@@ -193,13 +197,18 @@ rlbk::EosView eos_view(const rlb_ctx* c) {
   return v;
 }
 
-Shape ctx_shape(const rlb_ctx* c) { return {c->ns, c->rows, c->events.size()}; }
+Shape ctx_shape(const rlb_ctx* c) { return {c->ns, c->events.size()}; }
+
+// CTA grid of the per-site kernels (see rlbk::locate_site)
+dim3 site_grid(const rlb_ctx* c) {
+  if (c->events.size() == 1) return dim3((unsigned)c->events[0].ny, (unsigned)c->events[0].nx, 1);
+  return dim3((unsigned)c->ns, 1, 1);
+}
 
 rlbk::GridMap grid_map(const rlb_ctx* c, char* scr) {
   rlbk::GridMap g;
   g.ev = reinterpret_cast<const rlbk::EventInfo*>(scr + c->ev_off);
-  g.row_event = reinterpret_cast<const int*>(scr + c->rowev_off);
-  g.row_y = reinterpret_cast<const int*>(scr + c->rowy_off);
+  g.loc = reinterpret_cast<const int2*>(scr + c->loc_off);
   g.n_events = (int)c->events.size();
   g.nx0 = c->events[0].nx;
   g.ny0 = c->events[0].ny;
@@ -210,10 +219,9 @@ rlbk::GridMap grid_map(const rlb_ctx* c, char* scr) {
 rlb_status upload_tables(rlb_ctx* ctx, char* scr, cudaStream_t st) {
   RLB_CUDA(cudaMemcpyAsync(scr + ctx->ev_off, ctx->events.data(), ctx->events.size() * sizeof(rlbk::EventInfo),
                            cudaMemcpyHostToDevice, st), "event table upload");
-  RLB_CUDA(cudaMemcpyAsync(scr + ctx->rowev_off, ctx->row_event.data(), ctx->rows * sizeof(int),
-                           cudaMemcpyHostToDevice, st), "row table upload");
-  RLB_CUDA(cudaMemcpyAsync(scr + ctx->rowy_off, ctx->row_y.data(), ctx->rows * sizeof(int),
-                           cudaMemcpyHostToDevice, st), "row table upload");
+  if (ctx->events.size() > 1)
+    RLB_CUDA(cudaMemcpyAsync(scr + ctx->loc_off, ctx->loc.data(), ctx->loc.size() * sizeof(int2),
+                             cudaMemcpyHostToDevice, st), "site locator upload");
   return RLB_OK;
 }
 
@@ -223,23 +231,20 @@ rlb_status set_clock(rlb_ctx* ctx, char* scr, double tau, cudaStream_t st) {
   return RLB_OK;
 }
 
-// events and rows of a configuration (ctx->gp holds the shared parameters)
+// events of a configuration and, for a batch, the per-site locator (ctx->gp
+// holds the shared parameters)
 void set_events(rlb_ctx* ctx, const std::vector<rlbk::EventInfo>& ev) {
   ctx->events = ev;
-  ctx->row_event.clear();
-  ctx->row_y.clear();
-  ctx->max_nx = 0;
+  ctx->loc.clear();
   size_t ns = 0;
-  for (size_t e = 0; e < ev.size(); ++e) {
-    for (int y = 0; y < ev[e].ny; ++y) {
-      ctx->row_event.push_back((int)e);
-      ctx->row_y.push_back(y);
-    }
-    ctx->max_nx = std::max(ctx->max_nx, (size_t)ev[e].nx);
-    ns += (size_t)ev[e].nx * ev[e].ny;
-  }
+  for (size_t e = 0; e < ev.size(); ++e) ns += (size_t)ev[e].nx * ev[e].ny;
   ctx->ns = ns;
-  ctx->rows = ctx->row_event.size();
+  if (ev.size() > 1) {
+    ctx->loc.reserve(ns);
+    for (size_t e = 0; e < ev.size(); ++e)
+      for (int y = 0; y < ev[e].ny; ++y)
+        for (int x = 0; x < ev[e].nx; ++x) ctx->loc.push_back(make_int2((int)e, (y << 16) | x));
+  }
 }
 
 enum Kind { K_STAGE = 0, K_MATCH = 1, K_INIT = 2 };
@@ -301,13 +306,18 @@ struct Stager {
   static constexpr bool kX2 =
       std::is_same<R, float>::value && NXI % 2 == 0 && NTH % 2 == 0 && (NTH * NPH) % 32 == 0;
   static constexpr int NL = NTH * NPH;
+  // variants the autotuner times: packed kernel with the register cap, packed
+  // without it, generic kernel (lattices the packed kernel does not take: generic only)
+  static constexpr int kVariants = kX2 ? 3 : 1;
   rlbk::StageArgs<S, R, NXI, NTH, NPH> a;
   rlbk::StageArgsX2<S, NXI, NTH, NPH> b;
   dim3 grid;
+  int variant = 0;
 
   // scr: the scratch block holding the event tables and the clock
   Stager(const rlb_ctx* ctx, char* scr, const double* sc, const float* scf, int* err) {
-    grid = dim3((unsigned)ctx->rows, (unsigned)ctx->max_nx, 1);
+    variant = ctx->stage_variant < kVariants ? ctx->stage_variant : 0;
+    grid = site_grid(ctx);
     const double dtau = ctx->gp.dtau, inv2dx = 1.0 / (2.0 * ctx->gp.dx);
     const rlbk::GridMap gm = grid_map(ctx, scr);
     const rlbk::Clock* clock = reinterpret_cast<const rlbk::Clock*>(scr + ctx->clock_off);
@@ -315,6 +325,12 @@ struct Stager {
       b.scf = scf;
       b.err = err;
       b.grid = gm;
+      // the generic kernel as well, for variant 2
+      a.sc = sc; a.scf = scf; a.err = err; a.grid = gm; a.clock = clock;
+      a.milne_on = ctx->gp.metric == RLB_MILNE;
+      a.dtau = dtau; a.inv2dx = inv2dx; a.dtau_r = (R)dtau; a.inv2dx_r = (R)inv2dx;
+      a.Z = (R)ctx->eosp.Z;
+      a.op = make_ops<R, NXI, NTH, NPH>(ctx->lat);
       b.clock = clock;
       b.milne_on = ctx->gp.metric == RLB_MILNE;
       b.dtau = dtau;
@@ -344,11 +360,16 @@ struct Stager {
   void launch(const S* f_in, const double* lnM_in, const S* f_base, const double* lnM_base, S* f_out,
               double* lnM_out, double* mom_out, int mode, cudaStream_t st) {
     if constexpr (kX2) {
-      b.f_in = f_in; b.lnM_in = lnM_in; b.f_base = f_base; b.lnM_base = lnM_base;
-      b.f_out = f_out; b.lnM_out = lnM_out; b.momf_out = reinterpret_cast<float*>(mom_out);
-      b.mode = mode;
-      rlbk::stage_kernel_x2<S, NXI, NTH, NPH><<<grid, NL, 0, st>>>(b);
-    } else {
+      if (variant < 2) {
+        b.f_in = f_in; b.lnM_in = lnM_in; b.f_base = f_base; b.lnM_base = lnM_base;
+        b.f_out = f_out; b.lnM_out = lnM_out; b.momf_out = reinterpret_cast<float*>(mom_out);
+        b.mode = mode;
+        if (variant == 0) rlbk::stage_kernel_x2<S, NXI, NTH, NPH><<<grid, NL, 0, st>>>(b);
+        else rlbk::stage_kernel_x2<S, NXI, NTH, NPH, 1><<<grid, NL, 0, st>>>(b);
+        return;
+      }
+    }
+    {
       a.f_in = f_in; a.lnM_in = lnM_in; a.f_base = f_base; a.lnM_base = lnM_base;
       a.f_out = f_out; a.lnM_out = lnM_out; a.mom_out = mom_out; a.momf_out = reinterpret_cast<float*>(mom_out);
       a.mode = mode;
@@ -399,8 +420,9 @@ struct Runner {
     return RLB_OK;
   }
 
-  // One predictor-corrector step = match(f) -> stage(f -> f*) -> match(f*) -> stage(f*, f -> f).
-  static rlb_status step(rlb_ctx* ctx, int nsteps, cudaStream_t st) {
+  // One predictor-corrector step = match(f) -> stage(f -> f*) -> match(f*) -> stage(f*, f -> f),
+  // enqueued on st (the host clock is not advanced here).
+  static rlb_status enqueue_step(rlb_ctx* ctx, cudaStream_t st) {
     S* f = reinterpret_cast<S*>(ctx->state + ctx->f_off);
     S* fs = reinterpret_cast<S*>(ctx->scratch + ctx->fs_off);
     double* m = reinterpret_cast<double*>(ctx->state + ctx->lnM_off);
@@ -411,26 +433,129 @@ struct Runner {
                                    reinterpret_cast<const float*>(ctx->scratch + ctx->scf_off),
                                    reinterpret_cast<int*>(ctx->scratch + ctx->err_off));
     rlbk::Clock* clock = reinterpret_cast<rlbk::Clock*>(ctx->scratch + ctx->clock_off);
+    // predictor: f* = f + dtau RHS(f) at tau
+    rlb_status r = match(ctx, mom, m, nullptr, st);
+    if (r) return r;
+    {
+      Timed tm(ctx, K_STAGE, st);
+      sg.launch(f, m, f, m, fs, ms, moms, 0, st);
+    }
+    RLB_CUDA(cudaGetLastError(), "stage kernel (predictor) launch");
+    // corrector: f = (f + f* + dtau RHS(f*))/2 at tau + dtau, in place over f;
+    // its matching moves the device clock to tau + dtau
+    r = match(ctx, moms, ms, nullptr, st, clock);
+    if (r) return r;
+    {
+      Timed tm(ctx, K_STAGE, st);
+      sg.launch(fs, ms, f, m, f, m, mom, 1, st);
+    }
+    RLB_CUDA(cudaGetLastError(), "stage kernel (corrector) launch");
+    return RLB_OK;
+  }
+
+  // One step captured once as a CUDA graph on the context's own stream (all of
+  // its launch parameters are the same from step to step: the time lives in the
+  // device clock).  A failed capture turns graphs off for the context.
+  static rlb_status ensure_graph(rlb_ctx* ctx) {
+    if (ctx->gexec) return RLB_OK;
+    if (!ctx->gstream) {
+      RLB_CUDA(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking), "graph stream");
+      RLB_CUDA(cudaEventCreateWithFlags(&ctx->gev[0], cudaEventDisableTiming), "graph event");
+      RLB_CUDA(cudaEventCreateWithFlags(&ctx->gev[1], cudaEventDisableTiming), "graph event");
+    }
+    RLB_CUDA(cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal), "graph capture");
+    const rlb_status r = enqueue_step(ctx, ctx->gstream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(ctx->gstream, &g);
+    if (r != RLB_OK || e != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      ctx->graphs = false;
+      return r != RLB_OK ? r : cuda_fail(ctx, e, "graph capture");
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&ctx->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      ctx->gexec = nullptr;
+      ctx->graphs = false;
+      return cuda_fail(ctx, ei, "graph instantiate");
+    }
+    return RLB_OK;
+  }
+
+  static rlb_status step(rlb_ctx* ctx, int nsteps, cudaStream_t st) {
+    if (nsteps <= 0) return RLB_OK;
+    if (ctx->graphs && !ctx->timing && ensure_graph(ctx) == RLB_OK) {
+      RLB_CUDA(cudaEventRecord(ctx->gev[0], st), "graph order");
+      RLB_CUDA(cudaStreamWaitEvent(ctx->gstream, ctx->gev[0], 0), "graph order");
+      for (int s = 0; s < nsteps; ++s) {
+        RLB_CUDA(cudaGraphLaunch(ctx->gexec, ctx->gstream), "graph launch");
+        ctx->tau += ctx->gp.dtau;
+      }
+      RLB_CUDA(cudaEventRecord(ctx->gev[1], ctx->gstream), "graph order");
+      RLB_CUDA(cudaStreamWaitEvent(st, ctx->gev[1], 0), "graph order");
+      return RLB_OK;
+    }
     for (int s = 0; s < nsteps; ++s) {
-      // predictor: f* = f + dtau RHS(f) at tau
-      rlb_status r = match(ctx, mom, m, nullptr, st);
+      rlb_status r = enqueue_step(ctx, st);
       if (r) return r;
-      {
-        Timed tm(ctx, K_STAGE, st);
-        sg.launch(f, m, f, m, fs, ms, moms, 0, st);
-      }
-      RLB_CUDA(cudaGetLastError(), "stage kernel (predictor) launch");
-      // corrector: f = (f + f* + dtau RHS(f*))/2 at tau + dtau, in place over f;
-      // its matching moves the device clock to tau + dtau
-      r = match(ctx, moms, ms, nullptr, st, clock);
-      if (r) return r;
-      {
-        Timed tm(ctx, K_STAGE, st);
-        sg.launch(fs, ms, f, m, f, m, mom, 1, st);
-      }
-      RLB_CUDA(cudaGetLastError(), "stage kernel (corrector) launch");
       ctx->tau += ctx->gp.dtau;
     }
+    return RLB_OK;
+  }
+
+  // Time every stage-kernel variant on predictor launches over the current state
+  // and keep the fastest; f, ln M and the clock are untouched, the Newton
+  // starting temperatures are restored.
+  static rlb_status autotune(rlb_ctx* ctx, double* ms, int* nvar, cudaStream_t st) {
+    constexpr int NV = Stager<S, R, NXI, NTH, NPH>::kVariants;
+    S* f = reinterpret_cast<S*>(ctx->state + ctx->f_off);
+    S* fs = reinterpret_cast<S*>(ctx->scratch + ctx->fs_off);
+    double* m = reinterpret_cast<double*>(ctx->state + ctx->lnM_off);
+    double* ms_ = reinterpret_cast<double*>(ctx->scratch + ctx->lnMs_off);
+    double* mom = reinterpret_cast<double*>(ctx->scratch + ctx->mom_off);
+    double* moms = reinterpret_cast<double*>(ctx->scratch + ctx->moms_off);
+    double* Tsite = reinterpret_cast<double*>(ctx->scratch + ctx->T_off);
+    double* Tsave = reinterpret_cast<double*>(ctx->scratch + ctx->eps_off);  // free between steps
+    RLB_CUDA(cudaMemcpyAsync(Tsave, Tsite, ctx->ns * sizeof(double), cudaMemcpyDeviceToDevice, st), "autotune save");
+    rlb_status r = match(ctx, mom, m, nullptr, st);
+    if (r) return r;
+    cudaEvent_t e0, e1;
+    RLB_CUDA(cudaEventCreate(&e0), "autotune event");
+    RLB_CUDA(cudaEventCreate(&e1), "autotune event");
+    const int keep = ctx->stage_variant;
+    int best = 0;
+    for (int v = 0; v < NV; ++v) {
+      ctx->stage_variant = v;
+      Stager<S, R, NXI, NTH, NPH> sg(ctx, ctx->scratch, reinterpret_cast<const double*>(ctx->scratch + ctx->sc_off),
+                                     reinterpret_cast<const float*>(ctx->scratch + ctx->scf_off),
+                                     reinterpret_cast<int*>(ctx->scratch + ctx->err_off));
+      sg.launch(f, m, f, m, fs, ms_, moms, 0, st);  // warm-up
+      cudaEventRecord(e0, st);
+      for (int k = 0; k < 3; ++k) sg.launch(f, m, f, m, fs, ms_, moms, 0, st);
+      cudaEventRecord(e1, st);
+      const cudaError_t ce = cudaEventSynchronize(e1);
+      if (ce != cudaSuccess) {
+        ctx->stage_variant = keep;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return cuda_fail(ctx, ce, "autotune launch");
+      }
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (ms) ms[v] = t / 3.0;
+      if (v > 0 && ms && ms[v] < ms[best]) best = v;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    RLB_CUDA(cudaMemcpyAsync(Tsite, Tsave, ctx->ns * sizeof(double), cudaMemcpyDeviceToDevice, st), "autotune restore");
+    RLB_CUDA(cudaStreamSynchronize(st), "autotune synchronise");
+    ctx->stage_variant = best;
+    if (ctx->gexec) {  // the captured step used the previous choice
+      cudaGraphExecDestroy(ctx->gexec);
+      ctx->gexec = nullptr;
+    }
+    if (nvar) *nvar = NV;
     return RLB_OK;
   }
 };
@@ -458,13 +583,19 @@ rlb_status observables(rlb_ctx* ctx, double* out_dev, cudaStream_t st) {
   return RLB_OK;
 }
 
-enum Op { OP_INIT, OP_STEP, OP_MOMENTS, OP_OBS };
+enum Op { OP_INIT, OP_STEP, OP_MOMENTS, OP_OBS, OP_TUNE };
 
 template <class S, class R, int NXI, int NTH, int NPH>
 rlb_status run_op(rlb_ctx* c, Op op, int n, double* p, cudaStream_t st) {
   using Rn = Runner<S, R, NXI, NTH, NPH>;
   if (op == OP_INIT) return Rn::init(c, p, st);
   if (op == OP_STEP) return Rn::step(c, n, st);
+  if (op == OP_TUNE) {
+    int nv = 0;
+    rlb_status r = Rn::autotune(c, p, &nv, st);
+    if (!r && p) p[3] = nv;  // p: 4 doubles (3 variant times + count)
+    return r;
+  }
   if (op == OP_OBS) return observables<S, R, NXI, NTH, NPH>(c, p, st);
   return RLB_ERR_ARG;
 }
@@ -638,6 +769,10 @@ rlb_status rlb_create(rlb_ctx** out, int cuda_device) {
 
 void rlb_destroy(rlb_ctx* ctx) {
   if (!ctx) return;
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
+  for (cudaEvent_t e : ctx->gev)
+    if (e) cudaEventDestroy(e);
   for (auto& p : ctx->ev_pending) { ctx->ev_pool.push_back(p.second.first); ctx->ev_pool.push_back(p.second.second); }
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   delete ctx;
@@ -711,8 +846,8 @@ rlb_status rlb_configure_batch(rlb_ctx* ctx, const rlb_grid_params* base, int n_
   int max_nx = 0;
   for (int e = 0; e < n_events; ++e) {
     const rlb_event_desc& d = events[e];
-    if (d.nx < 1 || d.ny < 1 || d.nx > 65535 || !(d.eta_over_s > 0))
-      return fail(ctx, RLB_ERR_ARG, "invalid event (nx in [1, 65535], ny >= 1, eta/s > 0)");
+    if (d.nx < 1 || d.ny < 1 || d.nx > 65535 || d.ny > 32767 || !(d.eta_over_s > 0))
+      return fail(ctx, RLB_ERR_ARG, "invalid event (nx in [1, 65535], ny in [1, 32767], eta/s > 0)");
     ev[e] = rlbk::EventInfo{(int)ns, d.nx, d.ny, 0, d.eta_over_s, 0.0};
     ns += (size_t)d.nx * d.ny;
     rows += (size_t)d.ny;
@@ -740,6 +875,10 @@ rlb_status rlb_bind_buffers(rlb_ctx* ctx, void* state, void* scratch, void* stre
   if (s) return s;
   ctx->state = static_cast<char*>(state);
   ctx->scratch = static_cast<char*>(scratch);
+  if (ctx->gexec) {  // captured with the previous buffers
+    cudaGraphExecDestroy(ctx->gexec);
+    ctx->gexec = nullptr;
+  }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   RLB_CUDA(cudaMemcpyAsync(ctx->scratch + ctx->tab_off, ctx->tab.data.data(),
                            ctx->tab.data.size() * sizeof(double), cudaMemcpyHostToDevice, st),
@@ -994,6 +1133,28 @@ rlb_status rlb_load_state(rlb_ctx* ctx, const void* host_buf, size_t bytes, void
   if (s) return s;
   RLB_CUDA(cudaStreamSynchronize(st), "state upload synchronise");
   ctx->inited = true;
+  return RLB_OK;
+}
+
+rlb_status rlb_autotune(rlb_ctx* ctx, void* stream, int* chosen, double* variant_ms, int* n_variants) {
+  if (!ctx || !chosen) return RLB_ERR_ARG;
+  if (!ctx->inited) return fail(ctx, RLB_ERR_STATE, "rlb_init_grid or rlb_load_state must come first");
+  rlb_status s = set_device(ctx);
+  if (s) return s;
+  double t[4] = {0.0, 0.0, 0.0, 0.0};
+  s = dispatch(ctx, OP_TUNE, 0, t, static_cast<cudaStream_t>(stream));
+  if (s) return s;
+  *chosen = ctx->stage_variant;
+  const int nv = (int)t[3];
+  if (n_variants) *n_variants = nv;
+  if (variant_ms)
+    for (int v = 0; v < nv; ++v) variant_ms[v] = t[v];
+  return RLB_OK;
+}
+
+rlb_status rlb_set_graphs(rlb_ctx* ctx, int enable) {
+  if (!ctx) return RLB_ERR_ARG;
+  ctx->graphs = enable != 0;
   return RLB_OK;
 }
 

@@ -487,49 +487,39 @@ struct alignas(16) EventInfo {
 static_assert(sizeof(EventInfo) == 32 && alignof(EventInfo) == 16, "EventInfo layout");
 struct GridMap {
   const EventInfo* ev;   // n_events entries (device)
-  const int* row_event;  // event of every global row (device)
-  const int* row_y;      // y of every global row inside its event (device)
+  const int2* loc;       // per site (event, y << 16 | x) when n_events > 1 (device)
   int n_events;
   int nx0, ny0;          // the grid when n_events == 1 (no table reads)
 };
 
-// Position of the site of CTA (row, x) of a stage launch (grid = global rows x
-// widest row); false for the padding CTAs beyond a narrower event's row.
+// Launch grid of the per-site kernels: (ny, nx) CTAs for one grid (CTA (y, x)),
+// one CTA per site for a batch.
 struct SiteLoc {
   int site, x, y, nx, ny, base;
 };
-__device__ __forceinline__ bool locate_site(const GridMap& G, int row, int x, SiteLoc* L) {
+__device__ __forceinline__ void locate_site(const GridMap& G, int bx, int by, SiteLoc* L) {
   if (G.n_events == 1) {
-    if (x >= G.nx0) return false;
     L->base = 0;
     L->nx = G.nx0;
     L->ny = G.ny0;
-    L->x = x;
-    L->y = row;
-    L->site = row * G.nx0 + x;
-    return true;
+    L->x = by;
+    L->y = bx;
+    L->site = bx * G.nx0 + by;
+    return;
   }
-  const int e = __ldg(G.row_event + row);
-  const int4 v = __ldg(reinterpret_cast<const int4*>(G.ev + e));  // site_off, nx, ny, pad
-  if (x >= v.y) return false;
+  const int2 c = __ldg(G.loc + bx);
+  const int4 v = __ldg(reinterpret_cast<const int4*>(G.ev + c.x));  // site_off, nx, ny, pad
   L->base = v.x;
   L->nx = v.y;
   L->ny = v.z;
-  L->x = x;
-  L->y = __ldg(G.row_y + row);
-  L->site = v.x + L->y * v.y + x;
-  return true;
+  L->x = c.y & 0xffff;
+  L->y = c.y >> 16;
+  L->site = bx;
 }
 
-// Event holding `site` (binary search over the event offsets, log2 n_events steps).
+// Event holding `site`.
 __device__ __forceinline__ int event_of_site(const GridMap& G, int site) {
-  int lo = 0, hi = G.n_events - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (G.ev[mid].site_off <= site) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
+  return G.n_events == 1 ? 0 : __ldg(G.loc + site).x;
 }
 
 // Proper time of the state being advanced, in device memory: the matching
@@ -559,11 +549,16 @@ struct MatchArgs {
 
 // Position of a site inside its event (matching: one thread per site).
 __device__ __forceinline__ void site_xy(const GridMap& G, int site, int* e, int* x, int* y) {
-  *e = event_of_site(G, site);
-  const EventInfo& v = G.ev[*e];
-  const int loc = site - v.site_off;
-  *y = loc / v.nx;
-  *x = loc - *y * v.nx;
+  if (G.n_events == 1) {
+    *e = 0;
+    *y = site / G.nx0;
+    *x = site - *y * G.nx0;
+    return;
+  }
+  const int2 c = __ldg(G.loc + site);
+  *e = c.x;
+  *y = c.y >> 16;
+  *x = c.y & 0xffff;
 }
 
 // Matching of one site in FP64 (FP64 storage path): Landau (u, eps_kin), T from
@@ -941,7 +936,7 @@ __global__ void __launch_bounds__(NTH* NPH)
   constexpr int NW = (NL + 31) / 32;
   const auto& op = A.op;
   SiteLoc L;
-  if (!locate_site(A.grid, blockIdx.x, blockIdx.y, &L)) return;  // padding CTA: whole block
+  locate_site(A.grid, blockIdx.x, blockIdx.y, &L);
   const int x = L.x, y = L.y, site = L.site, nx = L.nx, ny = L.ny;
   const int t = threadIdx.x;
   const int j = t % NTH, l = t / NTH;

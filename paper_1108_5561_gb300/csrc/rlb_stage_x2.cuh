@@ -132,10 +132,11 @@ __device__ __forceinline__ void store_pairs(S* __restrict__ p, float2 (&v)[NP]) 
   }
 }
 
-// 8 resident blocks of 96 threads cap the registers at 80: measured faster than
-// the uncapped 88 (fewer warps left waiting on memory)
-template <class S, int NXI, int NTH, int NPH>
-__global__ void __launch_bounds__(NTH* NPH, (NTH * NPH <= 96 ? 8 : 3))
+// MINB resident blocks per SM bound the registers (8 blocks of 96 threads: 80
+// registers, measured faster than the uncapped 88 on the 256^2 workload; the
+// autotuner times both)
+template <class S, int NXI, int NTH, int NPH, int MINB = (NTH * NPH <= 96 ? 8 : 3)>
+__global__ void __launch_bounds__(NTH* NPH, MINB)
     stage_kernel_x2(const __grid_constant__ StageArgsX2<S, NXI, NTH, NPH> A) {
   static_assert(NXI % 2 == 0 && NTH % 2 == 0, "paired radial nodes, half polar lines");
   constexpr int NL = NTH * NPH;
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(NTH* NPH, (NTH * NPH <= 96 ? 8 : 3))
   constexpr int LDK = NPH * LDL + (((12 - NPH * LDL) % 16) + 16) % 16;
   const auto& op = A.op;
   SiteLoc L;
-  if (!locate_site(A.grid, blockIdx.x, blockIdx.y, &L)) return;  // padding CTA: whole block
+  locate_site(A.grid, blockIdx.x, blockIdx.y, &L);
   const int x = L.x, y = L.y, site = L.site, nx = L.nx, ny = L.ny;
   const int t = threadIdx.x;
   const int j = t % NTH, l = t / NTH;

@@ -67,3 +67,15 @@ def hotspots(nx: int, ny: int, dx: float = 0.1, n: int = 40, seed: int = 1108, w
     for a, (cx, cy) in zip(amps, cen):
         eps += a * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (2 * width * width))
     return eps, amps, cen
+
+
+def batch_events(n: int = 512, seed: int = 1108, n_min: int = 64, n_max: int = 192,
+                 eta_min: float = 0.04, eta_max: float = 0.3):
+    """Events of a batch: square grids with side uniform in {n_min..n_max} and
+    eta/s uniform in (eta_min, eta_max); returns [(side, eta/s), ...]."""
+    r = SplitMix64(seed)
+    out = []
+    for _ in range(n):
+        side = n_min + min(int(r.uniform() * (n_max - n_min + 1)), n_max - n_min)
+        out.append((side, eta_min + (eta_max - eta_min) * r.uniform()))
+    return out

@@ -220,6 +220,19 @@ class Run:
     def lnM(self):
         return self.state[self._m_off:self._m_off + 8 * self.ns].view(self.torch.float64)
 
+    def autotune(self):
+        """Time the stage-kernel variants on the current state and keep the fastest.
+        Returns (chosen variant, [ms per launch of each variant])."""
+        c, n = ctypes.c_int(), ctypes.c_int()
+        ms = np.zeros(4)
+        self._chk(self.lib.rlb_autotune(self._h, self._stream(), ctypes.byref(c),
+                                        ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        ctypes.byref(n)), "rlb_autotune")
+        return c.value, [float(x) for x in ms[:n.value]]
+
+    def set_graphs(self, enable: bool = True):
+        self._chk(self.lib.rlb_set_graphs(self._h, int(enable)), "rlb_set_graphs")
+
     def set_timing(self, enable: bool = True):
         self._chk(self.lib.rlb_set_timing(self._h, int(enable)), "rlb_set_timing")
 

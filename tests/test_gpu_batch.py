@@ -48,3 +48,41 @@ def test_batch_rejects_bad_events():
         rlb.Run(g, events=[rlb.Event(0, 4, 0.1)])
     with pytest.raises(rlb.RLBError):
         rlb.Run(g, events=[rlb.Event(4, 4, -1.0)])
+
+
+@pytest.mark.parametrize("prec", [rlb.RLB_F64, rlb.RLB_F32])
+def test_graph_replay_equals_plain_launches(prec):
+    g = rlb.GridParams(dx=0.1, prec=prec, tau0=0.4, dtau=0.0036)
+    eps = np.concatenate([_eps(e, i).reshape(-1) for i, e in enumerate(EVENTS)])
+    runs = []
+    for graphs in (True, False):
+        r = rlb.Run(g, events=EVENTS)
+        r.set_graphs(graphs)
+        r.init_grid(eps)
+        r.step(5)
+        r.step(4)
+        runs.append(r)
+    torch.cuda.synchronize()
+    assert torch.equal(runs[0].populations(), runs[1].populations())
+    assert torch.equal(runs[0].lnM(), runs[1].lnM())
+    assert runs[0].tau == runs[1].tau
+
+
+def test_autotune_keeps_state_and_picks_a_variant():
+    g = rlb.GridParams(dx=0.1, prec=rlb.RLB_F32, tau0=0.4, dtau=0.0036)
+    eps = np.concatenate([_eps(e, i).reshape(-1) for i, e in enumerate(EVENTS)])
+    r = rlb.Run(g, events=EVENTS)
+    r.init_grid(eps)
+    r.step(3)
+    before = r.populations().clone()
+    tau = r.tau
+    chosen, ms = r.autotune()
+    assert len(ms) == 3 and 0 <= chosen < 3 and all(t > 0 for t in ms)
+    assert ms[chosen] == min(ms)
+    assert torch.equal(before, r.populations()) and r.tau == tau
+    r.step(3)  # steps with the chosen variant stay within FP32 parity of the default one
+    ref = rlb.Run(g, events=EVENTS)
+    ref.init_grid(eps)
+    ref.step(6)
+    d = np.abs(r.moments()[:, 0] / ref.moments()[:, 0] - 1).max()
+    assert d < 1e-5, d
