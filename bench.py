@@ -258,14 +258,107 @@ def batch_main(args, rank, world, local):
     return 0
 
 
+def sweep_main(args, rank, world, local):
+    """Precision sweep on the 16 x 8 x 16 lattice (2048 populations per site):
+    1024 x 1024 grid of 40 hotspots, eta/s 0.16, timed for FP32 and BF16
+    population storage (FP32 arithmetic and moments, FP64 final steps of the
+    matching), plus the error of both against the FP64 oracle on a 128 x 128
+    sub-run.  The JSON line's value is the BF16 rate; both rates and the errors
+    are in "sweep"."""
+    import torch
+    import paper_1108_5561_gb300 as rlb
+    from paper_1108_5561_gb300.inputs import hotspots
+
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+    torch.cuda.set_device(local)
+    side, lat = 1024, dict(n_xi=16, n_theta=8, n_phi_half=8)
+    eps0, _, _ = hotspots(side, side, n=40, seed=1108)
+    stream = torch.cuda.current_stream()
+    res, kern = {}, {}
+    peak, peak_kind = peaks()
+    sampler = ClockSampler(None) if rank == 0 else None
+    for name, prec, b in (("fp32", rlb.RLB_F32, 4), ("bf16", rlb.RLB_BF16, 2)):
+        g = rlb.GridParams(nx=side, ny=side, dx=DX, prec=prec, eta_over_s=ETA_S, tau0=TAU0, dtau=DTAU, **lat)
+        run = rlb.Run(g, device=local)
+        run.init_grid(eps0)
+        run.step(args.warmup)
+        torch.cuda.synchronize()
+        run.check()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        run.set_timing(True)
+        run.step(min(args.steps, 20))
+        torch.cuda.synchronize()
+        sm, sn, mm, mn = run.timing()
+        run.set_timing(False)
+        run.check()
+        ns, nn = side * side, g.nodes
+        alg = 2.5 * b * ns * nn + ns * (56 + 64 + 8 + 8 + 4)
+        res[name] = {"updates_per_s": ns * nn * args.steps / t, "ms_per_step": 1e3 * t / args.steps}
+        kern[name] = {"stage_ms_per_launch": sm / sn, "match_ms_per_launch": mm / mn,
+                      "achieved_GBps": alg / (sm / sn / 1e3) / 1e9}
+        del run
+        torch.cuda.empty_cache()
+    clocks = sampler.stop() if sampler else None
+    # accuracy: 128 x 128 sub-run against the oracle
+    sub, sub_steps = 128, args.sweep_oracle_steps
+    errs = {}
+    if rank == 0:
+        from oracle.oracle import Oracle
+        c = side // 2
+        win = eps0[c - sub // 2:c + sub // 2, c - sub // 2:c + sub // 2]
+        o = Oracle(nx=sub, ny=sub, dx=DX, eta_over_s=ETA_S, **lat)
+        f, lnM = o.init_state(win, os.cpu_count() or 1)
+        o.step(f, lnM, TAU0, DTAU, sub_steps, os.cpu_count() or 1)
+        mo = o.moments(f, lnM, os.cpu_count() or 1)
+        for name, prec in (("fp32", rlb.RLB_F32), ("bf16", rlb.RLB_BF16)):
+            g = rlb.GridParams(nx=sub, ny=sub, dx=DX, prec=prec, eta_over_s=ETA_S, tau0=TAU0, dtau=DTAU, **lat)
+            r = rlb.Run(g, device=local)
+            r.init_grid(win)
+            r.step(sub_steps)
+            mg = r.moments()
+            errs[name] = {"eps": float(np.abs(mg[:, 0] / mo[:, 0] - 1).max()),
+                          "T": float(np.abs(mg[:, 1] / mo[:, 1] - 1).max()),
+                          "u": float((np.abs(mg[:, 2:5] - mo[:, 2:5]).max(axis=1) /
+                                      np.abs(mo[:, 2:5]).max(axis=1)).max())}
+    if rank == 0:
+        bf = res["bf16"]
+        line = {
+            "metric": "site-population updates/s", "value": bf["updates_per_s"], "unit": "updates/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": bf["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic",
+            "config": {"workload": "precision sweep: 1024x1024 grid, 16x8x16 = 2048 populations/site, "
+                                   "40 hotspots, BF16 vs FP32 storage",
+                       "grid": [side, side], "nodes_per_site": 2048, "eta_over_s": ETA_S, "dtau": DTAU,
+                       "tau0": TAU0, "l2": "inputs larger than L2 (4.3 GB BF16 / 8.6 GB FP32 per array)",
+                       "parallelism": "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": kern["bf16"]["achieved_GBps"], "peak": peak, "unit": "GB/s",
+                         "frac": kern["bf16"]["achieved_GBps"] / peak, "traffic": None, "peak_source": peak_kind,
+                         "kernel": "stage_kernel_x2 <bf16, 16, 8, 16>", "algorithmic_bytes_per_update": 10},
+            "sweep": {"rates": res, "kernels": kern, "oracle_subrun": {"grid": [sub, sub], "steps": sub_steps,
+                                                                      "max_rel_error": errs}},
+            "e2e": None, "gpu_launches": 4 * args.steps, "clocks": clocks, "cpu_baseline": None,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
                     help="timed steps (default 1000 for the grid workload, 40 for the batch)")
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="grid", choices=["grid", "batch"],
-                    help="grid: 256x256 FP32 (site-population updates/s); batch: 512 events (events/s)")
+    ap.add_argument("--workload", default="grid", choices=["grid", "batch", "sweep"],
+                    help="grid: 256x256 FP32 (site-population updates/s); batch: 512 events (events/s); "
+                         "sweep: 1024x1024 x 2048 nodes, BF16 vs FP32")
+    ap.add_argument("--sweep-oracle-steps", type=int, default=10,
+                    help="steps of the 128x128 oracle sub-run of the sweep")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling)")
@@ -273,7 +366,7 @@ def main():
                     help="grid side; the benchmark workload is 256 (smaller sides for profiling)")
     args = ap.parse_args()
     if args.steps is None:
-        args.steps = 40 if args.workload == "batch" else 1000
+        args.steps = {"batch": 40, "sweep": 500}.get(args.workload, 1000)
     global NX, NY
     NX = NY = args.grid
     rank = int(os.environ.get("RANK", "0"))
@@ -283,6 +376,8 @@ def main():
         return reference_arm(args, rank, world)
     if args.workload == "batch":
         return batch_main(args, rank, world, local)
+    if args.workload == "sweep":
+        return sweep_main(args, rank, world, local)
 
     import torch
     import paper_1108_5561_gb300 as rlb
