@@ -348,15 +348,88 @@ def sweep_main(args, rank, world, local):
     return 0
 
 
+def adjoint_main(args, rank, world, local):
+    """Adjoint workload: 128 x 128 grid, 768 nodes, FP32 populations, 40
+    hotspots, eta/s 0.08, 300 steps from tau 0.4 fm/c; gradient of the final
+    p_perp-weighted v2 with respect to the 40 hotspot amplitudes and eta/s by the
+    discrete adjoint (FP64 arithmetic) with a checkpoint every 32 steps.  Value:
+    time of the gradient (forward with checkpoints + adjoint sweep) over the time
+    of the plain forward run; two amplitude components are checked against
+    central finite differences of the forward run."""
+    import torch
+    import paper_1108_5561_gb300 as rlb
+    from paper_1108_5561_gb300 import adjoint as ADJ
+    from paper_1108_5561_gb300.inputs import hotspot_basis, hotspots
+
+    torch.cuda.set_device(local)
+    side, steps, every, etas = 128, args.steps, 32, 0.08
+    _, amps, cen = hotspots(side, side, n=40, seed=1108)
+    basis_h = hotspot_basis(side, side, cen, dx=DX)
+    floor = 10.0
+    g = rlb.GridParams(nx=side, ny=side, dx=DX, prec=rlb.RLB_F32, eta_over_s=etas, tau0=TAU0, dtau=DTAU)
+    run = rlb.Run(g, device=local)
+    eps0 = torch.as_tensor(floor + amps @ basis_h, dtype=torch.float64, device="cuda")
+    basis = torch.as_tensor(basis_h, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):  # warm-up: forward runs
+        run.init_grid(eps0)
+        run.step(steps)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(None) if rank == 0 else None
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    run.init_grid(eps0)
+    run.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_fwd = e0.elapsed_time(e1) / 1e3
+    t0 = time.perf_counter()
+    v2, gA, geta = ADJ.v2_gradient(run, eps0, basis, steps, every)
+    torch.cuda.synchronize()
+    t_grad = time.perf_counter() - t0
+    clocks = sampler.stop() if sampler else None
+    run.check()
+    # finite differences of the forward run for the two largest amplitudes
+    def v2_of(a):
+        run.init_grid(torch.as_tensor(floor + a @ basis_h, dtype=torch.float64, device="cuda"))
+        run.step(steps)
+        return run.observables()[1]
+    checks = []
+    for i in np.argsort(-amps)[:2]:
+        h = 0.05 * amps[i]
+        ap, am = amps.copy(), amps.copy()
+        ap[i] += h
+        am[i] -= h
+        fd = (v2_of(ap) - v2_of(am)) / (2 * h)
+        checks.append({"hotspot": int(i), "adjoint": float(gA[i]), "finite_difference": float(fd),
+                       "rel_diff": float(abs(gA[i] - fd) / max(abs(fd), 1e-300))})
+    if rank == 0:
+        line = {
+            "metric": "adjoint/forward time", "value": t_grad / t_fwd, "unit": "x",
+            "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_fwd / steps,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "adjoint: 128x128, 768 nodes, FP32 populations, 40 hotspots, eta/s 0.08, "
+                                   "%d steps, checkpoint every %d, gradient of final p_perp-weighted v2 wrt "
+                                   "40 amplitudes and eta/s (FP64 adjoint arithmetic)" % (steps, every),
+                       "grid": [side, side], "forward_s": t_fwd, "gradient_s": t_grad, "v2": v2,
+                       "dv2_deta": geta, "dv2_dA_norm": float(np.linalg.norm(gA)), "fd_checks": checks,
+                       "parallelism": "single GPU"},
+            "roofline": None, "e2e": None, "gpu_launches": None, "clocks": clocks, "cpu_baseline": None,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
                     help="timed steps (default 1000 for the grid workload, 40 for the batch)")
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="grid", choices=["grid", "batch", "sweep"],
+    ap.add_argument("--workload", default="grid", choices=["grid", "batch", "sweep", "adjoint"],
                     help="grid: 256x256 FP32 (site-population updates/s); batch: 512 events (events/s); "
-                         "sweep: 1024x1024 x 2048 nodes, BF16 vs FP32")
+                         "sweep: 1024x1024 x 2048 nodes, BF16 vs FP32; adjoint: gradient of v2, 128x128")
     ap.add_argument("--sweep-oracle-steps", type=int, default=10,
                     help="steps of the 128x128 oracle sub-run of the sweep")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -366,7 +439,7 @@ def main():
                     help="grid side; the benchmark workload is 256 (smaller sides for profiling)")
     args = ap.parse_args()
     if args.steps is None:
-        args.steps = {"batch": 40, "sweep": 500}.get(args.workload, 1000)
+        args.steps = {"batch": 40, "sweep": 500, "adjoint": 300}.get(args.workload, 1000)
     global NX, NY
     NX = NY = args.grid
     rank = int(os.environ.get("RANK", "0"))
@@ -378,6 +451,8 @@ def main():
         return batch_main(args, rank, world, local)
     if args.workload == "sweep":
         return sweep_main(args, rank, world, local)
+    if args.workload == "adjoint":
+        return adjoint_main(args, rank, world, local)
 
     import torch
     import paper_1108_5561_gb300 as rlb

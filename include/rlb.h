@@ -198,7 +198,7 @@ rlb_status rlb_step(rlb_ctx* ctx, int nsteps, void* stream);
  * management only. */
 rlb_status rlb_step_static_scratch(rlb_ctx* ctx, void* state, int nsteps, void* stream);
 
-/* Checkpoint and restart.  A state blob holds a header (grid, lattice and
+/* Checkpoint and restart (blobs in host or device memory).  A state blob holds a header (grid, lattice and
  * precision it belongs to, and tau), the populations f, ln M, the per-site
  * Newton starting temperatures and the stored moments of f, so that a run
  * restarted from a blob continues bit for bit like the uninterrupted run (same
@@ -232,6 +232,41 @@ rlb_status rlb_load_state(rlb_ctx* ctx, const void* host_buf, size_t bytes, void
  * `stream`.  Implementation choices, not part of the paper's scheme. */
 rlb_status rlb_autotune(rlb_ctx* ctx, void* stream, int* chosen, double* variant_ms, int* n_variants);
 rlb_status rlb_set_graphs(rlb_ctx* ctx, int enable);
+
+/* Adjoint of the time evolution (discrete adjoint of the predictor-corrector of
+ * Sec. 4.4 with the 2+1D terms, FP64 arithmetic for every storage precision).
+ * The objective is the final-state elliptic flow v2_pt of rlb_observables; the
+ * gradients are with respect to the initial energy density (projected on a
+ * caller basis, e.g. the hotspot Gaussians) and to eta/s.  The paper has no
+ * adjoint; this is the sensitivity of its scheme.
+ *
+ *   rlb_adjoint_workspace_size / rlb_adjoint_bind
+ *       FP64 device workspace (caller-owned, 256-byte aligned): the adjoints of
+ *       f and ln M and per-stage intermediates (about 3 x 8 bytes x populations).
+ *   rlb_adjoint_seed_v2
+ *       v2_pt of the current state (written to *v2) and the adjoint buffers set
+ *       to d v2_pt / d(f, ln M) of that state; the eta/s accumulator is cleared.
+ *   rlb_adjoint_step
+ *       The adjoint buffers hold the adjoints of the output of one time step;
+ *       the context state (f, ln M, tau: e.g. restored with rlb_load_state) is
+ *       that step's input.  Replaces them by the adjoints of the step's input
+ *       and adds the step's contribution to d v2/d(eta/s).  The step's
+ *       predictor output is recomputed with the forward kernels, bit for bit as
+ *       in the forward run; the matchings are recomputed in FP64.
+ *   rlb_adjoint_ic
+ *       After the last rlb_adjoint_step (the adjoint buffers hold the adjoints
+ *       of the initial state rlb_init_grid made from eps0, device FP64,
+ *       GeV/fm^3): grad[i] = sum_x basis[i][x] d v2/d eps0(x) for the n_basis
+ *       rows of `basis` (device FP64, n_basis x sites, n_basis <= sites), then
+ *       grad[n_basis] = d v2/d(eta/s).  `grad` is host memory; synchronises.
+ * Checkpointing (which states to keep and recompute) is the caller's choice;
+ * the Python module adjoint.py keeps one every k steps. */
+rlb_status rlb_adjoint_workspace_size(rlb_ctx* ctx, size_t* bytes);
+rlb_status rlb_adjoint_bind(rlb_ctx* ctx, void* workspace);
+rlb_status rlb_adjoint_seed_v2(rlb_ctx* ctx, double* v2, void* stream);
+rlb_status rlb_adjoint_step(rlb_ctx* ctx, void* stream);
+rlb_status rlb_adjoint_ic(rlb_ctx* ctx, const double* eps0, const double* basis, int n_basis, double* grad,
+                          void* stream);
 
 /* Current proper time (host bookkeeping, fm/c). */
 rlb_status rlb_get_tau(const rlb_ctx* ctx, double* tau);

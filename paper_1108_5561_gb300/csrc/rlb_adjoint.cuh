@@ -1,0 +1,599 @@
+// rlb_adjoint.cuh -- discrete adjoint of one Heun stage of the scheme
+// (Romatschke, arXiv:1108.5561, Sec. 4.4 with the 2+1D terms of the forward
+// kernels), in FP64 arithmetic for every storage precision.
+//
+// Forward stage at a site (nodes n = (k, j, l), per-line constants as in
+// stage_kernel; s = site scalars of the matching of f_in):
+//   r_n   = tv_k [nsx Sx_n + nsy Sy_n] + (1/tau) [mu_j^2 (Dr f)_n + (Dth f)_n]
+//           + feq_n (fc_n + cc_n) - f_n cc_n
+//   Sx_n  = 3 f_n(x) - 4 f_n(x + sx) + f_n(x + 2 sx)     (upwind, periodic)
+//   feq_n = Z exp(-invT (ut E_k - M vu s_k)),  E_k = sqrt(Meq^2 + M^2 s_k^2)
+//   fc_n  = Gp q1_k / E_k + Hp q2_k + Jp / c_k,  cc_n = itr (ut - tv_k vu)
+//   Gp = -invT A1 ut M^2,  Hp = invT A1 M vu,  Jp = invT M (a.u)
+//   vu = sth (cp ux + sp uy),  A1 = sth (ax cp + ay sp)
+//   g  = -D A / (Kh + D (4E + Q - Kh)),  {A, Q, E} = sum_n wj ecw_k pu_n^2 {r, Dr f, f},
+//   pu_n = c_k ut - s_k vu
+//   out_n = c [f_n + dtau (r_n + g (Dr f)_n)] (+ (1/2) f_base,n),   c = 1 or 1/2
+//   ln M_out = c [ln M + dtau g] (+ (1/2) ln M_base)
+// The adjoint runs in three launches: adj_stage1 (per site: the adjoints of r,
+// of the site-local uses of f and of the site scalars), adj_match (per site: the
+// matching -- Landau eigenproblem and EOS inversion -- differentiated
+// implicitly, giving the adjoints of the moments, of ln M and of eta/s) and
+// adj_stage3 (per site: the transposed streaming stencil and the grad ln M
+// terms gathered from the neighbours, plus the moment weights).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "rlb_kernels.cuh"
+
+namespace rlbk {
+
+// adjoints of the site scalars, per site
+constexpr int kAdjS = 12;
+enum : int { AS_UT = 0, AS_UX, AS_UY, AS_INVT, AS_MEQ, AS_M, AS_ITR, AS_D, AS_KH, AS_AX, AS_AY, AS_PAD };
+
+template <class S, int NXI, int NTH, int NPH>
+struct AdjStageArgs {
+  const S* f_in;       // stage input populations
+  const double* sc;    // FP64 matching of f_in, kSc per site
+  const double* ob;    // adjoint of the stage output populations (per node)
+  const double* lb;    // adjoint of the stage output ln M (per site)
+  double* rbar;        // out: adjoint of r (per node)
+  double* fbar;        // out: site-local part of the adjoint of f_in (per node)
+  double* sbar;        // out: adjoints of the site scalars (kAdjS per site)
+  GridMap grid;
+  double milne;        // 1/tau of f_in (Milne) or 0
+  double c;            // 1 (predictor) or 1/2 (corrector)
+  double dtau, inv2dx, Z;
+  Ops<double, NXI, NTH, NPH> op;
+};
+
+template <int NV, int NT>
+__device__ __forceinline__ void block_sum_d(double (&v)[NV], double* red) {
+  // sum over the block of NV doubles, result broadcast to every thread
+  constexpr int NW = (NT + 31) / 32;
+  if constexpr (NT < 32) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) red[threadIdx.x * NV + q] = v[q];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double a = 0.0;
+      for (int i = 0; i < NT; ++i) a += red[i * NV + q];
+      v[q] = a;
+    }
+    __syncthreads();
+  } else {
+    warp_sum<NV>(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+      for (int q = 0; q < NV; ++q) red[wid * NV + q] = v[q];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double a = 0.0;
+      for (int w = 0; w < NW; ++w) a += red[w * NV + q];
+      v[q] = a;
+    }
+    __syncthreads();
+  }
+}
+
+template <class S, int NXI, int NTH, int NPH>
+__global__ void __launch_bounds__(NTH* NPH)
+    adj_stage1(const __grid_constant__ AdjStageArgs<S, NXI, NTH, NPH> A) {
+  constexpr int NL = NTH * NPH;
+  constexpr int NN = NL * NXI;
+  constexpr int LD = NL + 1;
+  constexpr int NRED = NL < 32 ? NL : (NL + 31) / 32;
+  const auto& op = A.op;
+  SiteLoc L;
+  locate_site(A.grid, blockIdx.x, blockIdx.y, &L);
+  const int x = L.x, y = L.y, site = L.site, nx = L.nx, ny = L.ny;
+  const int t = threadIdx.x, j = t % NTH, l = t / NTH;
+  __shared__ double fs[NXI * LD];
+  __shared__ double red[16 * NRED];
+
+  // forward recompute
+  double f[NXI], fx1[NXI], fx2[NXI], fy1[NXI], fy2[NXI];
+  load_line<S, double, NXI>(A.f_in + (size_t)site * NN + t * NXI, f);
+  const double cp = op.cph[l], sp = op.sph[l];
+  const int sx = (cp > 0.0) ? -1 : 1, sy = (sp > 0.0) ? -1 : 1;
+  int x1 = x + sx, x2 = x + 2 * sx, y1 = y + sy, y2 = y + 2 * sy;
+  x1 += (x1 < 0) ? nx : (x1 >= nx ? -nx : 0);
+  x2 += (x2 < 0) ? nx : (x2 >= nx ? -nx : 0);
+  x2 += (x2 < 0) ? nx : (x2 >= nx ? -nx : 0);
+  y1 += (y1 < 0) ? ny : (y1 >= ny ? -ny : 0);
+  y2 += (y2 < 0) ? ny : (y2 >= ny ? -ny : 0);
+  y2 += (y2 < 0) ? ny : (y2 >= ny ? -ny : 0);
+  load_line<S, double, NXI>(A.f_in + (size_t)(L.base + y * nx + x1) * NN + t * NXI, fx1);
+  load_line<S, double, NXI>(A.f_in + (size_t)(L.base + y * nx + x2) * NN + t * NXI, fx2);
+  load_line<S, double, NXI>(A.f_in + (size_t)(L.base + y1 * nx + x) * NN + t * NXI, fy1);
+  load_line<S, double, NXI>(A.f_in + (size_t)(L.base + y2 * nx + x) * NN + t * NXI, fy2);
+  const double* q = A.sc + (size_t)site * kSc;
+  const double ut = q[SC_UT], ux = q[SC_UX], uy = q[SC_UY], invT = q[SC_INVT], Meq = q[SC_MEQ];
+  const double M = q[SC_M], itr = q[SC_ITR], D = q[SC_D], Kh = q[SC_KH], ax = q[SC_AX], ay = q[SC_AY];
+  const double M2 = M * M;
+#pragma unroll
+  for (int k = 0; k < NXI; ++k) fs[k * LD + t] = f[k];
+  double Drf[NXI];
+#pragma unroll
+  for (int kp = 0; kp < NXI; ++kp) {
+    double a = 0.0;
+#pragma unroll
+    for (int k = 0; k < NXI; ++k) a += op.Dr[kp * NXI + k] * f[k];
+    Drf[kp] = a;
+  }
+  __syncthreads();
+  double pth[NXI];  // (Dth f) on the own line
+#pragma unroll
+  for (int k = 0; k < NXI; ++k) {
+    double a = 0.0;
+#pragma unroll
+    for (int jj = 0; jj < NTH; ++jj) a += op.Dth[j * NTH + jj] * fs[k * LD + l * NTH + jj];
+    pth[k] = a;
+  }
+  const double st = op.sth[j], mu2 = op.mu2[j], wj = op.wj[j];
+  const double vu = st * (cp * ux + sp * uy), A1 = st * (ax * cp + ay * sp), au = ax * ux + ay * uy;
+  const double nsx = -st * fabs(cp) * A.inv2dx, nsy = -st * fabs(sp) * A.inv2dx;
+  const double Gp = -invT * A1 * ut * M2, Hp = invT * A1 * M * vu, Jp = invT * M * au;
+  double E[NXI], feq[NXI], cc[NXI], fc[NXI], r[NXI], pu[NXI], wp[NXI];
+  double sums[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int k = 0; k < NXI; ++k) {
+    const double s = op.s[k], c = op.c[k], tv = op.tv[k];
+    E[k] = sqrt(Meq * Meq + M2 * op.s2[k]);
+    feq[k] = A.Z * exp(-invT * (ut * E[k] - M * vu * s));
+    cc[k] = itr * (ut - tv * vu);
+    fc[k] = Gp * op.q1[k] / E[k] + Hp * op.q2[k] + Jp * op.inv_c[k];
+    const double Sx = 3.0 * f[k] - 4.0 * fx1[k] + fx2[k], Sy = 3.0 * f[k] - 4.0 * fy1[k] + fy2[k];
+    r[k] = tv * (nsx * Sx + nsy * Sy) + A.milne * (mu2 * Drf[k] + pth[k]) + feq[k] * (fc[k] + cc[k]) -
+           f[k] * cc[k];
+    pu[k] = c * ut - s * vu;
+    wp[k] = wj * op.ecw[k] * pu[k] * pu[k];
+    sums[0] += wp[k] * r[k];
+    sums[1] += wp[k] * Drf[k];
+    sums[2] += wp[k] * f[k];
+  }
+  // site sums and sum_n ob_n (Dr f)_n in one reduction
+  const double* ob = A.ob + (size_t)site * NN + t * NXI;
+  double red4[4] = {sums[0], sums[1], sums[2], 0.0};
+#pragma unroll
+  for (int k = 0; k < NXI; ++k) red4[3] += ob[k] * Drf[k];
+  block_sum_d<4, NL>(red4, red);
+  const double SA = red4[0], SQ = red4[1], SE = red4[2];
+  const double den = Kh + D * (4.0 * SE + SQ - Kh);
+  const double g = (D == 0.0) ? 0.0 : -D * SA / den;
+
+  // adjoint of g and of its sums (every thread, identical values)
+  const double cdt = A.c * A.dtau;
+  const double gbar = cdt * (red4[3] + A.lb[site]);
+  double Abar = 0.0, Qbar = 0.0, Ebar = 0.0, Dbar = 0.0, Khbar = 0.0;
+  if (D != 0.0) {
+    const double denbar = D * SA / (den * den) * gbar;
+    Abar = -D / den * gbar;
+    Dbar = -SA / den * gbar + denbar * (4.0 * SE + SQ - Kh);
+    Ebar = denbar * 4.0 * D;
+    Qbar = denbar * D;
+    Khbar = denbar * (1.0 - D);
+  }
+
+  // per node
+  double rb[NXI], Drfb[NXI], fb[NXI];
+  double b_ut = 0.0, b_vu = 0.0, b_invT = 0.0, b_Meq = 0.0, b_M = 0.0, b_itr = 0.0;
+  double b_Gp = 0.0, b_Hp = 0.0, b_Jp = 0.0;
+#pragma unroll
+  for (int k = 0; k < NXI; ++k) {
+    const double s = op.s[k], c = op.c[k], tv = op.tv[k];
+    const double o = ob[k];
+    rb[k] = cdt * o + Abar * wp[k];
+    Drfb[k] = cdt * g * o + Qbar * wp[k] + A.milne * mu2 * rb[k];
+    fb[k] = A.c * o + Ebar * wp[k] - rb[k] * cc[k] + 3.0 * tv * (nsx + nsy) * rb[k];
+    // pu through the weights of the sums
+    const double wpb = Abar * r[k] + Qbar * Drf[k] + Ebar * f[k];
+    const double pub = 2.0 * wj * op.ecw[k] * pu[k] * wpb;
+    b_ut += c * pub;
+    b_vu -= s * pub;
+    // feq, cc, fc
+    const double feqb = rb[k] * (fc[k] + cc[k]);
+    const double fcb = rb[k] * feq[k];
+    const double ccb = rb[k] * (feq[k] - f[k]);
+    const double argb = feqb * feq[k];
+    b_invT -= argb * (ut * E[k] - M * vu * s);
+    b_ut -= argb * invT * E[k];
+    double Eb = -argb * invT * ut;
+    b_M += argb * invT * vu * s;
+    b_vu += argb * invT * M * s;
+    b_itr += ccb * (ut - tv * vu);
+    b_ut += ccb * itr;
+    b_vu -= ccb * itr * tv;
+    b_Gp += fcb * op.q1[k] / E[k];
+    Eb -= fcb * Gp * op.q1[k] / (E[k] * E[k]);
+    b_Hp += fcb * op.q2[k];
+    b_Jp += fcb * op.inv_c[k];
+    b_Meq += Eb * Meq / E[k];
+    b_M += Eb * M * op.s2[k] / E[k];
+  }
+  double b_A1 = 0.0, b_au = 0.0;
+  b_invT -= b_Gp * A1 * ut * M2;
+  b_A1 -= b_Gp * invT * ut * M2;
+  b_ut -= b_Gp * invT * A1 * M2;
+  b_M -= b_Gp * invT * A1 * ut * 2.0 * M;
+  b_invT += b_Hp * A1 * M * vu;
+  b_A1 += b_Hp * invT * M * vu;
+  b_M += b_Hp * invT * A1 * vu;
+  b_vu += b_Hp * invT * A1 * M;
+  b_invT += b_Jp * M * au;
+  b_M += b_Jp * invT * au;
+  b_au += b_Jp * invT * M;
+  double sb[9];
+  sb[0] = b_ut;
+  sb[1] = b_vu * st * cp + b_au * ax;   // ux
+  sb[2] = b_vu * st * sp + b_au * ay;   // uy
+  sb[3] = b_invT;
+  sb[4] = b_Meq;
+  sb[5] = b_M;
+  sb[6] = b_itr;
+  sb[7] = b_A1 * st * cp + b_au * ux;   // ax
+  sb[8] = b_A1 * st * sp + b_au * uy;   // ay
+
+  // f through Dr^T on the own line and Dth^T along the polar lines
+#pragma unroll
+  for (int k = 0; k < NXI; ++k) {
+    double a = 0.0;
+#pragma unroll
+    for (int kp = 0; kp < NXI; ++kp) a += op.Dr[kp * NXI + k] * Drfb[kp];
+    fb[k] += a;
+  }
+#pragma unroll
+  for (int k = 0; k < NXI; ++k) fs[k * LD + t] = A.milne * rb[k];  // adjoint of (Dth f)
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NXI; ++k) {
+    double a = 0.0;
+#pragma unroll
+    for (int jj = 0; jj < NTH; ++jj) a += op.Dth[jj * NTH + j] * fs[k * LD + l * NTH + jj];
+    fb[k] += a;
+  }
+  double* rbo = A.rbar + (size_t)site * NN + t * NXI;
+  double* fbo = A.fbar + (size_t)site * NN + t * NXI;
+#pragma unroll
+  for (int k = 0; k < NXI; ++k) {
+    rbo[k] = rb[k];
+    fbo[k] = fb[k];
+  }
+  // site scalar adjoints
+  double s9[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) s9[i] = sb[i];
+  block_sum_d<9, NL>(s9, red);
+  if (t == 0) {
+    double* o = A.sbar + (size_t)site * kAdjS;
+    o[AS_UT] = s9[0]; o[AS_UX] = s9[1]; o[AS_UY] = s9[2]; o[AS_INVT] = s9[3]; o[AS_MEQ] = s9[4];
+    o[AS_M] = s9[5]; o[AS_ITR] = s9[6]; o[AS_AX] = s9[7]; o[AS_AY] = s9[8];
+    o[AS_D] = Dbar; o[AS_KH] = Khbar; o[AS_PAD] = 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// adjoint of the matching of one site (FP64): from the adjoints of the site
+// scalars to those of the moments (mbar, kMom per site), of ln M (local part,
+// lbar) and of eta/s (ebar)
+// ---------------------------------------------------------------------------
+struct AdjMatchArgs {
+  const double* mom;   // FP64 moments of f_in, kMom per site
+  const double* lnM;
+  const double* sbar;
+  double* mbar;
+  double* lbar;
+  double* ebar;
+  int* err;
+  EosView eos;
+  GridMap grid;
+  int ns;
+};
+
+// value and d/dy (y = ln T) of a table field
+__device__ __forceinline__ void eos_field_dy(const EosView& E, double y, int field, double* v, double* dv) {
+  int i0;
+  double t, w[6], dw[6];
+  if (!eos_cell(E, y, &i0, &t)) { *v = 0.0; *dv = 0.0; return; }
+  lagrange6(t, w);
+  lagrange6_d(t, dw);
+  double a = 0.0, b = 0.0;
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    const double tv = __ldg(E.tab + (size_t)(i0 - 2 + m) * 8 + field);
+    a += w[m] * tv;
+    b += dw[m] * tv;
+  }
+  *v = a;
+  *dv = b * E.inv_h;
+}
+
+// solve the 4x4 system M x = b by Gaussian elimination with partial pivoting
+__device__ __forceinline__ bool solve4(double (&Mx)[4][4], double (&b)[4]) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    int p = c;
+    for (int r = c + 1; r < 4; ++r)
+      if (fabs(Mx[r][c]) > fabs(Mx[p][c])) p = r;
+    if (!(fabs(Mx[p][c]) > 0.0)) return false;
+    if (p != c) {
+      for (int k = 0; k < 4; ++k) { const double tmp = Mx[c][k]; Mx[c][k] = Mx[p][k]; Mx[p][k] = tmp; }
+      const double tb = b[c]; b[c] = b[p]; b[p] = tb;
+    }
+    for (int r = c + 1; r < 4; ++r) {
+      const double fct = Mx[r][c] / Mx[c][c];
+      for (int k = c; k < 4; ++k) Mx[r][k] -= fct * Mx[c][k];
+      b[r] -= fct * b[c];
+    }
+  }
+  for (int c = 3; c >= 0; --c) {
+    double a = b[c];
+    for (int k = c + 1; k < 4; ++k) a -= Mx[c][k] * b[k];
+    b[c] = a / Mx[c][c];
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(128) adj_match(const AdjMatchArgs A) {
+  const int site = blockIdx.x * blockDim.x + threadIdx.x;
+  if (site >= A.ns) return;
+  const double* m = A.mom + (size_t)site * kMom;
+  const double lnM = A.lnM[site], M = exp(lnM);
+  const double pref = M * M * M * M * (1.0 / (2.0 * 3.14159265358979323846 * 3.14159265358979323846));
+  double tm[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) tm[i] = pref * m[1 + i];
+  double u[3], eps;
+  int err = 0;
+  if (!landau3(tm, u, &eps)) err |= ERR_LANDAU;
+  double y = 0.0;
+  if (!eos_invert(A.eos, EOS_E, eps, log(0.3), &y)) err |= ERR_EOS;
+  const double T = exp(y);
+  double e, de, xv, dx, Dv, dD, ih, dih;
+  eos_field_dy(A.eos, y, EOS_E, &e, &de);
+  eos_field_dy(A.eos, y, EOS_X, &xv, &dx);
+  eos_field_dy(A.eos, y, EOS_D, &Dv, &dD);
+  eos_field_dy(A.eos, y, EOS_INVH, &ih, &dih);
+  const double* sb = A.sbar + (size_t)site * kAdjS;
+  const EventInfo& ev = A.grid.ev[event_of_site(A.grid, site)];
+  const double eta = ev.eta_over_s;
+  // T from e(T) = eps: Tbar -> epsbar; scalars: invT = 1/T, Meq = x T,
+  // D = D(T), itr = (1/h)(T) / eta (d/dT = (1/T) d/dy)
+  const double Tbar = -sb[AS_INVT] / (T * T) + sb[AS_MEQ] * (xv + dx) + sb[AS_D] * dD / T +
+                      sb[AS_ITR] * dih / (T * eta);
+  A.ebar[site] = -sb[AS_ITR] * ih / (eta * eta);
+  const double epsbar = Tbar * T / de;  // de/dT = de/dy / T
+  // Landau: F_mu = T^{mu l} (g u)_l - eps u^mu = 0, F_3 = u.g.u - 1 = 0 in
+  // z = (u, eps); lambda = J^{-T} zbar, Tbar^{ab} = -lambda_a (g u)_b
+  const double gu[3] = {u[0], -u[1], -u[2]};
+  const double Tm[3][3] = {{tm[0], tm[1], tm[2]}, {tm[1], tm[3], tm[4]}, {tm[2], tm[4], tm[5]}};
+  double Jt[4][4];  // J transposed
+#pragma unroll
+  for (int mu = 0; mu < 3; ++mu)
+#pragma unroll
+    for (int nu = 0; nu < 3; ++nu) {
+      // J[mu][nu] = T^{mu l} g_{l nu} - eps delta
+      const double gnu = nu == 0 ? 1.0 : -1.0;
+      Jt[nu][mu] = Tm[mu][nu] * gnu - (mu == nu ? eps : 0.0);
+    }
+#pragma unroll
+  for (int mu = 0; mu < 3; ++mu) {
+    Jt[3][mu] = -u[mu];      // J[mu][3]
+    Jt[mu][3] = 2.0 * gu[mu];  // J[3][mu]
+  }
+  Jt[3][3] = 0.0;
+  double lam[4] = {sb[AS_UT], sb[AS_UX], sb[AS_UY], epsbar};
+  if (!solve4(Jt, lam)) err |= ERR_LANDAU;
+  // symmetric moment adjoints: tm = {T00, T01, T02, T11, T12, T22}
+  double tb[6];
+  tb[0] = -lam[0] * gu[0];
+  tb[1] = -(lam[0] * gu[1] + lam[1] * gu[0]);
+  tb[2] = -(lam[0] * gu[2] + lam[2] * gu[0]);
+  tb[3] = -lam[1] * gu[1];
+  tb[4] = -(lam[1] * gu[2] + lam[2] * gu[1]);
+  tb[5] = -lam[2] * gu[2];
+  double* mb = A.mbar + (size_t)site * kMom;
+  mb[0] = sb[AS_KH];
+  double lb = sb[AS_M] * M;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    mb[1 + i] = pref * tb[i];
+    lb += 4.0 * tb[i] * tm[i];
+  }
+  mb[7] = 0.0;
+  A.lbar[site] = lb;
+  if (err) atomicOr(A.err, err);
+}
+
+// ---------------------------------------------------------------------------
+// assembly: adjoint of f_in (per node) and of ln M_in (per site)
+// ---------------------------------------------------------------------------
+template <int NXI, int NTH, int NPH>
+struct AdjAssembleArgs {
+  const double* fbar;   // site-local part (adj_stage1)
+  const double* rbar;   // adjoint of r (neighbours gathered)
+  const double* mbar;   // moment adjoints (adj_match)
+  const double* sbar;   // scalar adjoints (grad ln M gathered)
+  const double* lbar;   // ln M local part (adj_match)
+  const double* lb;     // adjoint of the stage output ln M
+  double* fout;         // adjoint of f_in
+  double* lout;         // adjoint of ln M_in
+  GridMap grid;
+  double c, inv2dx;
+  Ops<double, NXI, NTH, NPH> op;
+};
+
+template <int NXI, int NTH, int NPH>
+__global__ void __launch_bounds__(NTH* NPH)
+    adj_stage3(const __grid_constant__ AdjAssembleArgs<NXI, NTH, NPH> A) {
+  constexpr int NL = NTH * NPH;
+  constexpr int NN = NL * NXI;
+  const auto& op = A.op;
+  SiteLoc L;
+  locate_site(A.grid, blockIdx.x, blockIdx.y, &L);
+  const int x = L.x, y = L.y, site = L.site, nx = L.nx, ny = L.ny;
+  const int t = threadIdx.x, j = t % NTH, l = t / NTH;
+  const double cp = op.cph[l], sp = op.sph[l], st = op.sth[j], wj = op.wj[j];
+  const double nsx = -st * fabs(cp) * A.inv2dx, nsy = -st * fabs(sp) * A.inv2dx;
+  // downwind neighbours: the forward stencil of site i - s uses f(i) with -4,
+  // that of i - 2 s with +1 (s = the upwind offset)
+  const int sx = (cp > 0.0) ? -1 : 1, sy = (sp > 0.0) ? -1 : 1;
+  auto wrap = [](int i, int n) {
+    i += (i < 0) ? n : (i >= n ? -n : 0);
+    return i + ((i < 0) ? n : (i >= n ? -n : 0));
+  };
+  const size_t d1x = L.base + y * nx + wrap(x - sx, nx), d2x = L.base + y * nx + wrap(x - 2 * sx, nx);
+  const size_t d1y = L.base + wrap(y - sy, ny) * nx + x, d2y = L.base + wrap(y - 2 * sy, ny) * nx + x;
+  const double* m = A.mbar + (size_t)site * kMom;
+  const double w0 = wj, w1 = wj * st * cp, w1y = wj * st * sp, w3x = wj * st * st * cp * cp;
+  const double w3xy = wj * st * st * cp * sp, w3y = wj * st * st * sp * sp;
+  const double* fb = A.fbar + (size_t)site * NN + t * NXI;
+  double* fo = A.fout + (size_t)site * NN + t * NXI;
+#pragma unroll
+  for (int k = 0; k < NXI; ++k) {
+    const double tv = op.tv[k];
+    const double a = tv * nsx, b = tv * nsy;
+    double v = fb[k];
+    v += a * (-4.0 * A.rbar[d1x * NN + t * NXI + k] + A.rbar[d2x * NN + t * NXI + k]);
+    v += b * (-4.0 * A.rbar[d1y * NN + t * NXI + k] + A.rbar[d2y * NN + t * NXI + k]);
+    // moment weights: K, T00, T01, T02, T11, T12, T22 (ecw-scaled radial parts)
+    v += m[0] * w0 * op.w0[k] + m[1] * w0 * op.w2[k] + (m[2] * w1 + m[3] * w1y) * op.w1[k] +
+         (m[4] * w3x + m[5] * w3xy + m[6] * w3y) * op.w3[k];
+    fo[k] = v;
+  }
+  if (t == 0) {
+    const double* sb = A.sbar;
+    const int xm = wrap(x - 1, nx), xp = wrap(x + 1, nx), ym = wrap(y - 1, ny), yp = wrap(y + 1, ny);
+    // ln M(i) enters a_x(i -/+ 1) = (ln M(i) - ln M(i -/+ 2)) / (2 dx) with sign +/-
+    const double gx = sb[(size_t)(L.base + y * nx + xm) * kAdjS + AS_AX] - sb[(size_t)(L.base + y * nx + xp) * kAdjS + AS_AX];
+    const double gy = sb[(size_t)(L.base + ym * nx + x) * kAdjS + AS_AY] - sb[(size_t)(L.base + yp * nx + x) * kAdjS + AS_AY];
+    A.lout[site] = A.c * A.lb[site] + A.lbar[site] + A.inv2dx * (gx + gy);
+  }
+}
+
+// adjoint seed of v2 = NUM / DEN (per-site partials part[4 i + 2], part[4 i + 3]
+// = M^3/(2 pi^2) {num_i, den_i}, grid sums in sums[2], sums[3]):
+//   fbar_n = M^3/(2 pi^2) w_n s_k sth_j (cos 2phi_l / DEN - NUM / DEN^2)
+//   lbar   = 3 (part_num / DEN - part_den NUM / DEN^2)
+template <class S, int NXI, int NTH, int NPH>
+struct SeedArgs {
+  const double* lnM;
+  const double* part;
+  const double* tot;   // {.., .., NUM, DEN}
+  double* fbar;
+  double* lbar;
+  Ops<double, NXI, NTH, NPH> op;
+};
+
+template <class S, int NXI, int NTH, int NPH>
+__global__ void __launch_bounds__(NTH* NPH) adj_seed_v2(const __grid_constant__ SeedArgs<S, NXI, NTH, NPH> A) {
+  constexpr int NL = NTH * NPH, NN = NL * NXI;
+  const int site = blockIdx.x, t = threadIdx.x, j = t % NTH, l = t / NTH;
+  const auto& op = A.op;
+  const double NUM = A.tot[2], DEN = A.tot[3];
+  const double bn = 1.0 / DEN, bd = -NUM / (DEN * DEN);
+  const double M = exp(A.lnM[site]);
+  const double m3 = M * M * M / (2.0 * 3.14159265358979323846 * 3.14159265358979323846);
+  const double cp = op.cph[l], sp = op.sph[l];
+  const double wl = m3 * op.wj[j] * op.sth[j] * (bn * (cp * cp - sp * sp) + bd);
+  double* o = A.fbar + (size_t)site * NN + t * NXI;
+#pragma unroll
+  for (int k = 0; k < NXI; ++k) o[k] = wl * op.ecw[k] * op.s[k];
+  if (t == 0) A.lbar[site] = 3.0 * (bn * A.part[(size_t)site * 4 + 2] + bd * A.part[(size_t)site * 4 + 3]);
+}
+
+// adjoint of the initial condition (Sec. 4.4: f = Z exp(-M cosh xi / T) at
+// rest, M = x(T) T, eps_EOS(T) = eps0): from the adjoints of f and ln M of the
+// initial state to that of eps0 [GeV/fm^3], per site
+template <class S, int NXI, int NTH, int NPH>
+struct AdjIcArgs {
+  const double* eps0;
+  const double* fbar;
+  const double* lbar;
+  double* epsbar;
+  int* err;
+  EosView eos;
+  double eps_scale, Z;
+  Ops<double, NXI, NTH, NPH> op;
+};
+
+template <class S, int NXI, int NTH, int NPH>
+__global__ void __launch_bounds__(NTH* NPH) adj_ic(const __grid_constant__ AdjIcArgs<S, NXI, NTH, NPH> A) {
+  constexpr int NL = NTH * NPH, NN = NL * NXI;
+  constexpr int NRED = NL < 32 ? NL : (NL + 31) / 32;
+  __shared__ double red[NRED * 2];
+  __shared__ double sT[2];
+  const int site = blockIdx.x, t = threadIdx.x;
+  const auto& op = A.op;
+  if (t == 0) {
+    double y = 0.0;
+    if (!eos_invert(A.eos, EOS_EPS, A.eps0[site] * A.eps_scale, log(0.3), &y)) atomicOr(A.err, (int)ERR_EOS);
+    double xv, dx;
+    eos_field_dy(A.eos, y, EOS_X, &xv, &dx);
+    sT[0] = y;
+    sT[1] = xv;
+  }
+  __syncthreads();
+  const double xv = sT[1];
+  const double* fb = A.fbar + (size_t)site * NN + t * NXI;
+  double a[1] = {0.0};
+#pragma unroll
+  for (int k = 0; k < NXI; ++k) {
+    const double fk = A.Z * exp(-xv * op.c[k]);
+    a[0] += fb[k] * fk * (-op.c[k]);  // d f / d x
+  }
+  block_sum_d<1, NL>(a, red);
+  if (t == 0) {
+    const double y = sT[0], T = exp(y);
+    double xx, dx, ee, de;
+    eos_field_dy(A.eos, y, EOS_X, &xx, &dx);
+    eos_field_dy(A.eos, y, EOS_EPS, &ee, &de);
+    // x(T), ln M = ln x + ln T;  d/dT = (1/T) d/dy
+    const double Tbar = a[0] * dx / T + A.lbar[site] * (dx / xx + 1.0) / T;
+    A.epsbar[site] = Tbar * T / de * A.eps_scale;
+  }
+}
+
+// out[i] = sum_s basis[i * ns + s] epsbar[s]  (one block per row, fixed order)
+__global__ void __launch_bounds__(1024) project_kernel(const double* basis, const double* v, size_t ns, double* out) {
+  __shared__ double red[32];
+  const double* b = basis + (size_t)blockIdx.x * ns;
+  double a[1] = {0.0};
+  for (size_t s = threadIdx.x; s < ns; s += 1024) a[0] += b[s] * v[s];
+  warp_sum<1>(a);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a[0];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 32; ++w) s += red[w];
+    out[blockIdx.x] = s;
+  }
+}
+
+// out = beta * out + alpha * in (n doubles)
+__global__ void axpby_kernel(double* out, const double* in, double alpha, double beta, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = beta * out[i] + (in ? alpha * in[i] : 0.0);
+}
+
+// sum of n doubles into out[0] (one block, fixed order)
+__global__ void __launch_bounds__(1024) sum_kernel(const double* in, size_t n, double* out, int accumulate) {
+  __shared__ double red[32];
+  double a[1] = {0.0};
+  for (size_t i = threadIdx.x; i < n; i += 1024) a[0] += in[i];
+  warp_sum<1>(a);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a[0];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 32; ++w) s += red[w];
+    out[0] = accumulate ? out[0] + s : s;
+  }
+}
+
+}  // namespace rlbk

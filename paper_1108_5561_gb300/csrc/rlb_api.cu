@@ -16,6 +16,7 @@
 #include "rlb_host.hpp"
 #include "rlb_kernels.cuh"
 #include "rlb_stage_x2.cuh"
+#include "rlb_adjoint.cuh"
 
 struct rlb_ctx {
   int device = 0;
@@ -42,6 +43,10 @@ struct rlb_ctx {
   cudaGraphExec_t gexec = nullptr;
   cudaEvent_t gev[2] = {nullptr, nullptr};
   int stage_variant = 0;  // rlb_autotune's choice (see Stager)
+  // adjoint workspace (caller-owned, FP64): offsets in bytes
+  char* adj = nullptr;
+  size_t a_f = 0, a_l = 0, a_fb = 0, a_rb = 0, a_lin = 0, a_lbar = 0, a_sbar = 0, a_mbar = 0;
+  size_t a_ebar = 0, a_mom = 0, a_sc = 0, a_T = 0, a_tot = 0, a_eps = 0, a_eta = 0;
   // optional per-kernel timing (CUDA events on the launch stream)
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -119,6 +124,28 @@ void layout(const rlb_grid_params& g, const Shape& sh, size_t table_points, size
     c->mom_off = mom_off; c->moms_off = moms_off; c->sc_off = sc_off;
     c->tabf_off = tabf_off; c->scf_off = scf_off;
   }
+}
+
+// adjoint workspace: FP64 adjoints of f (twice), of r, and per-site arrays
+size_t adj_layout(rlb_ctx* c) {
+  const size_t ns = c->ns, pn = align256(ns * c->nn * sizeof(double)), s1 = align256(ns * sizeof(double));
+  size_t off = 0;
+  c->a_f = off; off += pn;
+  c->a_fb = off; off += pn;
+  c->a_rb = off; off += pn;
+  c->a_l = off; off += s1;
+  c->a_lin = off; off += s1;
+  c->a_lbar = off; off += s1;
+  c->a_ebar = off; off += s1;
+  c->a_T = off; off += s1;
+  c->a_eps = off; off += s1;
+  c->a_sbar = off; off += align256(ns * rlbk::kAdjS * sizeof(double));
+  c->a_mbar = off; off += align256(ns * rlbk::kMom * sizeof(double));
+  c->a_mom = off; off += align256(ns * rlbk::kMom * sizeof(double));
+  c->a_sc = off; off += align256(ns * rlbk::kSc * sizeof(double));
+  c->a_tot = off; off += 256;
+  c->a_eta = off; off += 256;
+  return off;
 }
 
 template <class R, int NXI, int NTH, int NPH>
@@ -583,13 +610,172 @@ rlb_status observables(rlb_ctx* ctx, double* out_dev, cudaStream_t st) {
   return RLB_OK;
 }
 
-enum Op { OP_INIT, OP_STEP, OP_MOMENTS, OP_OBS, OP_TUNE };
+// ---------------------------------------------------------------------------
+// adjoint of the step (FP64 arithmetic): see rlb_adjoint.cuh
+// ---------------------------------------------------------------------------
+template <class S, class R, int NXI, int NTH, int NPH>
+struct Adjoint {
+  static constexpr int NL = NTH * NPH;
+  static double* D(rlb_ctx* c, size_t off) { return reinterpret_cast<double*>(c->adj + off); }
+
+  // adjoint of one stage with input (f_in, lnM_in): from (ob, lb) to (fout, lout)
+  static rlb_status stage(rlb_ctx* ctx, const S* f_in, const double* lnM_in, double milne, double c,
+                          const double* ob, const double* lb, double* fout, double* lout, cudaStream_t st) {
+    const auto opd = make_ops<double, NXI, NTH, NPH>(ctx->lat);
+    const rlbk::GridMap gm = grid_map(ctx, ctx->scratch);
+    int* err = reinterpret_cast<int*>(ctx->scratch + ctx->err_off);
+    {  // FP64 moments and matching of f_in
+      rlbk::MomentsArgs<S, double, NXI, NTH, NPH> a;
+      a.f = f_in;
+      a.mom = D(ctx, ctx->a_mom);
+      a.momf = nullptr;
+      a.op = opd;
+      rlbk::moments_kernel<S, double, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
+      RLB_CUDA(cudaGetLastError(), "adjoint moments launch");
+      rlbk::MatchArgs ma = match_args(ctx, D(ctx, ctx->a_mom), lnM_in, nullptr);
+      ma.Tsite = D(ctx, ctx->a_T);
+      ma.sc = D(ctx, ctx->a_sc);
+      ma.scf = nullptr;
+      rlbk::match_kernel<false><<<(unsigned)((ctx->ns + 127) / 128), 128, 0, st>>>(ma);
+      RLB_CUDA(cudaGetLastError(), "adjoint matching launch");
+    }
+    {
+      rlbk::AdjStageArgs<S, NXI, NTH, NPH> a;
+      a.f_in = f_in; a.sc = D(ctx, ctx->a_sc); a.ob = ob; a.lb = lb;
+      a.rbar = D(ctx, ctx->a_rb); a.fbar = D(ctx, ctx->a_fb); a.sbar = D(ctx, ctx->a_sbar);
+      a.grid = gm; a.milne = milne; a.c = c; a.dtau = ctx->gp.dtau; a.inv2dx = 1.0 / (2.0 * ctx->gp.dx);
+      a.Z = ctx->eosp.Z; a.op = opd;
+      rlbk::adj_stage1<S, NXI, NTH, NPH><<<site_grid(ctx), NL, 0, st>>>(a);
+      RLB_CUDA(cudaGetLastError(), "adj_stage1 launch");
+    }
+    {
+      rlbk::AdjMatchArgs a;
+      a.mom = D(ctx, ctx->a_mom); a.lnM = lnM_in; a.sbar = D(ctx, ctx->a_sbar); a.mbar = D(ctx, ctx->a_mbar);
+      a.lbar = D(ctx, ctx->a_lbar); a.ebar = D(ctx, ctx->a_ebar); a.err = err; a.eos = eos_view(ctx);
+      a.grid = gm; a.ns = (int)ctx->ns;
+      rlbk::adj_match<<<(unsigned)((ctx->ns + 127) / 128), 128, 0, st>>>(a);
+      RLB_CUDA(cudaGetLastError(), "adj_match launch");
+      rlbk::sum_kernel<<<1, 1024, 0, st>>>(D(ctx, ctx->a_ebar), ctx->ns, D(ctx, ctx->a_eta), 1);
+      RLB_CUDA(cudaGetLastError(), "adjoint eta sum launch");
+    }
+    {
+      rlbk::AdjAssembleArgs<NXI, NTH, NPH> a;
+      a.fbar = D(ctx, ctx->a_fb); a.rbar = D(ctx, ctx->a_rb); a.mbar = D(ctx, ctx->a_mbar);
+      a.sbar = D(ctx, ctx->a_sbar); a.lbar = D(ctx, ctx->a_lbar); a.lb = lb; a.fout = fout; a.lout = lout;
+      a.grid = gm; a.c = c; a.inv2dx = 1.0 / (2.0 * ctx->gp.dx); a.op = opd;
+      rlbk::adj_stage3<NXI, NTH, NPH><<<site_grid(ctx), NL, 0, st>>>(a);
+      RLB_CUDA(cudaGetLastError(), "adj_stage3 launch");
+    }
+    return RLB_OK;
+  }
+
+  static rlb_status axpby(rlb_ctx* ctx, double* out, const double* in, double a, double b, size_t n, cudaStream_t st) {
+    rlbk::axpby_kernel<<<(unsigned)std::min<size_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(out, in, a, b, n);
+    RLB_CUDA(cudaGetLastError(), "axpby launch");
+    return RLB_OK;
+  }
+
+  // the adjoint buffers hold the adjoints of a step's output; the context state
+  // is that step's input (at ctx->tau): replace them by the adjoints of the input
+  static rlb_status step(rlb_ctx* ctx, cudaStream_t st) {
+    S* f = reinterpret_cast<S*>(ctx->state + ctx->f_off);
+    S* fs = reinterpret_cast<S*>(ctx->scratch + ctx->fs_off);
+    double* m = reinterpret_cast<double*>(ctx->state + ctx->lnM_off);
+    double* ms = reinterpret_cast<double*>(ctx->scratch + ctx->lnMs_off);
+    double* mom = reinterpret_cast<double*>(ctx->scratch + ctx->mom_off);
+    double* moms = reinterpret_cast<double*>(ctx->scratch + ctx->moms_off);
+    // the predictor output f*, ln M* exactly as the forward run made it
+    rlb_status r = match(ctx, mom, m, nullptr, st);
+    if (r) return r;
+    Stager<S, R, NXI, NTH, NPH> sg(ctx, ctx->scratch, reinterpret_cast<const double*>(ctx->scratch + ctx->sc_off),
+                                   reinterpret_cast<const float*>(ctx->scratch + ctx->scf_off),
+                                   reinterpret_cast<int*>(ctx->scratch + ctx->err_off));
+    sg.launch(f, m, f, m, fs, ms, moms, 0, st);
+    RLB_CUDA(cudaGetLastError(), "adjoint predictor recompute");
+    const double tau = ctx->tau, dt = ctx->gp.dtau;
+    const bool milne = ctx->gp.metric == RLB_MILNE;
+    const size_t npop = ctx->ns * ctx->nn;
+    // corrector f_new = (f + f* + dtau RHS(f*)) / 2
+    r = stage(ctx, fs, ms, milne ? 1.0 / (tau + dt) : 0.0, 0.5, D(ctx, ctx->a_f), D(ctx, ctx->a_l),
+              D(ctx, ctx->a_fb), D(ctx, ctx->a_lin), st);
+    if (r) return r;
+    r = axpby(ctx, D(ctx, ctx->a_f), nullptr, 0.0, 0.5, npop, st);  // base terms (1/2) fbar_new
+    if (r) return r;
+    r = axpby(ctx, D(ctx, ctx->a_l), nullptr, 0.0, 0.5, ctx->ns, st);
+    if (r) return r;
+    // predictor f* = f + dtau RHS(f)
+    r = stage(ctx, f, m, milne ? 1.0 / tau : 0.0, 1.0, D(ctx, ctx->a_fb), D(ctx, ctx->a_lin),
+              D(ctx, ctx->a_fb), D(ctx, ctx->a_lin), st);
+    if (r) return r;
+    r = axpby(ctx, D(ctx, ctx->a_f), D(ctx, ctx->a_fb), 1.0, 1.0, npop, st);
+    if (r) return r;
+    return axpby(ctx, D(ctx, ctx->a_l), D(ctx, ctx->a_lin), 1.0, 1.0, ctx->ns, st);
+  }
+
+  // seed: adjoints of v2 (p_perp-weighted) of the current state; out[0] = v2
+  static rlb_status seed(rlb_ctx* ctx, double* out, cudaStream_t st) {
+    double* dev = reinterpret_cast<double*>(ctx->scratch + ctx->eps_off);
+    rlb_status r = observables<S, R, NXI, NTH, NPH>(ctx, dev, st);
+    if (r) return r;
+    rlbk::SeedArgs<S, NXI, NTH, NPH> a;
+    a.lnM = reinterpret_cast<const double*>(ctx->state + ctx->lnM_off);
+    a.part = reinterpret_cast<const double*>(ctx->scratch + ctx->moms_off);
+    a.tot = dev + 2;
+    a.fbar = D(ctx, ctx->a_f);
+    a.lbar = D(ctx, ctx->a_l);
+    a.op = make_ops<double, NXI, NTH, NPH>(ctx->lat);
+    rlbk::adj_seed_v2<S, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
+    RLB_CUDA(cudaGetLastError(), "adjoint seed launch");
+    RLB_CUDA(cudaMemsetAsync(D(ctx, ctx->a_eta), 0, sizeof(double), st), "adjoint eta reset");
+    RLB_CUDA(cudaMemcpyAsync(out, dev + 1, sizeof(double), cudaMemcpyDeviceToHost, st), "v2 download");
+    RLB_CUDA(cudaStreamSynchronize(st), "adjoint seed synchronise");
+    return RLB_OK;
+  }
+
+  // initial condition: p[0] = eps0 (device, GeV/fm^3), p[1] = basis (device,
+  // n x ns), p[2] = n, p[3] = output (host, n + 1: dJ/dA_i, then dJ/d(eta/s))
+  static rlb_status ic(rlb_ctx* ctx, const double* eps0, const double* basis, int n, double* out, cudaStream_t st) {
+    rlbk::AdjIcArgs<S, NXI, NTH, NPH> a;
+    a.eps0 = eps0; a.fbar = D(ctx, ctx->a_f); a.lbar = D(ctx, ctx->a_l); a.epsbar = D(ctx, ctx->a_eps);
+    a.err = reinterpret_cast<int*>(ctx->scratch + ctx->err_off); a.eos = eos_view(ctx);
+    a.eps_scale = rlb::kHbarc * rlb::kHbarc * rlb::kHbarc; a.Z = ctx->eosp.Z;
+    a.op = make_ops<double, NXI, NTH, NPH>(ctx->lat);
+    rlbk::adj_ic<S, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
+    RLB_CUDA(cudaGetLastError(), "adj_ic launch");
+    double* proj = D(ctx, ctx->a_ebar);  // n <= ns doubles (checked by the caller)
+    if (n > 0) {
+      rlbk::project_kernel<<<(unsigned)n, 1024, 0, st>>>(basis, D(ctx, ctx->a_eps), ctx->ns, proj);
+      RLB_CUDA(cudaGetLastError(), "projection launch");
+      RLB_CUDA(cudaMemcpyAsync(out, proj, n * sizeof(double), cudaMemcpyDeviceToHost, st), "gradient download");
+    }
+    RLB_CUDA(cudaMemcpyAsync(out + n, D(ctx, ctx->a_eta), sizeof(double), cudaMemcpyDeviceToHost, st),
+             "eta gradient download");
+    RLB_CUDA(cudaStreamSynchronize(st), "adjoint ic synchronise");
+    return RLB_OK;
+  }
+};
+
+enum Op { OP_INIT, OP_STEP, OP_MOMENTS, OP_OBS, OP_TUNE, OP_ADJ_SEED, OP_ADJ_STEP, OP_ADJ_IC };
+
+// arguments of the adjoint initial-condition call, passed through dispatch
+struct AdjIcCall {
+  const double* eps0;
+  const double* basis;
+  int n;
+  double* out;
+};
 
 template <class S, class R, int NXI, int NTH, int NPH>
 rlb_status run_op(rlb_ctx* c, Op op, int n, double* p, cudaStream_t st) {
   using Rn = Runner<S, R, NXI, NTH, NPH>;
   if (op == OP_INIT) return Rn::init(c, p, st);
   if (op == OP_STEP) return Rn::step(c, n, st);
+  if (op == OP_ADJ_SEED) return Adjoint<S, R, NXI, NTH, NPH>::seed(c, p, st);
+  if (op == OP_ADJ_STEP) return Adjoint<S, R, NXI, NTH, NPH>::step(c, st);
+  if (op == OP_ADJ_IC) {
+    const AdjIcCall* a = reinterpret_cast<const AdjIcCall*>(p);
+    return Adjoint<S, R, NXI, NTH, NPH>::ic(c, a->eps0, a->basis, a->n, a->out, st);
+  }
   if (op == OP_TUNE) {
     int nv = 0;
     rlb_status r = Rn::autotune(c, p, &nv, st);
@@ -1089,13 +1275,14 @@ rlb_status rlb_save_state(rlb_ctx* ctx, void* host_buf, size_t bytes, void* stre
   if (s) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   char* p = static_cast<char*>(host_buf);
-  std::memcpy(p, &h, sizeof h);
+  RLB_CUDA(cudaMemcpyAsync(p, &h, sizeof h, cudaMemcpyDefault, st), "state header");
+  RLB_CUDA(cudaStreamSynchronize(st), "state header synchronise");  // h lives on this stack
   p += sizeof h;
   const struct { const char* src; uint64_t n; } parts[4] = {
       {ctx->state + ctx->f_off, h.f_bytes}, {ctx->state + ctx->lnM_off, h.lnM_bytes},
       {ctx->scratch + ctx->T_off, h.T_bytes}, {ctx->scratch + ctx->mom_off, h.mom_bytes}};
   for (const auto& q : parts) {
-    RLB_CUDA(cudaMemcpyAsync(p, q.src, q.n, cudaMemcpyDeviceToHost, st), "state download");
+    RLB_CUDA(cudaMemcpyAsync(p, q.src, q.n, cudaMemcpyDefault, st), "state copy");
     p += q.n;
   }
   RLB_CUDA(cudaStreamSynchronize(st), "state download synchronise");
@@ -1108,7 +1295,7 @@ rlb_status rlb_load_state(rlb_ctx* ctx, const void* host_buf, size_t bytes, void
   BlobHeader want, got;
   blob_parts(ctx, &want);
   if (bytes < sizeof got) return fail(ctx, RLB_ERR_ARG, "state blob shorter than its header");
-  std::memcpy(&got, host_buf, sizeof got);
+  RLB_CUDA(cudaMemcpy(&got, host_buf, sizeof got, cudaMemcpyDefault), "state header");
   if (std::memcmp(got.magic, want.magic, 8) != 0 || got.version != want.version)
     return fail(ctx, RLB_ERR_ARG, "not a state blob of this library version");
   if (got.prec != want.prec || got.nx != want.nx || got.ny != want.ny || got.n_xi != want.n_xi ||
@@ -1125,7 +1312,7 @@ rlb_status rlb_load_state(rlb_ctx* ctx, const void* host_buf, size_t bytes, void
       {ctx->state + ctx->f_off, got.f_bytes}, {ctx->state + ctx->lnM_off, got.lnM_bytes},
       {ctx->scratch + ctx->T_off, got.T_bytes}, {ctx->scratch + ctx->mom_off, got.mom_bytes}};
   for (const auto& q : parts) {
-    RLB_CUDA(cudaMemcpyAsync(q.dst, p, q.n, cudaMemcpyHostToDevice, st), "state upload");
+    RLB_CUDA(cudaMemcpyAsync(q.dst, p, q.n, cudaMemcpyDefault, st), "state copy");
     p += q.n;
   }
   ctx->tau = got.tau;
@@ -1150,6 +1337,57 @@ rlb_status rlb_autotune(rlb_ctx* ctx, void* stream, int* chosen, double* variant
   if (variant_ms)
     for (int v = 0; v < nv; ++v) variant_ms[v] = t[v];
   return RLB_OK;
+}
+
+rlb_status rlb_adjoint_workspace_size(rlb_ctx* ctx, size_t* bytes) {
+  if (!ctx || !bytes || !ctx->grid_ok) return RLB_ERR_ARG;
+  *bytes = adj_layout(ctx);
+  return RLB_OK;
+}
+
+rlb_status rlb_adjoint_bind(rlb_ctx* ctx, void* workspace) {
+  if (!ctx || !workspace || ((uintptr_t)workspace & 255)) return RLB_ERR_ARG;
+  if (!ctx->grid_ok) return fail(ctx, RLB_ERR_STATE, "rlb_configure must come first");
+  adj_layout(ctx);
+  ctx->adj = static_cast<char*>(workspace);
+  rlb_status s = set_device(ctx);
+  if (s) return s;
+  // the FP64 matchings of the adjoint start their Newton solves from zeros here:
+  // results do not depend on what the memory held
+  RLB_CUDA(cudaMemset(ctx->adj + ctx->a_T, 0, ctx->ns * sizeof(double)), "adjoint workspace reset");
+  return RLB_OK;
+}
+
+rlb_status rlb_adjoint_seed_v2(rlb_ctx* ctx, double* v2, void* stream) {
+  if (!ctx || !v2) return RLB_ERR_ARG;
+  if (!ctx->inited || !ctx->adj) return fail(ctx, RLB_ERR_STATE, "state and adjoint workspace needed");
+  rlb_status s = set_device(ctx);
+  if (s) return s;
+  s = dispatch(ctx, OP_ADJ_SEED, 0, v2, static_cast<cudaStream_t>(stream));
+  if (s) return s;
+  return rlb_check(ctx, stream);
+}
+
+rlb_status rlb_adjoint_step(rlb_ctx* ctx, void* stream) {
+  if (!ctx) return RLB_ERR_ARG;
+  if (!ctx->inited || !ctx->adj) return fail(ctx, RLB_ERR_STATE, "state and adjoint workspace needed");
+  rlb_status s = set_device(ctx);
+  if (s) return s;
+  return dispatch(ctx, OP_ADJ_STEP, 0, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+rlb_status rlb_adjoint_ic(rlb_ctx* ctx, const double* eps0, const double* basis, int n_basis, double* grad,
+                          void* stream) {
+  if (!ctx || !eps0 || !grad || n_basis < 0 || (n_basis > 0 && !basis)) return RLB_ERR_ARG;
+  if (!ctx->adj) return fail(ctx, RLB_ERR_STATE, "adjoint workspace needed");
+  if ((size_t)n_basis > ctx->ns) return fail(ctx, RLB_ERR_ARG, "at most one basis row per site");
+  if (ctx->gp.family != RLB_RADIAL_PAPER) return fail(ctx, RLB_ERR_ARG, "initial-condition adjoint needs the dynamical mass");
+  rlb_status s = set_device(ctx);
+  if (s) return s;
+  AdjIcCall a{eps0, basis, n_basis, grad};
+  s = dispatch(ctx, OP_ADJ_IC, 0, reinterpret_cast<double*>(&a), static_cast<cudaStream_t>(stream));
+  if (s) return s;
+  return rlb_check(ctx, stream);
 }
 
 rlb_status rlb_set_graphs(rlb_ctx* ctx, int enable) {

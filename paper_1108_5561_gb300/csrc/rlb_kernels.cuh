@@ -1275,7 +1275,8 @@ __global__ void __launch_bounds__(NTH* NPH)
   }
 }
 
-// out[0] = eps_p, out[1] = v2; one block of 1024 threads, fixed summation order
+// out[0] = eps_p, out[1] = v2, out[2..5] the four grid sums; one block of 1024
+// threads, fixed summation order
 __global__ void __launch_bounds__(1024) observables_reduce_kernel(const double* part, int ns, double* out) {
   __shared__ double red[4 * 32];
   double a[4] = {0.0, 0.0, 0.0, 0.0};
@@ -1295,6 +1296,8 @@ __global__ void __launch_bounds__(1024) observables_reduce_kernel(const double* 
       for (int q = 0; q < 4; ++q) s[q] += red[w * 4 + q];
     out[0] = (s[0] - s[1]) / (s[0] + s[1]);
     out[1] = s[2] / s[3];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[2 + q] = s[q];  // the grid sums
   }
 }
 

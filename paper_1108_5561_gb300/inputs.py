@@ -79,3 +79,11 @@ def batch_events(n: int = 512, seed: int = 1108, n_min: int = 64, n_max: int = 1
         side = n_min + min(int(r.uniform() * (n_max - n_min + 1)), n_max - n_min)
         out.append((side, eta_min + (eta_max - eta_min) * r.uniform()))
     return out
+
+
+def hotspot_basis(nx: int, ny: int, centres, dx: float = 0.1, width: float = 0.4):
+    """The unit Gaussians of hotspots at `centres`, one row per hotspot, sites in
+    storage order (row-major): eps0 = floor + amplitudes @ basis."""
+    X, Y = coords(nx, ny, dx)
+    return np.stack([np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (2 * width * width)).reshape(-1)
+                     for cx, cy in centres])

@@ -197,16 +197,25 @@ class Run:
                   "rlb_observables")
         return a.value, b.value
 
-    def save_state(self) -> bytes:
-        """Checkpoint blob of the current state (host bytes)."""
+    def save_state(self, device: bool = False):
+        """Checkpoint blob of the current state: host bytes, or a CUDA uint8 tensor."""
         n = ctypes.c_size_t()
         self._chk(self.lib.rlb_state_blob_size(self._h, ctypes.byref(n)), "rlb_state_blob_size")
+        if device:
+            t = self.torch.empty(n.value, dtype=self.torch.uint8, device=self.device)
+            self._chk(self.lib.rlb_save_state(self._h, ctypes.c_void_p(t.data_ptr()), n, self._stream()),
+                      "rlb_save_state")
+            return t
         buf = ctypes.create_string_buffer(n.value)
         self._chk(self.lib.rlb_save_state(self._h, buf, n, self._stream()), "rlb_save_state")
         return buf.raw
 
-    def load_state(self, blob: bytes):
+    def load_state(self, blob):
         """Replace the state (and tau) by a blob from save_state of the same grid."""
+        if isinstance(blob, self.torch.Tensor):
+            self._chk(self.lib.rlb_load_state(self._h, ctypes.c_void_p(blob.data_ptr()), blob.numel(),
+                                              self._stream()), "rlb_load_state")
+            return
         buf = ctypes.create_string_buffer(blob, len(blob))
         self._chk(self.lib.rlb_load_state(self._h, buf, len(blob), self._stream()), "rlb_load_state")
 

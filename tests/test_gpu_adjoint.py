@@ -1,0 +1,138 @@
+"""Adjoint of the time evolution (rlb_adjoint_*): gradient of the final
+p_perp-weighted v2 with respect to hotspot amplitudes and eta/s, against
+central finite differences of the GPU forward run (FP64 and FP32 storage),
+against central finite differences of the FP64 oracle, independent of the
+checkpoint interval, and through torch.autograd."""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1108_5561_gb300 as rlb  # noqa: E402
+from paper_1108_5561_gb300 import adjoint as ADJ  # noqa: E402
+from paper_1108_5561_gb300.inputs import hotspot_basis, hotspots  # noqa: E402
+
+NT = os.cpu_count() or 1
+NX, NY, STEPS, ETA, FLOOR = 8, 7, 4, 0.16, 10.0
+
+
+def _case():
+    _, amps, cen = hotspots(NX, NY, dx=0.1, n=3, seed=5, spread=0.25, mean_amp=15.0)
+    basis = hotspot_basis(NX, NY, cen, dx=0.1)
+    return amps, basis
+
+
+def _grid(prec, eta=ETA):
+    return rlb.GridParams(nx=NX, ny=NY, dx=0.1, prec=prec, eta_over_s=eta, tau0=0.4, dtau=0.0036)
+
+
+def _v2(prec, amps, basis, eta=ETA):
+    run = rlb.Run(_grid(prec, eta))
+    run.init_grid(FLOOR + amps @ basis)
+    run.step(STEPS)
+    return run.observables()[1]
+
+
+def _adjoint(prec, amps, basis, every):
+    run = rlb.Run(_grid(prec))
+    eps0 = torch.as_tensor(FLOOR + amps @ basis, dtype=torch.float64, device="cuda")
+    b = torch.as_tensor(basis, dtype=torch.float64, device="cuda")
+    return ADJ.v2_gradient(run, eps0, b, STEPS, every)
+
+
+def _fd(prec, amps, basis, rel_h, with_eta=True):
+    fd = []
+    for i in range(len(amps)):
+        h = rel_h * amps[i]
+        ap, am = amps.copy(), amps.copy()
+        ap[i] += h
+        am[i] -= h
+        fd.append((_v2(prec, ap, basis) - _v2(prec, am, basis)) / (2 * h))
+    fde = None
+    if with_eta:
+        he = rel_h * ETA
+        fde = (_v2(prec, amps, basis, ETA + he) - _v2(prec, amps, basis, ETA - he)) / (2 * he)
+    return np.array(fd), fde
+
+
+def test_fp64_adjoint_matches_finite_differences():
+    amps, basis = _case()
+    v2, gA, geta = _adjoint(rlb.RLB_F64, amps, basis, every=2)
+    assert v2 == pytest.approx(_v2(rlb.RLB_F64, amps, basis), rel=1e-12)
+    fd, fde = _fd(rlb.RLB_F64, amps, basis, 1e-4)
+    print("fp64 adjoint", gA, geta, "fd", fd, fde)
+    scale = np.abs(fd).max()
+    assert np.abs(gA - fd).max() < 1e-6 * scale, (gA, fd)
+    assert abs(geta - fde) < 1e-5 * abs(fde), (geta, fde)
+
+
+def test_fp32_adjoint():
+    # the adjoint of the FP32-storage trajectory against the FP64 adjoint, and the
+    # amplitude gradients against finite differences of the FP32 forward run
+    # (the eta/s effect, ~1e-9 in v2 over a usable step, is below the FP32 noise)
+    amps, basis = _case()
+    _, g32, e32 = _adjoint(rlb.RLB_F32, amps, basis, every=2)
+    _, g64, e64 = _adjoint(rlb.RLB_F64, amps, basis, every=2)
+    scale = np.abs(g64).max()
+    print("fp32 adjoint", g32, e32, "fp64", g64, e64)
+    assert np.abs(g32 - g64).max() < 1e-3 * scale and abs(e32 - e64) < 1e-3 * abs(e64)
+    fd, _ = _fd(rlb.RLB_F32, amps, basis, 0.1, with_eta=False)
+    print("fp32 fd", fd)
+    assert np.abs(g32 - fd).max() < 0.03 * scale, (g32, fd)
+
+
+def test_adjoint_matches_oracle_finite_differences(oracle_mod):
+    amps, basis = _case()
+    _, gA, geta = _adjoint(rlb.RLB_F64, amps, basis, every=4)
+
+    def v2o(a, eta=ETA):
+        o = oracle_mod.Oracle(nx=NX, ny=NY, dx=0.1, eta_over_s=eta)
+        f, lnM = o.init_state(FLOOR + a @ basis, NT)
+        o.step(f, lnM, 0.4, 0.0036, STEPS, NT)
+        return o.observables(f, lnM, NT)[1]
+
+    fd = []
+    for i in range(len(amps)):
+        h = 1e-4 * amps[i]
+        ap, am = amps.copy(), amps.copy()
+        ap[i] += h
+        am[i] -= h
+        fd.append((v2o(ap) - v2o(am)) / (2 * h))
+    fd = np.array(fd)
+    he = 1e-4 * ETA
+    fde = (v2o(amps, ETA + he) - v2o(amps, ETA - he)) / (2 * he)
+    print("oracle fd", fd, fde, "adjoint", gA, geta)
+    scale = np.abs(fd).max()
+    assert np.abs(gA - fd).max() < 1e-6 * scale
+    assert abs(geta - fde) < 1e-5 * abs(fde)  # a ~1e-11 change of v2 over the eta step
+
+
+def test_checkpoint_interval_does_not_change_the_gradient():
+    amps, basis = _case()
+    a = _adjoint(rlb.RLB_F32, amps, basis, every=1)
+    b = _adjoint(rlb.RLB_F32, amps, basis, every=3)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1]) and a[2] == b[2]
+
+
+def test_autograd_function():
+    amps, basis = _case()
+    run = rlb.Run(_grid(rlb.RLB_F64))
+    b = torch.as_tensor(basis, dtype=torch.float64, device="cuda")
+    A = torch.tensor(amps, dtype=torch.float64, requires_grad=True)
+    eta = torch.tensor(ETA, dtype=torch.float64, requires_grad=True)
+    F = ADJ.elliptic_flow_function()
+    v2 = F.apply(A, eta, run, b, FLOOR, STEPS, 2)
+    v2.backward()
+    _, gA, geta = _adjoint(rlb.RLB_F64, amps, basis, every=2)
+    rel = np.abs(A.grad.numpy() - gA) / np.abs(gA).max()
+    print("autograd", A.grad.numpy(), eta.grad.item(), "direct", gA, geta, "rel", rel)
+    # the same gradient (the initial state is summed on the device here, on the host
+    # there: rounding-level differences of eps0)
+    assert rel.max() < 1e-8
+    assert eta.grad.item() == pytest.approx(geta, rel=1e-8)
