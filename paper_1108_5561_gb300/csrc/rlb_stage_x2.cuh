@@ -132,10 +132,11 @@ __device__ __forceinline__ void store_pairs(S* __restrict__ p, float2 (&v)[NP]) 
   }
 }
 
-// MINB resident blocks per SM bound the registers (8 blocks of 96 threads: 80
-// registers, measured faster than the uncapped 88 on the 256^2 workload; the
-// autotuner times both)
-template <class S, int NXI, int NTH, int NPH, int MINB = (NTH * NPH <= 96 ? 8 : 3)>
+// MINB resident blocks per SM bound the registers (12 blocks of 96 threads: 56
+// registers; measured at 160^2: 75 us against 79 us uncapped (72 registers)
+// and 89-93 us at 40 registers, which spill; the autotuner also times the
+// uncapped kernel)
+template <class S, int NXI, int NTH, int NPH, int MINB = (NTH * NPH <= 96 ? 12 : 3)>
 __global__ void __launch_bounds__(NTH* NPH, MINB)
     stage_kernel_x2(const __grid_constant__ StageArgsX2<S, NXI, NTH, NPH> A) {
   static_assert(NXI % 2 == 0 && NTH % 2 == 0, "paired radial nodes, half polar lines");
@@ -181,6 +182,20 @@ __global__ void __launch_bounds__(NTH* NPH, MINB)
   load_pairs<S, NP>(fev + (size_t)(y * nx + x2) * NN, fx2);
   load_pairs<S, NP>(fev + (size_t)(y1 * nx + x) * NN, fy1);
   load_pairs<S, NP>(fev + (size_t)(y2 * nx + x) * NN, fy2);
+  // streaming term right away: the neighbour lines die here instead of staying
+  // live across the barriers below (fewer registers, more resident blocks)
+  float2 strm[NP];
+  {
+    const float st0 = op.sth[j];
+    const float2 nsx0 = bc2(-st0 * fabsf(cp) * A.inv2dx_r), nsy0 = bc2(-st0 * fabsf(sp) * A.inv2dx_r);
+    const float2 three0 = bc2(3.f), mfour0 = bc2(-4.f);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const float2 Sx = fma2(mfour0, fx1[p], fma2(three0, f[p], fx2[p]));
+      const float2 Sy = fma2(mfour0, fy1[p], fma2(three0, f[p], fy2[p]));
+      strm[p] = mul2(op.tv[p], fma2(nsy0, Sy, mul2(nsx0, Sx)));
+    }
+  }
 
   // site scalars of the matching of f_in
   const float* q = A.scf + (size_t)site * kSc;
@@ -238,7 +253,6 @@ __global__ void __launch_bounds__(NTH* NPH, MINB)
   const float vu = st * (cp * ux + sp * uy);
   const float A1 = st * (ax * cp + ay * sp);
   const float au = ax * ux + ay * uy;
-  const float2 nsx = bc2(-st * fabsf(cp) * A.inv2dx_r), nsy = bc2(-st * fabsf(sp) * A.inv2dx_r);
   const float2 mmu2 = bc2(milne * op.mu2[j]), milne2 = bc2(milne);
   constexpr float kLog2e = 1.4426950408889634f;
   const float2 c1 = bc2(-kLog2e * invT * ut), c2 = bc2(kLog2e * invT * M * vu), lZ = bc2(A.log2Z);
@@ -246,16 +260,13 @@ __global__ void __launch_bounds__(NTH* NPH, MINB)
   const float2 cc0 = bc2(ut * itr), cc1 = bc2(-vu * itr);
   const float2 ncc0 = bc2(-ut * itr), ncc1 = bc2(vu * itr);
   const float2 utb = bc2(ut), nvub = bc2(-vu);
-  const float2 three = bc2(3.f), mfour = bc2(-4.f);
   float2 Rn[NP];
   float2 sA = make_float2(0.f, 0.f), sQ = sA, sE = sA;
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
     const float4 tb = tab[p];
     const float2 E = make_float2(tb.x, tb.y), QE = make_float2(tb.z, tb.w);
-    const float2 Sx = fma2(mfour, fx1[p], fma2(three, f[p], fx2[p]));
-    const float2 Sy = fma2(mfour, fy1[p], fma2(three, f[p], fy2[p]));
-    float2 r = fma2(mmu2, Drf[p], mul2(op.tv[p], fma2(nsy, Sy, mul2(nsx, Sx))));
+    float2 r = fma2(mmu2, Drf[p], strm[p]);
     if (pol) r = fma2(milne2, pth[p * LDK + l * LDL + j], r);
     const float2 ex = fma2(c1, E, fma2(c2, op.s[p], lZ));
     const float2 feq = make_float2(ex2_ftz(ex.x), ex2_ftz(ex.y));
