@@ -36,6 +36,47 @@ WORKLOAD = ("rlb-milne-2+1d 256x256 grid dx 0.1 fm, 768 nodes (8xi x 8theta x 12
             "populations, 40 hotspots on 10 GeV/fm^3")
 
 
+
+class Ranks:
+    """One process per GPU (torchrun): rank and world size from the
+    environment, a process group when there is more than one rank, a barrier,
+    and the maximum of a host number over ranks (the timed region of the
+    slowest rank).  The replicas exchange nothing else."""
+
+    def __init__(self, backend: str = "nccl"):
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, x: float, device: str = "cuda") -> float:
+        if self.dist is None:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def job_rate(units_per_rank: float, world: int, t_max: float) -> float:
+    """Whole-job throughput of weak scaling: every rank processes the same
+    number of units, the job takes as long as the slowest rank."""
+    return world * units_per_rank / t_max
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -146,10 +187,7 @@ def batch_main(args, rank, world, local):
 
     assert args.warmup >= 3, "at least 3 warm-up steps"
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    ranks = Ranks("nccl")
     evs = batch_events(BATCH_EVENTS, seed=1108)
     events = [rlb.Event(n, n, eta) for n, eta in evs]
     eps = np.concatenate([hotspots(n, n, n=40, seed=1108 + i)[0].reshape(-1) for i, (n, _) in enumerate(evs)])
@@ -162,9 +200,7 @@ def batch_main(args, rank, world, local):
     torch.cuda.synchronize()
     run.check()
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
+    barrier = ranks.barrier
 
     props = torch.cuda.get_device_properties(local)
     dev_id = str(getattr(props, "uuid", "")) or None
@@ -189,13 +225,10 @@ def batch_main(args, rank, world, local):
     run.set_timing(False)
     clocks = sampler.stop() if sampler else None
     run.check()
-    if dist is not None:
-        tt = torch.tensor([t], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    t = ranks.max(t)
     ns, nn, b = run.ns, g.nodes, 4
     t_step = t / args.steps
-    value = world * BATCH_EVENTS / (t_step * BATCH_EVOLUTION_STEPS)
+    value = job_rate(BATCH_EVENTS / BATCH_EVOLUTION_STEPS, world, t_step)
     alg_bytes_launch = 2.5 * b * ns * nn + ns * (56 + 64 + 8 + 8 + 4)
     achieved = alg_bytes_launch / (stage_ms / stage_n / 1e3) / 1e9
     peak, peak_kind = peaks()
@@ -253,8 +286,7 @@ def batch_main(args, rank, world, local):
             "e2e": e2e, "gpu_launches": 4 * args.steps, "clocks": clocks, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    ranks.close()
     return 0
 
 
@@ -460,10 +492,7 @@ def main():
 
     assert args.warmup >= 3, "at least 3 warm-up steps"
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    ranks = Ranks("nccl")
     eps0, _, _ = hotspots(NX, NY, n=40, seed=1108)
     g = rlb.GridParams(nx=NX, ny=NY, dx=DX, prec=rlb.RLB_F32, eta_over_s=ETA_S, tau0=TAU0,
                        dtau=DTAU)
@@ -474,9 +503,7 @@ def main():
     torch.cuda.synchronize()
     run.check()
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
+    barrier = ranks.barrier
 
     props = torch.cuda.get_device_properties(local)
     dev_id = str(getattr(props, "uuid", "")) or None
@@ -503,13 +530,10 @@ def main():
     run.set_timing(False)
     clocks = sampler.stop() if sampler else None
     run.check()
-    if dist is not None:
-        tt = torch.tensor([t], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    t = ranks.max(t)
     ns, nn = NX * NY, g.nodes
     updates = world * ns * nn * args.steps
-    value = updates / t
+    value = job_rate(ns * nn * args.steps, world, t)
     b = 4  # FP32 storage
     launches = 4 * args.steps  # per step: (match + stream-collide) x (predictor, corrector)
     # algorithmic bytes of one stream-collide launch: predictor reads f and writes
@@ -538,7 +562,7 @@ def main():
     kern = {"stream_collide_ms_per_launch": stage_ms / stage_n,
             "match_ms_per_launch": match_ms / match_n, "timed_launches": stage_n + match_n}
     return finish(args, rank, world, t, value, achieved, peak, peak_kind, b, nn, launches, e2e,
-                  clocks, cpu, dist, kern)
+                  clocks, cpu, ranks, kern)
 
 
 def end_to_end(run, eps0, args, updates, barrier, torch):
@@ -563,7 +587,7 @@ def end_to_end(run, eps0, args, updates, barrier, torch):
 
 
 def finish(args, rank, world, t, value, achieved, peak, peak_kind, b, nn, launches, e2e, clocks,
-           cpu, dist, kern):
+           cpu, ranks, kern):
     if rank == 0:
         line = {
             "metric": "site-population updates/s", "value": value, "unit": "updates/s",
@@ -584,8 +608,7 @@ def finish(args, rank, world, t, value, achieved, peak, peak_kind, b, nn, launch
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    ranks.close()
     return 0
 
 

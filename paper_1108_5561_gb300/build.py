@@ -9,7 +9,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "librlb.so")
 SOURCES = ["rlb_api.cu", "rlb_host.cpp"]
-HEADERS = ["rlb_kernels.cuh", "rlb_stage_x2.cuh", "rlb_host.hpp", os.path.join("..", "..", "include", "rlb.h")]
+HEADERS = ["rlb_kernels.cuh", "rlb_stage_x2.cuh", "rlb_adjoint.cuh", "rlb_host.hpp", os.path.join("..", "..", "include", "rlb.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
