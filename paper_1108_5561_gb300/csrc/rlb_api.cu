@@ -57,6 +57,10 @@ struct rlb_ctx {
 
 namespace {
 
+// matching: one site per thread; 64-thread blocks spread the FP64-heavy sites
+// evenly over the SMs (65,536 sites: 1,024 blocks, 6.7 per SM)
+constexpr int kMatchThreads = 64;
+
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 rlb_status fail(rlb_ctx* c, rlb_status s, const std::string& m) {
@@ -214,6 +218,8 @@ void eos_geometry(const rlb::EosTable& tab, rlbk::EosView* v) {
   const double c = tab.y0 * v->inv_h;
   v->c_hi = (float)std::nearbyint(c);
   v->c_lo = (float)(c - (double)v->c_hi);
+  v->ylo_f = (float)(tab.y0 + 2.0 * tab.h);
+  v->yhi_f = (float)(tab.y0 + (tab.n - 4) * tab.h);
 }
 
 rlbk::EosView eos_view(const rlb_ctx* c) {
@@ -412,9 +418,9 @@ rlb_status match(rlb_ctx* ctx, const double* mom, const double* lnM, double* obs
   a.clock = clock;
   {
     Timed tm(ctx, K_MATCH, st);
-    const unsigned nb = (unsigned)((ctx->ns + 127) / 128);
-    if (ctx->gp.prec == RLB_F64) rlbk::match_kernel<false><<<nb, 128, 0, st>>>(a);
-    else rlbk::match_kernel<true><<<nb, 128, 0, st>>>(a);
+    const unsigned nb = (unsigned)((ctx->ns + kMatchThreads - 1) / kMatchThreads);
+    if (ctx->gp.prec == RLB_F64) rlbk::match_kernel<false><<<nb, kMatchThreads, 0, st>>>(a);
+    else rlbk::match_kernel<true><<<nb, kMatchThreads, 0, st>>>(a);
   }
   RLB_CUDA(cudaGetLastError(), "match_kernel launch");
   return RLB_OK;
@@ -901,9 +907,9 @@ rlb_status step_static(rlb_ctx* ctx, char* state, char* scr, int nsteps, cudaStr
     ma.momf = reinterpret_cast<const float*>(mm);
     ma.lnM = lnM;
     ma.clock = adv;
-    const unsigned nb = (unsigned)((ctx->ns + 127) / 128);
-    if (ctx->gp.prec == RLB_F64) rlbk::match_kernel<false><<<nb, 128, 0, st>>>(ma);
-    else rlbk::match_kernel<true><<<nb, 128, 0, st>>>(ma);
+    const unsigned nb = (unsigned)((ctx->ns + kMatchThreads - 1) / kMatchThreads);
+    if (ctx->gp.prec == RLB_F64) rlbk::match_kernel<false><<<nb, kMatchThreads, 0, st>>>(ma);
+    else rlbk::match_kernel<true><<<nb, kMatchThreads, 0, st>>>(ma);
     RLB_CUDA(cudaGetLastError(), "match_kernel launch");
     return RLB_OK;
   };

@@ -44,6 +44,8 @@ struct EosView {
   // c = y0/h split into an integer c_hi and a remainder, so that the offset in
   // the cell keeps FP32 relative precision (u itself reaches n ~ 6.5e4)
   float ih_hi, ih_lo, c_hi, c_lo;
+  // the interior of the table in FP32: [y0 + 2h, y0 + (n - 4)h]
+  float ylo_f, yhi_f;
 };
 
 
@@ -282,7 +284,7 @@ __device__ __forceinline__ bool eos_cellf(const EosView& E, float y, int* i0, fl
 // kernels consume.
 __device__ bool eos_invert_f(const EosView& E, int field, float target, float y, float* y_out) {
   const float ih = E.ih_hi + E.ih_lo;
-  float lo = (float)(E.y0 + 2.0 / E.inv_h), hi = (float)(E.y0 + (E.n - 4) / E.inv_h);
+  float lo = E.ylo_f, hi = E.yhi_f;
   const float ymin = lo, ymax = hi;
   float yf = (y > ymin && y < ymax) ? y : 0.5f * (lo + hi);
   bool ok = false;
@@ -316,14 +318,19 @@ __device__ bool eos_invert_f(const EosView& E, int field, float target, float y,
 
 // One FP64 Newton step of e(y) = target on the FP64 table from an FP32 root
 // (slope from the FP32 table): the EOS inversion of the FP32 storage path.
+// The cell comes from the FP32 location (at a cell edge the two locations may
+// differ by one cell; the offset is then just outside [0, 1), where the same
+// interpolating polynomial still holds to the table's accuracy).
 __device__ __forceinline__ double eos_refine(const EosView& E, int field, double target, float y) {
-  double yd = (double)y;
+  const double yd = (double)y;
   int i0;
-  double t, w[6];
-  if (!eos_cell(E, yd, &i0, &t)) return yd;
+  float tf;
+  if (!eos_cellf(E, y, &i0, &tf)) return yd;
+  const double t = (yd - E.y0) * E.inv_h - (double)i0;
+  double w[6];
   lagrange6(t, w);
   float dw[6];
-  lagrange6f_d((float)t, dw);
+  lagrange6f_d(tf, dw);
   double F = 0.0;
   float dF = 0.f;
 #pragma unroll
@@ -353,14 +360,11 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // space of A - eps (largest cross product of two rows), normalised by the
 // Minkowski norm; eps is then the Rayleigh quotient u_mu u_nu T^{mu nu}.
 // ---------------------------------------------------------------------------
-// Mixed version for the FP32 storage path: Newton from the infinity-norm bound
-// in FP32 on the scaled matrix, then one FP64 Newton step on the FP64 cubic for
+// Mixed version for the FP32 storage path (tm: the same matrix in FP32): Newton
+// from the infinity-norm bound in FP32 on the scaled matrix, then one FP64 Newton step on the FP64 cubic for
 // the eigenvalue (eps = lambda); the eigenvector by the same cross products in
 // FP32 (it is consumed in FP32).
-__device__ bool landau3_mixed(const double tmd[6], float u[3], double* eps) {
-  float tm[6];
-#pragma unroll
-  for (int i = 0; i < 6; ++i) tm[i] = (float)tmd[i];
+__device__ bool landau3_mixed(const double tmd[6], const float tm[6], float u[3], double* eps) {
   const float sc = fmaxf(fabsf(tm[0]) + fabsf(tm[1]) + fabsf(tm[2]),
                          fmaxf(fabsf(tm[1]) + fabsf(tm[3]) + fabsf(tm[4]),
                                fabsf(tm[2]) + fabsf(tm[4]) + fabsf(tm[5])));
@@ -648,17 +652,25 @@ __device__ __forceinline__ int match_site_f(const MatchArgs& A, int site, float 
     e += e1 + e2;
     two_sum(s, e, m[i], mlo[i]);  // m + mlo = the compensated sum
   }
+  // M = exp(ln M) in FP32 (M is consumed in FP32; its rounding scales all of
+  // T^{mu nu} alike, which moves eps by the same relative amount and leaves u)
   const double lnMd = A.lnM[site];
-  const double Md = exp(lnMd);
-  const double prefd = Md * Md * Md * Md * (1.0 / (2.0 * 3.14159265358979323846 * 3.14159265358979323846));
-  const float M = (float)Md, pref = (float)prefd;
+  const float lh = (float)lnMd, ll = (float)(lnMd - (double)lh);
+  const float M = expf(lh) * (1.f + ll);
+  const float M2 = M * M;
+  const float pref = M2 * M2 * (float)(1.0 / (2.0 * 3.14159265358979323846 * 3.14159265358979323846));
+  const double prefd = (double)pref;
   double tmd[6];
+  float tmf[6];
 #pragma unroll
-  for (int i = 0; i < 6; ++i) tmd[i] = prefd * ((double)m[1 + i] + (double)mlo[1 + i]);
+  for (int i = 0; i < 6; ++i) {
+    tmd[i] = prefd * ((double)m[1 + i] + (double)mlo[1 + i]);
+    tmf[i] = pref * m[1 + i];
+  }
   int err = 0;
   float u[3];
   double epsd;
-  if (!landau3_mixed(tmd, u, &epsd)) {
+  if (!landau3_mixed(tmd, tmf, u, &epsd)) {
     err |= ERR_LANDAU;
     u[0] = 1.f; u[1] = 0.f; u[2] = 0.f;
     epsd = fmax(tmd[0], 1e-300);
@@ -669,7 +681,7 @@ __device__ __forceinline__ int match_site_f(const MatchArgs& A, int site, float 
   float y;
   if (!eos_invert_f(A.eos, EOS_E, eps, yg, &y)) {
     err |= ERR_EOS;
-    y = fminf(fmaxf(yg, (float)(A.eos.y0 + 2.0 / A.eos.inv_h)), (float)(A.eos.y0 + (A.eos.n - 4) / A.eos.inv_h));
+    y = fminf(fmaxf(yg, A.eos.ylo_f), A.eos.yhi_f);
   } else {
     y = (float)eos_refine(A.eos, EOS_E, epsd, y);
   }
