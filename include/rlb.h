@@ -223,14 +223,22 @@ rlb_status rlb_load_state(rlb_ctx* ctx, const void* host_buf, size_t bytes, void
  * recaptured after rlb_bind_buffers or rlb_autotune.
  *
  * rlb_autotune times every compiled variant of the stage kernel for the
- * configured lattice and precision (packed FP32 kernel with and without its
- * register cap, generic kernel; one variant for lattices only the generic
- * kernel takes) on three predictor launches over the current state, and keeps
- * the fastest for later steps.  The state (f, ln M, tau) is unchanged.  Outputs:
- * the chosen variant, optionally the milliseconds per launch of each variant
- * (variant_ms holds at least 3 doubles) and their number.  Synchronises
+ * configured lattice and precision (packed FP32 kernel with one site per CTA,
+ * with and without its register cap; generic kernel; packed kernel with two
+ * sites per CTA, with and without its cap; one variant for lattices only the
+ * generic kernel takes) on three predictor launches over the current state,
+ * and keeps the fastest for later steps.  The state (f, ln M, tau) is
+ * unchanged.  Outputs: the chosen variant, optionally the milliseconds per
+ * launch of each variant (variant_ms holds at least RLB_MAX_STAGE_VARIANTS
+ * doubles) and their number.  Synchronises
  * `stream`.  Implementation choices, not part of the paper's scheme. */
+#define RLB_MAX_STAGE_VARIANTS 8
 rlb_status rlb_autotune(rlb_ctx* ctx, void* stream, int* chosen, double* variant_ms, int* n_variants);
+/* rlb_set_stage_variant picks a stage-kernel variant by number (the order of
+ * rlb_autotune's list) for later steps; variant < 0 only reports their number
+ * in n_variants (optional).  RLB_ERR_ARG for a number outside the list; every
+ * variant computes the same result.  Needs rlb_configure (or rlb_init_grid). */
+rlb_status rlb_set_stage_variant(rlb_ctx* ctx, int variant, int* n_variants);
 rlb_status rlb_set_graphs(rlb_ctx* ctx, int enable);
 
 /* Adjoint of the time evolution (discrete adjoint of the predictor-corrector of

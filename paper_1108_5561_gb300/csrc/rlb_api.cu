@@ -238,6 +238,12 @@ dim3 site_grid(const rlb_ctx* c) {
   return dim3((unsigned)c->ns, 1, 1);
 }
 
+// The same for kernels with two sites per CTA (rlbk::locate_sites<2>).
+dim3 site_pair_grid(const rlb_ctx* c) {
+  if (c->events.size() == 1) return dim3((unsigned)c->events[0].ny, (unsigned)(c->events[0].nx + 1) / 2, 1);
+  return dim3((unsigned)((c->ns + 1) / 2), 1, 1);
+}
+
 rlbk::GridMap grid_map(const rlb_ctx* c, char* scr) {
   rlbk::GridMap g;
   g.ev = reinterpret_cast<const rlbk::EventInfo*>(scr + c->ev_off);
@@ -245,6 +251,7 @@ rlbk::GridMap grid_map(const rlb_ctx* c, char* scr) {
   g.n_events = (int)c->events.size();
   g.nx0 = c->events[0].nx;
   g.ny0 = c->events[0].ny;
+  g.n_sites = (int)c->ns;
   return g;
 }
 
@@ -340,17 +347,20 @@ struct Stager {
       std::is_same<R, float>::value && NXI % 2 == 0 && NTH % 2 == 0 && (NTH * NPH) % 32 == 0;
   static constexpr int NL = NTH * NPH;
   // variants the autotuner times: packed kernel with the register cap, packed
-  // without it, generic kernel (lattices the packed kernel does not take: generic only)
-  static constexpr int kVariants = kX2 ? 3 : 1;
+  // without it, generic kernel, packed with two sites per CTA (capped, uncapped)
+  // (lattices the packed kernel does not take: generic only)
+  static constexpr int kVariants = kX2 ? 5 : 1;
+  static_assert(kVariants <= RLB_MAX_STAGE_VARIANTS, "rlb_autotune output size");
   rlbk::StageArgs<S, R, NXI, NTH, NPH> a;
   rlbk::StageArgsX2<S, NXI, NTH, NPH> b;
-  dim3 grid;
+  dim3 grid, grid2;
   int variant = 0;
 
   // scr: the scratch block holding the event tables and the clock
   Stager(const rlb_ctx* ctx, char* scr, const double* sc, const float* scf, int* err) {
     variant = ctx->stage_variant < kVariants ? ctx->stage_variant : 0;
     grid = site_grid(ctx);
+    grid2 = site_pair_grid(ctx);
     const double dtau = ctx->gp.dtau, inv2dx = 1.0 / (2.0 * ctx->gp.dx);
     const rlbk::GridMap gm = grid_map(ctx, scr);
     const rlbk::Clock* clock = reinterpret_cast<const rlbk::Clock*>(scr + ctx->clock_off);
@@ -393,12 +403,15 @@ struct Stager {
   void launch(const S* f_in, const double* lnM_in, const S* f_base, const double* lnM_base, S* f_out,
               double* lnM_out, double* mom_out, int mode, cudaStream_t st) {
     if constexpr (kX2) {
-      if (variant < 2) {
+      if (variant != 2) {
+        constexpr int kMinb2 = NL <= 96 ? 6 : 2;  // two sites per CTA: resident blocks per SM
         b.f_in = f_in; b.lnM_in = lnM_in; b.f_base = f_base; b.lnM_base = lnM_base;
         b.f_out = f_out; b.lnM_out = lnM_out; b.momf_out = reinterpret_cast<float*>(mom_out);
         b.mode = mode;
         if (variant == 0) rlbk::stage_kernel_x2<S, NXI, NTH, NPH><<<grid, NL, 0, st>>>(b);
-        else rlbk::stage_kernel_x2<S, NXI, NTH, NPH, 1><<<grid, NL, 0, st>>>(b);
+        else if (variant == 1) rlbk::stage_kernel_x2<S, NXI, NTH, NPH, 1, 1><<<grid, NL, 0, st>>>(b);
+        else if (variant == 3) rlbk::stage_kernel_x2<S, NXI, NTH, NPH, 2, kMinb2><<<grid2, NL, 0, st>>>(b);
+        else rlbk::stage_kernel_x2<S, NXI, NTH, NPH, 2, 1><<<grid2, NL, 0, st>>>(b);
         return;
       }
     }
@@ -761,7 +774,7 @@ struct Adjoint {
   }
 };
 
-enum Op { OP_INIT, OP_STEP, OP_MOMENTS, OP_OBS, OP_TUNE, OP_ADJ_SEED, OP_ADJ_STEP, OP_ADJ_IC };
+enum Op { OP_INIT, OP_STEP, OP_MOMENTS, OP_OBS, OP_TUNE, OP_NVAR, OP_ADJ_SEED, OP_ADJ_STEP, OP_ADJ_IC };
 
 // arguments of the adjoint initial-condition call, passed through dispatch
 struct AdjIcCall {
@@ -785,8 +798,12 @@ rlb_status run_op(rlb_ctx* c, Op op, int n, double* p, cudaStream_t st) {
   if (op == OP_TUNE) {
     int nv = 0;
     rlb_status r = Rn::autotune(c, p, &nv, st);
-    if (!r && p) p[3] = nv;  // p: 4 doubles (3 variant times + count)
+    if (!r && p) p[RLB_MAX_STAGE_VARIANTS] = nv;  // p: the variant times, then their count
     return r;
+  }
+  if (op == OP_NVAR) {
+    p[0] = Stager<S, R, NXI, NTH, NPH>::kVariants;
+    return RLB_OK;
   }
   if (op == OP_OBS) return observables<S, R, NXI, NTH, NPH>(c, p, st);
   return RLB_ERR_ARG;
@@ -1334,11 +1351,11 @@ rlb_status rlb_autotune(rlb_ctx* ctx, void* stream, int* chosen, double* variant
   if (!ctx->inited) return fail(ctx, RLB_ERR_STATE, "rlb_init_grid or rlb_load_state must come first");
   rlb_status s = set_device(ctx);
   if (s) return s;
-  double t[4] = {0.0, 0.0, 0.0, 0.0};
+  double t[RLB_MAX_STAGE_VARIANTS + 1] = {};
   s = dispatch(ctx, OP_TUNE, 0, t, static_cast<cudaStream_t>(stream));
   if (s) return s;
   *chosen = ctx->stage_variant;
-  const int nv = (int)t[3];
+  const int nv = (int)t[RLB_MAX_STAGE_VARIANTS];
   if (n_variants) *n_variants = nv;
   if (variant_ms)
     for (int v = 0; v < nv; ++v) variant_ms[v] = t[v];
@@ -1394,6 +1411,23 @@ rlb_status rlb_adjoint_ic(rlb_ctx* ctx, const double* eps0, const double* basis,
   s = dispatch(ctx, OP_ADJ_IC, 0, reinterpret_cast<double*>(&a), static_cast<cudaStream_t>(stream));
   if (s) return s;
   return rlb_check(ctx, stream);
+}
+
+rlb_status rlb_set_stage_variant(rlb_ctx* ctx, int variant, int* n_variants) {
+  if (!ctx) return RLB_ERR_ARG;
+  if (!ctx->grid_ok) return fail(ctx, RLB_ERR_STATE, "rlb_configure must come first");
+  double nv = 0.0;
+  rlb_status s = dispatch(ctx, OP_NVAR, 0, &nv, nullptr);
+  if (s) return s;
+  if (n_variants) *n_variants = (int)nv;
+  if (variant < 0) return RLB_OK;  // query only
+  if (variant >= (int)nv) return fail(ctx, RLB_ERR_ARG, "no such stage-kernel variant");
+  ctx->stage_variant = variant;
+  if (ctx->gexec) {  // the captured step used the previous choice
+    cudaGraphExecDestroy(ctx->gexec);
+    ctx->gexec = nullptr;
+  }
+  return RLB_OK;
 }
 
 rlb_status rlb_set_graphs(rlb_ctx* ctx, int enable) {

@@ -494,6 +494,7 @@ struct GridMap {
   const int2* loc;       // per site (event, y << 16 | x) when n_events > 1 (device)
   int n_events;
   int nx0, ny0;          // the grid when n_events == 1 (no table reads)
+  int n_sites;           // all events
 };
 
 // Launch grid of the per-site kernels: (ny, nx) CTAs for one grid (CTA (y, x)),

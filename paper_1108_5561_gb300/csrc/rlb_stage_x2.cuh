@@ -132,14 +132,45 @@ __device__ __forceinline__ void store_pairs(S* __restrict__ p, float2 (&v)[NP]) 
   }
 }
 
-// MINB resident blocks per SM bound the registers (12 blocks of 96 threads: 56
-// registers; measured at 160^2: 75 us against 79 us uncapped (72 registers)
-// and 89-93 us at 40 registers, which spill; the autotuner also times the
-// uncapped kernel)
-template <class S, int NXI, int NTH, int NPH, int MINB = (NTH * NPH <= 96 ? 12 : 3)>
+// Sites of one CTA.  SPT = 1: the site of locate_site.  SPT = 2: sites (2c, y)
+// and (2c + 1, y) of a grid row (launch grid (ny, ceil(nx / 2)), CTA (y, c)), or
+// sites 2b and 2b + 1 of a batch (launch grid ceil(ns / 2)); a missing second
+// site (odd row length or site count) repeats the first and stores nothing.
+template <int SPT>
+__device__ __forceinline__ void locate_sites(const GridMap& G, int bx, int by, SiteLoc (&L)[SPT],
+                                             bool* has2) {
+  if constexpr (SPT == 1) {
+    locate_site(G, bx, by, &L[0]);
+    *has2 = false;
+  } else {
+    static_assert(SPT == 2, "one or two sites per CTA");
+    if (G.n_events == 1) {
+      const int x0 = 2 * by;
+      *has2 = x0 + 1 < G.nx0;
+      locate_site(G, bx, x0, &L[0]);
+      locate_site(G, bx, *has2 ? x0 + 1 : x0, &L[1]);
+    } else {
+      const int s0 = 2 * bx;
+      *has2 = s0 + 1 < G.n_sites;
+      locate_site(G, s0, 0, &L[0]);
+      locate_site(G, *has2 ? s0 + 1 : s0, 0, &L[1]);
+    }
+  }
+}
+
+// SPT sites per CTA: with two, every per-node constant a thread loads (radial
+// and polar operator entries, radial tables) and every per-line scalar serves
+// both sites, and the warp reductions carry both sites' sums.  The arithmetic
+// of each site is the same as with one.
+// MINB resident blocks per SM bound the registers (one site, 12 blocks of 96
+// threads: 56 registers; measured at 160^2: 75 us against 79 us uncapped (72
+// registers) and 89-93 us at 40 registers, which spill; the autotuner also
+// times the uncapped kernel)
+template <class S, int NXI, int NTH, int NPH, int SPT = 1, int MINB = (NTH * NPH <= 96 ? 12 : 3)>
 __global__ void __launch_bounds__(NTH* NPH, MINB)
     stage_kernel_x2(const __grid_constant__ StageArgsX2<S, NXI, NTH, NPH> A) {
   static_assert(NXI % 2 == 0 && NTH % 2 == 0, "paired radial nodes, half polar lines");
+  static_assert(SPT == 1 || SPT == 2, "one or two sites per CTA");
   constexpr int NL = NTH * NPH;
   constexpr int NN = NL * NXI;
   constexpr int NP = NXI / 2;
@@ -153,72 +184,86 @@ __global__ void __launch_bounds__(NTH* NPH, MINB)
   constexpr int LDL = NTH + 1;
   constexpr int LDK = NPH * LDL + (((12 - NPH * LDL) % 16) + 16) % 16;
   const auto& op = A.op;
-  SiteLoc L;
-  locate_site(A.grid, blockIdx.x, blockIdx.y, &L);
-  const int x = L.x, y = L.y, site = L.site, nx = L.nx, ny = L.ny;
+  SiteLoc L[SPT];
+  bool has2;
+  locate_sites<SPT>(A.grid, blockIdx.x, blockIdx.y, L, &has2);
   const int t = threadIdx.x;
   const int j = t % NTH, l = t / NTH;
 
-  __shared__ float2 fs[NP * LDK];
-  __shared__ float2 pth[NP * LDK];
-  __shared__ float4 tab[NP];  // (E_eq at 2p, 2p+1;  q1/E_eq at 2p, 2p+1)
-  __shared__ float4 red[NW];  // per-warp partial sums for d ln M / d tau
+  __shared__ float2 fs[SPT][NP * LDK];
+  __shared__ float2 pth[SPT][NP * LDK];
+  __shared__ float4 tab[SPT][NP];  // (E_eq at 2p, 2p+1;  q1/E_eq at 2p, 2p+1)
+  __shared__ float4 red[SPT][NW];  // per-warp partial sums for d ln M / d tau
 
-  // 1. own line and the upwind neighbours (periodic)
-  float2 f[NP];
-  load_pairs<S, NP>(A.f_in + (size_t)site * NN + t * NXI, f);
+  // 1. own line and the upwind neighbours (periodic), and the streaming term
+  //    right away: the neighbour lines die here instead of staying live across
+  //    the barriers below (fewer registers, more resident blocks)
   const float cp = op.cph[l], sp = op.sph[l];
   const int sx = (cp > 0.f) ? -1 : 1, sy = (sp > 0.f) ? -1 : 1;
-  int x1 = x + sx, x2 = x + 2 * sx, y1 = y + sy, y2 = y + 2 * sy;
-  x1 += (x1 < 0) ? nx : (x1 >= nx ? -nx : 0);
-  x2 += (x2 < 0) ? nx : (x2 >= nx ? -nx : 0);
-  x2 += (x2 < 0) ? nx : (x2 >= nx ? -nx : 0);  // grids of one site
-  y1 += (y1 < 0) ? ny : (y1 >= ny ? -ny : 0);
-  y2 += (y2 < 0) ? ny : (y2 >= ny ? -ny : 0);
-  y2 += (y2 < 0) ? ny : (y2 >= ny ? -ny : 0);
-  float2 fx1[NP], fx2[NP], fy1[NP], fy2[NP];
-  const S* fev = A.f_in + (size_t)L.base * NN + t * NXI;
-  load_pairs<S, NP>(fev + (size_t)(y * nx + x1) * NN, fx1);
-  load_pairs<S, NP>(fev + (size_t)(y * nx + x2) * NN, fx2);
-  load_pairs<S, NP>(fev + (size_t)(y1 * nx + x) * NN, fy1);
-  load_pairs<S, NP>(fev + (size_t)(y2 * nx + x) * NN, fy2);
-  // streaming term right away: the neighbour lines die here instead of staying
-  // live across the barriers below (fewer registers, more resident blocks)
-  float2 strm[NP];
+  float2 f[SPT][NP], strm[SPT][NP];
   {
     const float st0 = op.sth[j];
     const float2 nsx0 = bc2(-st0 * fabsf(cp) * A.inv2dx_r), nsy0 = bc2(-st0 * fabsf(sp) * A.inv2dx_r);
     const float2 three0 = bc2(3.f), mfour0 = bc2(-4.f);
 #pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      const float2 Sx = fma2(mfour0, fx1[p], fma2(three0, f[p], fx2[p]));
-      const float2 Sy = fma2(mfour0, fy1[p], fma2(three0, f[p], fy2[p]));
-      strm[p] = mul2(op.tv[p], fma2(nsy0, Sy, mul2(nsx0, Sx)));
+    for (int s = 0; s < SPT; ++s) {
+      const int x = L[s].x, y = L[s].y, nx = L[s].nx, ny = L[s].ny;
+      load_pairs<S, NP>(A.f_in + (size_t)L[s].site * NN + t * NXI, f[s]);
+      int x1 = x + sx, x2 = x + 2 * sx, y1 = y + sy, y2 = y + 2 * sy;
+      x1 += (x1 < 0) ? nx : (x1 >= nx ? -nx : 0);
+      x2 += (x2 < 0) ? nx : (x2 >= nx ? -nx : 0);
+      x2 += (x2 < 0) ? nx : (x2 >= nx ? -nx : 0);  // grids of one site
+      y1 += (y1 < 0) ? ny : (y1 >= ny ? -ny : 0);
+      y2 += (y2 < 0) ? ny : (y2 >= ny ? -ny : 0);
+      y2 += (y2 < 0) ? ny : (y2 >= ny ? -ny : 0);
+      float2 fx1[NP], fx2[NP], fy1[NP], fy2[NP];
+      const S* fev = A.f_in + (size_t)L[s].base * NN + t * NXI;
+      load_pairs<S, NP>(fev + (size_t)(y * nx + x1) * NN, fx1);
+      load_pairs<S, NP>(fev + (size_t)(y * nx + x2) * NN, fx2);
+      load_pairs<S, NP>(fev + (size_t)(y1 * nx + x) * NN, fy1);
+      load_pairs<S, NP>(fev + (size_t)(y2 * nx + x) * NN, fy2);
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        const float2 Sx = fma2(mfour0, fx1[p], fma2(three0, f[s][p], fx2[p]));
+        const float2 Sy = fma2(mfour0, fy1[p], fma2(three0, f[s][p], fy2[p]));
+        strm[s][p] = mul2(op.tv[p], fma2(nsy0, Sy, mul2(nsx0, Sx)));
+      }
     }
   }
 
   // site scalars of the matching of f_in
-  const float* q = A.scf + (size_t)site * kSc;
-  const float ut = __ldg(q + SC_UT), ux = __ldg(q + SC_UX), uy = __ldg(q + SC_UY);
-  const float invT = __ldg(q + SC_INVT), Meq = __ldg(q + SC_MEQ), M = __ldg(q + SC_M);
-  const float itr = __ldg(q + SC_ITR), ax = __ldg(q + SC_AX), ay = __ldg(q + SC_AY);
-  const float M2 = M * M;
-  if (t < NP) {  // per-site radial table
-    const float e0 = sqrtf(Meq * Meq + M2 * op.s2[2 * t]), e1 = sqrtf(Meq * Meq + M2 * op.s2[2 * t + 1]);
-    tab[t] = make_float4(e0, e1, op.q1[2 * t] / e0, op.q1[2 * t + 1] / e1);
+  float ut[SPT], ux[SPT], uy[SPT], invT[SPT], M[SPT], itr[SPT], ax[SPT], ay[SPT];
+#pragma unroll
+  for (int s = 0; s < SPT; ++s) {
+    const float* q = A.scf + (size_t)L[s].site * kSc;
+    ut[s] = __ldg(q + SC_UT); ux[s] = __ldg(q + SC_UX); uy[s] = __ldg(q + SC_UY);
+    invT[s] = __ldg(q + SC_INVT); M[s] = __ldg(q + SC_M);
+    itr[s] = __ldg(q + SC_ITR); ax[s] = __ldg(q + SC_AX); ay[s] = __ldg(q + SC_AY);
+    if (t < NP) {  // per-site radial table
+      const float Meq = __ldg(q + SC_MEQ), M2 = M[s] * M[s];
+      const float e0 = sqrtf(Meq * Meq + M2 * op.s2[2 * t]), e1 = sqrtf(Meq * Meq + M2 * op.s2[2 * t + 1]);
+      tab[s][t] = make_float4(e0, e1, op.q1[2 * t] / e0, op.q1[2 * t + 1] / e1);
+    }
   }
 
-  // 2. stage the site for the polar operator; radial operator on the own line
+  // 2. stage the sites for the polar operator; radial operator on the own lines
 #pragma unroll
-  for (int p = 0; p < NP; ++p) fs[p * LDK + l * LDL + j] = f[p];
-  float2 Drf[NP];
+  for (int s = 0; s < SPT; ++s)
 #pragma unroll
-  for (int p = 0; p < NP; ++p) Drf[p] = make_float2(0.f, 0.f);
+    for (int p = 0; p < NP; ++p) fs[s][p * LDK + l * LDL + j] = f[s][p];
+  float2 Drf[SPT][NP];
+#pragma unroll
+  for (int s = 0; s < SPT; ++s)
+#pragma unroll
+    for (int p = 0; p < NP; ++p) Drf[s][p] = make_float2(0.f, 0.f);
 #pragma unroll
   for (int k = 0; k < NXI; ++k) {
-    const float2 fk = bc2((k & 1) ? f[k >> 1].y : f[k >> 1].x);
 #pragma unroll
-    for (int p = 0; p < NP; ++p) Drf[p] = fma2(op.Drb[k * NP + p], fk, Drf[p]);
+    for (int p = 0; p < NP; ++p) {
+      const float2 d = op.Drb[k * NP + p];
+#pragma unroll
+      for (int s = 0; s < SPT; ++s) Drf[s][p] = fma2(d, bc2((k & 1) ? f[s][k >> 1].y : f[s][k >> 1].x), Drf[s][p]);
+    }
   }
   __syncthreads();
   const float milne = A.milne_on ? A.clock->inv_tau_f : 0.f;
@@ -227,116 +272,174 @@ __global__ void __launch_bounds__(NTH* NPH, MINB)
     for (int it = t; it < NXI * NPH; it += NL) {
       const int lq = it % NPH, r = it / NPH, kp = r % NP, half = r / NP;
       const int base = kp * LDK + lq * LDL;
-      float2 g[NTH];
+      float2 g[SPT][NTH];
 #pragma unroll
-      for (int jj = 0; jj < NTH; ++jj) g[jj] = fs[base + jj];
+      for (int s = 0; s < SPT; ++s)
+#pragma unroll
+        for (int jj = 0; jj < NTH; ++jj) g[s][jj] = fs[s][base + jj];
 #pragma unroll
       for (int hh = 0; hh < 2; ++hh) {
         if (half != hh) continue;
 #pragma unroll
         for (int qq = 0; qq < H; ++qq) {
           const int jp = hh * H + qq;
-          float2 acc = mul2(op.Dthb[jp * NTH], g[0]);
+          float2 acc[SPT];
 #pragma unroll
-          for (int jj = 1; jj < NTH; ++jj) acc = fma2(op.Dthb[jp * NTH + jj], g[jj], acc);
-          pth[base + jp] = acc;
+          for (int s = 0; s < SPT; ++s) acc[s] = mul2(op.Dthb[jp * NTH], g[s][0]);
+#pragma unroll
+          for (int jj = 1; jj < NTH; ++jj) {
+            const float2 d = op.Dthb[jp * NTH + jj];
+#pragma unroll
+            for (int s = 0; s < SPT; ++s) acc[s] = fma2(d, g[s][jj], acc[s]);
+          }
+#pragma unroll
+          for (int s = 0; s < SPT; ++s) pth[s][base + jp] = acc[s];
         }
       }
     }
   }
   __syncthreads();
 
-  // 3. right-hand side on the own line (same algebra as stage_kernel):
+  // 3. right-hand side on the own lines (same algebra as stage_kernel):
   //    f_eq = Z 2^(c1 E_eq + c2 sinh),  force = f_eq [Gp q1/E_eq + Hp q2 + Jp/cosh],
   //    collision = -(f - f_eq) cc,  cc = (u^tau - tanh vu)/tau_R
   const float st = op.sth[j];
-  const float vu = st * (cp * ux + sp * uy);
-  const float A1 = st * (ax * cp + ay * sp);
-  const float au = ax * ux + ay * uy;
   const float2 mmu2 = bc2(milne * op.mu2[j]), milne2 = bc2(milne);
   constexpr float kLog2e = 1.4426950408889634f;
-  const float2 c1 = bc2(-kLog2e * invT * ut), c2 = bc2(kLog2e * invT * M * vu), lZ = bc2(A.log2Z);
-  const float2 Gp = bc2(-invT * A1 * ut * M2), Hp = bc2(invT * A1 * M * vu), Jp = bc2(invT * M * au);
-  const float2 cc0 = bc2(ut * itr), cc1 = bc2(-vu * itr);
-  const float2 ncc0 = bc2(-ut * itr), ncc1 = bc2(vu * itr);
-  const float2 utb = bc2(ut), nvub = bc2(-vu);
-  float2 Rn[NP];
-  float2 sA = make_float2(0.f, 0.f), sQ = sA, sE = sA;
+  const float2 lZ = bc2(A.log2Z);
+  float2 c1[SPT], c2[SPT], Gp[SPT], Hp[SPT], Jp[SPT], cc0[SPT], cc1[SPT], ncc0[SPT], ncc1[SPT], utb[SPT], nvub[SPT];
+#pragma unroll
+  for (int s = 0; s < SPT; ++s) {
+    const float vu = st * (cp * ux[s] + sp * uy[s]);
+    const float A1 = st * (ax[s] * cp + ay[s] * sp);
+    const float au = ax[s] * ux[s] + ay[s] * uy[s];
+    const float M2 = M[s] * M[s];
+    c1[s] = bc2(-kLog2e * invT[s] * ut[s]); c2[s] = bc2(kLog2e * invT[s] * M[s] * vu);
+    Gp[s] = bc2(-invT[s] * A1 * ut[s] * M2); Hp[s] = bc2(invT[s] * A1 * M[s] * vu); Jp[s] = bc2(invT[s] * M[s] * au);
+    cc0[s] = bc2(ut[s] * itr[s]); cc1[s] = bc2(-vu * itr[s]);
+    ncc0[s] = bc2(-ut[s] * itr[s]); ncc1[s] = bc2(vu * itr[s]);
+    utb[s] = bc2(ut[s]); nvub[s] = bc2(-vu);
+  }
+  float2 Rn[SPT][NP];
+  float2 sA[SPT], sQ[SPT], sE[SPT];
+#pragma unroll
+  for (int s = 0; s < SPT; ++s) sA[s] = sQ[s] = sE[s] = make_float2(0.f, 0.f);
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
-    const float4 tb = tab[p];
-    const float2 E = make_float2(tb.x, tb.y), QE = make_float2(tb.z, tb.w);
-    float2 r = fma2(mmu2, Drf[p], strm[p]);
-    if (pol) r = fma2(milne2, pth[p * LDK + l * LDL + j], r);
-    const float2 ex = fma2(c1, E, fma2(c2, op.s[p], lZ));
-    const float2 feq = make_float2(ex2_ftz(ex.x), ex2_ftz(ex.y));
-    const float2 cc = fma2(cc1, op.tv[p], cc0), ncc = fma2(ncc1, op.tv[p], ncc0);
-    const float2 fcc = fma2(Gp, QE, fma2(Hp, op.q2[p], fma2(Jp, op.ic[p], cc)));
-    r = fma2(f[p], ncc, fma2(feq, fcc, r));
-    Rn[p] = r;
-    const float2 pu = fma2(op.Sw[p], nvub, mul2(op.Cw[p], utb));
-    const float2 w = mul2(pu, pu);
-    sA = fma2(w, r, sA);
-    sQ = fma2(w, Drf[p], sQ);
-    sE = fma2(w, f[p], sE);
+#pragma unroll
+    for (int s = 0; s < SPT; ++s) {
+      const float4 tb = tab[s][p];
+      const float2 E = make_float2(tb.x, tb.y), QE = make_float2(tb.z, tb.w);
+      float2 r = fma2(mmu2, Drf[s][p], strm[s][p]);
+      if (pol) r = fma2(milne2, pth[s][p * LDK + l * LDL + j], r);
+      const float2 ex = fma2(c1[s], E, fma2(c2[s], op.s[p], lZ));
+      const float2 feq = make_float2(ex2_ftz(ex.x), ex2_ftz(ex.y));
+      const float2 cc = fma2(cc1[s], op.tv[p], cc0[s]), ncc = fma2(ncc1[s], op.tv[p], ncc0[s]);
+      const float2 fcc = fma2(Gp[s], QE, fma2(Hp[s], op.q2[p], fma2(Jp[s], op.ic[p], cc)));
+      r = fma2(f[s][p], ncc, fma2(feq, fcc, r));
+      Rn[s][p] = r;
+      const float2 pu = fma2(op.Sw[p], nvub[s], mul2(op.Cw[p], utb[s]));
+      const float2 w = mul2(pu, pu);
+      sA[s] = fma2(w, r, sA[s]);
+      sQ[s] = fma2(w, Drf[s][p], sQ[s]);
+      sE[s] = fma2(w, f[s][p], sE[s]);
+    }
   }
   const float wj = op.wj[j];
-  // warp partial sums, then every thread combines the NW partials itself
+  // warp partial sums, then every thread combines the NW partials itself;
+  // after the halving reduction of 4 SPT values the site-s sums sit on lanes
+  // s 4d, s 4d + d and s 4d + 2d (d = 8 / SPT lanes per value)
   const int lane = t & 31, wid = t >> 5;
   {
-    float v4[4] = {wj * (sA.x + sA.y), wj * (sQ.x + sQ.y), wj * (sE.x + sE.y), 0.f};
-    warp_reduce_halving<4>(v4, lane);  // lane 8 qq holds value qq
-    const float s1 = __shfl_sync(0xffffffffu, v4[0], 8), s2 = __shfl_sync(0xffffffffu, v4[0], 16);
-    if (lane == 0) red[wid] = make_float4(v4[0], s1, s2, 0.f);
+    constexpr int K = 4 * SPT, dl = 32 / K;
+    float v[K];
+#pragma unroll
+    for (int s = 0; s < SPT; ++s) {
+      v[4 * s] = wj * (sA[s].x + sA[s].y);
+      v[4 * s + 1] = wj * (sQ[s].x + sQ[s].y);
+      v[4 * s + 2] = wj * (sE[s].x + sE[s].y);
+      v[4 * s + 3] = 0.f;
+    }
+    warp_reduce_halving<K>(v, lane);
+    const float s1 = __shfl_down_sync(0xffffffffu, v[0], dl), s2 = __shfl_down_sync(0xffffffffu, v[0], 2 * dl);
+    if (lane % (4 * dl) == 0) red[lane / (4 * dl)][wid] = make_float4(v[0], s1, s2, 0.f);
   }
   __syncthreads();
-  float Af = 0.f, Qf = 0.f, Ef = 0.f;
+  float2 gb[SPT];
 #pragma unroll
-  for (int w = 0; w < NW; ++w) {
-    const float4 rw = red[w];
-    Af += rw.x; Qf += rw.y; Ef += rw.z;
+  for (int s = 0; s < SPT; ++s) {
+    float Af = 0.f, Qf = 0.f, Ef = 0.f;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      const float4 rw = red[s][w];
+      Af += rw.x; Qf += rw.y; Ef += rw.z;
+    }
+    // d ln M / d tau from the consistency condition
+    const float* q = A.scf + (size_t)L[s].site * kSc;
+    const float D = __ldg(q + SC_D), Kh = __ldg(q + SC_KH);
+    const float g = (D == 0.f) ? 0.f : -D * Af / (Kh + D * (4.f * Ef + Qf - Kh));
+    if (t == 0 && (s == 0 || has2)) {
+      const int site = L[s].site;
+      if (!isfinite(g)) atomicOr(A.err, (int)ERR_NONFINITE);
+      const double lnM = __ldg(A.lnM_in + site), gd = (double)g;
+      A.lnM_out[site] = A.mode == 0 ? lnM + A.dtau * gd : 0.5 * (__ldg(A.lnM_base + site) + lnM + A.dtau * gd);
+    }
+    gb[s] = bc2(g);
   }
-  // d ln M / d tau from the consistency condition
-  const float D = __ldg(q + SC_D), Kh = __ldg(q + SC_KH);
-  const float g = (D == 0.f) ? 0.f : -D * Af / (Kh + D * (4.f * Ef + Qf - Kh));
-  if (t == 0) {
-    if (!isfinite(g)) atomicOr(A.err, (int)ERR_NONFINITE);
-    const double lnM = __ldg(A.lnM_in + site), gd = (double)g;
-    A.lnM_out[site] = A.mode == 0 ? lnM + A.dtau * gd : 0.5 * (__ldg(A.lnM_base + site) + lnM + A.dtau * gd);
-  }
-  const float2 gb = bc2(g), dt = bc2(A.dtau_r);
-  float2 out[NP];
+  const float2 dt = bc2(A.dtau_r);
+  float2 out[SPT][NP];
   if (A.mode == 0) {
 #pragma unroll
-    for (int p = 0; p < NP; ++p) out[p] = fma2(dt, fma2(gb, Drf[p], Rn[p]), f[p]);
+    for (int s = 0; s < SPT; ++s)
+#pragma unroll
+      for (int p = 0; p < NP; ++p) out[s][p] = fma2(dt, fma2(gb[s], Drf[s][p], Rn[s][p]), f[s][p]);
   } else {
-    float2 fb[NP];
-    load_pairs<S, NP>(A.f_base + (size_t)site * NN + t * NXI, fb);
     const float2 half = bc2(0.5f), hdt = bc2(0.5f * A.dtau_r);
 #pragma unroll
-    for (int p = 0; p < NP; ++p) out[p] = fma2(hdt, fma2(gb, Drf[p], Rn[p]), mul2(half, add2(fb[p], f[p])));
+    for (int s = 0; s < SPT; ++s) {
+      float2 fb[NP];
+      load_pairs<S, NP>(A.f_base + (size_t)L[s].site * NN + t * NXI, fb);
+#pragma unroll
+      for (int p = 0; p < NP; ++p)
+        out[s][p] = fma2(hdt, fma2(gb[s], Drf[s][p], Rn[s][p]), mul2(half, add2(fb[p], f[s][p])));
+    }
   }
-  store_pairs<S, NP>(A.f_out + (size_t)site * NN + t * NXI, out);  // out now holds the stored values
+#pragma unroll
+  for (int s = 0; s < SPT; ++s)  // out now holds the stored values
+    if (s == 0 || has2) store_pairs<S, NP>(A.f_out + (size_t)L[s].site * NN + t * NXI, out[s]);
 
   // 4. moments of what was stored
-  float2 r0 = make_float2(0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
-#pragma unroll
-  for (int p = 0; p < NP; ++p) {
-    r0 = fma2(op.w0[p], out[p], r0);
-    r1 = fma2(op.w1[p], out[p], r1);
-    r2 = fma2(op.w2[p], out[p], r2);
-    r3 = fma2(op.w3[p], out[p], r3);
-  }
   const float mu = op.mu[j];
-  const float a1 = wj * (r1.x + r1.y) * st, a3 = wj * (r3.x + r3.y) * st * st;
-  float mom[kMom] = {wj * (r0.x + r0.y), wj * (r2.x + r2.y), a1 * cp, a1 * sp,
-                     a3 * cp * cp, a3 * cp * sp, a3 * sp * sp, wj * (r3.x + r3.y) * mu * mu};
-  warp_reduce_halving<kMom>(mom, lane);  // lanes 4 qq .. 4 qq + 3 hold moment qq
-  // slot wid of moment qq; warp 0 also clears the slots no warp owns
-  float* dst = A.momf_out + (size_t)site * kMom * kMomParts + (lane >> 2) * kMomParts;
-  const int r = lane & 3;
-  if (r == 0) dst[wid] = mom[0];
-  else if (wid == 0 && r >= NW) dst[r] = 0.f;
+  constexpr int KM = kMom * SPT, dm = 32 / KM;
+  float mom[KM];
+#pragma unroll
+  for (int s = 0; s < SPT; ++s) {
+    float2 r0 = make_float2(0.f, 0.f), r1 = r0, r2 = r0, r3 = r0;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      r0 = fma2(op.w0[p], out[s][p], r0);
+      r1 = fma2(op.w1[p], out[s][p], r1);
+      r2 = fma2(op.w2[p], out[s][p], r2);
+      r3 = fma2(op.w3[p], out[s][p], r3);
+    }
+    const float a1 = wj * (r1.x + r1.y) * st, a3 = wj * (r3.x + r3.y) * st * st;
+    float* m = mom + kMom * s;
+    m[0] = wj * (r0.x + r0.y); m[1] = wj * (r2.x + r2.y); m[2] = a1 * cp; m[3] = a1 * sp;
+    m[4] = a3 * cp * cp; m[5] = a3 * cp * sp; m[6] = a3 * sp * sp; m[7] = wj * (r3.x + r3.y) * mu * mu;
+  }
+  warp_reduce_halving<KM>(mom, lane);  // lanes dm qq .. dm qq + dm - 1 hold value qq
+  // slot wid of moment qq % kMom of site qq / kMom; warp 0 also clears the
+  // slots no warp owns
+  const int qq = lane / dm, sq = qq / kMom, r = lane % dm;
+  if (sq == 0 || has2) {
+    const int site = (SPT == 1 || sq == 0) ? L[0].site : L[SPT - 1].site;
+    float* dst = A.momf_out + ((size_t)site * kMom + (qq % kMom)) * kMomParts;
+    if (r == 0) dst[wid] = mom[0];
+    else if (wid == 0 && r == 1) {
+#pragma unroll
+      for (int w = NW; w < kMomParts; ++w) dst[w] = 0.f;
+    }
+  }
 }
 
 }  // namespace rlbk

@@ -233,11 +233,19 @@ class Run:
         """Time the stage-kernel variants on the current state and keep the fastest.
         Returns (chosen variant, [ms per launch of each variant])."""
         c, n = ctypes.c_int(), ctypes.c_int()
-        ms = np.zeros(4)
+        ms = np.zeros(8)  # RLB_MAX_STAGE_VARIANTS
         self._chk(self.lib.rlb_autotune(self._h, self._stream(), ctypes.byref(c),
                                         ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                         ctypes.byref(n)), "rlb_autotune")
         return c.value, [float(x) for x in ms[:n.value]]
+
+    def set_stage_variant(self, variant: int) -> int:
+        """Use stage-kernel variant `variant` (rlb_autotune's numbering) from now
+        on; variant < 0 only asks.  Returns the number of variants."""
+        n = ctypes.c_int()
+        self._chk(self.lib.rlb_set_stage_variant(self._h, int(variant), ctypes.byref(n)),
+                  "rlb_set_stage_variant")
+        return n.value
 
     def set_graphs(self, enable: bool = True):
         self._chk(self.lib.rlb_set_graphs(self._h, int(enable)), "rlb_set_graphs")
