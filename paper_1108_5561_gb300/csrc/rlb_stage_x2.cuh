@@ -162,11 +162,13 @@ __device__ __forceinline__ void locate_sites(const GridMap& G, int bx, int by, S
 // and polar operator entries, radial tables) and every per-line scalar serves
 // both sites, and the warp reductions carry both sites' sums.  The arithmetic
 // of each site is the same as with one.
-// MINB resident blocks per SM bound the registers (one site, 12 blocks of 96
-// threads: 56 registers; measured at 160^2: 75 us against 79 us uncapped (72
-// registers) and 89-93 us at 40 registers, which spill; the autotuner also
-// times the uncapped kernel)
-template <class S, int NXI, int NTH, int NPH, int SPT = 1, int MINB = (NTH * NPH <= 96 ? 12 : 3)>
+// MINB resident blocks per SM bound the registers.  768 nodes (96 threads):
+// 12 blocks, 56 registers; measured at 160^2: 75 us against 79 us uncapped (72
+// registers) and 89-93 us at 40 registers, which spill.  2048 nodes (128
+// threads): 5 blocks, 96 registers; at 512^2 a BF16 stage takes 1.65 ms
+// against 1.80 ms with 4 blocks (114 registers) and 1.73 ms with 6 (80,
+// spilling).  The autotuner also times the uncapped kernel.
+template <class S, int NXI, int NTH, int NPH, int SPT = 1, int MINB = (NTH * NPH <= 96 ? 12 : 5)>
 __global__ void __launch_bounds__(NTH* NPH, MINB)
     stage_kernel_x2(const __grid_constant__ StageArgsX2<S, NXI, NTH, NPH> A) {
   static_assert(NXI % 2 == 0 && NTH % 2 == 0, "paired radial nodes, half polar lines");
@@ -189,6 +191,8 @@ __global__ void __launch_bounds__(NTH* NPH, MINB)
   locate_sites<SPT>(A.grid, blockIdx.x, blockIdx.y, L, &has2);
   const int t = threadIdx.x;
   const int j = t % NTH, l = t / NTH;
+  // 1/tau of f_in, issued first: its latency hides behind the population loads
+  const float milne = A.milne_on ? A.clock->inv_tau_f : 0.f;
 
   __shared__ float2 fs[SPT][NP * LDK];
   __shared__ float2 pth[SPT][NP * LDK];
@@ -232,13 +236,14 @@ __global__ void __launch_bounds__(NTH* NPH, MINB)
   }
 
   // site scalars of the matching of f_in
-  float ut[SPT], ux[SPT], uy[SPT], invT[SPT], M[SPT], itr[SPT], ax[SPT], ay[SPT];
+  float ut[SPT], ux[SPT], uy[SPT], invT[SPT], M[SPT], itr[SPT], ax[SPT], ay[SPT], Dm[SPT], Kh[SPT];
 #pragma unroll
   for (int s = 0; s < SPT; ++s) {
     const float* q = A.scf + (size_t)L[s].site * kSc;
     ut[s] = __ldg(q + SC_UT); ux[s] = __ldg(q + SC_UX); uy[s] = __ldg(q + SC_UY);
     invT[s] = __ldg(q + SC_INVT); M[s] = __ldg(q + SC_M);
     itr[s] = __ldg(q + SC_ITR); ax[s] = __ldg(q + SC_AX); ay[s] = __ldg(q + SC_AY);
+    Dm[s] = __ldg(q + SC_D); Kh[s] = __ldg(q + SC_KH);
     if (t < NP) {  // per-site radial table
       const float Meq = __ldg(q + SC_MEQ), M2 = M[s] * M[s];
       const float e0 = sqrtf(Meq * Meq + M2 * op.s2[2 * t]), e1 = sqrtf(Meq * Meq + M2 * op.s2[2 * t + 1]);
@@ -266,7 +271,6 @@ __global__ void __launch_bounds__(NTH* NPH, MINB)
     }
   }
   __syncthreads();
-  const float milne = A.milne_on ? A.clock->inv_tau_f : 0.f;
   const bool pol = milne != 0.f;
   if (pol) {  // polar lines (pair, l), one half of the outputs per item
     for (int it = t; it < NXI * NPH; it += NL) {
@@ -375,9 +379,8 @@ __global__ void __launch_bounds__(NTH* NPH, MINB)
       Af += rw.x; Qf += rw.y; Ef += rw.z;
     }
     // d ln M / d tau from the consistency condition
-    const float* q = A.scf + (size_t)L[s].site * kSc;
-    const float D = __ldg(q + SC_D), Kh = __ldg(q + SC_KH);
-    const float g = (D == 0.f) ? 0.f : -D * Af / (Kh + D * (4.f * Ef + Qf - Kh));
+    const float D = Dm[s];
+    const float g = (D == 0.f) ? 0.f : -D * Af / (Kh[s] + D * (4.f * Ef + Qf - Kh[s]));
     if (t == 0 && (s == 0 || has2)) {
       const int site = L[s].site;
       if (!isfinite(g)) atomicOr(A.err, (int)ERR_NONFINITE);
