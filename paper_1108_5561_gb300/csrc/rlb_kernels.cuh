@@ -474,12 +474,15 @@ __device__ __forceinline__ void store_mom_parts(float* dst, const float* pairs) 
 #pragma unroll
   for (int q = 0; q < kMom; ++q) d[q] = make_float4(pairs[2 * q], pairs[2 * q + 1], 0.f, 0.f);
 }
-// per-site matching results consumed by the stage kernel
-constexpr int kSc = 14;
+// per-site matching results consumed by the stage kernel: kScUsed values,
+// stored kSc apart (64 bytes in FP32: four 16-byte loads per site; the two
+// padding slots hold zeros)
+constexpr int kScUsed = 14, kSc = 16;
 enum : int {
   SC_UT = 0, SC_UX, SC_UY, SC_INVT, SC_MEQ, SC_M, SC_ITR, SC_D, SC_B, SC_K, SC_KH, SC_T,
   SC_AX, SC_AY  // grad ln M (central differences, 1/fm)
 };
+static_assert(SC_AY + 1 == kScUsed && kSc % 4 == 0, "site scalar layout");
 
 // Grid of one or more independent events: periodic transverse grids of their
 // own size and eta/s, stored event after event, row-major inside an event.
@@ -740,22 +743,25 @@ __global__ void __launch_bounds__(128) match_kernel(const MatchArgs A) {
   if (site >= A.ns) return;
   if constexpr (FAST) {
     float o[kSc];
+    o[kSc - 2] = o[kSc - 1] = 0.f;
     const int err = match_site_f(A, site, o);
     if (err) atomicOr(A.err, err);
-    float* of = A.scf + (size_t)site * kSc;
+    float4* of = reinterpret_cast<float4*>(A.scf + (size_t)site * kSc);  // 64 bytes per site
 #pragma unroll
-    for (int q = 0; q < kSc; ++q) of[q] = o[q];
+    for (int q = 0; q < kSc / 4; ++q) of[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
   } else {
     double o[kSc];
+    o[kSc - 2] = o[kSc - 1] = 0.0;
     const int err = match_site_d(A, site, o);
     if (err) atomicOr(A.err, err);
-    double* od = A.sc + (size_t)site * kSc;
+    double2* od = reinterpret_cast<double2*>(A.sc + (size_t)site * kSc);
 #pragma unroll
-    for (int q = 0; q < kSc; ++q) od[q] = o[q];
+    for (int q = 0; q < kSc / 2; ++q) od[q] = make_double2(o[2 * q], o[2 * q + 1]);
     if (A.scf) {
-      float* of = A.scf + (size_t)site * kSc;
+      float4* of = reinterpret_cast<float4*>(A.scf + (size_t)site * kSc);
 #pragma unroll
-      for (int q = 0; q < kSc; ++q) of[q] = (float)o[q];
+      for (int q = 0; q < kSc / 4; ++q)
+        of[q] = make_float4((float)o[4 * q], (float)o[4 * q + 1], (float)o[4 * q + 2], (float)o[4 * q + 3]);
     }
   }
 }
@@ -991,11 +997,11 @@ __global__ void __launch_bounds__(NTH* NPH)
   if constexpr (sizeof(R) == 4) {
     const float* q = A.scf + (size_t)site * kSc;
 #pragma unroll
-    for (int i = 0; i < kSc; ++i) scl[i] = __ldg(q + i);
+    for (int i = 0; i < kScUsed; ++i) scl[i] = __ldg(q + i);
   } else {
     const double* q = A.sc + (size_t)site * kSc;
 #pragma unroll
-    for (int i = 0; i < kSc; ++i) scl[i] = __ldg(q + i);
+    for (int i = 0; i < kScUsed; ++i) scl[i] = __ldg(q + i);
   }
   const R ut = scl[SC_UT], ux = scl[SC_UX], uy = scl[SC_UY];
   const R invT = scl[SC_INVT], Meq = scl[SC_MEQ], M = scl[SC_M], itr = scl[SC_ITR];

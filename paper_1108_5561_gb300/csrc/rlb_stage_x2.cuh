@@ -239,13 +239,15 @@ __global__ void __launch_bounds__(NTH* NPH, MINB)
   float ut[SPT], ux[SPT], uy[SPT], invT[SPT], M[SPT], itr[SPT], ax[SPT], ay[SPT], Dm[SPT], Kh[SPT];
 #pragma unroll
   for (int s = 0; s < SPT; ++s) {
-    const float* q = A.scf + (size_t)L[s].site * kSc;
-    ut[s] = __ldg(q + SC_UT); ux[s] = __ldg(q + SC_UX); uy[s] = __ldg(q + SC_UY);
-    invT[s] = __ldg(q + SC_INVT); M[s] = __ldg(q + SC_M);
-    itr[s] = __ldg(q + SC_ITR); ax[s] = __ldg(q + SC_AX); ay[s] = __ldg(q + SC_AY);
-    Dm[s] = __ldg(q + SC_D); Kh[s] = __ldg(q + SC_KH);
+    static_assert(kSc == 16 && SC_UT == 0 && SC_MEQ == 4 && SC_B == 8 && SC_AX == 12, "float4 groups");
+    const float4* q = reinterpret_cast<const float4*>(A.scf + (size_t)L[s].site * kSc);
+    const float4 q0 = __ldg(q), q1 = __ldg(q + 1), q2 = __ldg(q + 2), q3 = __ldg(q + 3);
+    ut[s] = q0.x; ux[s] = q0.y; uy[s] = q0.z; invT[s] = q0.w;  // SC_UT .. SC_INVT
+    M[s] = q1.y; itr[s] = q1.z; Dm[s] = q1.w;                  // SC_MEQ .. SC_D
+    Kh[s] = q2.z;                                              // SC_B .. SC_T
+    ax[s] = q3.x; ay[s] = q3.y;                                // SC_AX, SC_AY
     if (t < NP) {  // per-site radial table
-      const float Meq = __ldg(q + SC_MEQ), M2 = M[s] * M[s];
+      const float Meq = q1.x, M2 = M[s] * M[s];
       const float e0 = sqrtf(Meq * Meq + M2 * op.s2[2 * t]), e1 = sqrtf(Meq * Meq + M2 * op.s2[2 * t + 1]);
       tab[s][t] = make_float4(e0, e1, op.q1[2 * t] / e0, op.q1[2 * t + 1] / e1);
     }
