@@ -77,6 +77,27 @@ def job_rate(units_per_rank: float, world: int, t_max: float) -> float:
     return world * units_per_rank / t_max
 
 
+# DRAM traffic of the stage kernel on the 256 x 256 workload: ncu
+# dram__bytes_read.sum + dram__bytes_write.sum, mean of one predictor and one
+# corrector launch of `bench.py --steps 3 --warmup 3 --no-cpu-baseline --no-e2e`
+# on a GB300.  It describes the kernel sources it was taken on (their SHA-1) and
+# is reported only while they are unchanged.
+STAGE_TRAFFIC = {"sources": ("rlb_stage_x2.cuh", "rlb_kernels.cuh"),
+                 "sha1": "1258ed59dcf34a44c512c44faf4b220590da3197", "bytes_per_launch": 480.4e6}
+
+
+def stage_traffic(grid: int):
+    """Measured DRAM bytes per stage launch, or None (other grid, changed kernel)."""
+    import hashlib
+    if grid != 256:
+        return None
+    h = hashlib.sha1()
+    for f in STAGE_TRAFFIC["sources"]:
+        with open(os.path.join(ROOT, "paper_1108_5561_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return STAGE_TRAFFIC["bytes_per_launch"] if h.hexdigest() == STAGE_TRAFFIC["sha1"] else None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -599,7 +620,7 @@ def finish(args, rank, world, t, value, achieved, peak, peak_kind, b, nn, launch
                        "l2": "inputs larger than L2 (two 201 MB population arrays)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": stage_traffic(NX),
                          "peak_source": peak_kind, "kernel": "stage_kernel_x2 (fused stream-collide, packed FP32 pairs)",
                          "algorithmic_bytes_per_update": 5 * b, **kern},
             "e2e": e2e,
