@@ -405,10 +405,11 @@ def adjoint_main(args, rank, world, local):
     """Adjoint workload: 128 x 128 grid, 768 nodes, FP32 populations, 40
     hotspots, eta/s 0.08, 300 steps from tau 0.4 fm/c; gradient of the final
     p_perp-weighted v2 with respect to the 40 hotspot amplitudes and eta/s by the
-    discrete adjoint (FP64 arithmetic) with a checkpoint every 32 steps.  Value:
-    time of the gradient (forward with checkpoints + adjoint sweep) over the time
-    of the plain forward run; two amplitude components are checked against
-    central finite differences of the forward run."""
+    discrete adjoint with a checkpoint every 32 steps.  Value: time of the
+    gradient with FP32 per-node adjoint arithmetic (forward with checkpoints +
+    adjoint sweep) over the time of the plain forward run; the FP64-arithmetic
+    gradient is timed too and the two are compared, and two amplitude components
+    are checked against central finite differences of the forward run."""
     import torch
     import paper_1108_5561_gb300 as rlb
     from paper_1108_5561_gb300 import adjoint as ADJ
@@ -437,9 +438,13 @@ def adjoint_main(args, rank, world, local):
     torch.cuda.synchronize()
     t_fwd = e0.elapsed_time(e1) / 1e3
     t0 = time.perf_counter()
-    v2, gA, geta = ADJ.v2_gradient(run, eps0, basis, steps, every)
+    v2, gA, geta = ADJ.v2_gradient(run, eps0, basis, steps, every, arithmetic=rlb.RLB_F32)
     torch.cuda.synchronize()
     t_grad = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, gA64, geta64 = ADJ.v2_gradient(run, eps0, basis, steps, every, arithmetic=rlb.RLB_F64)
+    torch.cuda.synchronize()
+    t_grad64 = time.perf_counter() - t0
     clocks = sampler.stop() if sampler else None
     run.check()
     # finite differences of the forward run for the two largest amplitudes
@@ -454,8 +459,10 @@ def adjoint_main(args, rank, world, local):
         ap[i] += h
         am[i] -= h
         fd = (v2_of(ap) - v2_of(am)) / (2 * h)
-        checks.append({"hotspot": int(i), "adjoint": float(gA[i]), "finite_difference": float(fd),
-                       "rel_diff": float(abs(gA[i] - fd) / max(abs(fd), 1e-300))})
+        checks.append({"hotspot": int(i), "adjoint": float(gA[i]), "adjoint_fp64": float(gA64[i]),
+                       "finite_difference": float(fd),
+                       "rel_diff": float(abs(gA[i] - fd) / max(abs(fd), 1e-300)),
+                       "rel_diff_fp64": float(abs(gA64[i] - fd) / max(abs(fd), 1e-300))})
     if rank == 0:
         line = {
             "metric": "adjoint/forward time", "value": t_grad / t_fwd, "unit": "x",
@@ -464,8 +471,14 @@ def adjoint_main(args, rank, world, local):
             "data": "synthetic",
             "config": {"workload": "adjoint: 128x128, 768 nodes, FP32 populations, 40 hotspots, eta/s 0.08, "
                                    "%d steps, checkpoint every %d, gradient of final p_perp-weighted v2 wrt "
-                                   "40 amplitudes and eta/s (FP64 adjoint arithmetic)" % (steps, every),
-                       "grid": [side, side], "forward_s": t_fwd, "gradient_s": t_grad, "v2": v2,
+                                   "40 amplitudes and eta/s (FP32 per-node adjoint arithmetic, FP64 matching "
+                                   "adjoint)" % (steps, every),
+                       "grid": [side, side], "forward_s": t_fwd, "gradient_s": t_grad,
+                       "gradient_fp64_s": t_grad64, "fp64_over_forward": t_grad64 / t_fwd,
+                       "fp32_vs_fp64_rel": {
+                           "amplitudes": float(np.linalg.norm(gA - gA64) / np.linalg.norm(gA64)),
+                           "eta": float(abs(geta - geta64) / abs(geta64))},
+                       "v2": v2,
                        "dv2_deta": geta, "dv2_dA_norm": float(np.linalg.norm(gA)), "fd_checks": checks,
                        "parallelism": "single GPU"},
             "roofline": None, "e2e": None, "gpu_launches": None, "clocks": clocks, "cpu_baseline": None,

@@ -242,15 +242,23 @@ rlb_status rlb_set_stage_variant(rlb_ctx* ctx, int variant, int* n_variants);
 rlb_status rlb_set_graphs(rlb_ctx* ctx, int enable);
 
 /* Adjoint of the time evolution (discrete adjoint of the predictor-corrector of
- * Sec. 4.4 with the 2+1D terms, FP64 arithmetic for every storage precision).
+ * Sec. 4.4 with the 2+1D terms, for every storage precision; per-node work in
+ * FP64 (default) or FP32 arithmetic, per-site matching adjoint in FP64).
  * The objective is the final-state elliptic flow v2_pt of rlb_observables; the
  * gradients are with respect to the initial energy density (projected on a
  * caller basis, e.g. the hotspot Gaussians) and to eta/s.  The paper has no
  * adjoint; this is the sensitivity of its scheme.
  *
+ *   rlb_adjoint_set_arithmetic
+ *       RLB_F64 (default) or RLB_F32: the arithmetic and storage of the
+ *       per-node adjoints (the stage adjoints: forward recompute, transposed
+ *       operators and stencil).  A change unbinds the workspace (its layout
+ *       changes); call before rlb_adjoint_workspace_size.  RLB_ERR_ARG for
+ *       another value.
  *   rlb_adjoint_workspace_size / rlb_adjoint_bind
- *       FP64 device workspace (caller-owned, 256-byte aligned): the adjoints of
- *       f and ln M and per-stage intermediates (about 3 x 8 bytes x populations).
+ *       Device workspace (caller-owned, 256-byte aligned): the adjoints of f
+ *       and ln M and per-stage intermediates (about 3 x 8 bytes x populations
+ *       in FP64, 3 x 4 in FP32).
  *   rlb_adjoint_seed_v2
  *       v2_pt of the current state (written to *v2) and the adjoint buffers set
  *       to d v2_pt / d(f, ln M) of that state; the eta/s accumulator is cleared.
@@ -269,6 +277,7 @@ rlb_status rlb_set_graphs(rlb_ctx* ctx, int enable);
  *       grad[n_basis] = d v2/d(eta/s).  `grad` is host memory; synchronises.
  * Checkpointing (which states to keep and recompute) is the caller's choice;
  * the Python module adjoint.py keeps one every k steps. */
+rlb_status rlb_adjoint_set_arithmetic(rlb_ctx* ctx, int prec);
 rlb_status rlb_adjoint_workspace_size(rlb_ctx* ctx, size_t* bytes);
 rlb_status rlb_adjoint_bind(rlb_ctx* ctx, void* workspace);
 rlb_status rlb_adjoint_seed_v2(rlb_ctx* ctx, double* v2, void* stream);

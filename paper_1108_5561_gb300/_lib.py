@@ -18,7 +18,7 @@ EXPORTS = ["rlb_create", "rlb_destroy", "rlb_last_error", "rlb_init_eos", "rlb_w
            "rlb_moments", "rlb_check", "rlb_state_offsets", "rlb_lattice", "rlb_operators",
            "rlb_set_timing", "rlb_get_timing", "rlb_step_static_scratch", "rlb_observables",
            "rlb_state_blob_size", "rlb_save_state", "rlb_load_state", "rlb_configure_batch",
-           "rlb_init_batch", "rlb_autotune", "rlb_set_stage_variant", "rlb_set_graphs", "rlb_adjoint_workspace_size",
+           "rlb_init_batch", "rlb_autotune", "rlb_set_stage_variant", "rlb_set_graphs", "rlb_adjoint_set_arithmetic", "rlb_adjoint_workspace_size",
            "rlb_adjoint_bind", "rlb_adjoint_seed_v2", "rlb_adjoint_step", "rlb_adjoint_ic"]
 
 
@@ -97,6 +97,7 @@ def load(build_if_missing: bool = True):
     lib.rlb_autotune.argtypes = [vp, vp, P(ctypes.c_int), dp, P(ctypes.c_int)]
     lib.rlb_set_graphs.argtypes = [vp, ctypes.c_int]
     lib.rlb_set_stage_variant.argtypes = [vp, ctypes.c_int, P(ctypes.c_int)]
+    lib.rlb_adjoint_set_arithmetic.argtypes = [vp, ctypes.c_int]
     lib.rlb_adjoint_workspace_size.argtypes = [vp, P(sz)]
     lib.rlb_adjoint_bind.argtypes = [vp, vp]
     lib.rlb_adjoint_seed_v2.argtypes = [vp, dp, vp]

@@ -2,8 +2,9 @@
 rlb_observables) with respect to eta/s and to the amplitudes of the initial
 hotspots, through the whole time evolution.  The adjoint of every time step
 runs in the CUDA library (rlb_adjoint_step: the discrete adjoint of the
-predictor-corrector, FP64 arithmetic); this module only orders the calls,
-keeps step checkpoints and wraps the result as a torch.autograd.Function.
+predictor-corrector; per-node work in FP64 or FP32 arithmetic, per-site
+matching adjoint in FP64); this module only orders the calls, keeps step
+checkpoints and wraps the result as a torch.autograd.Function.
 
 Checkpointing: the forward run stores the state every `every` steps; the
 backward sweep reruns each segment from its checkpoint, storing the state of
@@ -17,12 +18,16 @@ import ctypes
 
 import numpy as np
 
+from . import _lib as L
+
 
 class Adjoint:
-    """FP64 adjoint workspace of a Run (device memory from torch)."""
+    """Adjoint workspace of a Run (device memory from torch); `arithmetic` is
+    RLB_F64 (default) or RLB_F32 for the per-node adjoint work."""
 
-    def __init__(self, run):
+    def __init__(self, run, arithmetic: int = L.RLB_F64):
         self.run, self.lib, torch = run, run.lib, run.torch
+        run._chk(self.lib.rlb_adjoint_set_arithmetic(run._h, int(arithmetic)), "rlb_adjoint_set_arithmetic")
         n = ctypes.c_size_t()
         run._chk(self.lib.rlb_adjoint_workspace_size(run._h, ctypes.byref(n)), "rlb_adjoint_workspace_size")
         self.ws = torch.empty(n.value, dtype=torch.uint8, device=run.device)
@@ -78,20 +83,21 @@ def reverse_sweep(run, adj: Adjoint, cks, steps: int, every: int):
             adj.step()
 
 
-def v2_gradient(run, eps0, basis, steps: int, every: int = 32):
+def v2_gradient(run, eps0, basis, steps: int, every: int = 32, arithmetic: int = L.RLB_F64):
     """v2 after `steps` steps from eps0 and its gradient: (v2, dv2/dA over the
     rows of basis, dv2/d(eta/s))."""
     cks = forward_with_checkpoints(run, eps0, steps, every)
-    adj = Adjoint(run)
+    adj = Adjoint(run, arithmetic)
     v2 = adj.seed_v2()
     reverse_sweep(run, adj, cks, steps, every)
     gA, geta = adj.ic(eps0, basis)
     return v2, gA, geta
 
 
-def elliptic_flow_function():
+def elliptic_flow_function(arithmetic: int = L.RLB_F64):
     """torch.autograd.Function: v2(amplitudes, eta) = final p_perp-weighted v2
-    of the run started from eps0 = floor + amplitudes @ basis."""
+    of the run started from eps0 = floor + amplitudes @ basis (adjoint in
+    `arithmetic`, RLB_F64 or RLB_F32)."""
     import torch
 
     class EllipticFlow(torch.autograd.Function):
@@ -101,7 +107,7 @@ def elliptic_flow_function():
                 raise ValueError("eta must be the run's eta/s")
             eps0 = (floor + amps.to(device=basis.device, dtype=torch.float64) @ basis).contiguous()
             cks = forward_with_checkpoints(run, eps0, steps, every)
-            adj = Adjoint(run)
+            adj = Adjoint(run, arithmetic)
             v2 = adj.seed_v2()
             ctx.run, ctx.adj, ctx.cks, ctx.eps0, ctx.basis = run, adj, cks, eps0, basis
             ctx.steps, ctx.every = steps, every

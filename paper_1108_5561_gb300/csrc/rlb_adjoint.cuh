@@ -1,6 +1,7 @@
 // rlb_adjoint.cuh -- discrete adjoint of one Heun stage of the scheme
 // (Romatschke, arXiv:1108.5561, Sec. 4.4 with the 2+1D terms of the forward
-// kernels), in FP64 arithmetic for every storage precision.
+// kernels), for every storage precision, with the per-node work in FP64 or in
+// FP32 arithmetic (the per-site matching adjoint is FP64 in both).
 //
 // Forward stage at a site (nodes n = (k, j, l), per-line constants as in
 // stage_kernel; s = site scalars of the matching of f_in):
@@ -33,25 +34,28 @@ namespace rlbk {
 constexpr int kAdjS = 12;
 enum : int { AS_UT = 0, AS_UX, AS_UY, AS_INVT, AS_MEQ, AS_M, AS_ITR, AS_D, AS_KH, AS_AX, AS_AY, AS_PAD };
 
-template <class S, int NXI, int NTH, int NPH>
+// AR: arithmetic of the per-node adjoint work and type of the per-node adjoint
+// arrays (double, or float for the FP32-arithmetic adjoint); the per-site
+// quantities (site scalars and their adjoints, the matching) stay FP64.
+template <class S, class AR, int NXI, int NTH, int NPH>
 struct AdjStageArgs {
   const S* f_in;       // stage input populations
   const double* sc;    // FP64 matching of f_in, kSc per site
-  const double* ob;    // adjoint of the stage output populations (per node)
+  const AR* ob;        // adjoint of the stage output populations (per node)
   const double* lb;    // adjoint of the stage output ln M (per site)
-  double* rbar;        // out: adjoint of r (per node)
-  double* fbar;        // out: site-local part of the adjoint of f_in (per node)
+  AR* rbar;            // out: adjoint of r (per node)
+  AR* fbar;            // out: site-local part of the adjoint of f_in (per node)
   double* sbar;        // out: adjoints of the site scalars (kAdjS per site)
   GridMap grid;
-  double milne;        // 1/tau of f_in (Milne) or 0
-  double c;            // 1 (predictor) or 1/2 (corrector)
-  double dtau, inv2dx, Z;
-  Ops<double, NXI, NTH, NPH> op;
+  AR milne;            // 1/tau of f_in (Milne) or 0
+  AR c;                // 1 (predictor) or 1/2 (corrector)
+  AR dtau, inv2dx, Z;
+  Ops<AR, NXI, NTH, NPH> op;
 };
 
-template <int NV, int NT>
-__device__ __forceinline__ void block_sum_d(double (&v)[NV], double* red) {
-  // sum over the block of NV doubles, result broadcast to every thread
+// sum over the block of NV values of type T, result broadcast to every thread
+template <int NV, int NT, class T>
+__device__ __forceinline__ void block_sum_t(T (&v)[NV], T* red) {
   constexpr int NW = (NT + 31) / 32;
   if constexpr (NT < 32) {
 #pragma unroll
@@ -59,13 +63,16 @@ __device__ __forceinline__ void block_sum_d(double (&v)[NV], double* red) {
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      double a = 0.0;
+      T a = T(0);
       for (int i = 0; i < NT; ++i) a += red[i * NV + q];
       v[q] = a;
     }
     __syncthreads();
   } else {
-    warp_sum<NV>(v);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+      for (int q = 0; q < NV; ++q) v[q] += __shfl_down_sync(0xffffffffu, v[q], off);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0)
 #pragma unroll
@@ -73,7 +80,7 @@ __device__ __forceinline__ void block_sum_d(double (&v)[NV], double* red) {
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      double a = 0.0;
+      T a = T(0);
       for (int w = 0; w < NW; ++w) a += red[w * NV + q];
       v[q] = a;
     }
@@ -81,26 +88,28 @@ __device__ __forceinline__ void block_sum_d(double (&v)[NV], double* red) {
   }
 }
 
-template <class S, int NXI, int NTH, int NPH>
+template <class S, class AR, int NXI, int NTH, int NPH>
 __global__ void __launch_bounds__(NTH* NPH)
-    adj_stage1(const __grid_constant__ AdjStageArgs<S, NXI, NTH, NPH> A) {
+    adj_stage1(const __grid_constant__ AdjStageArgs<S, AR, NXI, NTH, NPH> A) {
+  using T = AR;
   constexpr int NL = NTH * NPH;
   constexpr int NN = NL * NXI;
   constexpr int LD = NL + 1;
   constexpr int NRED = NL < 32 ? NL : (NL + 31) / 32;
+  const T k0 = T(0), k1 = T(1), k2 = T(2), k3 = T(3), k4 = T(4);
   const auto& op = A.op;
   SiteLoc L;
   locate_site(A.grid, blockIdx.x, blockIdx.y, &L);
   const int x = L.x, y = L.y, site = L.site, nx = L.nx, ny = L.ny;
   const int t = threadIdx.x, j = t % NTH, l = t / NTH;
-  __shared__ double fs[NXI * LD];
-  __shared__ double red[16 * NRED];
+  __shared__ T fs[NXI * LD];
+  __shared__ T red[16 * NRED];
 
   // forward recompute
-  double f[NXI], fx1[NXI], fx2[NXI], fy1[NXI], fy2[NXI];
-  load_line<S, double, NXI>(A.f_in + (size_t)site * NN + t * NXI, f);
-  const double cp = op.cph[l], sp = op.sph[l];
-  const int sx = (cp > 0.0) ? -1 : 1, sy = (sp > 0.0) ? -1 : 1;
+  T f[NXI], fx1[NXI], fx2[NXI], fy1[NXI], fy2[NXI];
+  load_line<S, T, NXI>(A.f_in + (size_t)site * NN + t * NXI, f);
+  const T cp = op.cph[l], sp = op.sph[l];
+  const int sx = (cp > k0) ? -1 : 1, sy = (sp > k0) ? -1 : 1;
   int x1 = x + sx, x2 = x + 2 * sx, y1 = y + sy, y2 = y + 2 * sy;
   x1 += (x1 < 0) ? nx : (x1 >= nx ? -nx : 0);
   x2 += (x2 < 0) ? nx : (x2 >= nx ? -nx : 0);
@@ -108,47 +117,48 @@ __global__ void __launch_bounds__(NTH* NPH)
   y1 += (y1 < 0) ? ny : (y1 >= ny ? -ny : 0);
   y2 += (y2 < 0) ? ny : (y2 >= ny ? -ny : 0);
   y2 += (y2 < 0) ? ny : (y2 >= ny ? -ny : 0);
-  load_line<S, double, NXI>(A.f_in + (size_t)(L.base + y * nx + x1) * NN + t * NXI, fx1);
-  load_line<S, double, NXI>(A.f_in + (size_t)(L.base + y * nx + x2) * NN + t * NXI, fx2);
-  load_line<S, double, NXI>(A.f_in + (size_t)(L.base + y1 * nx + x) * NN + t * NXI, fy1);
-  load_line<S, double, NXI>(A.f_in + (size_t)(L.base + y2 * nx + x) * NN + t * NXI, fy2);
+  load_line<S, T, NXI>(A.f_in + (size_t)(L.base + y * nx + x1) * NN + t * NXI, fx1);
+  load_line<S, T, NXI>(A.f_in + (size_t)(L.base + y * nx + x2) * NN + t * NXI, fx2);
+  load_line<S, T, NXI>(A.f_in + (size_t)(L.base + y1 * nx + x) * NN + t * NXI, fy1);
+  load_line<S, T, NXI>(A.f_in + (size_t)(L.base + y2 * nx + x) * NN + t * NXI, fy2);
   const double* q = A.sc + (size_t)site * kSc;
-  const double ut = q[SC_UT], ux = q[SC_UX], uy = q[SC_UY], invT = q[SC_INVT], Meq = q[SC_MEQ];
-  const double M = q[SC_M], itr = q[SC_ITR], D = q[SC_D], Kh = q[SC_KH], ax = q[SC_AX], ay = q[SC_AY];
-  const double M2 = M * M;
+  const T ut = (T)q[SC_UT], ux = (T)q[SC_UX], uy = (T)q[SC_UY], invT = (T)q[SC_INVT], Meq = (T)q[SC_MEQ];
+  const T M = (T)q[SC_M], itr = (T)q[SC_ITR], D = (T)q[SC_D], Kh = (T)q[SC_KH], ax = (T)q[SC_AX],
+          ay = (T)q[SC_AY];
+  const T M2 = M * M;
 #pragma unroll
   for (int k = 0; k < NXI; ++k) fs[k * LD + t] = f[k];
-  double Drf[NXI];
+  T Drf[NXI];
 #pragma unroll
   for (int kp = 0; kp < NXI; ++kp) {
-    double a = 0.0;
+    T a = k0;
 #pragma unroll
     for (int k = 0; k < NXI; ++k) a += op.Dr[kp * NXI + k] * f[k];
     Drf[kp] = a;
   }
   __syncthreads();
-  double pth[NXI];  // (Dth f) on the own line
+  T pth[NXI];  // (Dth f) on the own line
 #pragma unroll
   for (int k = 0; k < NXI; ++k) {
-    double a = 0.0;
+    T a = k0;
 #pragma unroll
     for (int jj = 0; jj < NTH; ++jj) a += op.Dth[j * NTH + jj] * fs[k * LD + l * NTH + jj];
     pth[k] = a;
   }
-  const double st = op.sth[j], mu2 = op.mu2[j], wj = op.wj[j];
-  const double vu = st * (cp * ux + sp * uy), A1 = st * (ax * cp + ay * sp), au = ax * ux + ay * uy;
-  const double nsx = -st * fabs(cp) * A.inv2dx, nsy = -st * fabs(sp) * A.inv2dx;
-  const double Gp = -invT * A1 * ut * M2, Hp = invT * A1 * M * vu, Jp = invT * M * au;
-  double E[NXI], feq[NXI], cc[NXI], fc[NXI], r[NXI], pu[NXI], wp[NXI];
-  double sums[3] = {0.0, 0.0, 0.0};
+  const T st = op.sth[j], mu2 = op.mu2[j], wj = op.wj[j];
+  const T vu = st * (cp * ux + sp * uy), A1 = st * (ax * cp + ay * sp), au = ax * ux + ay * uy;
+  const T nsx = -st * fabs(cp) * A.inv2dx, nsy = -st * fabs(sp) * A.inv2dx;
+  const T Gp = -invT * A1 * ut * M2, Hp = invT * A1 * M * vu, Jp = invT * M * au;
+  T E[NXI], feq[NXI], cc[NXI], fc[NXI], r[NXI], pu[NXI], wp[NXI];
+  T sums[3] = {k0, k0, k0};
 #pragma unroll
   for (int k = 0; k < NXI; ++k) {
-    const double s = op.s[k], c = op.c[k], tv = op.tv[k];
+    const T s = op.s[k], c = op.c[k], tv = op.tv[k];
     E[k] = sqrt(Meq * Meq + M2 * op.s2[k]);
     feq[k] = A.Z * exp(-invT * (ut * E[k] - M * vu * s));
     cc[k] = itr * (ut - tv * vu);
     fc[k] = Gp * op.q1[k] / E[k] + Hp * op.q2[k] + Jp * op.inv_c[k];
-    const double Sx = 3.0 * f[k] - 4.0 * fx1[k] + fx2[k], Sy = 3.0 * f[k] - 4.0 * fy1[k] + fy2[k];
+    const T Sx = k3 * f[k] - k4 * fx1[k] + fx2[k], Sy = k3 * f[k] - k4 * fy1[k] + fy2[k];
     r[k] = tv * (nsx * Sx + nsy * Sy) + A.milne * (mu2 * Drf[k] + pth[k]) + feq[k] * (fc[k] + cc[k]) -
            f[k] * cc[k];
     pu[k] = c * ut - s * vu;
@@ -158,52 +168,52 @@ __global__ void __launch_bounds__(NTH* NPH)
     sums[2] += wp[k] * f[k];
   }
   // site sums and sum_n ob_n (Dr f)_n in one reduction
-  const double* ob = A.ob + (size_t)site * NN + t * NXI;
-  double red4[4] = {sums[0], sums[1], sums[2], 0.0};
+  const T* ob = A.ob + (size_t)site * NN + t * NXI;
+  T red4[4] = {sums[0], sums[1], sums[2], k0};
 #pragma unroll
   for (int k = 0; k < NXI; ++k) red4[3] += ob[k] * Drf[k];
-  block_sum_d<4, NL>(red4, red);
-  const double SA = red4[0], SQ = red4[1], SE = red4[2];
-  const double den = Kh + D * (4.0 * SE + SQ - Kh);
-  const double g = (D == 0.0) ? 0.0 : -D * SA / den;
+  block_sum_t<4, NL>(red4, red);
+  const T SA = red4[0], SQ = red4[1], SE = red4[2];
+  const T den = Kh + D * (k4 * SE + SQ - Kh);
+  const T g = (D == k0) ? k0 : -D * SA / den;
 
   // adjoint of g and of its sums (every thread, identical values)
-  const double cdt = A.c * A.dtau;
-  const double gbar = cdt * (red4[3] + A.lb[site]);
-  double Abar = 0.0, Qbar = 0.0, Ebar = 0.0, Dbar = 0.0, Khbar = 0.0;
-  if (D != 0.0) {
-    const double denbar = D * SA / (den * den) * gbar;
+  const T cdt = A.c * A.dtau;
+  const T gbar = cdt * (red4[3] + (T)A.lb[site]);
+  T Abar = k0, Qbar = k0, Ebar = k0, Dbar = k0, Khbar = k0;
+  if (D != k0) {
+    const T denbar = D * SA / (den * den) * gbar;
     Abar = -D / den * gbar;
-    Dbar = -SA / den * gbar + denbar * (4.0 * SE + SQ - Kh);
-    Ebar = denbar * 4.0 * D;
+    Dbar = -SA / den * gbar + denbar * (k4 * SE + SQ - Kh);
+    Ebar = denbar * k4 * D;
     Qbar = denbar * D;
-    Khbar = denbar * (1.0 - D);
+    Khbar = denbar * (k1 - D);
   }
 
   // per node
-  double rb[NXI], Drfb[NXI], fb[NXI];
-  double b_ut = 0.0, b_vu = 0.0, b_invT = 0.0, b_Meq = 0.0, b_M = 0.0, b_itr = 0.0;
-  double b_Gp = 0.0, b_Hp = 0.0, b_Jp = 0.0;
+  T rb[NXI], Drfb[NXI], fb[NXI];
+  T b_ut = k0, b_vu = k0, b_invT = k0, b_Meq = k0, b_M = k0, b_itr = k0;
+  T b_Gp = k0, b_Hp = k0, b_Jp = k0;
 #pragma unroll
   for (int k = 0; k < NXI; ++k) {
-    const double s = op.s[k], c = op.c[k], tv = op.tv[k];
-    const double o = ob[k];
+    const T s = op.s[k], c = op.c[k], tv = op.tv[k];
+    const T o = ob[k];
     rb[k] = cdt * o + Abar * wp[k];
     Drfb[k] = cdt * g * o + Qbar * wp[k] + A.milne * mu2 * rb[k];
-    fb[k] = A.c * o + Ebar * wp[k] - rb[k] * cc[k] + 3.0 * tv * (nsx + nsy) * rb[k];
+    fb[k] = A.c * o + Ebar * wp[k] - rb[k] * cc[k] + k3 * tv * (nsx + nsy) * rb[k];
     // pu through the weights of the sums
-    const double wpb = Abar * r[k] + Qbar * Drf[k] + Ebar * f[k];
-    const double pub = 2.0 * wj * op.ecw[k] * pu[k] * wpb;
+    const T wpb = Abar * r[k] + Qbar * Drf[k] + Ebar * f[k];
+    const T pub = k2 * wj * op.ecw[k] * pu[k] * wpb;
     b_ut += c * pub;
     b_vu -= s * pub;
     // feq, cc, fc
-    const double feqb = rb[k] * (fc[k] + cc[k]);
-    const double fcb = rb[k] * feq[k];
-    const double ccb = rb[k] * (feq[k] - f[k]);
-    const double argb = feqb * feq[k];
+    const T feqb = rb[k] * (fc[k] + cc[k]);
+    const T fcb = rb[k] * feq[k];
+    const T ccb = rb[k] * (feq[k] - f[k]);
+    const T argb = feqb * feq[k];
     b_invT -= argb * (ut * E[k] - M * vu * s);
     b_ut -= argb * invT * E[k];
-    double Eb = -argb * invT * ut;
+    T Eb = -argb * invT * ut;
     b_M += argb * invT * vu * s;
     b_vu += argb * invT * M * s;
     b_itr += ccb * (ut - tv * vu);
@@ -216,11 +226,11 @@ __global__ void __launch_bounds__(NTH* NPH)
     b_Meq += Eb * Meq / E[k];
     b_M += Eb * M * op.s2[k] / E[k];
   }
-  double b_A1 = 0.0, b_au = 0.0;
+  T b_A1 = k0, b_au = k0;
   b_invT -= b_Gp * A1 * ut * M2;
   b_A1 -= b_Gp * invT * ut * M2;
   b_ut -= b_Gp * invT * A1 * M2;
-  b_M -= b_Gp * invT * A1 * ut * 2.0 * M;
+  b_M -= b_Gp * invT * A1 * ut * k2 * M;
   b_invT += b_Hp * A1 * M * vu;
   b_A1 += b_Hp * invT * M * vu;
   b_M += b_Hp * invT * A1 * vu;
@@ -228,7 +238,7 @@ __global__ void __launch_bounds__(NTH* NPH)
   b_invT += b_Jp * M * au;
   b_M += b_Jp * invT * au;
   b_au += b_Jp * invT * M;
-  double sb[9];
+  T sb[9];
   sb[0] = b_ut;
   sb[1] = b_vu * st * cp + b_au * ax;   // ux
   sb[2] = b_vu * st * sp + b_au * ay;   // uy
@@ -242,7 +252,7 @@ __global__ void __launch_bounds__(NTH* NPH)
   // f through Dr^T on the own line and Dth^T along the polar lines
 #pragma unroll
   for (int k = 0; k < NXI; ++k) {
-    double a = 0.0;
+    T a = k0;
 #pragma unroll
     for (int kp = 0; kp < NXI; ++kp) a += op.Dr[kp * NXI + k] * Drfb[kp];
     fb[k] += a;
@@ -252,23 +262,23 @@ __global__ void __launch_bounds__(NTH* NPH)
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < NXI; ++k) {
-    double a = 0.0;
+    T a = k0;
 #pragma unroll
     for (int jj = 0; jj < NTH; ++jj) a += op.Dth[jj * NTH + j] * fs[k * LD + l * NTH + jj];
     fb[k] += a;
   }
-  double* rbo = A.rbar + (size_t)site * NN + t * NXI;
-  double* fbo = A.fbar + (size_t)site * NN + t * NXI;
+  T* rbo = A.rbar + (size_t)site * NN + t * NXI;
+  T* fbo = A.fbar + (size_t)site * NN + t * NXI;
 #pragma unroll
   for (int k = 0; k < NXI; ++k) {
     rbo[k] = rb[k];
     fbo[k] = fb[k];
   }
   // site scalar adjoints
-  double s9[9];
+  T s9[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) s9[i] = sb[i];
-  block_sum_d<9, NL>(s9, red);
+  block_sum_t<9, NL>(s9, red);
   if (t == 0) {
     double* o = A.sbar + (size_t)site * kAdjS;
     o[AS_UT] = s9[0]; o[AS_UX] = s9[1]; o[AS_UY] = s9[2]; o[AS_INVT] = s9[3]; o[AS_MEQ] = s9[4];
@@ -413,24 +423,25 @@ __global__ void __launch_bounds__(128) adj_match(const AdjMatchArgs A) {
 // ---------------------------------------------------------------------------
 // assembly: adjoint of f_in (per node) and of ln M_in (per site)
 // ---------------------------------------------------------------------------
-template <int NXI, int NTH, int NPH>
+template <class AR, int NXI, int NTH, int NPH>
 struct AdjAssembleArgs {
-  const double* fbar;   // site-local part (adj_stage1)
-  const double* rbar;   // adjoint of r (neighbours gathered)
+  const AR* fbar;       // site-local part (adj_stage1)
+  const AR* rbar;       // adjoint of r (neighbours gathered)
   const double* mbar;   // moment adjoints (adj_match)
   const double* sbar;   // scalar adjoints (grad ln M gathered)
   const double* lbar;   // ln M local part (adj_match)
   const double* lb;     // adjoint of the stage output ln M
-  double* fout;         // adjoint of f_in
+  AR* fout;             // adjoint of f_in
   double* lout;         // adjoint of ln M_in
   GridMap grid;
   double c, inv2dx;
-  Ops<double, NXI, NTH, NPH> op;
+  Ops<AR, NXI, NTH, NPH> op;
 };
 
-template <int NXI, int NTH, int NPH>
+template <class AR, int NXI, int NTH, int NPH>
 __global__ void __launch_bounds__(NTH* NPH)
-    adj_stage3(const __grid_constant__ AdjAssembleArgs<NXI, NTH, NPH> A) {
+    adj_stage3(const __grid_constant__ AdjAssembleArgs<AR, NXI, NTH, NPH> A) {
+  using T = AR;
   constexpr int NL = NTH * NPH;
   constexpr int NN = NL * NXI;
   const auto& op = A.op;
@@ -438,32 +449,37 @@ __global__ void __launch_bounds__(NTH* NPH)
   locate_site(A.grid, blockIdx.x, blockIdx.y, &L);
   const int x = L.x, y = L.y, site = L.site, nx = L.nx, ny = L.ny;
   const int t = threadIdx.x, j = t % NTH, l = t / NTH;
-  const double cp = op.cph[l], sp = op.sph[l], st = op.sth[j], wj = op.wj[j];
-  const double nsx = -st * fabs(cp) * A.inv2dx, nsy = -st * fabs(sp) * A.inv2dx;
+  const T cp = op.cph[l], sp = op.sph[l], st = op.sth[j], wj = op.wj[j];
+  const T nsx = -st * fabs(cp) * (T)A.inv2dx, nsy = -st * fabs(sp) * (T)A.inv2dx;
   // downwind neighbours: the forward stencil of site i - s uses f(i) with -4,
   // that of i - 2 s with +1 (s = the upwind offset)
-  const int sx = (cp > 0.0) ? -1 : 1, sy = (sp > 0.0) ? -1 : 1;
+  const int sx = (cp > T(0)) ? -1 : 1, sy = (sp > T(0)) ? -1 : 1;
   auto wrap = [](int i, int n) {
     i += (i < 0) ? n : (i >= n ? -n : 0);
     return i + ((i < 0) ? n : (i >= n ? -n : 0));
   };
   const size_t d1x = L.base + y * nx + wrap(x - sx, nx), d2x = L.base + y * nx + wrap(x - 2 * sx, nx);
   const size_t d1y = L.base + wrap(y - sy, ny) * nx + x, d2y = L.base + wrap(y - 2 * sy, ny) * nx + x;
-  const double* m = A.mbar + (size_t)site * kMom;
-  const double w0 = wj, w1 = wj * st * cp, w1y = wj * st * sp, w3x = wj * st * st * cp * cp;
-  const double w3xy = wj * st * st * cp * sp, w3y = wj * st * st * sp * sp;
-  const double* fb = A.fbar + (size_t)site * NN + t * NXI;
-  double* fo = A.fout + (size_t)site * NN + t * NXI;
+  const double* md = A.mbar + (size_t)site * kMom;
+  T m[7];
+#pragma unroll
+  for (int i = 0; i < 7; ++i) m[i] = (T)md[i];
+  const T w0 = wj, w1 = wj * st * cp, w1y = wj * st * sp, w3x = wj * st * st * cp * cp;
+  const T w3xy = wj * st * st * cp * sp, w3y = wj * st * st * sp * sp;
+  // the per-line moment coefficients of the four radial weights
+  const T c0 = m[0] * w0, c2 = m[1] * w0, c1 = m[2] * w1 + m[3] * w1y, c3 = m[4] * w3x + m[5] * w3xy + m[6] * w3y;
+  const T* fb = A.fbar + (size_t)site * NN + t * NXI;
+  T* fo = A.fout + (size_t)site * NN + t * NXI;
+  const T m4 = T(-4);
 #pragma unroll
   for (int k = 0; k < NXI; ++k) {
-    const double tv = op.tv[k];
-    const double a = tv * nsx, b = tv * nsy;
-    double v = fb[k];
-    v += a * (-4.0 * A.rbar[d1x * NN + t * NXI + k] + A.rbar[d2x * NN + t * NXI + k]);
-    v += b * (-4.0 * A.rbar[d1y * NN + t * NXI + k] + A.rbar[d2y * NN + t * NXI + k]);
+    const T tv = op.tv[k];
+    const T a = tv * nsx, b = tv * nsy;
+    T v = fb[k];
+    v += a * (m4 * A.rbar[d1x * NN + t * NXI + k] + A.rbar[d2x * NN + t * NXI + k]);
+    v += b * (m4 * A.rbar[d1y * NN + t * NXI + k] + A.rbar[d2y * NN + t * NXI + k]);
     // moment weights: K, T00, T01, T02, T11, T12, T22 (ecw-scaled radial parts)
-    v += m[0] * w0 * op.w0[k] + m[1] * w0 * op.w2[k] + (m[2] * w1 + m[3] * w1y) * op.w1[k] +
-         (m[4] * w3x + m[5] * w3xy + m[6] * w3y) * op.w3[k];
+    v += c0 * op.w0[k] + c2 * op.w2[k] + c1 * op.w1[k] + c3 * op.w3[k];
     fo[k] = v;
   }
   if (t == 0) {
@@ -480,18 +496,18 @@ __global__ void __launch_bounds__(NTH* NPH)
 // = M^3/(2 pi^2) {num_i, den_i}, grid sums in sums[2], sums[3]):
 //   fbar_n = M^3/(2 pi^2) w_n s_k sth_j (cos 2phi_l / DEN - NUM / DEN^2)
 //   lbar   = 3 (part_num / DEN - part_den NUM / DEN^2)
-template <class S, int NXI, int NTH, int NPH>
+template <class S, class AR, int NXI, int NTH, int NPH>
 struct SeedArgs {
   const double* lnM;
   const double* part;
   const double* tot;   // {.., .., NUM, DEN}
-  double* fbar;
+  AR* fbar;
   double* lbar;
   Ops<double, NXI, NTH, NPH> op;
 };
 
-template <class S, int NXI, int NTH, int NPH>
-__global__ void __launch_bounds__(NTH* NPH) adj_seed_v2(const __grid_constant__ SeedArgs<S, NXI, NTH, NPH> A) {
+template <class S, class AR, int NXI, int NTH, int NPH>
+__global__ void __launch_bounds__(NTH* NPH) adj_seed_v2(const __grid_constant__ SeedArgs<S, AR, NXI, NTH, NPH> A) {
   constexpr int NL = NTH * NPH, NN = NL * NXI;
   const int site = blockIdx.x, t = threadIdx.x, j = t % NTH, l = t / NTH;
   const auto& op = A.op;
@@ -501,19 +517,19 @@ __global__ void __launch_bounds__(NTH* NPH) adj_seed_v2(const __grid_constant__ 
   const double m3 = M * M * M / (2.0 * 3.14159265358979323846 * 3.14159265358979323846);
   const double cp = op.cph[l], sp = op.sph[l];
   const double wl = m3 * op.wj[j] * op.sth[j] * (bn * (cp * cp - sp * sp) + bd);
-  double* o = A.fbar + (size_t)site * NN + t * NXI;
+  AR* o = A.fbar + (size_t)site * NN + t * NXI;
 #pragma unroll
-  for (int k = 0; k < NXI; ++k) o[k] = wl * op.ecw[k] * op.s[k];
+  for (int k = 0; k < NXI; ++k) o[k] = (AR)(wl * op.ecw[k] * op.s[k]);
   if (t == 0) A.lbar[site] = 3.0 * (bn * A.part[(size_t)site * 4 + 2] + bd * A.part[(size_t)site * 4 + 3]);
 }
 
 // adjoint of the initial condition (Sec. 4.4: f = Z exp(-M cosh xi / T) at
 // rest, M = x(T) T, eps_EOS(T) = eps0): from the adjoints of f and ln M of the
 // initial state to that of eps0 [GeV/fm^3], per site
-template <class S, int NXI, int NTH, int NPH>
+template <class S, class AR, int NXI, int NTH, int NPH>
 struct AdjIcArgs {
   const double* eps0;
-  const double* fbar;
+  const AR* fbar;
   const double* lbar;
   double* epsbar;
   int* err;
@@ -522,8 +538,8 @@ struct AdjIcArgs {
   Ops<double, NXI, NTH, NPH> op;
 };
 
-template <class S, int NXI, int NTH, int NPH>
-__global__ void __launch_bounds__(NTH* NPH) adj_ic(const __grid_constant__ AdjIcArgs<S, NXI, NTH, NPH> A) {
+template <class S, class AR, int NXI, int NTH, int NPH>
+__global__ void __launch_bounds__(NTH* NPH) adj_ic(const __grid_constant__ AdjIcArgs<S, AR, NXI, NTH, NPH> A) {
   constexpr int NL = NTH * NPH, NN = NL * NXI;
   constexpr int NRED = NL < 32 ? NL : (NL + 31) / 32;
   __shared__ double red[NRED * 2];
@@ -540,14 +556,14 @@ __global__ void __launch_bounds__(NTH* NPH) adj_ic(const __grid_constant__ AdjIc
   }
   __syncthreads();
   const double xv = sT[1];
-  const double* fb = A.fbar + (size_t)site * NN + t * NXI;
+  const AR* fb = A.fbar + (size_t)site * NN + t * NXI;
   double a[1] = {0.0};
 #pragma unroll
   for (int k = 0; k < NXI; ++k) {
     const double fk = A.Z * exp(-xv * op.c[k]);
-    a[0] += fb[k] * fk * (-op.c[k]);  // d f / d x
+    a[0] += (double)fb[k] * fk * (-op.c[k]);  // d f / d x
   }
-  block_sum_d<1, NL>(a, red);
+  block_sum_t<1, NL>(a, red);
   if (t == 0) {
     const double y = sT[0], T = exp(y);
     double xx, dx, ee, de;
@@ -575,10 +591,11 @@ __global__ void __launch_bounds__(1024) project_kernel(const double* basis, cons
   }
 }
 
-// out = beta * out + alpha * in (n doubles)
-__global__ void axpby_kernel(double* out, const double* in, double alpha, double beta, size_t n) {
+// out = beta * out + alpha * in (n values)
+template <class T>
+__global__ void axpby_kernel(T* out, const T* in, T alpha, T beta, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    out[i] = beta * out[i] + (in ? alpha * in[i] : 0.0);
+    out[i] = beta * out[i] + (in ? alpha * in[i] : T(0));
 }
 
 // sum of n doubles into out[0] (one block, fixed order)

@@ -43,8 +43,10 @@ struct rlb_ctx {
   cudaGraphExec_t gexec = nullptr;
   cudaEvent_t gev[2] = {nullptr, nullptr};
   int stage_variant = 0;  // rlb_autotune's choice (see Stager)
-  // adjoint workspace (caller-owned, FP64): offsets in bytes
+  // adjoint workspace (caller-owned): offsets in bytes; per-node adjoints in
+  // FP64 or FP32 (adj_prec, RLB_F64 or RLB_F32), per-site quantities in FP64
   char* adj = nullptr;
+  int adj_prec = RLB_F64;
   size_t a_f = 0, a_l = 0, a_fb = 0, a_rb = 0, a_lin = 0, a_lbar = 0, a_sbar = 0, a_mbar = 0;
   size_t a_ebar = 0, a_mom = 0, a_sc = 0, a_T = 0, a_tot = 0, a_eps = 0, a_eta = 0;
   // optional per-kernel timing (CUDA events on the launch stream)
@@ -132,7 +134,8 @@ void layout(const rlb_grid_params& g, const Shape& sh, size_t table_points, size
 
 // adjoint workspace: FP64 adjoints of f (twice), of r, and per-site arrays
 size_t adj_layout(rlb_ctx* c) {
-  const size_t ns = c->ns, pn = align256(ns * c->nn * sizeof(double)), s1 = align256(ns * sizeof(double));
+  const size_t pe = c->adj_prec == RLB_F32 ? sizeof(float) : sizeof(double);
+  const size_t ns = c->ns, pn = align256(ns * c->nn * pe), s1 = align256(ns * sizeof(double));
   size_t off = 0;
   c->a_f = off; off += pn;
   c->a_fb = off; off += pn;
@@ -636,11 +639,16 @@ template <class S, class R, int NXI, int NTH, int NPH>
 struct Adjoint {
   static constexpr int NL = NTH * NPH;
   static double* D(rlb_ctx* c, size_t off) { return reinterpret_cast<double*>(c->adj + off); }
+  template <class AR>
+  static AR* P(rlb_ctx* c, size_t off) { return reinterpret_cast<AR*>(c->adj + off); }
 
-  // adjoint of one stage with input (f_in, lnM_in): from (ob, lb) to (fout, lout)
+  // adjoint of one stage with input (f_in, lnM_in): from (ob, lb) to (fout, lout);
+  // AR: arithmetic of the per-node adjoint work and type of the per-node arrays
+  template <class AR>
   static rlb_status stage(rlb_ctx* ctx, const S* f_in, const double* lnM_in, double milne, double c,
-                          const double* ob, const double* lb, double* fout, double* lout, cudaStream_t st) {
+                          const AR* ob, const double* lb, AR* fout, double* lout, cudaStream_t st) {
     const auto opd = make_ops<double, NXI, NTH, NPH>(ctx->lat);
+    const auto opa = make_ops<AR, NXI, NTH, NPH>(ctx->lat);
     const rlbk::GridMap gm = grid_map(ctx, ctx->scratch);
     int* err = reinterpret_cast<int*>(ctx->scratch + ctx->err_off);
     {  // FP64 moments and matching of f_in
@@ -659,12 +667,12 @@ struct Adjoint {
       RLB_CUDA(cudaGetLastError(), "adjoint matching launch");
     }
     {
-      rlbk::AdjStageArgs<S, NXI, NTH, NPH> a;
+      rlbk::AdjStageArgs<S, AR, NXI, NTH, NPH> a;
       a.f_in = f_in; a.sc = D(ctx, ctx->a_sc); a.ob = ob; a.lb = lb;
-      a.rbar = D(ctx, ctx->a_rb); a.fbar = D(ctx, ctx->a_fb); a.sbar = D(ctx, ctx->a_sbar);
-      a.grid = gm; a.milne = milne; a.c = c; a.dtau = ctx->gp.dtau; a.inv2dx = 1.0 / (2.0 * ctx->gp.dx);
-      a.Z = ctx->eosp.Z; a.op = opd;
-      rlbk::adj_stage1<S, NXI, NTH, NPH><<<site_grid(ctx), NL, 0, st>>>(a);
+      a.rbar = P<AR>(ctx, ctx->a_rb); a.fbar = P<AR>(ctx, ctx->a_fb); a.sbar = D(ctx, ctx->a_sbar);
+      a.grid = gm; a.milne = (AR)milne; a.c = (AR)c; a.dtau = (AR)ctx->gp.dtau;
+      a.inv2dx = (AR)(1.0 / (2.0 * ctx->gp.dx)); a.Z = (AR)ctx->eosp.Z; a.op = opa;
+      rlbk::adj_stage1<S, AR, NXI, NTH, NPH><<<site_grid(ctx), NL, 0, st>>>(a);
       RLB_CUDA(cudaGetLastError(), "adj_stage1 launch");
     }
     {
@@ -678,18 +686,19 @@ struct Adjoint {
       RLB_CUDA(cudaGetLastError(), "adjoint eta sum launch");
     }
     {
-      rlbk::AdjAssembleArgs<NXI, NTH, NPH> a;
-      a.fbar = D(ctx, ctx->a_fb); a.rbar = D(ctx, ctx->a_rb); a.mbar = D(ctx, ctx->a_mbar);
+      rlbk::AdjAssembleArgs<AR, NXI, NTH, NPH> a;
+      a.fbar = P<AR>(ctx, ctx->a_fb); a.rbar = P<AR>(ctx, ctx->a_rb); a.mbar = D(ctx, ctx->a_mbar);
       a.sbar = D(ctx, ctx->a_sbar); a.lbar = D(ctx, ctx->a_lbar); a.lb = lb; a.fout = fout; a.lout = lout;
-      a.grid = gm; a.c = c; a.inv2dx = 1.0 / (2.0 * ctx->gp.dx); a.op = opd;
-      rlbk::adj_stage3<NXI, NTH, NPH><<<site_grid(ctx), NL, 0, st>>>(a);
+      a.grid = gm; a.c = c; a.inv2dx = 1.0 / (2.0 * ctx->gp.dx); a.op = opa;
+      rlbk::adj_stage3<AR, NXI, NTH, NPH><<<site_grid(ctx), NL, 0, st>>>(a);
       RLB_CUDA(cudaGetLastError(), "adj_stage3 launch");
     }
     return RLB_OK;
   }
 
-  static rlb_status axpby(rlb_ctx* ctx, double* out, const double* in, double a, double b, size_t n, cudaStream_t st) {
-    rlbk::axpby_kernel<<<(unsigned)std::min<size_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(out, in, a, b, n);
+  template <class T>
+  static rlb_status axpby(rlb_ctx* ctx, T* out, const T* in, double a, double b, size_t n, cudaStream_t st) {
+    rlbk::axpby_kernel<T><<<(unsigned)std::min<size_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(out, in, (T)a, (T)b, n);
     RLB_CUDA(cudaGetLastError(), "axpby launch");
     return RLB_OK;
   }
@@ -697,6 +706,10 @@ struct Adjoint {
   // the adjoint buffers hold the adjoints of a step's output; the context state
   // is that step's input (at ctx->tau): replace them by the adjoints of the input
   static rlb_status step(rlb_ctx* ctx, cudaStream_t st) {
+    return ctx->adj_prec == RLB_F32 ? step_t<float>(ctx, st) : step_t<double>(ctx, st);
+  }
+  template <class AR>
+  static rlb_status step_t(rlb_ctx* ctx, cudaStream_t st) {
     S* f = reinterpret_cast<S*>(ctx->state + ctx->f_off);
     S* fs = reinterpret_cast<S*>(ctx->scratch + ctx->fs_off);
     double* m = reinterpret_cast<double*>(ctx->state + ctx->lnM_off);
@@ -715,35 +728,39 @@ struct Adjoint {
     const bool milne = ctx->gp.metric == RLB_MILNE;
     const size_t npop = ctx->ns * ctx->nn;
     // corrector f_new = (f + f* + dtau RHS(f*)) / 2
-    r = stage(ctx, fs, ms, milne ? 1.0 / (tau + dt) : 0.0, 0.5, D(ctx, ctx->a_f), D(ctx, ctx->a_l),
-              D(ctx, ctx->a_fb), D(ctx, ctx->a_lin), st);
+    r = stage<AR>(ctx, fs, ms, milne ? 1.0 / (tau + dt) : 0.0, 0.5, P<AR>(ctx, ctx->a_f), D(ctx, ctx->a_l),
+                  P<AR>(ctx, ctx->a_fb), D(ctx, ctx->a_lin), st);
     if (r) return r;
-    r = axpby(ctx, D(ctx, ctx->a_f), nullptr, 0.0, 0.5, npop, st);  // base terms (1/2) fbar_new
+    r = axpby<AR>(ctx, P<AR>(ctx, ctx->a_f), nullptr, 0.0, 0.5, npop, st);  // base terms (1/2) fbar_new
     if (r) return r;
-    r = axpby(ctx, D(ctx, ctx->a_l), nullptr, 0.0, 0.5, ctx->ns, st);
+    r = axpby<double>(ctx, D(ctx, ctx->a_l), nullptr, 0.0, 0.5, ctx->ns, st);
     if (r) return r;
     // predictor f* = f + dtau RHS(f)
-    r = stage(ctx, f, m, milne ? 1.0 / tau : 0.0, 1.0, D(ctx, ctx->a_fb), D(ctx, ctx->a_lin),
-              D(ctx, ctx->a_fb), D(ctx, ctx->a_lin), st);
+    r = stage<AR>(ctx, f, m, milne ? 1.0 / tau : 0.0, 1.0, P<AR>(ctx, ctx->a_fb), D(ctx, ctx->a_lin),
+                  P<AR>(ctx, ctx->a_fb), D(ctx, ctx->a_lin), st);
     if (r) return r;
-    r = axpby(ctx, D(ctx, ctx->a_f), D(ctx, ctx->a_fb), 1.0, 1.0, npop, st);
+    r = axpby<AR>(ctx, P<AR>(ctx, ctx->a_f), P<AR>(ctx, ctx->a_fb), 1.0, 1.0, npop, st);
     if (r) return r;
-    return axpby(ctx, D(ctx, ctx->a_l), D(ctx, ctx->a_lin), 1.0, 1.0, ctx->ns, st);
+    return axpby<double>(ctx, D(ctx, ctx->a_l), D(ctx, ctx->a_lin), 1.0, 1.0, ctx->ns, st);
   }
 
   // seed: adjoints of v2 (p_perp-weighted) of the current state; out[0] = v2
   static rlb_status seed(rlb_ctx* ctx, double* out, cudaStream_t st) {
+    return ctx->adj_prec == RLB_F32 ? seed_t<float>(ctx, out, st) : seed_t<double>(ctx, out, st);
+  }
+  template <class AR>
+  static rlb_status seed_t(rlb_ctx* ctx, double* out, cudaStream_t st) {
     double* dev = reinterpret_cast<double*>(ctx->scratch + ctx->eps_off);
     rlb_status r = observables<S, R, NXI, NTH, NPH>(ctx, dev, st);
     if (r) return r;
-    rlbk::SeedArgs<S, NXI, NTH, NPH> a;
+    rlbk::SeedArgs<S, AR, NXI, NTH, NPH> a;
     a.lnM = reinterpret_cast<const double*>(ctx->state + ctx->lnM_off);
     a.part = reinterpret_cast<const double*>(ctx->scratch + ctx->moms_off);
     a.tot = dev + 2;
-    a.fbar = D(ctx, ctx->a_f);
+    a.fbar = P<AR>(ctx, ctx->a_f);
     a.lbar = D(ctx, ctx->a_l);
     a.op = make_ops<double, NXI, NTH, NPH>(ctx->lat);
-    rlbk::adj_seed_v2<S, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
+    rlbk::adj_seed_v2<S, AR, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
     RLB_CUDA(cudaGetLastError(), "adjoint seed launch");
     RLB_CUDA(cudaMemsetAsync(D(ctx, ctx->a_eta), 0, sizeof(double), st), "adjoint eta reset");
     RLB_CUDA(cudaMemcpyAsync(out, dev + 1, sizeof(double), cudaMemcpyDeviceToHost, st), "v2 download");
@@ -754,12 +771,18 @@ struct Adjoint {
   // initial condition: p[0] = eps0 (device, GeV/fm^3), p[1] = basis (device,
   // n x ns), p[2] = n, p[3] = output (host, n + 1: dJ/dA_i, then dJ/d(eta/s))
   static rlb_status ic(rlb_ctx* ctx, const double* eps0, const double* basis, int n, double* out, cudaStream_t st) {
-    rlbk::AdjIcArgs<S, NXI, NTH, NPH> a;
-    a.eps0 = eps0; a.fbar = D(ctx, ctx->a_f); a.lbar = D(ctx, ctx->a_l); a.epsbar = D(ctx, ctx->a_eps);
+    return ctx->adj_prec == RLB_F32 ? ic_t<float>(ctx, eps0, basis, n, out, st)
+                                    : ic_t<double>(ctx, eps0, basis, n, out, st);
+  }
+  template <class AR>
+  static rlb_status ic_t(rlb_ctx* ctx, const double* eps0, const double* basis, int n, double* out,
+                         cudaStream_t st) {
+    rlbk::AdjIcArgs<S, AR, NXI, NTH, NPH> a;
+    a.eps0 = eps0; a.fbar = P<AR>(ctx, ctx->a_f); a.lbar = D(ctx, ctx->a_l); a.epsbar = D(ctx, ctx->a_eps);
     a.err = reinterpret_cast<int*>(ctx->scratch + ctx->err_off); a.eos = eos_view(ctx);
     a.eps_scale = rlb::kHbarc * rlb::kHbarc * rlb::kHbarc; a.Z = ctx->eosp.Z;
     a.op = make_ops<double, NXI, NTH, NPH>(ctx->lat);
-    rlbk::adj_ic<S, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
+    rlbk::adj_ic<S, AR, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
     RLB_CUDA(cudaGetLastError(), "adj_ic launch");
     double* proj = D(ctx, ctx->a_ebar);  // n <= ns doubles (checked by the caller)
     if (n > 0) {
@@ -1359,6 +1382,14 @@ rlb_status rlb_autotune(rlb_ctx* ctx, void* stream, int* chosen, double* variant
   if (n_variants) *n_variants = nv;
   if (variant_ms)
     for (int v = 0; v < nv; ++v) variant_ms[v] = t[v];
+  return RLB_OK;
+}
+
+rlb_status rlb_adjoint_set_arithmetic(rlb_ctx* ctx, int prec) {
+  if (!ctx) return RLB_ERR_ARG;
+  if (prec != RLB_F64 && prec != RLB_F32) return fail(ctx, RLB_ERR_ARG, "adjoint arithmetic: RLB_F64 or RLB_F32");
+  if (prec != ctx->adj_prec) ctx->adj = nullptr;  // the workspace layout changes: bind again
+  ctx->adj_prec = prec;
   return RLB_OK;
 }
 

@@ -39,11 +39,11 @@ def _v2(prec, amps, basis, eta=ETA):
     return run.observables()[1]
 
 
-def _adjoint(prec, amps, basis, every):
+def _adjoint(prec, amps, basis, every, arithmetic=rlb.RLB_F64):
     run = rlb.Run(_grid(prec))
     eps0 = torch.as_tensor(FLOOR + amps @ basis, dtype=torch.float64, device="cuda")
     b = torch.as_tensor(basis, dtype=torch.float64, device="cuda")
-    return ADJ.v2_gradient(run, eps0, b, STEPS, every)
+    return ADJ.v2_gradient(run, eps0, b, STEPS, every, arithmetic=arithmetic)
 
 
 def _fd(prec, amps, basis, rel_h, with_eta=True):
@@ -85,6 +85,29 @@ def test_fp32_adjoint():
     fd, _ = _fd(rlb.RLB_F32, amps, basis, 0.1, with_eta=False)
     print("fp32 fd", fd)
     assert np.abs(g32 - fd).max() < 0.03 * scale, (g32, fd)
+
+
+@pytest.mark.parametrize("prec", [rlb.RLB_F64, rlb.RLB_F32])
+def test_fp32_arithmetic_adjoint(prec):
+    # the per-node adjoint work in FP32 against the same adjoint in FP64 on the
+    # same trajectory (FP64 or FP32 storage), and against finite differences
+    amps, basis = _case()
+    v2a, g32, e32 = _adjoint(prec, amps, basis, every=2, arithmetic=rlb.RLB_F32)
+    v2b, g64, e64 = _adjoint(prec, amps, basis, every=2, arithmetic=rlb.RLB_F64)
+    assert v2a == v2b
+    scale = np.abs(g64).max()
+    print("fp32-arithmetic adjoint", g32, e32, "fp64", g64, e64)
+    assert np.abs(g32 - g64).max() < 1e-4 * scale, (g32, g64)
+    assert abs(e32 - e64) < 1e-3 * abs(e64), (e32, e64)
+    if prec == rlb.RLB_F64:
+        fd, _ = _fd(prec, amps, basis, 1e-4, with_eta=False)
+        assert np.abs(g32 - fd).max() < 1e-4 * scale, (g32, fd)
+
+
+def test_adjoint_arithmetic_is_checked():
+    run = rlb.Run(_grid(rlb.RLB_F32))
+    with pytest.raises(rlb.RLBError):
+        ADJ.Adjoint(run, rlb.RLB_BF16)
 
 
 def test_adjoint_matches_oracle_finite_differences(oracle_mod):
