@@ -262,6 +262,11 @@ rlb_status rlb_set_graphs(rlb_ctx* ctx, int enable);
  *   rlb_adjoint_seed_v2
  *       v2_pt of the current state (written to *v2) and the adjoint buffers set
  *       to d v2_pt / d(f, ln M) of that state; the eta/s accumulator is cleared.
+ *   rlb_adjoint_seed
+ *       A general objective J: the adjoint buffers set to fbar = dJ/df (sites x
+ *       nodes FP64, the state's layout) and lbar = dJ/d ln M (sites FP64) of the
+ *       current state, host or device memory (any pointer CUDA's unified
+ *       addressing knows); the eta/s accumulator is cleared.  Synchronises.
  *   rlb_adjoint_step
  *       The adjoint buffers hold the adjoints of the output of one time step;
  *       the context state (f, ln M, tau: e.g. restored with rlb_load_state) is
@@ -281,6 +286,7 @@ rlb_status rlb_adjoint_set_arithmetic(rlb_ctx* ctx, int prec);
 rlb_status rlb_adjoint_workspace_size(rlb_ctx* ctx, size_t* bytes);
 rlb_status rlb_adjoint_bind(rlb_ctx* ctx, void* workspace);
 rlb_status rlb_adjoint_seed_v2(rlb_ctx* ctx, double* v2, void* stream);
+rlb_status rlb_adjoint_seed(rlb_ctx* ctx, const double* fbar, const double* lbar, void* stream);
 rlb_status rlb_adjoint_step(rlb_ctx* ctx, void* stream);
 rlb_status rlb_adjoint_ic(rlb_ctx* ctx, const double* eps0, const double* basis, int n_basis, double* grad,
                           void* stream);

@@ -19,7 +19,7 @@ EXPORTS = ["rlb_create", "rlb_destroy", "rlb_last_error", "rlb_init_eos", "rlb_w
            "rlb_set_timing", "rlb_get_timing", "rlb_step_static_scratch", "rlb_observables",
            "rlb_state_blob_size", "rlb_save_state", "rlb_load_state", "rlb_configure_batch",
            "rlb_init_batch", "rlb_autotune", "rlb_set_stage_variant", "rlb_set_graphs", "rlb_adjoint_set_arithmetic", "rlb_adjoint_workspace_size",
-           "rlb_adjoint_bind", "rlb_adjoint_seed_v2", "rlb_adjoint_step", "rlb_adjoint_ic"]
+           "rlb_adjoint_bind", "rlb_adjoint_seed_v2", "rlb_adjoint_seed", "rlb_adjoint_step", "rlb_adjoint_ic"]
 
 
 class EosParamsC(ctypes.Structure):
@@ -101,6 +101,7 @@ def load(build_if_missing: bool = True):
     lib.rlb_adjoint_workspace_size.argtypes = [vp, P(sz)]
     lib.rlb_adjoint_bind.argtypes = [vp, vp]
     lib.rlb_adjoint_seed_v2.argtypes = [vp, dp, vp]
+    lib.rlb_adjoint_seed.argtypes = [vp, vp, vp, vp]
     lib.rlb_adjoint_step.argtypes = [vp, vp]
     lib.rlb_adjoint_ic.argtypes = [vp, dp, dp, ctypes.c_int, dp, vp]
     for name in EXPORTS:

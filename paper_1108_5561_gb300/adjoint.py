@@ -40,6 +40,19 @@ class Adjoint:
                       "rlb_adjoint_seed_v2")
         return v.value
 
+    def seed(self, fbar, lbar):
+        """A general objective: the adjoint buffers become (dJ/df, dJ/d ln M) of
+        the current state, given as FP64 tensors (sites x nodes, sites; host or
+        device)."""
+        torch = self.run.torch
+        fb = torch.as_tensor(fbar, dtype=torch.float64).contiguous()
+        lb = torch.as_tensor(lbar, dtype=torch.float64).contiguous()
+        if fb.numel() != self.run.ns * self.run.nn or lb.numel() != self.run.ns:
+            raise ValueError("seed shapes: (sites, nodes) and (sites,)")
+        self.run._chk(self.lib.rlb_adjoint_seed(self.run._h, ctypes.c_void_p(fb.data_ptr()),
+                                                ctypes.c_void_p(lb.data_ptr()), self.run._stream()),
+                      "rlb_adjoint_seed")
+
     def step(self):
         """Reverse one step; the run's state must be that step's input."""
         self.run._chk(self.lib.rlb_adjoint_step(self.run._h, self.run._stream()), "rlb_adjoint_step")

@@ -598,6 +598,13 @@ __global__ void axpby_kernel(T* out, const T* in, T alpha, T beta, size_t n) {
     out[i] = beta * out[i] + (in ? alpha * in[i] : T(0));
 }
 
+// out[i] = (T) in[i]
+template <class T>
+__global__ void convert_kernel(T* out, const double* in, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (T)in[i];
+}
+
 // sum of n doubles into out[0] (one block, fixed order)
 __global__ void __launch_bounds__(1024) sum_kernel(const double* in, size_t n, double* out, int accumulate) {
   __shared__ double red[32];

@@ -1412,6 +1412,31 @@ rlb_status rlb_adjoint_bind(rlb_ctx* ctx, void* workspace) {
   return RLB_OK;
 }
 
+rlb_status rlb_adjoint_seed(rlb_ctx* ctx, const double* fbar, const double* lbar, void* stream) {
+  if (!ctx || !fbar || !lbar) return RLB_ERR_ARG;
+  if (!ctx->inited || !ctx->adj) return fail(ctx, RLB_ERR_STATE, "state and adjoint workspace needed");
+  rlb_status s = set_device(ctx);
+  if (s) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t npop = ctx->ns * ctx->nn;
+  if (ctx->adj_prec == RLB_F64) {
+    RLB_CUDA(cudaMemcpyAsync(ctx->adj + ctx->a_f, fbar, npop * sizeof(double), cudaMemcpyDefault, st),
+             "adjoint seed upload");
+  } else {
+    // FP64 staging in the two per-stage FP32 arrays that follow a_f (>= npop doubles)
+    double* stage = reinterpret_cast<double*>(ctx->adj + ctx->a_fb);
+    RLB_CUDA(cudaMemcpyAsync(stage, fbar, npop * sizeof(double), cudaMemcpyDefault, st), "adjoint seed upload");
+    rlbk::convert_kernel<float><<<(unsigned)std::min<size_t>((npop + 255) / 256, 152 * 16), 256, 0, st>>>(
+        reinterpret_cast<float*>(ctx->adj + ctx->a_f), stage, npop);
+    RLB_CUDA(cudaGetLastError(), "adjoint seed conversion");
+  }
+  RLB_CUDA(cudaMemcpyAsync(ctx->adj + ctx->a_l, lbar, ctx->ns * sizeof(double), cudaMemcpyDefault, st),
+           "adjoint seed upload");
+  RLB_CUDA(cudaMemsetAsync(ctx->adj + ctx->a_eta, 0, sizeof(double), st), "adjoint eta reset");
+  RLB_CUDA(cudaStreamSynchronize(st), "adjoint seed synchronise");
+  return RLB_OK;
+}
+
 rlb_status rlb_adjoint_seed_v2(rlb_ctx* ctx, double* v2, void* stream) {
   if (!ctx || !v2) return RLB_ERR_ARG;
   if (!ctx->inited || !ctx->adj) return fail(ctx, RLB_ERR_STATE, "state and adjoint workspace needed");

@@ -104,6 +104,42 @@ def test_fp32_arithmetic_adjoint(prec):
         assert np.abs(g32 - fd).max() < 1e-4 * scale, (g32, fd)
 
 
+@pytest.mark.parametrize("arith,tol", [(rlb.RLB_F64, 1e-7), (rlb.RLB_F32, 1e-4)])
+def test_dot_product_with_a_random_seed(arith, tol):
+    # <w, J d> with J the derivative of eps0 -> (f, ln M) after STEPS steps (FP64
+    # storage), by central differences along a random direction d, against
+    # <J^T w, d> from the adjoint seeded with a random w (rlb_adjoint_seed),
+    # reversed through every step and the initial condition
+    amps, _ = _case()
+    rng = np.random.default_rng(11)
+    g = _grid(rlb.RLB_F64)
+    eps0 = FLOOR + amps @ _case()[1]
+    d = rng.standard_normal(NX * NY)
+    h = 1e-4
+
+    def state(e):
+        run = rlb.Run(g)
+        run.init_grid(e)
+        run.step(STEPS)
+        return run.populations().cpu().numpy().copy(), run.lnM().cpu().numpy().copy()
+
+    fp, lp = state(eps0 + h * d)
+    fm, lm = state(eps0 - h * d)
+    wf = rng.standard_normal(fp.shape) * np.abs(fp).max(axis=1, keepdims=True) ** -1
+    wl = rng.standard_normal(lp.shape)
+    lhs = float(np.sum(wf * (fp - fm)) / (2 * h) + np.sum(wl * (lp - lm)) / (2 * h))
+    run = rlb.Run(g)
+    e0 = torch.as_tensor(eps0, dtype=torch.float64, device="cuda")
+    cks = ADJ.forward_with_checkpoints(run, e0, STEPS, 1)
+    adj = ADJ.Adjoint(run, arith)
+    adj.seed(torch.as_tensor(wf, device="cuda"), torch.as_tensor(wl, device="cuda"))
+    ADJ.reverse_sweep(run, adj, cks, STEPS, 1)
+    gd, _ = adj.ic(e0, torch.as_tensor(d[None, :], dtype=torch.float64, device="cuda"))
+    rhs = float(gd[0])
+    print("dot product", arith, lhs, rhs, abs(lhs - rhs) / abs(lhs))
+    assert abs(lhs - rhs) < tol * abs(lhs), (lhs, rhs)
+
+
 def test_adjoint_arithmetic_is_checked():
     run = rlb.Run(_grid(rlb.RLB_F32))
     with pytest.raises(rlb.RLBError):
