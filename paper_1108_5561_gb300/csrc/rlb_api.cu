@@ -1059,6 +1059,26 @@ rlb_status rlb_configure(rlb_ctx* ctx, const rlb_grid_params* g) {
     return fail(ctx, RLB_ERR_ARG, "grid too large (nx <= 65535, nx * ny < 2^31)");
   std::string m = rlb::build_lattice(g->family, g->n_xi, g->n_theta, g->n_phi_half, g->z0, &ctx->lat);
   if (!m.empty()) return fail(ctx, RLB_ERR_ARG, m);
+  {
+    // streaming stability: the second-order upwind difference with the Heun
+    // stages keeps every Fourier mode bounded while the Courant numbers of the
+    // two axes, (dtau/dx) |V_x| + (dtau/dx) |V_y|, stay at or below 1/2 for every
+    // node (an axis of one site has no streaming)
+    const rlb::Lattice& L = ctx->lat;
+    const double ax = g->nx > 1 ? 1.0 : 0.0, ay = g->ny > 1 ? 1.0 : 0.0;
+    double vmax = 0.0;
+    for (int k = 0; k < L.nxi; ++k)
+      for (int j = 0; j < L.nth; ++j)
+        for (int l = 0; l < L.nph; ++l)
+          vmax = std::max(vmax, L.s[k] / L.c[k] * L.sth[j] * (ax * std::fabs(L.cph[l]) + ay * std::fabs(L.sph[l])));
+    const double courant = g->dtau / g->dx * vmax;
+    if (courant > 0.5) {
+      char buf[160];
+      snprintf(buf, sizeof buf, "time step above the streaming stability limit: (dtau/dx) max(|V_x| + |V_y|) = %.3g > 0.5",
+               courant);
+      return fail(ctx, RLB_ERR_ARG, buf);
+    }
+  }
   ctx->gp = *g;
   set_events(ctx, {rlbk::EventInfo{0, g->nx, g->ny, 0, g->eta_over_s, 0.0}});
   ctx->nn = (size_t)g->n_xi * g->n_theta * 2 * g->n_phi_half;

@@ -68,6 +68,16 @@ def test_longest_row_one_step_sampled(oracle_mod, variant):
     assert e["eps"] < 1e-5 and e["T"] < 1e-5 and e["u"] < 1e-5, e
 
 
+def test_streaming_stability_limit():
+    # (dtau/dx) max(|V_x| + |V_y|) <= 1/2; max |V| < 1, so dtau = 0.3 dx passes and
+    # dtau = 0.8 dx fails; a 1 x 1 grid has no streaming and takes any step
+    rlb.Run(rlb.GridParams(nx=4, ny=4, dx=0.1, dtau=0.03, prec=rlb.RLB_F32))
+    with pytest.raises(rlb.RLBError) as ei:
+        rlb.Run(rlb.GridParams(nx=4, ny=4, dx=0.1, dtau=0.08, prec=rlb.RLB_F32))
+    assert "stability" in str(ei.value)
+    rlb.Run(rlb.GridParams(nx=1, ny=1, dx=0.1, dtau=0.2, prec=rlb.RLB_F32))
+
+
 def test_sizes_beyond_the_limits_are_rejected():
     with pytest.raises(rlb.RLBError):
         rlb.Run(rlb.GridParams(nx=NX_MAX + 1, ny=1, prec=rlb.RLB_F32))
