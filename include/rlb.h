@@ -26,7 +26,11 @@
  *     failures found on the device (no timelike Landau eigenvector, temperature
  *     inversion outside the EOS table, non-finite values) set a device error
  *     word that rlb_check, rlb_moments and rlb_sync_error report as
- *     RLB_ERR_NUMERIC.
+ *     RLB_ERR_NUMERIC.  Bits: 1 Landau, 2 EOS inversion, 4 non-finite, 8 index
+ *     check.  The library built with checks (RLB_CHECKS; the Python front end
+ *     loads it when RLB_CHECKED=1) also range-checks every site index and grid
+ *     coordinate the kernels derive (bit 8, the access then goes to site 0)
+ *     and the finiteness of every stored population (bit 4).
  *   - A context is not thread safe; use one per host thread.
  *
  * State layout (the bound state buffer; offsets from rlb_state_offsets):

@@ -56,13 +56,16 @@ def library_path() -> str:
 
 
 def load(build_if_missing: bool = True):
-    """Load librlb.so; raises if it cannot be built or loaded (no fallback)."""
+    """Load librlb.so (librlb_checked.so, the build with device-side range
+    checks, when the environment sets RLB_CHECKED=1); raises if it cannot be
+    built or loaded (no fallback)."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    checked = os.environ.get("RLB_CHECKED", "") == "1"
+    path = _build.LIB_CHECKED if checked else _build.LIB
     if build_if_missing:
-        path = _build.build()
+        path = _build.build(checked=checked)
     if not os.path.exists(path):
         raise RuntimeError("CUDA library %s is missing; run paper_1108_5561_gb300.build" % path)
     lib = ctypes.CDLL(path)

@@ -46,6 +46,7 @@ struct AdjStageArgs {
   AR* rbar;            // out: adjoint of r (per node)
   AR* fbar;            // out: site-local part of the adjoint of f_in (per node)
   double* sbar;        // out: adjoints of the site scalars (kAdjS per site)
+  int* err;            // error word (index checks of debug builds)
   GridMap grid;
   AR milne;            // 1/tau of f_in (Milne) or 0
   AR c;                // 1 (predictor) or 1/2 (corrector)
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(NTH* NPH)
   const auto& op = A.op;
   SiteLoc L;
   locate_site(A.grid, blockIdx.x, blockIdx.y, &L);
-  const int x = L.x, y = L.y, site = L.site, nx = L.nx, ny = L.ny;
+  const int x = L.x, y = L.y, site = idx_checked(L.site, A.grid.n_sites, A.err), nx = L.nx, ny = L.ny;
   const int t = threadIdx.x, j = t % NTH, l = t / NTH;
   __shared__ T fs[NXI * LD];
   __shared__ T red[16 * NRED];
@@ -117,10 +118,15 @@ __global__ void __launch_bounds__(NTH* NPH)
   y1 += (y1 < 0) ? ny : (y1 >= ny ? -ny : 0);
   y2 += (y2 < 0) ? ny : (y2 >= ny ? -ny : 0);
   y2 += (y2 < 0) ? ny : (y2 >= ny ? -ny : 0);
-  load_line<S, T, NXI>(A.f_in + (size_t)(L.base + y * nx + x1) * NN + t * NXI, fx1);
-  load_line<S, T, NXI>(A.f_in + (size_t)(L.base + y * nx + x2) * NN + t * NXI, fx2);
-  load_line<S, T, NXI>(A.f_in + (size_t)(L.base + y1 * nx + x) * NN + t * NXI, fy1);
-  load_line<S, T, NXI>(A.f_in + (size_t)(L.base + y2 * nx + x) * NN + t * NXI, fy2);
+  const int ns_all = A.grid.n_sites;
+  const int i1 = idx_checked(L.base + y * nx + idx_checked(x1, nx, A.err), ns_all, A.err);
+  const int i2 = idx_checked(L.base + y * nx + idx_checked(x2, nx, A.err), ns_all, A.err);
+  const int i3 = idx_checked(L.base + idx_checked(y1, ny, A.err) * nx + x, ns_all, A.err);
+  const int i4 = idx_checked(L.base + idx_checked(y2, ny, A.err) * nx + x, ns_all, A.err);
+  load_line<S, T, NXI>(A.f_in + (size_t)i1 * NN + t * NXI, fx1);
+  load_line<S, T, NXI>(A.f_in + (size_t)i2 * NN + t * NXI, fx2);
+  load_line<S, T, NXI>(A.f_in + (size_t)i3 * NN + t * NXI, fy1);
+  load_line<S, T, NXI>(A.f_in + (size_t)i4 * NN + t * NXI, fy2);
   const double* q = A.sc + (size_t)site * kSc;
   const T ut = (T)q[SC_UT], ux = (T)q[SC_UX], uy = (T)q[SC_UY], invT = (T)q[SC_INVT], Meq = (T)q[SC_MEQ];
   const T M = (T)q[SC_M], itr = (T)q[SC_ITR], D = (T)q[SC_D], Kh = (T)q[SC_KH], ax = (T)q[SC_AX],
@@ -433,6 +439,7 @@ struct AdjAssembleArgs {
   const double* lb;     // adjoint of the stage output ln M
   AR* fout;             // adjoint of f_in
   double* lout;         // adjoint of ln M_in
+  int* err;             // error word (index checks of debug builds)
   GridMap grid;
   double c, inv2dx;
   Ops<AR, NXI, NTH, NPH> op;
@@ -447,7 +454,7 @@ __global__ void __launch_bounds__(NTH* NPH)
   const auto& op = A.op;
   SiteLoc L;
   locate_site(A.grid, blockIdx.x, blockIdx.y, &L);
-  const int x = L.x, y = L.y, site = L.site, nx = L.nx, ny = L.ny;
+  const int x = L.x, y = L.y, site = idx_checked(L.site, A.grid.n_sites, A.err), nx = L.nx, ny = L.ny;
   const int t = threadIdx.x, j = t % NTH, l = t / NTH;
   const T cp = op.cph[l], sp = op.sph[l], st = op.sth[j], wj = op.wj[j];
   const T nsx = -st * fabs(cp) * (T)A.inv2dx, nsy = -st * fabs(sp) * (T)A.inv2dx;
@@ -458,8 +465,11 @@ __global__ void __launch_bounds__(NTH* NPH)
     i += (i < 0) ? n : (i >= n ? -n : 0);
     return i + ((i < 0) ? n : (i >= n ? -n : 0));
   };
-  const size_t d1x = L.base + y * nx + wrap(x - sx, nx), d2x = L.base + y * nx + wrap(x - 2 * sx, nx);
-  const size_t d1y = L.base + wrap(y - sy, ny) * nx + x, d2y = L.base + wrap(y - 2 * sy, ny) * nx + x;
+  const int ns_all = A.grid.n_sites;
+  const size_t d1x = idx_checked(L.base + y * nx + idx_checked(wrap(x - sx, nx), nx, A.err), ns_all, A.err);
+  const size_t d2x = idx_checked(L.base + y * nx + idx_checked(wrap(x - 2 * sx, nx), nx, A.err), ns_all, A.err);
+  const size_t d1y = idx_checked(L.base + idx_checked(wrap(y - sy, ny), ny, A.err) * nx + x, ns_all, A.err);
+  const size_t d2y = idx_checked(L.base + idx_checked(wrap(y - 2 * sy, ny), ny, A.err) * nx + x, ns_all, A.err);
   const double* md = A.mbar + (size_t)site * kMom;
   T m[7];
 #pragma unroll
@@ -486,8 +496,11 @@ __global__ void __launch_bounds__(NTH* NPH)
     const double* sb = A.sbar;
     const int xm = wrap(x - 1, nx), xp = wrap(x + 1, nx), ym = wrap(y - 1, ny), yp = wrap(y + 1, ny);
     // ln M(i) enters a_x(i -/+ 1) = (ln M(i) - ln M(i -/+ 2)) / (2 dx) with sign +/-
-    const double gx = sb[(size_t)(L.base + y * nx + xm) * kAdjS + AS_AX] - sb[(size_t)(L.base + y * nx + xp) * kAdjS + AS_AX];
-    const double gy = sb[(size_t)(L.base + ym * nx + x) * kAdjS + AS_AY] - sb[(size_t)(L.base + yp * nx + x) * kAdjS + AS_AY];
+    const int ns_all = A.grid.n_sites;
+    const size_t sxm = idx_checked(L.base + y * nx + xm, ns_all, A.err), sxp = idx_checked(L.base + y * nx + xp, ns_all, A.err);
+    const size_t sym = idx_checked(L.base + ym * nx + x, ns_all, A.err), syp = idx_checked(L.base + yp * nx + x, ns_all, A.err);
+    const double gx = sb[sxm * kAdjS + AS_AX] - sb[sxp * kAdjS + AS_AX];
+    const double gy = sb[sym * kAdjS + AS_AY] - sb[syp * kAdjS + AS_AY];
     A.lout[site] = A.c * A.lb[site] + A.lbar[site] + A.inv2dx * (gx + gy);
   }
 }

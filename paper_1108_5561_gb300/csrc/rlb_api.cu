@@ -670,7 +670,7 @@ struct Adjoint {
       rlbk::AdjStageArgs<S, AR, NXI, NTH, NPH> a;
       a.f_in = f_in; a.sc = D(ctx, ctx->a_sc); a.ob = ob; a.lb = lb;
       a.rbar = P<AR>(ctx, ctx->a_rb); a.fbar = P<AR>(ctx, ctx->a_fb); a.sbar = D(ctx, ctx->a_sbar);
-      a.grid = gm; a.milne = (AR)milne; a.c = (AR)c; a.dtau = (AR)ctx->gp.dtau;
+      a.err = err; a.grid = gm; a.milne = (AR)milne; a.c = (AR)c; a.dtau = (AR)ctx->gp.dtau;
       a.inv2dx = (AR)(1.0 / (2.0 * ctx->gp.dx)); a.Z = (AR)ctx->eosp.Z; a.op = opa;
       rlbk::adj_stage1<S, AR, NXI, NTH, NPH><<<site_grid(ctx), NL, 0, st>>>(a);
       RLB_CUDA(cudaGetLastError(), "adj_stage1 launch");
@@ -689,7 +689,7 @@ struct Adjoint {
       rlbk::AdjAssembleArgs<AR, NXI, NTH, NPH> a;
       a.fbar = P<AR>(ctx, ctx->a_fb); a.rbar = P<AR>(ctx, ctx->a_rb); a.mbar = D(ctx, ctx->a_mbar);
       a.sbar = D(ctx, ctx->a_sbar); a.lbar = D(ctx, ctx->a_lbar); a.lb = lb; a.fout = fout; a.lout = lout;
-      a.grid = gm; a.c = c; a.inv2dx = 1.0 / (2.0 * ctx->gp.dx); a.op = opa;
+      a.err = err; a.grid = gm; a.c = c; a.inv2dx = 1.0 / (2.0 * ctx->gp.dx); a.op = opa;
       rlbk::adj_stage3<AR, NXI, NTH, NPH><<<site_grid(ctx), NL, 0, st>>>(a);
       RLB_CUDA(cudaGetLastError(), "adj_stage3 launch");
     }
@@ -1240,7 +1240,8 @@ rlb_status rlb_check(rlb_ctx* ctx, void* stream) {
   RLB_CUDA(cudaStreamSynchronize(st), "synchronise");
   if (word) {
     char buf[160];
-    snprintf(buf, sizeof buf, "device error word 0x%x (1: Landau, 2: EOS inversion, 4: non-finite)", word);
+    snprintf(buf, sizeof buf, "device error word 0x%x (1: Landau, 2: EOS inversion, 4: non-finite, 8: index check)",
+             word);
     return fail(ctx, RLB_ERR_NUMERIC, buf);
   }
   return RLB_OK;

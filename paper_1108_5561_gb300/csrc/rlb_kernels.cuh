@@ -15,7 +15,38 @@
 
 namespace rlbk {
 
-enum : int { ERR_LANDAU = 1, ERR_EOS = 2, ERR_NONFINITE = 4 };
+enum : int { ERR_LANDAU = 1, ERR_EOS = 2, ERR_NONFINITE = 4, ERR_INDEX = 8 };
+
+// Debug builds (-DRLB_CHECKS, the library built with checks=True): every site
+// index and grid coordinate a kernel derives is checked against its range; a
+// failure sets ERR_INDEX in the error word and the value is replaced by 0 (a
+// valid index), so that no access leaves its array and no thread leaves the
+// CTA's barrier sequence.  Release builds return the value unchanged.
+__device__ __forceinline__ int idx_checked(int v, int n, int* err) {
+#ifdef RLB_CHECKS
+  if (v < 0 || v >= n) {
+    atomicOr(err, (int)ERR_INDEX);
+    return 0;
+  }
+#else
+  (void)n;
+  (void)err;
+#endif
+  return v;
+}
+// Debug builds: ERR_NONFINITE when one of the n values is not finite.
+template <class R>
+__device__ __forceinline__ void finite_checked(const R* v, int n, int* err) {
+#ifdef RLB_CHECKS
+  bool ok = true;
+  for (int i = 0; i < n; ++i) ok = ok && isfinite((double)v[i]);
+  if (!ok) atomicOr(err, (int)ERR_NONFINITE);
+#else
+  (void)v;
+  (void)n;
+  (void)err;
+#endif
+}
 
 // ---------------------------------------------------------------------------
 // per-run constants, passed by value (kernel parameter space = constant bank)
@@ -621,8 +652,9 @@ __device__ __forceinline__ int match_site_d(const MatchArgs& A, int site, double
     const double* lm = A.lnM + evi.site_off;
     const int xp = x + 1 == nx ? 0 : x + 1, xm = x == 0 ? nx - 1 : x - 1;
     const int yp = yy + 1 == ny ? 0 : yy + 1, ym = yy == 0 ? ny - 1 : yy - 1;
-    o[SC_AX] = (lm[yy * nx + xp] - lm[yy * nx + xm]) * A.inv2dx;
-    o[SC_AY] = (lm[yp * nx + x] - lm[ym * nx + x]) * A.inv2dx;
+    const int ne = nx * ny;
+    o[SC_AX] = (lm[idx_checked(yy * nx + xp, ne, A.err)] - lm[idx_checked(yy * nx + xm, ne, A.err)]) * A.inv2dx;
+    o[SC_AY] = (lm[idx_checked(yp * nx + x, ne, A.err)] - lm[idx_checked(ym * nx + x, ne, A.err)]) * A.inv2dx;
   }
   if (A.obs) {
     const double hc = 0.1973269804, h3 = hc * hc * hc;
@@ -713,8 +745,9 @@ __device__ __forceinline__ int match_site_f(const MatchArgs& A, int site, float 
     const int xp = x + 1 == nx ? 0 : x + 1, xm = x == 0 ? nx - 1 : x - 1;
     const int yp = yy + 1 == ny ? 0 : yy + 1, ym = yy == 0 ? ny - 1 : yy - 1;
     const float i2dx = (float)A.inv2dx;
-    o[SC_AX] = (float)(lm[yy * nx + xp] - lm[yy * nx + xm]) * i2dx;
-    o[SC_AY] = (float)(lm[yp * nx + x] - lm[ym * nx + x]) * i2dx;
+    const int ne = nx * ny;
+    o[SC_AX] = (float)(lm[idx_checked(yy * nx + xp, ne, A.err)] - lm[idx_checked(yy * nx + xm, ne, A.err)]) * i2dx;
+    o[SC_AY] = (float)(lm[idx_checked(yp * nx + x, ne, A.err)] - lm[idx_checked(ym * nx + x, ne, A.err)]) * i2dx;
   }
   if (A.obs) {
     const double hc = 0.1973269804, h3 = hc * hc * hc;
@@ -956,7 +989,7 @@ __global__ void __launch_bounds__(NTH* NPH)
   const auto& op = A.op;
   SiteLoc L;
   locate_site(A.grid, blockIdx.x, blockIdx.y, &L);
-  const int x = L.x, y = L.y, site = L.site, nx = L.nx, ny = L.ny;
+  const int x = L.x, y = L.y, site = idx_checked(L.site, A.grid.n_sites, A.err), nx = L.nx, ny = L.ny;
   const int t = threadIdx.x;
   const int j = t % NTH, l = t / NTH;
 
@@ -983,8 +1016,11 @@ __global__ void __launch_bounds__(NTH* NPH)
   y1 += (y1 < 0) ? ny : (y1 >= ny ? -ny : 0);
   y2 += (y2 < 0) ? ny : (y2 >= ny ? -ny : 0);
   y2 += (y2 < 0) ? ny : (y2 >= ny ? -ny : 0);
-  const int sx1 = L.base + y * nx + x1, sx2 = L.base + y * nx + x2;
-  const int sy1 = L.base + y1 * nx + x, sy2 = L.base + y2 * nx + x;
+  const int ns_all = A.grid.n_sites;
+  const int sx1 = idx_checked(L.base + y * nx + idx_checked(x1, nx, A.err), ns_all, A.err);
+  const int sx2 = idx_checked(L.base + y * nx + idx_checked(x2, nx, A.err), ns_all, A.err);
+  const int sy1 = idx_checked(L.base + idx_checked(y1, ny, A.err) * nx + x, ns_all, A.err);
+  const int sy2 = idx_checked(L.base + idx_checked(y2, ny, A.err) * nx + x, ns_all, A.err);
   R fx1[NXI], fx2[NXI], fy1[NXI], fy2[NXI];
   load_line<S, R, NXI>(A.f_in + (size_t)sx1 * NN + t * NXI, fx1);
   load_line<S, R, NXI>(A.f_in + (size_t)sx2 * NN + t * NXI, fx2);
@@ -1120,6 +1156,7 @@ __global__ void __launch_bounds__(NTH* NPH)
   // the moments describe exactly what is stored (after rounding to S)
 #pragma unroll
   for (int k = 0; k < NXI; ++k) out[k] = ld1<S, R>(st1<S, R>(out[k]));
+  finite_checked(out, NXI, A.err);
   store_line<S, R, NXI>(A.f_out + (size_t)site * NN + t * NXI, out);
   R mom[kMom];
   line_moments<R, NXI, NTH, NPH>(op, out, j, l, mom);

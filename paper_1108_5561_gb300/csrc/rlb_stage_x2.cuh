@@ -189,6 +189,8 @@ __global__ void __launch_bounds__(NTH* NPH, MINB)
   SiteLoc L[SPT];
   bool has2;
   locate_sites<SPT>(A.grid, blockIdx.x, blockIdx.y, L, &has2);
+#pragma unroll
+  for (int s = 0; s < SPT; ++s) L[s].site = idx_checked(L[s].site, A.grid.n_sites, A.err);
   const int t = threadIdx.x;
   const int j = t % NTH, l = t / NTH;
   // 1/tau of f_in, issued first: its latency hides behind the population loads
@@ -221,11 +223,16 @@ __global__ void __launch_bounds__(NTH* NPH, MINB)
       y2 += (y2 < 0) ? ny : (y2 >= ny ? -ny : 0);
       y2 += (y2 < 0) ? ny : (y2 >= ny ? -ny : 0);
       float2 fx1[NP], fx2[NP], fy1[NP], fy2[NP];
-      const S* fev = A.f_in + (size_t)L[s].base * NN + t * NXI;
-      load_pairs<S, NP>(fev + (size_t)(y * nx + x1) * NN, fx1);
-      load_pairs<S, NP>(fev + (size_t)(y * nx + x2) * NN, fx2);
-      load_pairs<S, NP>(fev + (size_t)(y1 * nx + x) * NN, fy1);
-      load_pairs<S, NP>(fev + (size_t)(y2 * nx + x) * NN, fy2);
+      const int ns_all = A.grid.n_sites, b0 = L[s].base;
+      const int i1 = idx_checked(b0 + y * nx + idx_checked(x1, nx, A.err), ns_all, A.err);
+      const int i2 = idx_checked(b0 + y * nx + idx_checked(x2, nx, A.err), ns_all, A.err);
+      const int i3 = idx_checked(b0 + idx_checked(y1, ny, A.err) * nx + x, ns_all, A.err);
+      const int i4 = idx_checked(b0 + idx_checked(y2, ny, A.err) * nx + x, ns_all, A.err);
+      const S* fl = A.f_in + t * NXI;
+      load_pairs<S, NP>(fl + (size_t)i1 * NN, fx1);
+      load_pairs<S, NP>(fl + (size_t)i2 * NN, fx2);
+      load_pairs<S, NP>(fl + (size_t)i3 * NN, fy1);
+      load_pairs<S, NP>(fl + (size_t)i4 * NN, fy2);
 #pragma unroll
       for (int p = 0; p < NP; ++p) {
         const float2 Sx = fma2(mfour0, fx1[p], fma2(three0, f[s][p], fx2[p]));
@@ -410,8 +417,10 @@ __global__ void __launch_bounds__(NTH* NPH, MINB)
     }
   }
 #pragma unroll
-  for (int s = 0; s < SPT; ++s)  // out now holds the stored values
+  for (int s = 0; s < SPT; ++s) {  // out now holds the stored values
     if (s == 0 || has2) store_pairs<S, NP>(A.f_out + (size_t)L[s].site * NN + t * NXI, out[s]);
+    finite_checked(reinterpret_cast<const float*>(out[s]), 2 * NP, A.err);
+  }
 
   // 4. moments of what was stored
   const float mu = op.mu[j];
