@@ -257,9 +257,10 @@ def batch_main(args, rank, world, local):
     e2e = None
     if not args.no_e2e:
         # pinned eps0 upload, initial condition, then every step the step and a
-        # download of the per-site observables (8 doubles per site)
+        # download of the per-site observables (8 doubles per site), each download
+        # overlapping the next step
         host_eps = torch.from_numpy(eps.copy()).pin_memory()
-        host_mom = torch.empty((ns, 8), dtype=torch.float64).pin_memory()
+        obs = ObservableStream(run, torch)
         dev_eps = torch.empty(ns, dtype=torch.float64, device="cuda")
         barrier()
         torch.cuda.synchronize()
@@ -268,7 +269,7 @@ def batch_main(args, rank, world, local):
         run.init_grid(dev_eps)
         for _ in range(args.steps):
             run.step(1)
-            host_mom.copy_(run.moments(host=False), non_blocking=True)
+            obs.step()
         torch.cuda.synchronize()
         barrier()
         t_e2e = time.perf_counter() - t0
@@ -599,10 +600,42 @@ def main():
                   clocks, cpu, ranks, kern)
 
 
+class ObservableStream:
+    """Per-step download of the per-site observables (8 doubles per site) to
+    pinned host memory on a copy stream, double-buffered, so that the copy of
+    step n overlaps step n + 1 on the compute stream."""
+
+    def __init__(self, run, torch):
+        self.run, self.torch = run, torch
+        shape = (run.ns, 8)
+        self.dev = [torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(2)]
+        self.host = [torch.empty(shape, dtype=torch.float64).pin_memory() for _ in range(2)]
+        self.done = [torch.cuda.Event(), torch.cuda.Event()]
+        self.copy = torch.cuda.Stream()
+        self.n = 0
+
+    def step(self):
+        torch, i = self.torch, self.n % 2
+        cur = torch.cuda.current_stream()
+        if self.n >= 2:
+            cur.wait_event(self.done[i])  # buffer i: its previous download has finished
+        self.run.moments(out=self.dev[i], host=False)
+        ready = torch.cuda.Event()
+        ready.record(cur)
+        self.copy.wait_event(ready)
+        with torch.cuda.stream(self.copy):
+            self.host[i].copy_(self.dev[i], non_blocking=True)
+            self.done[i].record(self.copy)
+        self.n += 1
+
+    def bytes_per_step(self) -> int:
+        return self.run.ns * 8 * 8
+
+
 def end_to_end(run, eps0, args, updates, barrier, torch):
     ns = NX * NY
     host_eps = torch.from_numpy(eps0.reshape(-1).copy()).pin_memory()
-    host_mom = torch.empty((ns, 8), dtype=torch.float64).pin_memory()
+    obs = ObservableStream(run, torch)
     dev_eps = torch.empty(ns, dtype=torch.float64, device="cuda")
     barrier()
     torch.cuda.synchronize()
@@ -611,7 +644,7 @@ def end_to_end(run, eps0, args, updates, barrier, torch):
     run.init_grid(dev_eps)
     for _ in range(args.steps):
         run.step(1)
-        host_mom.copy_(run.moments(host=False), non_blocking=True)
+        obs.step()
     torch.cuda.synchronize()
     barrier()
     t_e2e = time.perf_counter() - t0

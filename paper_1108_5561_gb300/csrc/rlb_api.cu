@@ -461,8 +461,15 @@ struct Runner {
     a.family = ctx->gp.family;
     a.T0 = ctx->gp.T0;
     a.op = make_ops<R, NXI, NTH, NPH>(ctx->lat);
+    // (T, M_eq, M) per site in the FP64 site-scalar scratch (free until the first matching)
+    double* tsm = reinterpret_cast<double*>(ctx->scratch + ctx->sc_off);
+    a.tsm = tsm;
+    rlbk::InitSiteArgs b;
+    b.eps0 = eps_dev; b.eps_scale = a.eps_scale; b.lnM = a.lnM; b.Tsite = a.Tsite; b.tsm = tsm; b.err = a.err;
+    b.eos = a.eos; b.family = a.family; b.T0 = a.T0; b.ns = (int)ctx->ns;
     {
       Timed tm(ctx, K_INIT, st);
+      rlbk::init_site_kernel<<<(unsigned)((ctx->ns + 127) / 128), 128, 0, st>>>(b);
       rlbk::init_kernel<S, R, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
     }
     RLB_CUDA(cudaGetLastError(), "init_kernel launch");

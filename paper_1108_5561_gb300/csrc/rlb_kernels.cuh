@@ -1179,6 +1179,7 @@ template <class S, class R, int NXI, int NTH, int NPH>
 struct InitArgs {
   const double* eps0;  // GeV/fm^3
   double eps_scale;    // (hbar c)^3: GeV/fm^3 -> GeV^4
+  const double* tsm;   // per site (T, M_eq, M) from init_site_kernel
   S* f;
   double* lnM;
   double* Tsite;
@@ -1192,6 +1193,44 @@ struct InitArgs {
   Ops<R, NXI, NTH, NPH> op;
 };
 
+// Initial condition, per site (one thread each: the FP64 Newton inversion of
+// the EOS is a serial chain, and a warp of sites keeps all 32 lanes of each
+// FP64 instruction busy): T from eps_EOS(T) = eps0, M_eq = x(T) T, M = M_eq
+// (or T0 for the conformal family); writes T, ln M and (T, M_eq, M) to tsm.
+struct InitSiteArgs {
+  const double* eps0;  // GeV/fm^3
+  double eps_scale;    // (hbar c)^3: GeV/fm^3 -> GeV^4
+  double* lnM;
+  double* Tsite;
+  double* tsm;         // 3 per site
+  int* err;
+  EosView eos;
+  int family;
+  double T0;
+  int ns;
+};
+
+__global__ void __launch_bounds__(128) init_site_kernel(const InitSiteArgs A) {
+  const int site = blockIdx.x * blockDim.x + threadIdx.x;
+  if (site >= A.ns) return;
+  double y = 0.0;
+  if (!eos_invert(A.eos, EOS_EPS, __ldg(A.eps0 + site) * A.eps_scale, log(0.3), &y)) {
+    atomicOr(A.err, (int)ERR_EOS);
+    y = log(0.3);
+  }
+  int i0;
+  double tt, w[6];
+  eos_cell(A.eos, y, &i0, &tt);
+  lagrange6(tt, w);
+  const double T = exp(y);
+  const double Meq = eos_field(A.eos, i0, w, EOS_X) * T;
+  const double M = A.family == 1 ? A.T0 : Meq;
+  A.Tsite[site] = T;
+  A.lnM[site] = log(M);
+  double* o = A.tsm + (size_t)site * 3;
+  o[0] = T; o[1] = Meq; o[2] = M;
+}
+
 template <class S, class R, int NXI, int NTH, int NPH>
 __global__ void __launch_bounds__(NTH* NPH)
     init_kernel(const __grid_constant__ InitArgs<S, R, NXI, NTH, NPH> A) {
@@ -1200,28 +1239,10 @@ __global__ void __launch_bounds__(NTH* NPH)
   constexpr int NW = (NL + 31) / 32;
   const int site = blockIdx.x, t = threadIdx.x;
   const int j = t % NTH, l = t / NTH;
-  __shared__ double sc[3];
   __shared__ double redd[kMom * NW];
   __shared__ float redf[2 * kMom * NW];
-  if (t == 0) {
-    double y = 0.0;
-    if (!eos_invert(A.eos, EOS_EPS, __ldg(A.eps0 + site) * A.eps_scale, log(0.3), &y)) {
-      atomicOr(A.err, (int)ERR_EOS);
-      y = log(0.3);
-    }
-    int i0;
-    double tt, w[6];
-    eos_cell(A.eos, y, &i0, &tt);
-    lagrange6(tt, w);
-    const double T = exp(y);
-    const double Meq = eos_field(A.eos, i0, w, EOS_X) * T;
-    const double M = A.family == 1 ? A.T0 : Meq;
-    A.Tsite[site] = T;
-    A.lnM[site] = log(M);
-    sc[0] = T; sc[1] = Meq; sc[2] = M;
-  }
-  __syncthreads();
-  const R invT = (R)(1.0 / sc[0]), Meq = (R)sc[1], M = (R)sc[2], Z = (R)A.Z;
+  const double* sc = A.tsm + (size_t)site * 3;  // (T, M_eq, M) of init_site_kernel
+  const R invT = (R)(1.0 / __ldg(sc)), Meq = (R)__ldg(sc + 1), M = (R)__ldg(sc + 2), Z = (R)A.Z;
   R out[NXI];
 #pragma unroll
   for (int k = 0; k < NXI; ++k)
