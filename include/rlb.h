@@ -302,7 +302,10 @@ rlb_status rlb_get_tau(const rlb_ctx* ctx, double* tau);
  *   eps [GeV/fm^3] (Landau energy density incl. B), T [GeV], u^tau, u^x, u^y,
  *   M [GeV] (dynamical mass), P_L [GeV/fm^3] (tau^2 T^{YY}), M(T) [GeV].
  * `out` is host memory (synchronises `stream`) or device memory
- * (out_on_device != 0, asynchronous). */
+ * (out_on_device != 0, asynchronous).  The call runs the matching of the
+ * current state (Landau condition and EOS inversion, Sec. 4.4); the next
+ * rlb_step starts from it instead of repeating it, so stepping with per-step
+ * observables costs no extra matching and gives the same states bit for bit. */
 rlb_status rlb_moments(rlb_ctx* ctx, double* out, int out_on_device, void* stream);
 
 /* Grid observables of the current state (two host doubles; synchronises

@@ -40,7 +40,12 @@ struct rlb_ctx {
   // one step captured as a CUDA graph (on the first rlb_step), replayed after
   bool graphs = true;
   cudaStream_t gstream = nullptr;
-  cudaGraphExec_t gexec = nullptr;
+  cudaGraphExec_t gexec = nullptr;     // the full step
+  cudaGraphExec_t gexec_nm = nullptr;  // the step without its first matching (scf_fresh)
+  // the FP32/FP64 site scalars hold the matching of the current state (set by
+  // rlb_moments, which matches it anyway): the next step skips its first
+  // matching, which would repeat the same work with the same result
+  bool scf_fresh = false;
   cudaEvent_t gev[2] = {nullptr, nullptr};
   int stage_variant = 0;  // rlb_autotune's choice (see Stager)
   // adjoint workspace (caller-owned): offsets in bytes; per-node adjoints in
@@ -62,6 +67,13 @@ namespace {
 // matching: one site per thread; 64-thread blocks spread the FP64-heavy sites
 // evenly over the SMs (65,536 sites: 1,024 blocks, 6.7 per SM)
 constexpr int kMatchThreads = 64;
+
+// forget the captured steps (buffers, variant or matching state changed)
+void drop_graphs(rlb_ctx* ctx) {
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  if (ctx->gexec_nm) cudaGraphExecDestroy(ctx->gexec_nm);
+  ctx->gexec = ctx->gexec_nm = nullptr;
+}
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -447,6 +459,7 @@ struct Runner {
   static constexpr int NL = NTH * NPH;
 
   static rlb_status init(rlb_ctx* ctx, const double* eps_dev, cudaStream_t st) {
+    ctx->scf_fresh = false;
     rlbk::InitArgs<S, R, NXI, NTH, NPH> a;
     a.eps0 = eps_dev;
     a.eps_scale = rlb::kHbarc * rlb::kHbarc * rlb::kHbarc;
@@ -478,7 +491,7 @@ struct Runner {
 
   // One predictor-corrector step = match(f) -> stage(f -> f*) -> match(f*) -> stage(f*, f -> f),
   // enqueued on st (the host clock is not advanced here).
-  static rlb_status enqueue_step(rlb_ctx* ctx, cudaStream_t st) {
+  static rlb_status enqueue_step(rlb_ctx* ctx, cudaStream_t st, bool first_match = true) {
     S* f = reinterpret_cast<S*>(ctx->state + ctx->f_off);
     S* fs = reinterpret_cast<S*>(ctx->scratch + ctx->fs_off);
     double* m = reinterpret_cast<double*>(ctx->state + ctx->lnM_off);
@@ -490,7 +503,7 @@ struct Runner {
                                    reinterpret_cast<int*>(ctx->scratch + ctx->err_off));
     rlbk::Clock* clock = reinterpret_cast<rlbk::Clock*>(ctx->scratch + ctx->clock_off);
     // predictor: f* = f + dtau RHS(f) at tau
-    rlb_status r = match(ctx, mom, m, nullptr, st);
+    rlb_status r = first_match ? match(ctx, mom, m, nullptr, st) : RLB_OK;
     if (r) return r;
     {
       Timed tm(ctx, K_STAGE, st);
@@ -512,15 +525,16 @@ struct Runner {
   // One step captured once as a CUDA graph on the context's own stream (all of
   // its launch parameters are the same from step to step: the time lives in the
   // device clock).  A failed capture turns graphs off for the context.
-  static rlb_status ensure_graph(rlb_ctx* ctx) {
-    if (ctx->gexec) return RLB_OK;
+  static rlb_status ensure_graph(rlb_ctx* ctx, bool first_match = true) {
+    cudaGraphExec_t* ge = first_match ? &ctx->gexec : &ctx->gexec_nm;
+    if (*ge) return RLB_OK;
     if (!ctx->gstream) {
       RLB_CUDA(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking), "graph stream");
       RLB_CUDA(cudaEventCreateWithFlags(&ctx->gev[0], cudaEventDisableTiming), "graph event");
       RLB_CUDA(cudaEventCreateWithFlags(&ctx->gev[1], cudaEventDisableTiming), "graph event");
     }
     RLB_CUDA(cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal), "graph capture");
-    const rlb_status r = enqueue_step(ctx, ctx->gstream);
+    const rlb_status r = enqueue_step(ctx, ctx->gstream, first_match);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(ctx->gstream, &g);
     if (r != RLB_OK || e != cudaSuccess || !g) {
@@ -529,10 +543,10 @@ struct Runner {
       ctx->graphs = false;
       return r != RLB_OK ? r : cuda_fail(ctx, e, "graph capture");
     }
-    const cudaError_t ei = cudaGraphInstantiate(&ctx->gexec, g, 0);
+    const cudaError_t ei = cudaGraphInstantiate(ge, g, 0);
     cudaGraphDestroy(g);
     if (ei != cudaSuccess) {
-      ctx->gexec = nullptr;
+      *ge = nullptr;
       ctx->graphs = false;
       return cuda_fail(ctx, ei, "graph instantiate");
     }
@@ -541,11 +555,15 @@ struct Runner {
 
   static rlb_status step(rlb_ctx* ctx, int nsteps, cudaStream_t st) {
     if (nsteps <= 0) return RLB_OK;
-    if (ctx->graphs && !ctx->timing && ensure_graph(ctx) == RLB_OK) {
+    const bool skip = ctx->scf_fresh;  // the first step's matching is already done
+    ctx->scf_fresh = false;
+    const bool graphs = ctx->graphs && !ctx->timing && (!skip || ensure_graph(ctx, false) == RLB_OK) &&
+                        ((skip && nsteps == 1) || ensure_graph(ctx) == RLB_OK);
+    if (graphs) {
       RLB_CUDA(cudaEventRecord(ctx->gev[0], st), "graph order");
       RLB_CUDA(cudaStreamWaitEvent(ctx->gstream, ctx->gev[0], 0), "graph order");
       for (int s = 0; s < nsteps; ++s) {
-        RLB_CUDA(cudaGraphLaunch(ctx->gexec, ctx->gstream), "graph launch");
+        RLB_CUDA(cudaGraphLaunch(s == 0 && skip ? ctx->gexec_nm : ctx->gexec, ctx->gstream), "graph launch");
         ctx->tau += ctx->gp.dtau;
       }
       RLB_CUDA(cudaEventRecord(ctx->gev[1], ctx->gstream), "graph order");
@@ -553,7 +571,7 @@ struct Runner {
       return RLB_OK;
     }
     for (int s = 0; s < nsteps; ++s) {
-      rlb_status r = enqueue_step(ctx, st);
+      rlb_status r = enqueue_step(ctx, st, !(s == 0 && skip));
       if (r) return r;
       ctx->tau += ctx->gp.dtau;
     }
@@ -607,10 +625,8 @@ struct Runner {
     RLB_CUDA(cudaMemcpyAsync(Tsite, Tsave, ctx->ns * sizeof(double), cudaMemcpyDeviceToDevice, st), "autotune restore");
     RLB_CUDA(cudaStreamSynchronize(st), "autotune synchronise");
     ctx->stage_variant = best;
-    if (ctx->gexec) {  // the captured step used the previous choice
-      cudaGraphExecDestroy(ctx->gexec);
-      ctx->gexec = nullptr;
-    }
+    drop_graphs(ctx);  // the captured step used the previous choice
+    ctx->scf_fresh = false;
     if (nvar) *nvar = NV;
     return RLB_OK;
   }
@@ -713,6 +729,7 @@ struct Adjoint {
   // the adjoint buffers hold the adjoints of a step's output; the context state
   // is that step's input (at ctx->tau): replace them by the adjoints of the input
   static rlb_status step(rlb_ctx* ctx, cudaStream_t st) {
+    ctx->scf_fresh = false;
     return ctx->adj_prec == RLB_F32 ? step_t<float>(ctx, st) : step_t<double>(ctx, st);
   }
   template <class AR>
@@ -1008,7 +1025,7 @@ rlb_status rlb_create(rlb_ctx** out, int cuda_device) {
 
 void rlb_destroy(rlb_ctx* ctx) {
   if (!ctx) return;
-  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  drop_graphs(ctx);
   if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
   for (cudaEvent_t e : ctx->gev)
     if (e) cudaEventDestroy(e);
@@ -1134,10 +1151,8 @@ rlb_status rlb_bind_buffers(rlb_ctx* ctx, void* state, void* scratch, void* stre
   if (s) return s;
   ctx->state = static_cast<char*>(state);
   ctx->scratch = static_cast<char*>(scratch);
-  if (ctx->gexec) {  // captured with the previous buffers
-    cudaGraphExecDestroy(ctx->gexec);
-    ctx->gexec = nullptr;
-  }
+  drop_graphs(ctx);  // captured with the previous buffers
+  ctx->scf_fresh = false;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   RLB_CUDA(cudaMemcpyAsync(ctx->scratch + ctx->tab_off, ctx->tab.data.data(),
                            ctx->tab.data.size() * sizeof(double), cudaMemcpyHostToDevice, st),
@@ -1203,6 +1218,7 @@ rlb_status rlb_step(rlb_ctx* ctx, int nsteps, void* stream) {
 rlb_status rlb_step_static_scratch(rlb_ctx* ctx, void* state, int nsteps, void* stream) {
   if (!ctx || !state || nsteps < 0) return RLB_ERR_ARG;
   if (!ctx->grid_ok) return fail(ctx, RLB_ERR_STATE, "rlb_configure must come first");
+  ctx->scf_fresh = false;  // another state: the context's site scalars no longer describe it
   if ((uintptr_t)state & 255) return fail(ctx, RLB_ERR_ARG, "state must be 256-byte aligned");
   size_t sb, xb;
   layout(ctx->gp, ctx_shape(ctx), (size_t)ctx->eosp.points, &sb, &xb, nullptr);
@@ -1262,13 +1278,18 @@ rlb_status rlb_moments(rlb_ctx* ctx, double* out, int out_on_device, void* strea
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const double* mom = reinterpret_cast<const double*>(ctx->scratch + ctx->mom_off);
   const double* lnM = reinterpret_cast<const double*>(ctx->state + ctx->lnM_off);
-  if (out_on_device) return match(ctx, mom, lnM, out, st);
+  if (out_on_device) {
+    s = match(ctx, mom, lnM, out, st);
+    ctx->scf_fresh = s == RLB_OK;  // the next step's first matching is this one
+    return s;
+  }
   // host output: stage through the predictor buffer (free between steps)
   double* dev = reinterpret_cast<double*>(ctx->scratch + ctx->fs_off);
   if (ctx->ns * 8 * sizeof(double) > ctx->ns * ctx->nn * ctx->pop_bytes)
     return fail(ctx, RLB_ERR_ARG, "lattice too small to stage host moments");
   s = match(ctx, mom, lnM, dev, st);
   if (s) return s;
+  ctx->scf_fresh = true;
   RLB_CUDA(cudaMemcpyAsync(out, dev, ctx->ns * 8 * sizeof(double), cudaMemcpyDeviceToHost, st),
            "moments download");
   return rlb_check(ctx, stream);
@@ -1366,6 +1387,7 @@ rlb_status rlb_save_state(rlb_ctx* ctx, void* host_buf, size_t bytes, void* stre
 rlb_status rlb_load_state(rlb_ctx* ctx, const void* host_buf, size_t bytes, void* stream) {
   if (!ctx || !host_buf) return RLB_ERR_ARG;
   if (!ctx->bound) return fail(ctx, RLB_ERR_STATE, "rlb_bind_buffers must come first");
+  ctx->scf_fresh = false;
   BlobHeader want, got;
   blob_parts(ctx, &want);
   if (bytes < sizeof got) return fail(ctx, RLB_ERR_ARG, "state blob shorter than its header");
@@ -1507,10 +1529,7 @@ rlb_status rlb_set_stage_variant(rlb_ctx* ctx, int variant, int* n_variants) {
   if (variant < 0) return RLB_OK;  // query only
   if (variant >= (int)nv) return fail(ctx, RLB_ERR_ARG, "no such stage-kernel variant");
   ctx->stage_variant = variant;
-  if (ctx->gexec) {  // the captured step used the previous choice
-    cudaGraphExecDestroy(ctx->gexec);
-    ctx->gexec = nullptr;
-  }
+  drop_graphs(ctx);  // the captured step used the previous choice
   return RLB_OK;
 }
 
