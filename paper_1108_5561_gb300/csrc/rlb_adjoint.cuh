@@ -26,6 +26,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "rlb_kernels.cuh"
 
 namespace rlbk {
@@ -40,7 +42,8 @@ enum : int { AS_UT = 0, AS_UX, AS_UY, AS_INVT, AS_MEQ, AS_M, AS_ITR, AS_D, AS_KH
 template <class S, class AR, int NXI, int NTH, int NPH>
 struct AdjStageArgs {
   const S* f_in;       // stage input populations
-  const double* sc;    // FP64 matching of f_in, kSc per site
+  const double* sc;    // FP64 matching of f_in, kSc per site (AR = double)
+  const float* scf;    // FP32 matching of f_in, kSc per site (AR = float)
   const AR* ob;        // adjoint of the stage output populations (per node)
   const double* lb;    // adjoint of the stage output ln M (per site)
   AR* rbar;            // out: adjoint of r (per node)
@@ -127,10 +130,16 @@ __global__ void __launch_bounds__(NTH* NPH)
   load_line<S, T, NXI>(A.f_in + (size_t)i2 * NN + t * NXI, fx2);
   load_line<S, T, NXI>(A.f_in + (size_t)i3 * NN + t * NXI, fy1);
   load_line<S, T, NXI>(A.f_in + (size_t)i4 * NN + t * NXI, fy2);
-  const double* q = A.sc + (size_t)site * kSc;
-  const T ut = (T)q[SC_UT], ux = (T)q[SC_UX], uy = (T)q[SC_UY], invT = (T)q[SC_INVT], Meq = (T)q[SC_MEQ];
-  const T M = (T)q[SC_M], itr = (T)q[SC_ITR], D = (T)q[SC_D], Kh = (T)q[SC_KH], ax = (T)q[SC_AX],
-          ay = (T)q[SC_AY];
+  T q[kScUsed];  // site scalars of the matching of f_in
+  if constexpr (std::is_same<T, float>::value) {
+#pragma unroll
+    for (int i = 0; i < kScUsed; ++i) q[i] = A.scf[(size_t)site * kSc + i];
+  } else {
+#pragma unroll
+    for (int i = 0; i < kScUsed; ++i) q[i] = (T)A.sc[(size_t)site * kSc + i];
+  }
+  const T ut = q[SC_UT], ux = q[SC_UX], uy = q[SC_UY], invT = q[SC_INVT], Meq = q[SC_MEQ];
+  const T M = q[SC_M], itr = q[SC_ITR], D = q[SC_D], Kh = q[SC_KH], ax = q[SC_AX], ay = q[SC_AY];
   const T M2 = M * M;
 #pragma unroll
   for (int k = 0; k < NXI; ++k) fs[k * LD + t] = f[k];
@@ -299,7 +308,9 @@ __global__ void __launch_bounds__(NTH* NPH)
 // lbar) and of eta/s (ebar)
 // ---------------------------------------------------------------------------
 struct AdjMatchArgs {
-  const double* mom;   // FP64 moments of f_in, kMom per site
+  const double* mom;   // FP64 moments of f_in, kMom per site (when momf is null)
+  const float* momf;   // or their FP32 partial sums, kMom x kMomParts per site
+  const double* Tstart;  // Newton start of the EOS inversion (the matching's T)
   const double* lnM;
   const double* sbar;
   double* mbar;
@@ -358,7 +369,18 @@ __device__ __forceinline__ bool solve4(double (&Mx)[4][4], double (&b)[4]) {
 __global__ void __launch_bounds__(128) adj_match(const AdjMatchArgs A) {
   const int site = blockIdx.x * blockDim.x + threadIdx.x;
   if (site >= A.ns) return;
-  const double* m = A.mom + (size_t)site * kMom;
+  double m[kMom];
+  if (A.momf) {  // FP32 partials summed in FP64 (exact up to one FP64 rounding per sum)
+    const float4* p = reinterpret_cast<const float4*>(A.momf + (size_t)site * kMom * kMomParts);
+#pragma unroll
+    for (int i = 0; i < kMom; ++i) {
+      const float4 v = __ldg(p + i);
+      m[i] = ((double)v.x + (double)v.y) + ((double)v.z + (double)v.w);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < kMom; ++i) m[i] = A.mom[(size_t)site * kMom + i];
+  }
   const double lnM = A.lnM[site], M = exp(lnM);
   const double pref = M * M * M * M * (1.0 / (2.0 * 3.14159265358979323846 * 3.14159265358979323846));
   double tm[6];
@@ -368,7 +390,8 @@ __global__ void __launch_bounds__(128) adj_match(const AdjMatchArgs A) {
   int err = 0;
   if (!landau3(tm, u, &eps)) err |= ERR_LANDAU;
   double y = 0.0;
-  if (!eos_invert(A.eos, EOS_E, eps, log(0.3), &y)) err |= ERR_EOS;
+  const double T0 = A.Tstart ? A.Tstart[site] : 0.3;
+  if (!eos_invert(A.eos, EOS_E, eps, log(T0 > 0.0 ? T0 : 0.3), &y)) err |= ERR_EOS;
   const double T = exp(y);
   double e, de, xv, dx, Dv, dD, ih, dih;
   eos_field_dy(A.eos, y, EOS_E, &e, &de);

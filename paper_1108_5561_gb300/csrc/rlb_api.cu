@@ -54,6 +54,7 @@ struct rlb_ctx {
   int adj_prec = RLB_F64;
   size_t a_f = 0, a_l = 0, a_fb = 0, a_rb = 0, a_lin = 0, a_lbar = 0, a_sbar = 0, a_mbar = 0;
   size_t a_ebar = 0, a_mom = 0, a_sc = 0, a_T = 0, a_tot = 0, a_eps = 0, a_eta = 0;
+  size_t a_momf = 0, a_scf = 0;  // FP32 adjoint: moment partials and site scalars of the stage input
   // optional per-kernel timing (CUDA events on the launch stream)
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -162,6 +163,9 @@ size_t adj_layout(rlb_ctx* c) {
   c->a_mbar = off; off += align256(ns * rlbk::kMom * sizeof(double));
   c->a_mom = off; off += align256(ns * rlbk::kMom * sizeof(double));
   c->a_sc = off; off += align256(ns * rlbk::kSc * sizeof(double));
+  const bool f32 = c->adj_prec == RLB_F32;
+  c->a_momf = off; off += f32 ? align256(ns * rlbk::kMom * rlbk::kMomParts * sizeof(float)) : 0;
+  c->a_scf = off; off += f32 ? align256(ns * rlbk::kSc * sizeof(float)) : 0;
   c->a_tot = off; off += 256;
   c->a_eta = off; off += 256;
   return off;
@@ -674,7 +678,24 @@ struct Adjoint {
     const auto opa = make_ops<AR, NXI, NTH, NPH>(ctx->lat);
     const rlbk::GridMap gm = grid_map(ctx, ctx->scratch);
     int* err = reinterpret_cast<int*>(ctx->scratch + ctx->err_off);
-    {  // FP64 moments and matching of f_in
+    constexpr bool kF32 = std::is_same<AR, float>::value;
+    const unsigned nbm = (unsigned)((ctx->ns + kMatchThreads - 1) / kMatchThreads);
+    if constexpr (kF32) {  // FP32 moment partials and the FP32 matching (FP64 final steps) of f_in
+      rlbk::MomentsArgs<S, float, NXI, NTH, NPH> a;
+      a.f = f_in;
+      a.mom = nullptr;
+      a.momf = P<float>(ctx, ctx->a_momf);
+      a.op = opa;
+      rlbk::moments_kernel<S, float, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
+      RLB_CUDA(cudaGetLastError(), "adjoint moments launch");
+      rlbk::MatchArgs ma = match_args(ctx, nullptr, lnM_in, nullptr);
+      ma.momf = P<float>(ctx, ctx->a_momf);
+      ma.Tsite = D(ctx, ctx->a_T);
+      ma.sc = nullptr;
+      ma.scf = P<float>(ctx, ctx->a_scf);
+      rlbk::match_kernel<true><<<nbm, kMatchThreads, 0, st>>>(ma);
+      RLB_CUDA(cudaGetLastError(), "adjoint matching launch");
+    } else {  // FP64 moments and matching of f_in
       rlbk::MomentsArgs<S, double, NXI, NTH, NPH> a;
       a.f = f_in;
       a.mom = D(ctx, ctx->a_mom);
@@ -686,12 +707,13 @@ struct Adjoint {
       ma.Tsite = D(ctx, ctx->a_T);
       ma.sc = D(ctx, ctx->a_sc);
       ma.scf = nullptr;
-      rlbk::match_kernel<false><<<(unsigned)((ctx->ns + 127) / 128), 128, 0, st>>>(ma);
+      rlbk::match_kernel<false><<<nbm, kMatchThreads, 0, st>>>(ma);
       RLB_CUDA(cudaGetLastError(), "adjoint matching launch");
     }
     {
       rlbk::AdjStageArgs<S, AR, NXI, NTH, NPH> a;
-      a.f_in = f_in; a.sc = D(ctx, ctx->a_sc); a.ob = ob; a.lb = lb;
+      a.f_in = f_in; a.sc = D(ctx, ctx->a_sc); a.scf = kF32 ? P<float>(ctx, ctx->a_scf) : nullptr;
+      a.ob = ob; a.lb = lb;
       a.rbar = P<AR>(ctx, ctx->a_rb); a.fbar = P<AR>(ctx, ctx->a_fb); a.sbar = D(ctx, ctx->a_sbar);
       a.err = err; a.grid = gm; a.milne = (AR)milne; a.c = (AR)c; a.dtau = (AR)ctx->gp.dtau;
       a.inv2dx = (AR)(1.0 / (2.0 * ctx->gp.dx)); a.Z = (AR)ctx->eosp.Z; a.op = opa;
@@ -700,10 +722,12 @@ struct Adjoint {
     }
     {
       rlbk::AdjMatchArgs a;
-      a.mom = D(ctx, ctx->a_mom); a.lnM = lnM_in; a.sbar = D(ctx, ctx->a_sbar); a.mbar = D(ctx, ctx->a_mbar);
+      a.mom = D(ctx, ctx->a_mom); a.momf = kF32 ? P<float>(ctx, ctx->a_momf) : nullptr;
+      a.Tstart = D(ctx, ctx->a_T);  // the matching just made: the EOS inversion starts there
+      a.lnM = lnM_in; a.sbar = D(ctx, ctx->a_sbar); a.mbar = D(ctx, ctx->a_mbar);
       a.lbar = D(ctx, ctx->a_lbar); a.ebar = D(ctx, ctx->a_ebar); a.err = err; a.eos = eos_view(ctx);
       a.grid = gm; a.ns = (int)ctx->ns;
-      rlbk::adj_match<<<(unsigned)((ctx->ns + 127) / 128), 128, 0, st>>>(a);
+      rlbk::adj_match<<<nbm, kMatchThreads, 0, st>>>(a);
       RLB_CUDA(cudaGetLastError(), "adj_match launch");
       rlbk::sum_kernel<<<1, 1024, 0, st>>>(D(ctx, ctx->a_ebar), ctx->ns, D(ctx, ctx->a_eta), 1);
       RLB_CUDA(cudaGetLastError(), "adjoint eta sum launch");
