@@ -92,8 +92,9 @@ __device__ __forceinline__ void block_sum_t(T (&v)[NV], T* red) {
   }
 }
 
-// FP32 on the 768-node lattice: 7 resident blocks of 96 threads (at most 96
-// registers; 2.5 % faster gradients than the uncapped 120 registers)
+// FP32 on the 768-node lattice: 7 resident blocks of 96 threads (80 registers,
+// 16 bytes of spill; gradients 2.5 % faster than uncapped at 120 registers,
+// and 1 % faster than 6 blocks at 96 registers without spill)
 template <class S, class AR, int NXI, int NTH, int NPH>
 __global__ void __launch_bounds__(NTH* NPH, (sizeof(AR) == 4 && NTH * NPH <= 96) ? 7 : 1)
     adj_stage1(const __grid_constant__ AdjStageArgs<S, AR, NXI, NTH, NPH> A) {
