@@ -18,3 +18,21 @@ def oracle_mod():
     from oracle import oracle as o
     o.build()
     return o
+
+
+def golden(name: str) -> dict:
+    """name -> value from tests/golden/<name>: one 'key value' per line, '#'
+    comments carry the citation of each value."""
+    out = {}
+    with open(os.path.join(ROOT, "tests", "golden", name)) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                k, v = line.split()[:2]
+                out[k] = float(v)
+    return out
+
+
+@pytest.fixture(scope="session")
+def paper_values():
+    return golden("paper_values.txt")

@@ -18,9 +18,14 @@ import sys
 import numpy as np
 from scipy.integrate import solve_ivp
 
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+from tests.conftest import golden  # noqa: E402
+
+PAPER = golden("paper_values.txt")  # the run parameters and hydro coefficients of Sec. 4.5
 HC = 0.1973269804
 H3 = HC ** 3
-TAU0, T0, DTAU, TAU1 = 0.4, 0.4, 0.2, 10.0
+TAU0, T0, DTAU, TAU1 = 0.4, 0.4, PAPER["fig2_dtau_fm"], 10.0
+N_XI, N_TH, Z0 = int(PAPER["fig2_N_xi"]), int(PAPER["fig2_N_theta"]), PAPER["fig2_z0"]
 ETAS = (0.08, 0.5, math.inf)
 
 
@@ -30,8 +35,8 @@ def lattice_boltzmann(etas):
     from oracle.oracle import Oracle
 
     eps0 = Oracle(nx=1, ny=1).eos(T0)["eps"] / H3  # GeV/fm^3
-    g = rlb.GridParams(nx=1, ny=1, n_xi=5, n_theta=5, n_phi_half=1, prec=rlb.RLB_F64,
-                       eta_over_s=etas, tau0=TAU0, dtau=DTAU)
+    g = rlb.GridParams(nx=1, ny=1, n_xi=N_XI, n_theta=N_TH, n_phi_half=1, prec=rlb.RLB_F64,
+                       eta_over_s=etas, tau0=TAU0, dtau=DTAU, z0=Z0)
     run = rlb.Run(g)
     run.init_grid(np.array([[eps0]]))
     taus, Ts = [TAU0], [run.moments()[0, 1]]
@@ -54,8 +59,8 @@ def viscous_hydro(etas, taus):
         eps, Phi = y
         e = o.eos(o.solve_T(eps, 1))
         P, eta = e["p"], etas * e["s"]
-        tp = 5 * eta / (eps + P)
-        lam = 5.0 / 7.0 * eta * tp
+        tp = PAPER["hydro_tau_pi_coeff"] * eta / (eps + P)
+        lam = PAPER["hydro_lambda1_num"] / PAPER["hydro_lambda1_den"] * eta * tp
         return [-(eps + P) / t + Phi / t,
                 -Phi / tp + 4 * eta / (3 * tp * t) - 4 * Phi / (3 * t) - lam / (2 * tp * eta ** 2) * Phi ** 2]
 

@@ -24,9 +24,10 @@ def test_bessel_matches_scipy(oracle_mod):
         assert np.allclose(K, ref, rtol=2e-14, atol=0), (x, K, ref)
 
 
-def test_Z_qcd_constant(oracle_mod):
-    # Sec. 3.1: Z = pi^4/180 (4 (N_c^2 - 1) + 7 N_c N_f), N_c = N_f = 3
-    assert oracle_mod.Z_QCD == pytest.approx(math.pi ** 4 / 180 * 95, rel=1e-15)
+def test_Z_qcd_constant(oracle_mod, paper_values):
+    # Sec. 3.1: Z = pi^4/180 (4 (N_c^2 - 1) + 7 N_c N_f), N_c = N_f = 3 (fixture)
+    nc, nf = paper_values["N_c"], paper_values["N_f"]
+    assert oracle_mod.Z_QCD == pytest.approx(math.pi ** 4 / 180 * (4 * (nc * nc - 1) + 7 * nc * nf), rel=1e-15)
     assert oracle_mod.Z_QCD == pytest.approx(51.41035360127905, rel=1e-14)
 
 
