@@ -314,6 +314,7 @@ struct AdjMatchArgs {
   const double* mom;   // FP64 moments of f_in, kMom per site (when momf is null)
   const float* momf;   // or their FP32 partial sums, kMom x kMomParts per site
   const double* Tstart;  // Newton start of the EOS inversion (the matching's T)
+  const float* scf;    // FP32 adjoint: the FP32 matching of f_in (u and T taken from it)
   const double* lnM;
   const double* sbar;
   double* mbar;
@@ -391,10 +392,21 @@ __global__ void __launch_bounds__(128) adj_match(const AdjMatchArgs A) {
   for (int i = 0; i < 6; ++i) tm[i] = pref * m[1 + i];
   double u[3], eps;
   int err = 0;
-  if (!landau3(tm, u, &eps)) err |= ERR_LANDAU;
   double y = 0.0;
-  const double T0 = A.Tstart ? A.Tstart[site] : 0.3;
-  if (!eos_invert(A.eos, EOS_E, eps, log(T0 > 0.0 ? T0 : 0.3), &y)) err |= ERR_EOS;
+  if (A.scf) {
+    // FP32 adjoint: the velocity and temperature of the FP32 matching of the
+    // same moments; eps as the Rayleigh quotient u_mu T^{mu nu} u_nu
+    const float* q = A.scf + (size_t)site * kSc;
+    u[0] = q[SC_UT]; u[1] = q[SC_UX]; u[2] = q[SC_UY];
+    const double g0 = u[0], g1 = -u[1], g2 = -u[2];
+    eps = tm[0] * g0 * g0 + 2.0 * (tm[1] * g0 * g1 + tm[2] * g0 * g2 + tm[4] * g1 * g2) + tm[3] * g1 * g1 +
+          tm[5] * g2 * g2;
+    y = log((double)q[SC_T]);
+  } else {
+    if (!landau3(tm, u, &eps)) err |= ERR_LANDAU;
+    const double T0 = A.Tstart ? A.Tstart[site] : 0.3;
+    if (!eos_invert(A.eos, EOS_E, eps, log(T0 > 0.0 ? T0 : 0.3), &y)) err |= ERR_EOS;
+  }
   const double T = exp(y);
   double e, de, xv, dx, Dv, dD, ih, dih;
   eos_field_dy(A.eos, y, EOS_E, &e, &de);

@@ -724,6 +724,7 @@ struct Adjoint {
       rlbk::AdjMatchArgs a;
       a.mom = D(ctx, ctx->a_mom); a.momf = kF32 ? P<float>(ctx, ctx->a_momf) : nullptr;
       a.Tstart = D(ctx, ctx->a_T);  // the matching just made: the EOS inversion starts there
+      a.scf = kF32 ? P<float>(ctx, ctx->a_scf) : nullptr;  // FP32: u and T from that matching
       a.lnM = lnM_in; a.sbar = D(ctx, ctx->a_sbar); a.mbar = D(ctx, ctx->a_mbar);
       a.lbar = D(ctx, ctx->a_lbar); a.ebar = D(ctx, ctx->a_ebar); a.err = err; a.eos = eos_view(ctx);
       a.grid = gm; a.ns = (int)ctx->ns;
