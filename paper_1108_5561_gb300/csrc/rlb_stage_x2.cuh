@@ -180,11 +180,17 @@ __global__ void __launch_bounds__(NTH* NPH, MINB)
   static_assert(NL % 32 == 0, "whole warps (the warp reductions use every lane)");
   static_assert(NW <= kMomParts, "one moment slot per warp");
   constexpr int H = NTH / 2;
-  // staged site: pair p of line (l, j) at p * LDK + l * LDL + j (float2 units).
-  // LDL odd and LDK = 12 (mod 16) keep both the line-wise writes and the
-  // polar-line reads (consecutive l, then the next pair) nearly conflict free.
-  constexpr int LDL = NTH + 1;
-  constexpr int LDK = NPH * LDL + (((12 - NPH * LDL) % 16) + 16) % 16;
+  // staged site: pair p of line (l, j) at p * LDK + l * LDL + j (float2 units),
+  // LDL = NTH and LDK = NPH NTH + 1 (odd).  The polar items of a warp are the
+  // (pair, half) of its own LPW lines of fixed phi, half fastest across the
+  // lanes: with this layout the line-wise stores and loads of the owners and
+  // the item loads and stores all run at the minimum number of shared-memory
+  // wavefronts (768 nodes: 120 per site against 168 with the padded layout;
+  // 1.1 % faster stage).
+  constexpr int LDL = NTH;
+  constexpr int LDK = NPH * NTH + 1;
+  constexpr int LPW = 32 / NTH;  // lines of one phi per warp
+  static_assert(32 % NTH == 0, "the lines of one phi inside one warp");
   const auto& op = A.op;
   SiteLoc L[SPT];
   bool has2;
@@ -282,8 +288,8 @@ __global__ void __launch_bounds__(NTH* NPH, MINB)
   __syncthreads();
   const bool pol = milne != 0.f;
   if (pol) {  // polar lines (pair, l), one half of the outputs per item
-    for (int it = t; it < NXI * NPH; it += NL) {
-      const int lq = it % NPH, r = it / NPH, kp = r % NP, half = r / NP;
+    for (int it = (t & 31); it < LPW * NXI; it += 32) {  // this warp's items
+      const int lq = (t >> 5) * LPW + it / NXI, r = it % NXI, kp = r / 2, half = r % 2;
       const int base = kp * LDK + lq * LDL;
       float2 g[SPT][NTH];
 #pragma unroll
