@@ -80,22 +80,33 @@ def job_rate(units_per_rank: float, world: int, t_max: float) -> float:
 # DRAM traffic of the stage kernel on the 256 x 256 workload: ncu
 # dram__bytes_read.sum + dram__bytes_write.sum, mean of one predictor and one
 # corrector launch of `bench.py --steps 3 --warmup 3 --no-cpu-baseline --no-e2e`
-# on a GB300.  It describes the kernel sources it was taken on (their SHA-1) and
-# is reported only while they are unchanged.
+# on a GB300.  It describes the kernel sources it was taken on (the SHA-1 of
+# their code, comments removed) and is reported only while they are unchanged.
 STAGE_TRAFFIC = {"sources": ("rlb_stage_x2.cuh", "rlb_kernels.cuh"),
-                 "sha1": "8e10cc611997108aedb7024a5b8782ae4d403167", "bytes_per_launch": 478.9e6}
+                 "sha1": "2c31acf8d2461ce01901b255d5f07b1cc9a4feeb", "bytes_per_launch": 478.9e6}
+
+
+def code_digest(files) -> str:
+    """SHA-1 of the code of the given kernel sources with comments and
+    whitespace runs removed (a comment edit does not change the kernel)."""
+    import hashlib
+    import re
+    h = hashlib.sha1()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1108_5561_gb300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(re.sub(r"\s+", " ", src).encode())
+    return h.hexdigest()
 
 
 def stage_traffic(grid: int):
     """Measured DRAM bytes per stage launch, or None (other grid, changed kernel)."""
-    import hashlib
     if grid != 256:
         return None
-    h = hashlib.sha1()
-    for f in STAGE_TRAFFIC["sources"]:
-        with open(os.path.join(ROOT, "paper_1108_5561_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return STAGE_TRAFFIC["bytes_per_launch"] if h.hexdigest() == STAGE_TRAFFIC["sha1"] else None
+    ok = code_digest(STAGE_TRAFFIC["sources"]) == STAGE_TRAFFIC["sha1"]
+    return STAGE_TRAFFIC["bytes_per_launch"] if ok else None
 
 
 def peaks():

@@ -160,8 +160,11 @@ __device__ __forceinline__ void locate_sites(const GridMap& G, int bx, int by, S
 
 // SPT sites per CTA: with two, every per-node constant a thread loads (radial
 // and polar operator entries, radial tables) and every per-line scalar serves
-// both sites, and the warp reductions carry both sites' sums.  The arithmetic
-// of each site is the same as with one.
+// both sites, and the warp reductions carry both sites' sums; each site goes
+// through the same operations as with one.  On the 768-node lattice two sites
+// per CTA measured slower (0.211 against 0.191 ms per stage at 256^2: the
+// doubled live state leaves 7 resident CTAs instead of 12); the autotuner
+// keeps both.
 // MINB resident blocks per SM bound the registers.  768 nodes (96 threads):
 // 12 blocks, 56 registers; measured at 160^2: 75 us against 79 us uncapped (72
 // registers) and 89-93 us at 40 registers, which spill.  2048 nodes (128
