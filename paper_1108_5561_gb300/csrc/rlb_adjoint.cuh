@@ -167,15 +167,17 @@ __global__ void __launch_bounds__(NTH* NPH, (sizeof(AR) == 4 && NTH * NPH <= 96)
   const T vu = st * (cp * ux + sp * uy), A1 = st * (ax * cp + ay * sp), au = ax * ux + ay * uy;
   const T nsx = -st * fabs(cp) * A.inv2dx, nsy = -st * fabs(sp) * A.inv2dx;
   const T Gp = -invT * A1 * ut * M2, Hp = invT * A1 * M * vu, Jp = invT * M * au;
-  T E[NXI], feq[NXI], cc[NXI], fc[NXI], r[NXI], pu[NXI], wp[NXI];
+  // iE = 1/E_eq: one division per node, the other quotients become products
+  T E[NXI], iE[NXI], feq[NXI], cc[NXI], fc[NXI], r[NXI], pu[NXI], wp[NXI];
   T sums[3] = {k0, k0, k0};
 #pragma unroll
   for (int k = 0; k < NXI; ++k) {
     const T s = op.s[k], c = op.c[k], tv = op.tv[k];
     E[k] = sqrt(Meq * Meq + M2 * op.s2[k]);
+    iE[k] = k1 / E[k];
     feq[k] = A.Z * exp(-invT * (ut * E[k] - M * vu * s));
     cc[k] = itr * (ut - tv * vu);
-    fc[k] = Gp * op.q1[k] / E[k] + Hp * op.q2[k] + Jp * op.inv_c[k];
+    fc[k] = Gp * op.q1[k] * iE[k] + Hp * op.q2[k] + Jp * op.inv_c[k];
     const T Sx = k3 * f[k] - k4 * fx1[k] + fx2[k], Sy = k3 * f[k] - k4 * fy1[k] + fy2[k];
     r[k] = tv * (nsx * Sx + nsy * Sy) + A.milne * (mu2 * Drf[k] + pth[k]) + feq[k] * (fc[k] + cc[k]) -
            f[k] * cc[k];
@@ -237,12 +239,12 @@ __global__ void __launch_bounds__(NTH* NPH, (sizeof(AR) == 4 && NTH * NPH <= 96)
     b_itr += ccb * (ut - tv * vu);
     b_ut += ccb * itr;
     b_vu -= ccb * itr * tv;
-    b_Gp += fcb * op.q1[k] / E[k];
-    Eb -= fcb * Gp * op.q1[k] / (E[k] * E[k]);
+    b_Gp += fcb * op.q1[k] * iE[k];
+    Eb -= fcb * Gp * op.q1[k] * iE[k] * iE[k];
     b_Hp += fcb * op.q2[k];
     b_Jp += fcb * op.inv_c[k];
-    b_Meq += Eb * Meq / E[k];
-    b_M += Eb * M * op.s2[k] / E[k];
+    b_Meq += Eb * Meq * iE[k];
+    b_M += Eb * M * op.s2[k] * iE[k];
   }
   T b_A1 = k0, b_au = k0;
   b_invT -= b_Gp * A1 * ut * M2;
