@@ -398,7 +398,9 @@ __global__ void __launch_bounds__(NTH* NPH, MINB)
     }
     // d ln M / d tau from the consistency condition
     const float D = Dm[s];
-    const float g = (D == 0.f) ? 0.f : -D * Af / (Kh[s] + D * (4.f * Ef + Qf - Kh[s]));
+    // (fast quotient, 2 ulp: the denominator is a moment sum far inside its range;
+    // 1 % faster stage than the IEEE division)
+    const float g = (D == 0.f) ? 0.f : __fdividef(-D * Af, Kh[s] + D * (4.f * Ef + Qf - Kh[s]));
     if (t == 0 && (s == 0 || has2)) {
       const int site = L[s].site;
       if (!isfinite(g)) atomicOr(A.err, (int)ERR_NONFINITE);
