@@ -222,9 +222,11 @@ rlb_status rlb_load_state(rlb_ctx* ctx, const void* host_buf, size_t bytes, void
  * time it runs and replays it for every step; the caller's stream is ordered
  * before and after the replays with events, so the call stays asynchronous on
  * `stream`.  The launch parameters are the same for every step because the
- * proper time lives in a device clock.  rlb_set_graphs(ctx, 0) switches back
- * to plain launches (per-kernel timing does so by itself).  The graph is
- * recaptured after rlb_bind_buffers or rlb_autotune.
+ * proper time lives in a device clock.  A step that follows rlb_moments
+ * starts from the matching rlb_moments made and replays a second graph without
+ * the first matching.  rlb_set_graphs(ctx, 0) switches back to plain launches
+ * (per-kernel timing does so by itself).  The graphs are recaptured after
+ * rlb_bind_buffers, rlb_autotune or rlb_set_stage_variant.
  *
  * rlb_autotune times every compiled variant of the stage kernel for the
  * configured lattice and precision (packed FP32 kernel with one site per CTA,
