@@ -37,6 +37,18 @@ WORKLOAD = ("rlb-milne-2+1d 256x256 grid dx 0.1 fm, 768 nodes (8xi x 8theta x 12
 
 
 
+RECORD = None  # --record PATH: every JSON line is also appended there (JSONL)
+
+
+def emit(line: dict):
+    """Print the benchmark's JSON line (and append it to the run record)."""
+    text = json.dumps(line)
+    print(text, flush=True)
+    if RECORD:
+        with open(RECORD, "a") as fh:
+            fh.write(text + "\n")
+
+
 class Ranks:
     """One process per GPU (torchrun): rank and world size from the
     environment, a process group when there is more than one rank, a barrier,
@@ -199,7 +211,7 @@ def reference_arm(args, rank, world):
         "e2e": {"value": rate, "unit": "updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line), flush=True)
+    emit(line)
     return 0
 
 
@@ -318,7 +330,7 @@ def batch_main(args, rank, world, local):
                          "stage_ms_per_launch": stage_ms / stage_n, "match_ms_per_launch": match_ms / match_n},
             "e2e": e2e, "gpu_launches": 4 * args.steps, "clocks": clocks, "cpu_baseline": cpu,
         }
-        print(json.dumps(line), flush=True)
+        emit(line)
     ranks.close()
     return 0
 
@@ -409,7 +421,7 @@ def sweep_main(args, rank, world, local):
                                                                       "max_rel_error": errs}},
             "e2e": None, "gpu_launches": 4 * args.steps, "clocks": clocks, "cpu_baseline": None,
         }
-        print(json.dumps(line), flush=True)
+        emit(line)
     return 0
 
 
@@ -495,7 +507,7 @@ def adjoint_main(args, rank, world, local):
                        "parallelism": "single GPU"},
             "roofline": None, "e2e": None, "gpu_launches": None, "clocks": clocks, "cpu_baseline": None,
         }
-        print(json.dumps(line), flush=True)
+        emit(line)
     return 0
 
 
@@ -515,7 +527,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling)")
     ap.add_argument("--grid", type=int, default=256,
                     help="grid side; the benchmark workload is 256 (smaller sides for profiling)")
+    ap.add_argument("--record", default=None, help="also append the JSON line to this JSONL file")
     args = ap.parse_args()
+    global RECORD
+    RECORD = args.record
     if args.steps is None:
         args.steps = {"batch": 40, "sweep": 500, "adjoint": 300}.get(args.workload, 1000)
     global NX, NY
@@ -685,7 +700,7 @@ def finish(args, rank, world, t, value, achieved, peak, peak_kind, b, nn, launch
             "clocks": clocks,
             "cpu_baseline": cpu,
         }
-        print(json.dumps(line), flush=True)
+        emit(line)
     ranks.close()
     return 0
 

@@ -78,3 +78,13 @@ def test_reference_arm_line(oracle_mod, monkeypatch):
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["metric"] == "site-population updates/s"
+
+
+def test_run_record_appends_jsonl(tmp_path, monkeypatch):
+    path = tmp_path / "runs.jsonl"
+    monkeypatch.setattr(bench, "RECORD", str(path))
+    args = argparse.Namespace(steps=1, warmup=0, gpus=1)
+    for _ in range(2):
+        d = _line(lambda: bench.reference_arm(args, 0, 1))
+    rows = [json.loads(x) for x in path.read_text().splitlines()]
+    assert len(rows) == 2 and rows[-1] == d
