@@ -16,6 +16,7 @@
 #include "rlb_host.hpp"
 #include "rlb_kernels.cuh"
 #include "rlb_stage_x2.cuh"
+#include "rlb_stage_mp.cuh"
 #include "rlb_adjoint.cuh"
 
 struct rlb_ctx {
@@ -30,7 +31,9 @@ struct rlb_ctx {
   size_t f_off = 0, lnM_off = 0;  // state
   size_t fs_off = 0, lnMs_off = 0, T_off = 0, err_off = 0, tab_off = 0, eps_off = 0;  // scratch
   size_t mom_off = 0, moms_off = 0, sc_off = 0, tabf_off = 0, scf_off = 0;
-  size_t ev_off = 0, loc_off = 0, clock_off = 0;
+  size_t ev_off = 0, loc_off = 0, clock_off = 0, lines_off = 0;
+  // per-thread line constants of the mirror-paired stage kernel (rlbk::LineMP)
+  std::vector<unsigned char> lines_mp;
   // events: one for a single grid, n for a batch (with a per-site locator)
   std::vector<rlbk::EventInfo> events;
   std::vector<int2> loc;
@@ -47,7 +50,7 @@ struct rlb_ctx {
   // matching, which would repeat the same work with the same result
   bool scf_fresh = false;
   cudaEvent_t gev[2] = {nullptr, nullptr};
-  int stage_variant = 0;  // rlb_autotune's choice (see Stager)
+  int stage_variant = -1;  // rlb_autotune's choice (see Stager); -1: the default of the lattice
   // adjoint workspace (caller-owned): offsets in bytes; per-node adjoints in
   // FP64 or FP32 (adj_prec, RLB_F64 or RLB_F32), per-site quantities in FP64
   char* adj = nullptr;
@@ -101,6 +104,15 @@ bool supported_shape(int nxi, int nth, int nph) {
          (nxi == 8 && nth == 8 && nph == 2);
 }
 
+// L2 prefetch distance of the mirror-paired stage kernel, in waves of resident
+// CTAs: a CTA prefetches the populations of the CTA launched this many waves
+// after it
+constexpr int kPrefetchWaves = 1;
+
+// room for the line constants of the mirror-paired stage kernel: (N_theta/2)
+// N_phi entries of 32 + 8 N_theta bytes (the largest lattice: 64 x 96 B)
+constexpr size_t kLinesBytes = 16384;
+
 // sites and events of a configuration (one grid or a batch of events)
 struct Shape {
   size_t ns, events;
@@ -134,9 +146,10 @@ void layout(const rlb_grid_params& g, const Shape& sh, size_t table_points, size
   size_t ev_off = off; off += align256(sh.events * sizeof(rlbk::EventInfo));
   size_t loc_off = off; off += sh.events > 1 ? align256(ns * sizeof(int2)) : 0;
   size_t clock_off = off; off += 256;
+  size_t lines_off = off; off += kLinesBytes;
   *scratch_b = off;
   if (c) {
-    c->ev_off = ev_off; c->loc_off = loc_off; c->clock_off = clock_off;
+    c->ev_off = ev_off; c->loc_off = loc_off; c->clock_off = clock_off; c->lines_off = lines_off;
     c->f_off = f_off; c->lnM_off = lnM_off;
     c->fs_off = fs_off; c->lnMs_off = lnMs_off; c->T_off = T_off; c->eps_off = eps_off;
     c->err_off = err_off; c->tab_off = tab_off;
@@ -226,6 +239,63 @@ rlbk::OpsX2<NXI, NTH, NPH> make_ops_x2(const rlb::Lattice& L) {
   return o;
 }
 
+// Per-thread line constants of stage_kernel_mp (rlbk::LineMP<H>, H = N_theta/2):
+// thread slot q = l H + j of a site owns the polar lines j and N_theta - 1 - j
+// at azimuth l.  The mirror lines share sin(theta), mu^2 and the polar weight
+// (averaged over the pair, equal up to rounding), and the even and odd blocks
+// of the polar operator come from its rows j < H.
+std::vector<unsigned char> make_lines_mp(const rlb::Lattice& L, double dx) {
+  const int nth = L.nth, nph = L.nph, H = nth / 2;
+  const size_t esz = 32 + 16 * (size_t)H;
+  std::vector<unsigned char> out(esz * H * nph, 0);
+  for (int l = 0; l < nph; ++l)
+    for (int jp = 0; jp < H; ++jp) {
+      float* e = reinterpret_cast<float*>(out.data() + esz * (size_t)(l * H + jp));
+      const int jb = nth - 1 - jp;
+      const double st = 0.5 * (L.sth[jp] + L.sth[jb]);
+      const double mu2 = 0.5 * (L.mu[jp] * L.mu[jp] + L.mu[jb] * L.mu[jb]);
+      const double wj = 0.5 * (L.wth[jp] + L.wth[jb]) / (2.0 * nph);
+      const double cp = L.cph[l], sp = L.sph[l];
+      e[0] = (float)st; e[1] = (float)mu2; e[2] = (float)wj; e[3] = (float)cp;
+      e[4] = (float)sp; e[5] = (float)(-st * std::fabs(cp) / (2.0 * dx));
+      e[6] = (float)(-st * std::fabs(sp) / (2.0 * dx)); e[7] = 0.f;
+      float* ae = e + 8;
+      float* ao = e + 8 + 2 * H;
+      for (int i = 0; i < H; ++i) {
+        const double d0 = L.Dth[jp * nth + i], d1 = L.Dth[jp * nth + (nth - 1 - i)];
+        ae[2 * i] = ae[2 * i + 1] = (float)(0.5 * (d0 + d1));
+        ao[2 * i] = ao[2 * i + 1] = (float)(0.5 * (d0 - d1));
+      }
+    }
+  return out;
+}
+
+template <int NXI>
+rlbk::OpsMP<NXI> make_ops_mp(const rlb::Lattice& L) {
+  rlbk::OpsMP<NXI> o;
+  constexpr int NP = NXI / 2;
+  auto pr = [](double a, double b) { return make_float2((float)a, (float)b); };
+  for (int k = 0; k < NXI; ++k)
+    for (int p = 0; p < NP; ++p) o.Drb[k * NP + p] = pr(L.Dr[(2 * p) * NXI + k], L.Dr[(2 * p + 1) * NXI + k]);
+  for (int p = 0; p < NP; ++p) {
+    double c[2], s[2], e[2];
+    for (int h = 0; h < 2; ++h) { c[h] = L.c[2 * p + h]; s[h] = L.s[2 * p + h]; e[h] = L.ecw[2 * p + h]; }
+    o.tv[p] = pr(s[0] / c[0], s[1] / c[1]);
+    o.s[p] = pr(s[0], s[1]);
+    o.q2[p] = pr(s[0] * s[0] / c[0], s[1] * s[1] / c[1]);
+    o.ic[p] = pr(1.0 / c[0], 1.0 / c[1]);
+    o.Cw[p] = pr(c[0] * std::sqrt(e[0]), c[1] * std::sqrt(e[1]));
+    o.Sw[p] = pr(s[0] * std::sqrt(e[0]), s[1] * std::sqrt(e[1]));
+    o.w0[p] = pr(e[0], e[1]);
+    o.w1[p] = pr(e[0] * c[0] * s[0], e[1] * c[1] * s[1]);
+    o.w2[p] = pr(e[0] * c[0] * c[0], e[1] * c[1] * c[1]);
+    o.w3[p] = pr(e[0] * s[0] * s[0], e[1] * s[1] * s[1]);
+    o.s2[p] = pr(s[0] * s[0], s[1] * s[1]);
+    o.q1[p] = pr(s[0] * (s[0] * s[0] + 1.0) / c[0], s[1] * (s[1] * s[1] + 1.0) / c[1]);
+  }
+  return o;
+}
+
 // Table geometry of an EosView, including the split constants of the FP32 cell
 // location (see EosView).
 void eos_geometry(const rlb::EosTable& tab, rlbk::EosView* v) {
@@ -276,6 +346,9 @@ rlbk::GridMap grid_map(const rlb_ctx* c, char* scr) {
 
 // event, row and clock tables into a scratch block (host memory of the context)
 rlb_status upload_tables(rlb_ctx* ctx, char* scr, cudaStream_t st) {
+  if (!ctx->lines_mp.empty())
+    RLB_CUDA(cudaMemcpyAsync(scr + ctx->lines_off, ctx->lines_mp.data(), ctx->lines_mp.size(),
+                             cudaMemcpyHostToDevice, st), "line table upload");
   RLB_CUDA(cudaMemcpyAsync(scr + ctx->ev_off, ctx->events.data(), ctx->events.size() * sizeof(rlbk::EventInfo),
                            cudaMemcpyHostToDevice, st), "event table upload");
   if (ctx->events.size() > 1)
@@ -364,20 +437,25 @@ template <class S, class R, int NXI, int NTH, int NPH>
 struct Stager {
   static constexpr bool kX2 =
       std::is_same<R, float>::value && NXI % 2 == 0 && NTH % 2 == 0 && (NTH * NPH) % 32 == 0;
+  using MPS = rlbk::MPShape<NTH, NPH>;
+  static constexpr bool kMP = kX2 && NXI <= 8 && MPS::NT % 32 == 0 && MPS::TS % 16 == 0 && 16 % MPS::H == 0;
   static constexpr int NL = NTH * NPH;
   // variants the autotuner times: packed kernel with the register cap, packed
-  // without it, generic kernel, packed with two sites per CTA (capped, uncapped)
-  // (lattices the packed kernel does not take: generic only)
-  static constexpr int kVariants = kX2 ? 5 : 1;
+  // without it, generic kernel, packed with two sites per CTA (capped,
+  // uncapped), mirror-paired kernel (lattices the packed kernel does not take:
+  // generic only)
+  static constexpr int kVariants = kMP ? 6 : (kX2 ? 5 : 1);
+  static constexpr int kDefault = kMP ? 5 : 0;  // used until rlb_autotune or rlb_set_stage_variant choose
   static_assert(kVariants <= RLB_MAX_STAGE_VARIANTS, "rlb_autotune output size");
   rlbk::StageArgs<S, R, NXI, NTH, NPH> a;
   rlbk::StageArgsX2<S, NXI, NTH, NPH> b;
+  rlbk::StageArgsMP<S, NXI, NTH, NPH> c;
   dim3 grid, grid2;
   int variant = 0;
 
   // scr: the scratch block holding the event tables and the clock
   Stager(const rlb_ctx* ctx, char* scr, const double* sc, const float* scf, int* err) {
-    variant = ctx->stage_variant < kVariants ? ctx->stage_variant : 0;
+    variant = (ctx->stage_variant >= 0 && ctx->stage_variant < kVariants) ? ctx->stage_variant : kDefault;
     grid = site_grid(ctx);
     grid2 = site_pair_grid(ctx);
     const double dtau = ctx->gp.dtau, inv2dx = 1.0 / (2.0 * ctx->gp.dx);
@@ -400,6 +478,21 @@ struct Stager {
       b.inv2dx_r = (float)inv2dx;
       b.log2Z = (float)std::log2(ctx->eosp.Z);
       b.op = make_ops_x2<NXI, NTH, NPH>(ctx->lat);
+      if constexpr (kMP) {
+        c.scf = scf; c.err = err; c.grid = gm; c.clock = clock;
+        c.lines = reinterpret_cast<const rlbk::LineMP<NTH / 2>*>(scr + ctx->lines_off);
+        c.milne_on = ctx->gp.metric == RLB_MILNE;
+        c.dtau = dtau;
+        c.dtau_r = (float)dtau;
+        c.log2Z = (float)std::log2(ctx->eosp.Z);
+        c.op = make_ops_mp<NXI>(ctx->lat);
+        c.prefetch_ahead = 0;
+        int per_sm = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rlbk::stage_kernel_mp<S, NXI, NTH, NPH>,
+                                                          MPS::NT, 0) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) == cudaSuccess)
+          c.prefetch_ahead = kPrefetchWaves * per_sm * sms;
+      }
     } else {
       a.sc = sc;
       a.scf = scf;
@@ -421,6 +514,15 @@ struct Stager {
   // device clock's.
   void launch(const S* f_in, const double* lnM_in, const S* f_base, const double* lnM_base, S* f_out,
               double* lnM_out, double* mom_out, int mode, cudaStream_t st) {
+    if constexpr (kMP) {
+      if (variant == 5) {
+        c.f_in = f_in; c.lnM_in = lnM_in; c.f_base = f_base; c.lnM_base = lnM_base;
+        c.f_out = f_out; c.lnM_out = lnM_out; c.momf_out = reinterpret_cast<float*>(mom_out);
+        c.mode = mode;
+        rlbk::stage_kernel_mp<S, NXI, NTH, NPH><<<MPS::SPC == 2 ? grid2 : grid, MPS::NT, 0, st>>>(c);
+        return;
+      }
+    }
     if constexpr (kX2) {
       if (variant != 2) {
         constexpr int kMinb2 = NL <= 96 ? 6 : 2;  // two sites per CTA: resident blocks per SM
@@ -462,9 +564,13 @@ template <class S, class R, int NXI, int NTH, int NPH>
 struct Runner {
   static constexpr int NL = NTH * NPH;
 
+  // The initial populations are computed in FP64 for every storage precision
+  // and rounded once to S (an FP32 evaluation of the equilibrium exponent,
+  // up to 40 in magnitude, would start the run 1e-6 away from the exact
+  // initial state).
   static rlb_status init(rlb_ctx* ctx, const double* eps_dev, cudaStream_t st) {
     ctx->scf_fresh = false;
-    rlbk::InitArgs<S, R, NXI, NTH, NPH> a;
+    rlbk::InitArgs<S, double, NXI, NTH, NPH> a;
     a.eps0 = eps_dev;
     a.eps_scale = rlb::kHbarc * rlb::kHbarc * rlb::kHbarc;
     a.f = reinterpret_cast<S*>(ctx->state + ctx->f_off);
@@ -477,7 +583,7 @@ struct Runner {
     a.Z = ctx->eosp.Z;
     a.family = ctx->gp.family;
     a.T0 = ctx->gp.T0;
-    a.op = make_ops<R, NXI, NTH, NPH>(ctx->lat);
+    a.op = make_ops<double, NXI, NTH, NPH>(ctx->lat);
     // (T, M_eq, M) per site in the FP64 site-scalar scratch (free until the first matching)
     double* tsm = reinterpret_cast<double*>(ctx->scratch + ctx->sc_off);
     a.tsm = tsm;
@@ -487,7 +593,7 @@ struct Runner {
     {
       Timed tm(ctx, K_INIT, st);
       rlbk::init_site_kernel<<<(unsigned)((ctx->ns + 127) / 128), 128, 0, st>>>(b);
-      rlbk::init_kernel<S, R, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
+      rlbk::init_kernel<S, double, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
     }
     RLB_CUDA(cudaGetLastError(), "init_kernel launch");
     return RLB_OK;
@@ -1129,6 +1235,9 @@ rlb_status rlb_configure(rlb_ctx* ctx, const rlb_grid_params* g) {
     }
   }
   ctx->gp = *g;
+  ctx->lines_mp.clear();
+  if (g->n_theta % 2 == 0) ctx->lines_mp = make_lines_mp(ctx->lat, g->dx);
+  if (ctx->lines_mp.size() > kLinesBytes) return fail(ctx, RLB_ERR_ARG, "line table larger than its scratch region");
   set_events(ctx, {rlbk::EventInfo{0, g->nx, g->ny, 0, g->eta_over_s, 0.0}});
   ctx->nn = (size_t)g->n_xi * g->n_theta * 2 * g->n_phi_half;
   ctx->pop_bytes = pop_size(g->prec);

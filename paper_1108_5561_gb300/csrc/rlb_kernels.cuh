@@ -1254,6 +1254,16 @@ __global__ void __launch_bounds__(NTH* NPH)
   if (t == 0) {
     if constexpr (sizeof(R) == 4) {
       store_mom_parts(A.momf + (size_t)site * kMom * kMomParts, redf);
+    } else if constexpr (sizeof(S) < 8) {
+      // FP64 sums for a path whose matching reads FP32 partial sums: each
+      // sum as its (hi, lo) FP32 split, recombined there by TwoSum
+      float pairs[2 * kMom];
+#pragma unroll
+      for (int q = 0; q < kMom; ++q) {
+        pairs[2 * q] = (float)redd[q];
+        pairs[2 * q + 1] = (float)(redd[q] - (double)pairs[2 * q]);
+      }
+      store_mom_parts(A.momf + (size_t)site * kMom * kMomParts, pairs);
     } else {
 #pragma unroll
       for (int q = 0; q < kMom; ++q) A.mom[(size_t)site * kMom + q] = redd[q];

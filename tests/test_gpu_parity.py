@@ -139,7 +139,27 @@ def test_fp32_hotspots_parity(oracle_mod):
     _, mg, mo, _ = run_pair(oracle_mod, g, eps0, 150)
     e = errors(mg, mo)
     print("fp32 errors", e)
-    assert e["eps"] < 1e-5 and e["T"] < 1e-5 and e["u"] < 1e-5, e
+    assert np.abs(mo[:, 3:5]).max() > 1e-2  # developed transverse flow
+    assert e["eps"] < 1e-5 and e["T"] < 1e-5 and e["u"] < 1e-5 and e["uperp"] < 1e-5, e
+
+
+def test_fp32_config2_window_full_run(oracle_mod):
+    # The 256x256 hotspot workload at its stated length: the central 32x32
+    # window of its initial condition (40 hotspots, seed 1108; the densest part
+    # of the grid), periodic, FP32 populations, eta/s = 0.16, 1000 steps of
+    # dtau = 0.0036 fm/c from tau = 0.4 fm/c, against the FP64 oracle.  uperp is
+    # |du_perp| / max |u_perp|: the flow is developed (max |u_perp| 0.33 at step
+    # 150, 0.11 at the end).
+    n = 256
+    full, _, _ = hotspots(n, n, n=40, seed=1108)
+    eps0 = full[112:144, 112:144].copy()
+    g = rlb.GridParams(nx=32, ny=32, dx=0.1, prec=rlb.RLB_F32, eta_over_s=0.16, tau0=0.4, dtau=0.0036)
+    run, mg, mo, _ = run_pair(oracle_mod, g, eps0, 1000)
+    assert run.tau == pytest.approx(4.0, rel=1e-12)
+    e = errors(mg, mo)
+    print("config-2 window, 1000 steps", e)
+    assert np.abs(mo[:, 3:5]).max() > 0.05
+    assert e["eps"] < 1e-5 and e["T"] < 1e-5 and e["u"] < 1e-5 and e["uperp"] < 1e-5, e
 
 
 def test_fp32_full_size_sampled(oracle_mod):

@@ -2,9 +2,10 @@
 one or two sites per CTA, with or without its register cap, does the same
 per-site arithmetic up to the compiler's fusing of scalar multiply-adds (which
 may differ between the instantiations), so the variants agree to FP32
-rounding; so does the generic kernel (other operation order).  Odd row lengths
-and odd site counts exercise the CTA whose second site is missing (it repeats
-the first and stores nothing)."""
+rounding; so do the generic kernel and the mirror-paired kernel (other
+operation order: the polar operator on even and odd parts, E_eq from a
+reciprocal square root).  Odd row lengths and odd site counts exercise the CTA
+whose second site is missing (it repeats the first and stores nothing)."""
 import numpy as np
 import pytest
 
@@ -19,6 +20,7 @@ from paper_1108_5561_gb300.inputs import hotspots  # noqa: E402
 
 PACKED = [0, 1, 3, 4]  # one site (capped, uncapped), two sites (capped, uncapped)
 GENERIC = 2
+MIRROR = [5]  # mirror-paired polar lines (8 x 8 x 12 lattice; the default there)
 
 
 def _grid(nx, ny, prec=rlb.RLB_F32, **lat):
@@ -29,7 +31,7 @@ def _grid(nx, ny, prec=rlb.RLB_F32, **lat):
 def _evolve(g, variant, eps, events=None, steps=8):
     r = rlb.Run(g, events=events)
     n = r.set_stage_variant(variant)
-    assert n == 5
+    assert n == (6 if g.n_xi == 8 and g.n_theta == 8 and g.n_phi_half == 6 else 5)
     r.init_grid(eps)
     r.step(steps)
     r.check()
@@ -78,8 +80,46 @@ def test_bf16_lattice16_packed_variants_agree():
         _same(ref, _evolve(g, v, eps, steps=4), tol=2e-2)  # BF16 storage: one rounding step apart
 
 
+@pytest.mark.parametrize("variant", MIRROR)
+@pytest.mark.parametrize("nx,ny", [(23, 17), (24, 16), (1, 5), (2, 3), (3, 1)])
+def test_mirror_paired_variants_within_fp32_rounding(nx, ny, variant):
+    g = _grid(nx, ny)
+    eps, _, _ = hotspots(nx, ny, n=4, seed=31 + nx, spread=0.4)
+    _same(_evolve(g, 0, eps), _evolve(g, variant, eps), tol=1e-5)
+
+
+def test_mirror_paired_variant_on_a_grid_larger_than_one_wave():
+    # more CTAs than fit on the GPU at once: the L2 prefetch of the CTA one wave
+    # ahead reaches real sites, and the last wave's prefetches fall off the end
+    g = _grid(160, 150)
+    eps, _, _ = hotspots(160, 150, n=20, seed=9, spread=2.0)
+    _same(_evolve(g, 0, eps, steps=3), _evolve(g, MIRROR[0], eps, steps=3), tol=1e-5)
+
+
+@pytest.mark.parametrize("variant", MIRROR)
+def test_mirror_paired_variants_on_a_batch_with_an_odd_site_count(variant):
+    events = [rlb.Event(7, 5, 0.08), rlb.Event(12, 9, 0.2), rlb.Event(4, 3, 0.3)]
+    g = rlb.GridParams(dx=0.1, prec=rlb.RLB_F32, tau0=0.4, dtau=0.0036)
+    eps = np.concatenate([hotspots(e.nx, e.ny, n=3, seed=7 + i, spread=0.4)[0].reshape(-1)
+                          for i, e in enumerate(events)])
+    _same(_evolve(g, 0, eps, events=events), _evolve(g, variant, eps, events=events), tol=1e-5)
+
+
+@pytest.mark.parametrize("variant", MIRROR)
+def test_mirror_paired_variants_bf16_and_minkowski(variant):
+    g = _grid(9, 7, prec=rlb.RLB_BF16)
+    eps, _, _ = hotspots(9, 7, n=3, seed=2, spread=0.4)
+    _same(_evolve(g, 0, eps, steps=4), _evolve(g, variant, eps, steps=4), tol=2e-2)
+    g = rlb.GridParams(nx=6, ny=5, dx=0.1, prec=rlb.RLB_F32, metric=rlb.RLB_MINKOWSKI, eta_over_s=0.12,
+                       tau0=1.0, dtau=0.0036)
+    eps, _, _ = hotspots(6, 5, n=3, seed=4, spread=0.3)
+    _same(_evolve(g, 0, eps), _evolve(g, variant, eps), tol=1e-5)
+
+
 def test_set_stage_variant_rejects_unknown_numbers():
     r = rlb.Run(_grid(4, 4))
-    assert r.set_stage_variant(-1) == 5
+    assert r.set_stage_variant(-1) == 6
     with pytest.raises(rlb.RLBError):
-        r.set_stage_variant(5)
+        r.set_stage_variant(6)
+    r = rlb.Run(_grid(4, 4, n_xi=16, n_phi_half=8))
+    assert r.set_stage_variant(-1) == 5
