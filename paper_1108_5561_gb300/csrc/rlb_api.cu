@@ -51,6 +51,10 @@ struct rlb_ctx {
   bool scf_fresh = false;
   cudaEvent_t gev[2] = {nullptr, nullptr};
   int stage_variant = -1;  // rlb_autotune's choice (see Stager); -1: the default of the lattice
+  // mean relative error of the hardware 2^x of the FP32 stage kernels on this
+  // device (ex2_bias_kernel), measured once per context
+  double ex2_bias = 0.0;
+  bool ex2_measured = false;
   // adjoint workspace (caller-owned): offsets in bytes; per-node adjoints in
   // FP64 or FP32 (adj_prec, RLB_F64 or RLB_F32), per-site quantities in FP64
   char* adj = nullptr;
@@ -296,6 +300,41 @@ rlbk::OpsMP<NXI> make_ops_mp(const rlb::Lattice& L) {
   return o;
 }
 
+// Mean relative error of the hardware approximation of 2^x used for the
+// equilibrium in the FP32 stage kernels (ex2.approx.ftz), over x in [-60, 0]
+// (the exponents of f_eq): 65,536 arguments against the FP64 exp2, summed in
+// FP64 into *out (zeroed by the caller).  The errors of the approximation are
+// not centred on zero (-5.2e-8 on GB300), and a factor common to every f_eq
+// makes the collision term create or remove energy at that rate, so the
+// stage kernel divides Z by 1 + the mean.
+__global__ void ex2_bias_kernel(double* out) {
+  constexpr int N = 1 << 16;
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const float x = -60.f * ((float)i + 0.5f) / (float)N;
+    acc += (double)rlbk::ex2_ftz(x) / exp2((double)x) - 1.0;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, acc / N);
+}
+
+// Measure ex2_bias_kernel's mean once per context, using 8 bytes of `scr` at
+// `off` (free at the time of the call) and synchronising the stream.
+rlb_status measure_ex2_bias(rlb_ctx* ctx, char* scr, size_t off, cudaStream_t st) {
+  if (ctx->ex2_measured) return RLB_OK;
+  double* d = reinterpret_cast<double*>(scr + off);
+  RLB_CUDA(cudaMemsetAsync(d, 0, sizeof(double), st), "ex2 bias reset");
+  ex2_bias_kernel<<<64, 256, 0, st>>>(d);
+  RLB_CUDA(cudaGetLastError(), "ex2_bias_kernel launch");
+  double b = 0.0;
+  RLB_CUDA(cudaMemcpyAsync(&b, d, sizeof(double), cudaMemcpyDeviceToHost, st), "ex2 bias read");
+  RLB_CUDA(cudaStreamSynchronize(st), "ex2 bias synchronise");
+  if (!(std::fabs(b) < 1e-6)) return fail(ctx, RLB_ERR_NUMERIC, "hardware 2^x error outside its expected range");
+  ctx->ex2_bias = b;
+  ctx->ex2_measured = true;
+  return RLB_OK;
+}
+
 // Table geometry of an EosView, including the split constants of the FP32 cell
 // location (see EosView).
 void eos_geometry(const rlb::EosTable& tab, rlbk::EosView* v) {
@@ -484,7 +523,11 @@ struct Stager {
         c.milne_on = ctx->gp.metric == RLB_MILNE;
         c.dtau = dtau;
         c.dtau_r = (float)dtau;
-        c.log2Z = (float)std::log2(ctx->eosp.Z);
+        {
+          const double zf = ctx->eosp.Z / (1.0 + ctx->ex2_bias);
+          c.Zh = (float)zf;
+          c.Zl = (float)(zf - (double)c.Zh);
+        }
         c.op = make_ops_mp<NXI>(ctx->lat);
         c.prefetch_ahead = 0;
         int per_sm = 0, sms = 0;
@@ -1068,6 +1111,10 @@ rlb_status step_static(rlb_ctx* ctx, char* state, char* scr, int nsteps, cudaStr
                              cudaMemcpyHostToDevice, st), "static FP32 EOS table upload");
     RLB_CUDA(cudaStreamSynchronize(st), "static table upload synchronise");
   }
+  {
+    rlb_status rb = measure_ex2_bias(ctx, scr, L.eps_off, st);
+    if (rb) return rb;
+  }
   RLB_CUDA(cudaMemsetAsync(Tsite, 0, ctx->ns * sizeof(double), st), "static Newton starts reset");
   RLB_CUDA(cudaMemsetAsync(err, 0, 256, st), "static error word reset");
   rlb_status r0 = upload_tables(ctx, scr, st);
@@ -1300,6 +1347,8 @@ rlb_status rlb_bind_buffers(rlb_ctx* ctx, void* state, void* scratch, void* stre
     RLB_CUDA(cudaStreamSynchronize(st), "bind synchronise");
   }
   RLB_CUDA(cudaMemsetAsync(ctx->scratch + ctx->err_off, 0, 256, st), "error word reset");
+  s = measure_ex2_bias(ctx, ctx->scratch, ctx->eps_off, st);  // eps0 space: free until rlb_init_grid
+  if (s) return s;
   s = upload_tables(ctx, ctx->scratch, st);
   if (s) return s;
   s = set_clock(ctx, ctx->scratch, ctx->tau, st);

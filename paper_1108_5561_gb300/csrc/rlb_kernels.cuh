@@ -508,12 +508,13 @@ __device__ __forceinline__ void store_mom_parts(float* dst, const float* pairs) 
 // per-site matching results consumed by the stage kernel: kScUsed values,
 // stored kSc apart (64 bytes in FP32: four 16-byte loads per site; the two
 // padding slots hold zeros)
-constexpr int kScUsed = 14, kSc = 16;
+constexpr int kScUsed = 15, kSc = 16;
 enum : int {
   SC_UT = 0, SC_UX, SC_UY, SC_INVT, SC_MEQ, SC_M, SC_ITR, SC_D, SC_B, SC_K, SC_KH, SC_T,
-  SC_AX, SC_AY  // grad ln M (central differences, 1/fm)
+  SC_AX, SC_AY,  // grad ln M (central differences, 1/fm)
+  SC_L2T         // log2(e) / T, one rounding from the product (the exponent scale of f_eq)
 };
-static_assert(SC_AY + 1 == kScUsed && kSc % 4 == 0, "site scalar layout");
+static_assert(SC_L2T + 1 == kScUsed && kSc % 4 == 0, "site scalar layout");
 
 // Grid of one or more independent events: periodic transverse grids of their
 // own size and eta/s, stored event after event, row-major inside an event.
@@ -646,6 +647,7 @@ __device__ __forceinline__ int match_site_d(const MatchArgs& A, int site, double
   A.Tsite[site] = T;
   o[SC_UT] = u[0]; o[SC_UX] = u[1]; o[SC_UY] = u[2];
   o[SC_INVT] = 1.0 / T; o[SC_MEQ] = Meq; o[SC_M] = M; o[SC_ITR] = itr; o[SC_D] = D;
+  o[SC_L2T] = 1.4426950408889634 / T;
   o[SC_B] = B; o[SC_K] = pref * m[0]; o[SC_KH] = m[0]; o[SC_T] = T;
   {
     const int nx = evi.nx, ny = evi.ny, x = sxi, yy = syi;
@@ -738,6 +740,14 @@ __device__ __forceinline__ int match_site_f(const MatchArgs& A, int site, float 
   A.Tsite[site] = (double)T;
   o[SC_UT] = u[0]; o[SC_UX] = u[1]; o[SC_UY] = u[2];
   o[SC_INVT] = 1.f / T; o[SC_MEQ] = Meq; o[SC_M] = M; o[SC_ITR] = itr; o[SC_D] = D;
+  {
+    // log2(e) / T with log2(e) split into FP32 hi + lo: the product is within
+    // an ulp of the exact one (an FP32 log2(e) alone is 1.3e-8 low, the same
+    // sign at every site)
+    constexpr float kL2eHi = 1.44269502162933349609375f, kL2eLo = 1.92596298909109e-8f;
+    const float iT = o[SC_INVT];
+    o[SC_L2T] = fmaf(kL2eHi, iT, kL2eLo * iT);
+  }
   o[SC_B] = B; o[SC_K] = pref * m[0]; o[SC_KH] = m[0]; o[SC_T] = T;
   {
     const int nx = evi.nx, ny = evi.ny, x = sxi, yy = syi;
@@ -776,7 +786,7 @@ __global__ void __launch_bounds__(128) match_kernel(const MatchArgs A) {
   if (site >= A.ns) return;
   if constexpr (FAST) {
     float o[kSc];
-    o[kSc - 2] = o[kSc - 1] = 0.f;
+    o[kSc - 1] = 0.f;
     const int err = match_site_f(A, site, o);
     if (err) atomicOr(A.err, err);
     float4* of = reinterpret_cast<float4*>(A.scf + (size_t)site * kSc);  // 64 bytes per site
@@ -784,7 +794,7 @@ __global__ void __launch_bounds__(128) match_kernel(const MatchArgs A) {
     for (int q = 0; q < kSc / 4; ++q) of[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
   } else {
     double o[kSc];
-    o[kSc - 2] = o[kSc - 1] = 0.0;
+    o[kSc - 1] = 0.0;
     const int err = match_site_d(A, site, o);
     if (err) atomicOr(A.err, err);
     double2* od = reinterpret_cast<double2*>(A.sc + (size_t)site * kSc);

@@ -81,7 +81,8 @@ struct StageArgsMP {
   int mode;               // 0 predictor, 1 corrector
   int prefetch_ahead;     // L2 prefetch of the sites of the CTA launched this many CTAs later (0: none)
   double dtau;
-  float dtau_r, log2Z;
+  float dtau_r;
+  float Zh, Zl;           // Z / (1 + mean error of the hardware 2^x), as FP32 hi + lo
   OpsMP<NXI> op;
 };
 
@@ -202,10 +203,10 @@ __device__ __forceinline__ void mp_offsets(const MPSite& m, int l, int jp, float
 
 // The stage at one site for the thread's two lines.  ld(i, v) delivers line i
 // of the ten of mp_offsets (i < 10) or, in the corrector, the thread's own
-// lines A (i = 10) and B (i = 11) of f_base.  Everything that needs only the
-// site's own lines (radial and polar operators, equilibrium, force,
-// collision) comes first, the streaming term last, so that the neighbour
-// lines can still be in flight meanwhile.  sc holds the site's FP32 matching
+// lines A (i = 10) and B (i = 11) of f_base.  The streaming term comes first
+// (the neighbour lines die before the site's own work; computing it last, so
+// that the neighbour loads overlap the own-line work, keeps them live and
+// measured 3 % slower).  sc holds the site's FP32 matching
 // (four float4); eo is the CTA's polar exchange area (NXI/2 16-byte chunks per
 // thread) and red its per-group partial sums.  Contains one CTA barrier.
 template <class S, int NXI, int NTH, int NPH, class LD>
@@ -227,12 +228,36 @@ __device__ __forceinline__ void mp_body(const StageArgsMP<S, NXI, NTH, NPH>& A, 
   ld(0, fA);
   ld(1, fB);
 
+  // 1. streaming -V.grad f from the upwind neighbour lines (periodic) into R
+  //    right away: the neighbour lines die here, before the site's own work
+  {
+    const float2 nsx = bc2(lb.y), nsy = bc2(lb.z), three = bc2(3.f), mfour = bc2(-4.f);
+    float2 n1[NP], n2[NP];
+    ld(2, n1);  // x, line A
+    ld(3, n2);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) RA[p] = mul2(mul2(op.tv[p], nsx), fma2(mfour, n1[p], fma2(three, fA[p], n2[p])));
+    ld(4, n1);  // x, line B
+    ld(5, n2);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) RB[p] = mul2(mul2(op.tv[p], nsx), fma2(mfour, n1[p], fma2(three, fB[p], n2[p])));
+    ld(6, n1);  // y, line A
+    ld(7, n2);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) RA[p] = fma2(mul2(op.tv[p], nsy), fma2(mfour, n1[p], fma2(three, fA[p], n2[p])), RA[p]);
+    ld(8, n1);  // y, line B
+    ld(9, n2);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) RB[p] = fma2(mul2(op.tv[p], nsy), fma2(mfour, n1[p], fma2(three, fB[p], n2[p])), RB[p]);
+  }
+
   // site scalars of the matching of f_in
-  static_assert(kSc == 16 && SC_UT == 0 && SC_MEQ == 4 && SC_B == 8 && SC_AX == 12, "float4 groups");
+  static_assert(kSc == 16 && SC_UT == 0 && SC_MEQ == 4 && SC_B == 8 && SC_AX == 12 && SC_L2T == 14,
+                "float4 groups");
   const float ut = sc[0].x, ux = sc[0].y, uy = sc[0].z, invT = sc[0].w;
   const float Meq = sc[1].x, M = sc[1].y, itr = sc[1].z, Dm = sc[1].w, Kh = sc[2].z, ax = sc[3].x, ay = sc[3].y;
 
-  // 1. radial operator on both lines; Milne term mu^2 Dr f / tau into R
+  // 2. radial operator on both lines; Milne term mu^2 Dr f / tau into R
   float2 DA[NP], DB[NP];
 #pragma unroll
   for (int p = 0; p < NP; ++p) DA[p] = DB[p] = make_float2(0.f, 0.f);
@@ -250,11 +275,11 @@ __device__ __forceinline__ void mp_body(const StageArgsMP<S, NXI, NTH, NPH>& A, 
   const float2 mmu2 = bc2(milne * mu2);
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
-    RA[p] = mul2(mmu2, DA[p]);
-    RB[p] = mul2(mmu2, DB[p]);
+    RA[p] = fma2(mmu2, DA[p], RA[p]);
+    RB[p] = fma2(mmu2, DB[p], RB[p]);
   }
 
-  // 2. polar operator on the even and odd parts, exchanged among the H
+  // 3. polar operator on the even and odd parts, exchanged among the H
   //    threads of this azimuth (same warp; eo chunk c of thread u at
   //    c ^ ((u >> 1) & 3), distinct bank groups for 8 consecutive threads)
   if (milne != 0.f) {
@@ -292,63 +317,53 @@ __device__ __forceinline__ void mp_body(const StageArgsMP<S, NXI, NTH, NPH>& A, 
     }
   }
 
-  // 3. equilibrium, force and collision (shared by the two lines):
-  //    f_eq = Z 2^(c1 E_eq + c2 sinh), force = f_eq [Gp q1/E_eq + Hp q2 + Jp/cosh],
-  //    collision = -(f - f_eq) cc, cc = (u^tau - tanh vu)/tau_R
-  constexpr float kLog2e = 1.4426950408889634f;
+  // 4. equilibrium, force and collision (shared by the two lines), and the
+  //    energy-weighted sums for d ln M / d tau:
+  //    f_eq = Z e2, e2 = 2^(c1 E_eq + c2 sinh), force = f_eq [Gp q1/E_eq + Hp q2 + Jp/cosh],
+  //    collision = -(f - f_eq) cc, cc = (u^tau - tanh vu)/tau_R.
+  //    Z multiplies the per-line coefficients of e2 (hi + lo product, about
+  //    an ulp) instead of entering the exponent as an FP32 log2 Z, whose
+  //    rounding would scale every f_eq by the same factor (7.7e-8 for the
+  //    QCD degeneracy); the factor also takes out the mean error of the
+  //    hardware 2^x, measured when the buffers are bound.
+  const float L2T = sc[3].z;  // log2(e) / T
   const float vu = st * (cp * ux + sp * uy);
   const float A1 = st * (ax * cp + ay * sp);
   const float au = ax * ux + ay * uy;
   const float M2 = M * M;
-  const float2 c1 = bc2(-kLog2e * invT * ut), c2 = bc2(kLog2e * invT * M * vu), lZ = bc2(A.log2Z);
-  const float2 Gp = bc2(-invT * A1 * ut * M2), Hp = bc2(invT * A1 * M * vu), Jp = bc2(invT * M * au);
-  const float2 cc0 = bc2(ut * itr), cc1 = bc2(-vu * itr), ncc0 = bc2(-ut * itr), ncc1 = bc2(vu * itr);
+  auto zs = [&](float v) { return bc2(fmaf(A.Zh, v, A.Zl * v)); };
+  const float2 c1 = bc2(-L2T * ut), c2 = bc2(L2T * M * vu);
+  const float2 Gp = zs(-invT * A1 * ut * M2), Hp = zs(invT * A1 * M * vu), Jp = zs(invT * M * au);
+  const float2 cc0 = zs(ut * itr), cc1 = zs(-vu * itr), ncc0 = bc2(-ut * itr), ncc1 = bc2(vu * itr);
   const float2 utb = bc2(ut), nvub = bc2(-vu), M2b = bc2(M2), Meq2 = bc2(Meq * Meq);
-  float2 sQ = make_float2(0.f, 0.f), sE = sQ, W[NP];
+  float2 sA = make_float2(0.f, 0.f), sQ = sA, sE = sA;
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
-    // per-site radial table: E_eq = sqrt(M_eq^2 + M^2 sinh^2), q1 / E_eq
+    // per-site radial table: E_eq = sqrt(M_eq^2 + M^2 sinh^2), q1 / E_eq.
+    // E_eq = e2 / sqrt(e2) from the Newton-refined reciprocal square root,
+    // then one residual step E += (e2 - E^2) / (2 E): the FP32 Newton step
+    // leaves 1/sqrt 1.5e-8 low on average (rounding near 1 is coarser above
+    // than below), which the exponent E_eq / T ~ 10 would turn into an f_eq
+    // 2e-7 too large at every node; after the residual step E_eq is within
+    // half an ulp with no mean error
     const float2 e2 = fma2(M2b, op.s2[p], Meq2);
     const float2 ie = rsqrt2_nr(e2);
-    const float2 E = mul2(e2, ie), QE = mul2(op.q1[p], ie);
-    const float2 ex = fma2(c1, E, fma2(c2, op.s[p], lZ));
+    float2 E = mul2(e2, ie);
+    E = fma2(mul2(bc2(0.5f), ie), fma2(mul2(bc2(-1.f), E), E, e2), E);  // e2 - E^2 in one rounding
+    const float2 QE = mul2(op.q1[p], ie);
+    const float2 ex = fma2(c1, E, mul2(c2, op.s[p]));
     const float2 feq = make_float2(ex2_ftz(ex.x), ex2_ftz(ex.y));
     const float2 cc = fma2(cc1, op.tv[p], cc0), ncc = fma2(ncc1, op.tv[p], ncc0);
     const float2 fcc = fma2(Gp, QE, fma2(Hp, op.q2[p], fma2(Jp, op.ic[p], cc)));
     RA[p] = fma2(fA[p], ncc, fma2(feq, fcc, RA[p]));
     RB[p] = fma2(fB[p], ncc, fma2(feq, fcc, RB[p]));
     const float2 pu = fma2(op.Sw[p], nvub, mul2(op.Cw[p], utb));
-    W[p] = mul2(pu, pu);
-    sQ = fma2(W[p], DA[p], fma2(W[p], DB[p], sQ));
-    sE = fma2(W[p], fA[p], fma2(W[p], fB[p], sE));
+    const float2 w = mul2(pu, pu);
+    sA = fma2(w, RA[p], fma2(w, RB[p], sA));
+    sQ = fma2(w, DA[p], fma2(w, DB[p], sQ));
+    sE = fma2(w, fA[p], fma2(w, fB[p], sE));
   }
 
-  // 4. streaming -V.grad f from the upwind neighbour lines (periodic), and
-  //    the energy-weighted sum of the full right-hand side
-  float2 sA = make_float2(0.f, 0.f);
-  {
-    const float2 nsx = bc2(lb.y), nsy = bc2(lb.z), three = bc2(3.f), mfour = bc2(-4.f);
-    float2 n1[NP], n2[NP];
-    ld(2, n1);  // x, line A
-    ld(3, n2);
-#pragma unroll
-    for (int p = 0; p < NP; ++p) RA[p] = fma2(mul2(op.tv[p], nsx), fma2(mfour, n1[p], fma2(three, fA[p], n2[p])), RA[p]);
-    ld(4, n1);  // x, line B
-    ld(5, n2);
-#pragma unroll
-    for (int p = 0; p < NP; ++p) RB[p] = fma2(mul2(op.tv[p], nsx), fma2(mfour, n1[p], fma2(three, fB[p], n2[p])), RB[p]);
-    ld(6, n1);  // y, line A
-    ld(7, n2);
-#pragma unroll
-    for (int p = 0; p < NP; ++p) RA[p] = fma2(mul2(op.tv[p], nsy), fma2(mfour, n1[p], fma2(three, fA[p], n2[p])), RA[p]);
-    ld(8, n1);  // y, line B
-    ld(9, n2);
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      RB[p] = fma2(mul2(op.tv[p], nsy), fma2(mfour, n1[p], fma2(three, fB[p], n2[p])), RB[p]);
-      sA = fma2(W[p], RA[p], fma2(W[p], RB[p], sA));
-    }
-  }
   // Heun base: predictor f + dtau R, corrector (f_base + f)/2 + dtau R / 2;
   // g Dr f is added once g is known
   if (A.mode == 0) {
