@@ -91,11 +91,13 @@ def job_rate(units_per_rank: float, world: int, t_max: float) -> float:
 
 # DRAM traffic of the stage kernel on the 256 x 256 workload: ncu
 # dram__bytes_read.sum + dram__bytes_write.sum, mean of one predictor and one
-# corrector launch of `bench.py --steps 3 --warmup 3 --no-cpu-baseline --no-e2e`
-# on a GB300.  It describes the kernel sources it was taken on (the SHA-1 of
-# their code, comments removed) and is reported only while they are unchanged.
-STAGE_TRAFFIC = {"sources": ("rlb_stage_x2.cuh", "rlb_kernels.cuh"),
-                 "sha1": "e7ad4cc45f39a444a8d471457d8a6e7ee9ed20ff", "bytes_per_launch": 480.4e6}
+# corrector launch of `bench.py --steps 3 --warmup 3 --no-cpu-baseline --no-e2e
+# --no-secondary` on a GB300 (the mirror-paired kernel, the default).  It
+# describes the kernel sources it was taken on (the SHA-1 of the code of the
+# stage-kernel headers, comments removed) and is reported only while they are
+# unchanged.
+STAGE_TRAFFIC = {"sources": ("rlb_stage_mp.cuh", "rlb_stage_x2.cuh"),
+                 "sha1": "3b6a5c7d9c7d108d336e6b9ec1d53c2c92343c21", "bytes_per_launch": 479.96e6}
 
 
 def code_digest(files) -> str:
@@ -279,26 +281,9 @@ def batch_main(args, rank, world, local):
 
     e2e = None
     if not args.no_e2e:
-        # pinned eps0 upload, initial condition, then every step the step and a
-        # download of the per-site observables (8 doubles per site), each download
-        # overlapping the next step
-        host_eps = torch.from_numpy(eps.copy()).pin_memory()
-        obs = ObservableStream(run, torch)
-        dev_eps = torch.empty(ns, dtype=torch.float64, device="cuda")
-        barrier()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        dev_eps.copy_(host_eps, non_blocking=True)
-        run.init_grid(dev_eps)
-        for _ in range(args.steps):
-            run.step(1)
-            obs.step()
-        torch.cuda.synchronize()
-        barrier()
-        t_e2e = time.perf_counter() - t0
-        e2e = {"value": world * BATCH_EVENTS * args.steps / (t_e2e * BATCH_EVOLUTION_STEPS),
-               "unit": "events/s", "h2d_bytes_per_step": ns * 8 / args.steps, "d2h_bytes_per_step": ns * 64}
-
+        t_e2e, e2e = end_to_end(run, eps, args.steps, barrier, torch)
+        e2e = {"value": world * BATCH_EVENTS * args.steps / (t_e2e * BATCH_EVOLUTION_STEPS), "unit": "events/s",
+               **e2e}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         side = 64
@@ -525,6 +510,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling)")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the short batch / adjoint / sweep / FP64 / ALU-peak records of the grid run")
     ap.add_argument("--grid", type=int, default=256,
                     help="grid side; the benchmark workload is 256 (smaller sides for profiling)")
     ap.add_argument("--record", default=None, help="also append the JSON line to this JSONL file")
@@ -605,13 +592,26 @@ def main():
     achieved = alg_bytes_launch / (stage_ms / stage_n / 1e3) / 1e9
     peak, peak_kind = peaks()
 
-    # end to end through the public API with host buffers: pinned eps0 upload,
-    # initial condition, then every step the step itself and a download of the
-    # per-site observables.
+    # end to end through the library's host-buffer calls: eps0 from pinned host
+    # memory, the initial condition, then every step the step itself and the
+    # per-site observables into pinned host memory.
     e2e = None
     if not args.no_e2e:
-        e2e = end_to_end(run, eps0, args, updates, barrier, torch)
+        t_e2e, e2e = end_to_end(run, eps0, args.steps, barrier, torch)
+        e2e = {"value": updates / t_e2e, "unit": "updates/s", **e2e}
 
+    kern = {"stream_collide_ms_per_launch": stage_ms / stage_n,
+            "match_ms_per_launch": match_ms / match_n, "timed_launches": stage_n + match_n}
+    sec = None
+    if rank == 0 and world == 1 and not args.no_secondary:
+        del run
+        torch.cuda.empty_cache()
+        sec = secondary(args, local, torch, rlb)
+        alu = sec["alu_peaks_tflops"]["fp32_ffma2_tflops"]
+        fl = FLOPS_PER_POP_STAGE["fp32_mirror_paired"] * ns * nn / (stage_ms / stage_n / 1e3) / 1e12
+        kern["alu_roofline"] = {"bound": "alu", "achieved": fl, "peak": alu, "unit": "TFLOP/s", "frac": fl / alu,
+                                "peak_source": "measured (rlb_alu_peaks, packed FP32 multiply-add)",
+                                "flops_per_population_stage": FLOPS_PER_POP_STAGE["fp32_mirror_paired"]}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         c = NX // 2
@@ -620,67 +620,158 @@ def main():
         rate, dt = oracle_rate(win, 16, cores)
         cpu = {"value": rate, "unit": "updates/s", "cores": cores, "kind": "oracle",
                "sample": "128x128 central window of the workload, 16 oracle steps (%.1f s)" % dt}
-    kern = {"stream_collide_ms_per_launch": stage_ms / stage_n,
-            "match_ms_per_launch": match_ms / match_n, "timed_launches": stage_n + match_n}
     return finish(args, rank, world, t, value, achieved, peak, peak_kind, b, nn, launches, e2e,
-                  clocks, cpu, ranks, kern)
+                  clocks, cpu, ranks, kern, sec)
 
 
-class ObservableStream:
-    """Per-step download of the per-site observables (8 doubles per site) to
-    pinned host memory on a copy stream, double-buffered, so that the copy of
-    step n overlaps step n + 1 on the compute stream."""
-
-    def __init__(self, run, torch):
-        self.run, self.torch = run, torch
-        shape = (run.ns, 8)
-        self.dev = [torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(2)]
-        self.host = [torch.empty(shape, dtype=torch.float64).pin_memory() for _ in range(2)]
-        self.done = [torch.cuda.Event(), torch.cuda.Event()]
-        self.copy = torch.cuda.Stream()
-        self.n = 0
-
-    def step(self):
-        torch, i = self.torch, self.n % 2
-        cur = torch.cuda.current_stream()
-        if self.n >= 2:
-            cur.wait_event(self.done[i])  # buffer i: its previous download has finished
-        self.run.moments(out=self.dev[i], host=False)
-        ready = torch.cuda.Event()
-        ready.record(cur)
-        self.copy.wait_event(ready)
-        with torch.cuda.stream(self.copy):
-            self.host[i].copy_(self.dev[i], non_blocking=True)
-            self.done[i].record(self.copy)
-        self.n += 1
-
-    def bytes_per_step(self) -> int:
-        return self.run.ns * 8 * 8
-
-
-def end_to_end(run, eps0, args, updates, barrier, torch):
-    ns = NX * NY
-    host_eps = torch.from_numpy(eps0.reshape(-1).copy()).pin_memory()
-    obs = ObservableStream(run, torch)
-    dev_eps = torch.empty(ns, dtype=torch.float64, device="cuda")
+def end_to_end(run, eps0, steps, barrier, torch):
+    """The same steps through the library's host-buffer calls: rlb_init_grid
+    reads eps0 from (pinned) host memory, and after every step rlb_moments
+    writes the per-site observables (8 doubles per site) into a pinned host
+    array and returns once they are there.  Returns (seconds, the e2e record
+    without its value)."""
+    ns = run.ns
+    host_eps = torch.from_numpy(np.ascontiguousarray(eps0).reshape(-1).copy()).pin_memory()
+    host_obs = torch.empty((ns, 8), dtype=torch.float64).pin_memory()
+    eps_np, obs_np = host_eps.numpy(), host_obs.numpy()
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    dev_eps.copy_(host_eps, non_blocking=True)
-    run.init_grid(dev_eps)
-    for _ in range(args.steps):
+    run.init_grid(eps_np)
+    for _ in range(steps):
         run.step(1)
-        obs.step()
+        run.moments(out=obs_np)
     torch.cuda.synchronize()
     barrier()
     t_e2e = time.perf_counter() - t0
     run.check()
-    return {"value": updates / t_e2e, "unit": "updates/s",
-            "h2d_bytes_per_step": ns * 8 / args.steps, "d2h_bytes_per_step": ns * 8 * 8}
+    return t_e2e, {"h2d_bytes_per_step": ns * 8 / steps, "d2h_bytes_per_step": ns * 8 * 8,
+                   "path": "rlb_init_grid(host eps0) once, then per step rlb_step + rlb_moments(host output)"}
+
+
+# Arithmetic per population and stage, counted from the kernels' per-node
+# operations (a multiply-add = 2 flops; the FP64 exponential of the generic
+# kernel counted as 20): the mirror-paired FP32 stage kernel about 80 FP32
+# flops (streaming 13, radial operator and Milne term 18, polar operator on the
+# even/odd parts 13, equilibrium/force/collision and the d ln M sums 26, Heun
+# 5, moments 5) plus one hardware exponential; the generic FP64 kernel about 110.
+FLOPS_PER_POP_STAGE = {"fp32_mirror_paired": 80, "fp64_generic": 110}
+
+
+def secondary(args, local, torch, rlb):
+    """Short runs of the other workloads, for the grid run's JSON line: ALU
+    peaks, the FP64 32x32 run (Gaussian, eta/s 0.08, 200 steps), the 512-event
+    batch, the 128x128 adjoint and the 1024x1024 BF16/FP32 sweep (a few timed
+    steps each; the dedicated --workload runs time them at length)."""
+    from paper_1108_5561_gb300.inputs import batch_events, hotspot_basis, hotspots, smooth_gaussian
+    from paper_1108_5561_gb300 import adjoint as ADJ
+    out = {}
+    stream = torch.cuda.current_stream()
+
+    def timed(run, steps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    def stage_ms(run, steps):
+        run.set_timing(True)
+        run.step(steps)
+        torch.cuda.synchronize()
+        sm, sn, mm, mn = run.timing()
+        run.set_timing(False)
+        return sm / sn, mm / mn
+
+    peaks_alu = rlb.alu_peaks(local)
+    out["alu_peaks_tflops"] = peaks_alu
+    # plain FP64 step: the 32x32 Gaussian run of the FP64 parity test
+    g = rlb.GridParams(nx=32, ny=32, dx=0.2, prec=rlb.RLB_F64, eta_over_s=0.08, tau0=0.4, dtau=0.018)
+    run = rlb.Run(g, device=local)
+    run.init_grid(smooth_gaussian(32, 32))
+    run.step(3)
+    t = timed(run, 200)
+    sms, mms = stage_ms(run, 20)
+    pops = 32 * 32 * g.nodes
+    fp64_rate = pops * 200 / t
+    fl = FLOPS_PER_POP_STAGE["fp64_generic"] * pops / (sms / 1e3) / 1e12
+    out["fp64_32x32"] = {"updates_per_s": fp64_rate, "ms_per_step": 1e3 * t / 200, "stage_ms_per_launch": sms,
+                         "match_ms_per_launch": mms, "stage_fp64_tflops": fl,
+                         "stage_frac_of_fp64_peak": fl / peaks_alu["fp64_dfma_tflops"]}
+    del run
+    # batch of 512 events
+    evs = batch_events(BATCH_EVENTS, seed=1108)
+    events = [rlb.Event(n, n, eta) for n, eta in evs]
+    eps = np.concatenate([hotspots(n, n, n=40, seed=1108 + i)[0].reshape(-1) for i, (n, _) in enumerate(evs)])
+    gb = rlb.GridParams(dx=DX, prec=rlb.RLB_F32, tau0=TAU0, dtau=DTAU)
+    run = rlb.Run(gb, device=local, events=events)
+    run.init_grid(eps)
+    run.step(1)
+    chosen, _ = run.autotune()
+    run.step(3)
+    t = timed(run, 8) / 8
+    sms, mms = stage_ms(run, 4)
+    batch_rate = run.ns * gb.nodes / t
+    out["batch_512"] = {"events_per_s": BATCH_EVENTS / BATCH_EVOLUTION_STEPS / t, "ms_per_step": 1e3 * t,
+                        "updates_per_s": batch_rate, "sites": run.ns, "stage_variant": chosen,
+                        "stage_ms_per_launch": sms, "match_ms_per_launch": mms,
+                        "vs_fp64_32x32_updates": batch_rate / fp64_rate}
+    del run, eps
+    torch.cuda.empty_cache()
+    # adjoint: gradient of v2 on 128x128, 300 steps, checkpoint every 32 (FP32 adjoint arithmetic)
+    side, steps = 128, 300
+    _, amps, cen = hotspots(side, side, n=40, seed=1108)
+    basis_h = hotspot_basis(side, side, cen, dx=DX)
+    ga = rlb.GridParams(nx=side, ny=side, dx=DX, prec=rlb.RLB_F32, eta_over_s=0.08, tau0=TAU0, dtau=DTAU)
+    run = rlb.Run(ga, device=local)
+    eps0 = torch.as_tensor(10.0 + amps @ basis_h, dtype=torch.float64, device="cuda")
+    basis = torch.as_tensor(basis_h, dtype=torch.float64, device="cuda")
+    run.init_grid(eps0)
+    run.step(steps)
+    run.init_grid(eps0)
+    t_fwd = timed(run, steps)
+    ADJ.v2_gradient(run, eps0, basis, 8, 4, arithmetic=rlb.RLB_F32)  # warm-up of the adjoint kernels
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ADJ.v2_gradient(run, eps0, basis, steps, 32, arithmetic=rlb.RLB_F32)
+    torch.cuda.synchronize()
+    t_grad = time.perf_counter() - t0
+    del run
+    g64 = rlb.GridParams(nx=side, ny=side, dx=DX, prec=rlb.RLB_F64, eta_over_s=0.08, tau0=TAU0, dtau=DTAU)
+    run = rlb.Run(g64, device=local)
+    run.init_grid(eps0)
+    run.step(3)
+    run.init_grid(eps0)
+    t_fwd64 = timed(run, steps)
+    del run
+    out["adjoint_128x128"] = {"gradient_s": t_grad, "forward_fp32_s": t_fwd, "over_forward_fp32": t_grad / t_fwd,
+                              "forward_fp64_s": t_fwd64, "over_forward_fp64": t_grad / t_fwd64,
+                              "steps": steps, "checkpoint_every": 32}
+    # precision sweep: 1024x1024, 16x8x16 lattice
+    sweep = {}
+    eps0 = hotspots(1024, 1024, n=40, seed=1108)[0]
+    for name, prec, b in (("fp32", rlb.RLB_F32, 4), ("bf16", rlb.RLB_BF16, 2)):
+        gs = rlb.GridParams(nx=1024, ny=1024, dx=DX, prec=prec, eta_over_s=ETA_S, tau0=TAU0, dtau=DTAU,
+                            n_xi=16, n_theta=8, n_phi_half=8)
+        run = rlb.Run(gs, device=local)
+        run.init_grid(eps0)
+        run.step(3)
+        t = timed(run, 6) / 6
+        sms, _ = stage_ms(run, 4)
+        ns, nn = 1024 * 1024, gs.nodes
+        alg = 2.5 * b * ns * nn + ns * (56 + 64 + 8 + 8 + 4)
+        sweep[name] = {"updates_per_s": ns * nn / t, "ms_per_step": 1e3 * t, "stage_ms_per_launch": sms,
+                       "stage_frac_of_hbm": alg / (sms / 1e3) / 1e9 / peaks()[0]}
+        del run
+        torch.cuda.empty_cache()
+    out["sweep_1024x1024_2048"] = sweep
+    return out
 
 
 def finish(args, rank, world, t, value, achieved, peak, peak_kind, b, nn, launches, e2e, clocks,
-           cpu, ranks, kern):
+           cpu, ranks, kern, sec=None):
     if rank == 0:
         line = {
             "metric": "site-population updates/s", "value": value, "unit": "updates/s",
@@ -693,12 +784,14 @@ def finish(args, rank, world, t, value, achieved, peak, peak_kind, b, nn, launch
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": stage_traffic(NX),
-                         "peak_source": peak_kind, "kernel": "stage_kernel_x2 (fused stream-collide, packed FP32 pairs)",
+                         "peak_source": peak_kind,
+                         "kernel": "stage_kernel_mp (fused stream-collide, mirror-paired polar lines, packed FP32 pairs)",
                          "algorithmic_bytes_per_update": 5 * b, **kern},
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
+            "secondary": sec,
         }
         emit(line)
     ranks.close()

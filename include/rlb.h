@@ -332,6 +332,16 @@ rlb_status rlb_set_timing(rlb_ctx* ctx, int enable);
 rlb_status rlb_get_timing(rlb_ctx* ctx, double* stage_ms, long* stage_launches, double* match_ms,
                           long* match_launches);
 
+/* Arithmetic-pipe peaks of device `cuda_device`, measured (not nominal), for
+ * the ALU rooflines of the stage kernels: tflops[0] FP32 fused multiply-add,
+ * tflops[1] packed FP32 pairs (FFMA2), tflops[2] FP64 fused multiply-add, in
+ * TFLOP/s (2 flops per multiply-add).  Independent multiply-add chains in 8
+ * CTAs of 256 threads per SM, one warm-up and one timed launch of about 20 ms
+ * each, CUDA events; at whatever SM clock the device runs.  A measurement
+ * helper with no counterpart in the paper.  Synchronises the device's work it
+ * launches; no context needed. */
+rlb_status rlb_alu_peaks(int cuda_device, double* tflops);
+
 /* Synchronise `stream` and report the device error word (RLB_ERR_NUMERIC if set). */
 rlb_status rlb_check(rlb_ctx* ctx, void* stream);
 

@@ -18,6 +18,7 @@
 #include "rlb_stage_x2.cuh"
 #include "rlb_stage_mp.cuh"
 #include "rlb_adjoint.cuh"
+#include "rlb_peaks.cuh"
 
 struct rlb_ctx {
   int device = 0;
@@ -607,13 +608,9 @@ template <class S, class R, int NXI, int NTH, int NPH>
 struct Runner {
   static constexpr int NL = NTH * NPH;
 
-  // The initial populations are computed in FP64 for every storage precision
-  // and rounded once to S (an FP32 evaluation of the equilibrium exponent,
-  // up to 40 in magnitude, would start the run 1e-6 away from the exact
-  // initial state).
   static rlb_status init(rlb_ctx* ctx, const double* eps_dev, cudaStream_t st) {
     ctx->scf_fresh = false;
-    rlbk::InitArgs<S, double, NXI, NTH, NPH> a;
+    rlbk::InitArgs<S, R, NXI, NTH, NPH> a;
     a.eps0 = eps_dev;
     a.eps_scale = rlb::kHbarc * rlb::kHbarc * rlb::kHbarc;
     a.f = reinterpret_cast<S*>(ctx->state + ctx->f_off);
@@ -626,7 +623,8 @@ struct Runner {
     a.Z = ctx->eosp.Z;
     a.family = ctx->gp.family;
     a.T0 = ctx->gp.T0;
-    a.op = make_ops<double, NXI, NTH, NPH>(ctx->lat);
+    a.op = make_ops<R, NXI, NTH, NPH>(ctx->lat);
+    for (int k = 0; k < NXI; ++k) a.s2d[k] = ctx->lat.s[k] * ctx->lat.s[k];
     // (T, M_eq, M) per site in the FP64 site-scalar scratch (free until the first matching)
     double* tsm = reinterpret_cast<double*>(ctx->scratch + ctx->sc_off);
     a.tsm = tsm;
@@ -636,7 +634,7 @@ struct Runner {
     {
       Timed tm(ctx, K_INIT, st);
       rlbk::init_site_kernel<<<(unsigned)((ctx->ns + 127) / 128), 128, 0, st>>>(b);
-      rlbk::init_kernel<S, double, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
+      rlbk::init_kernel<S, R, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
     }
     RLB_CUDA(cudaGetLastError(), "init_kernel launch");
     return RLB_OK;
@@ -1426,6 +1424,46 @@ rlb_status rlb_step_static_scratch(rlb_ctx* ctx, void* state, int nsteps, void* 
   if (a == 6 && b == 4 && d == 6) return step_static_prec<6, 4, 6>(ctx, stp, scr, nsteps, st);
   if (a == 8 && b == 8 && d == 2) return step_static_prec<8, 8, 2>(ctx, stp, scr, nsteps, st);
   return fail(ctx, RLB_ERR_ARG, "unsupported lattice shape");
+}
+
+rlb_status rlb_alu_peaks(int cuda_device, double* tflops) {
+  if (!tflops) return RLB_ERR_ARG;
+  rlb_ctx tmp;  // for the error macro only
+  rlb_ctx* ctx = &tmp;
+  RLB_CUDA(cudaSetDevice(cuda_device), "cudaSetDevice");
+  int sms = 0;
+  RLB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cuda_device), "SM count");
+  cudaStream_t st;
+  RLB_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "peak stream");
+  cudaEvent_t e0, e1;
+  RLB_CUDA(cudaEventCreate(&e0), "peak event");
+  RLB_CUDA(cudaEventCreate(&e1), "peak event");
+  const unsigned blocks = 8u * (unsigned)sms, threads = 256;
+  const double lanes = (double)blocks * threads * rlbk::kPeakChains * rlbk::kPeakUnroll;
+  // iterations sized for about 20 ms per timed launch
+  const int it32 = 20000, it32x2 = 10000, it64 = 400;
+  double ms[3] = {0, 0, 0};
+  for (int k = 0; k < 3; ++k) {
+    for (int rep = 0; rep < 2; ++rep) {  // the first launch warms up
+      RLB_CUDA(cudaEventRecord(e0, st), "peak event");
+      if (k == 0) rlbk::peak_ffma_kernel<<<blocks, threads, 0, st>>>(0.999999f, 1e-7f, it32);
+      else if (k == 1) rlbk::peak_ffma2_kernel<<<blocks, threads, 0, st>>>(0.999999f, 1e-7f, it32x2);
+      else rlbk::peak_dfma_kernel<<<blocks, threads, 0, st>>>(0.999999999, 1e-10, it64);
+      RLB_CUDA(cudaGetLastError(), "peak kernel launch");
+      RLB_CUDA(cudaEventRecord(e1, st), "peak event");
+      RLB_CUDA(cudaEventSynchronize(e1), "peak synchronise");
+      float t = 0.f;
+      RLB_CUDA(cudaEventElapsedTime(&t, e0, e1), "peak time");
+      ms[k] = t;
+    }
+  }
+  tflops[0] = 2.0 * lanes * it32 / (ms[0] * 1e-3) / 1e12;
+  tflops[1] = 4.0 * lanes * it32x2 / (ms[1] * 1e-3) / 1e12;
+  tflops[2] = 2.0 * lanes * it64 / (ms[2] * 1e-3) / 1e12;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(st);
+  return RLB_OK;
 }
 
 rlb_status rlb_get_tau(const rlb_ctx* ctx, double* tau) {

@@ -1200,6 +1200,7 @@ struct InitArgs {
   double Z;
   int family;
   double T0;
+  double s2d[NXI];  // sinh^2 xi_k in FP64 (the exponent of f_eq is evaluated in FP64)
   Ops<R, NXI, NTH, NPH> op;
 };
 
@@ -1244,19 +1245,29 @@ __global__ void __launch_bounds__(128) init_site_kernel(const InitSiteArgs A) {
 template <class S, class R, int NXI, int NTH, int NPH>
 __global__ void __launch_bounds__(NTH* NPH)
     init_kernel(const __grid_constant__ InitArgs<S, R, NXI, NTH, NPH> A) {
+  // At rest f_eq = Z exp(-E_eq/T) depends on the radial node only: the NXI
+  // values of a site are evaluated once, in FP64 (the exponent reaches ~40 in
+  // magnitude, where an FP32 evaluation would be off by ~1e-6), and rounded
+  // once to the storage precision; the moments of what is stored are summed
+  // in R.
   constexpr int NL = NTH * NPH;
   constexpr int NN = NL * NXI;
   constexpr int NW = (NL + 31) / 32;
+  static_assert(NXI <= NL, "one thread per radial node");
   const int site = blockIdx.x, t = threadIdx.x;
   const int j = t % NTH, l = t / NTH;
   __shared__ double redd[kMom * NW];
   __shared__ float redf[2 * kMom * NW];
-  const double* sc = A.tsm + (size_t)site * 3;  // (T, M_eq, M) of init_site_kernel
-  const R invT = (R)(1.0 / __ldg(sc)), Meq = (R)__ldg(sc + 1), M = (R)__ldg(sc + 2), Z = (R)A.Z;
+  __shared__ double fk[NXI];
+  if (t < NXI) {
+    const double* sc = A.tsm + (size_t)site * 3;  // (T, M_eq, M) of init_site_kernel
+    const double T = __ldg(sc), Meq = __ldg(sc + 1), M = __ldg(sc + 2);
+    fk[t] = A.Z * exp(-sqrt(Meq * Meq + M * M * A.s2d[t]) / T);
+  }
+  __syncthreads();
   R out[NXI];
 #pragma unroll
-  for (int k = 0; k < NXI; ++k)
-    out[k] = ld1<S, R>(st1<S, R>(Z * fexp<R>(-fsqrt<R>(Meq * Meq + M * M * A.op.s2[k]) * invT)));
+  for (int k = 0; k < NXI; ++k) out[k] = ld1<S, R>(st1<S, double>(fk[k]));
   store_line<S, R, NXI>(A.f + (size_t)site * NN + t * NXI, out);
   R mom[kMom];
   line_moments<R, NXI, NTH, NPH>(A.op, out, j, l, mom);
@@ -1264,16 +1275,6 @@ __global__ void __launch_bounds__(NTH* NPH)
   if (t == 0) {
     if constexpr (sizeof(R) == 4) {
       store_mom_parts(A.momf + (size_t)site * kMom * kMomParts, redf);
-    } else if constexpr (sizeof(S) < 8) {
-      // FP64 sums for a path whose matching reads FP32 partial sums: each
-      // sum as its (hi, lo) FP32 split, recombined there by TwoSum
-      float pairs[2 * kMom];
-#pragma unroll
-      for (int q = 0; q < kMom; ++q) {
-        pairs[2 * q] = (float)redd[q];
-        pairs[2 * q + 1] = (float)(redd[q] - (double)pairs[2 * q]);
-      }
-      store_mom_parts(A.momf + (size_t)site * kMom * kMomParts, pairs);
     } else {
 #pragma unroll
       for (int q = 0; q < kMom; ++q) A.mom[(size_t)site * kMom + q] = redd[q];

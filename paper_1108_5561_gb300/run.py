@@ -76,6 +76,18 @@ class Event:
     eta_over_s: float
 
 
+def alu_peaks(device: int = 0) -> dict:
+    """Measured FP32 (FFMA), packed FP32 (FFMA2) and FP64 multiply-add rates of
+    the device in TFLOP/s (rlb_alu_peaks)."""
+    out = np.zeros(3)
+    lib = L.load()
+    rc = lib.rlb_alu_peaks(int(device), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if rc != 0:
+        raise L.RLBError(rc, "rlb_alu_peaks")
+    return {"fp32_ffma_tflops": float(out[0]), "fp32_ffma2_tflops": float(out[1]),
+            "fp64_dfma_tflops": float(out[2])}
+
+
 class Run:
     """One simulation on one GPU: EOS table, grid (or batch of events), device
     buffers, state.  With `events`, the grid's lattice, precision, dx, tau0,

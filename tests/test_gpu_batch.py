@@ -1,7 +1,9 @@
-"""Batched events (rlb_configure_batch / rlb_init_batch): every event of a
-batch evolves exactly as the same event run alone (bit for bit: same kernels,
-same arithmetic, only the site indexing differs), with its own grid size and
-eta/s."""
+"""Batched events (rlb_configure_batch / rlb_init_batch): every event of an
+uneven batch matches the FP64 oracle run on that event alone with its own grid
+and eta/s, and evolves exactly as the same event run alone on the GPU (bit for
+bit: same kernels, same arithmetic, only the site indexing differs)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -40,6 +42,35 @@ def test_batch_equals_single_runs(prec):
         assert torch.equal(pb[o:o + n], one.populations()), i
         assert np.array_equal(mb[o:o + n], one.moments()), i
         assert one.tau == batch.tau
+
+
+ORACLE_EVENTS = [rlb.Event(7, 5, 0.04), rlb.Event(12, 9, 0.3), rlb.Event(1, 3, 0.16)]
+
+
+@pytest.mark.parametrize("prec,tol", [(rlb.RLB_F64, 1e-12), (rlb.RLB_F32, 1e-5)])
+def test_batch_events_match_the_oracle(oracle_mod, prec, tol):
+    # per event: eps, T relative per site, u as the 4-vector, u_perp against the
+    # event's own max |u_perp|
+    steps, nt = 20, os.cpu_count() or 1
+    g = rlb.GridParams(dx=0.1, prec=prec, tau0=0.4, dtau=0.0036)
+    batch = rlb.Run(g, events=ORACLE_EVENTS)
+    eps = [hotspots(e.nx, e.ny, n=4, seed=300 + i, spread=0.3)[0] for i, e in enumerate(ORACLE_EVENTS)]
+    batch.init_grid(np.concatenate([x.reshape(-1) for x in eps]))
+    batch.step(steps)
+    batch.check()
+    mb = batch.moments()
+    for i, e in enumerate(ORACLE_EVENTS):
+        o = oracle_mod.Oracle(nx=e.nx, ny=e.ny, dx=0.1, eta_over_s=e.eta_over_s)
+        f, lnM = o.init_state(eps[i], nt)
+        o.step(f, lnM, 0.4, 0.0036, steps, nt)
+        mo = o.moments(f, lnM, nt)
+        mg = mb[batch.event_offsets[i]:batch.event_offsets[i] + e.nx * e.ny]
+        err = [float(np.max(np.abs(mg[:, c] / mo[:, c] - 1))) for c in (0, 1)]
+        err.append(float(np.max(np.abs(mg[:, 2:5] - mo[:, 2:5]).max(axis=1) / np.abs(mo[:, 2:5]).max(axis=1))))
+        if e.nx > 1:
+            err.append(float(np.abs(mg[:, 3:5] - mo[:, 3:5]).max() / np.abs(mo[:, 3:5]).max()))
+        print("event", i, e, ["%.1e" % x for x in err])
+        assert max(err) < tol, (i, err)
 
 
 def test_batch_rejects_bad_events():

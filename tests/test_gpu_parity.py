@@ -93,6 +93,34 @@ def test_fp64_minkowski_and_free_streaming(oracle_mod):
     assert max(e.values()) < 1e-12, e
 
 
+def test_fp64_minkowski_mass_gradients_with_collisions(oracle_mod):
+    # Minkowski, crossover EOS, collisions on, one Gaussian bump: the mass-gradient
+    # force and node motion act (grad ln M up to ~0.6/fm).  The GPU state matches
+    # the oracle, and so does the change of sum_x (T^{tau tau}_kin + B) that the
+    # lattice makes (a spatial discretisation error, see the oracle tests)
+    from paper_1108_5561_gb300.inputs import coords
+    n, dx = 12, 0.1
+    X, Y = coords(n, n, dx)
+    eps0 = 10.0 + 25.0 * np.exp(-((X - 0.13) ** 2 + (Y + 0.07) ** 2) / (2 * 0.25 ** 2))
+    g = rlb.GridParams(nx=n, ny=n, dx=dx, prec=rlb.RLB_F64, metric=rlb.RLB_MINKOWSKI, eta_over_s=0.03,
+                       tau0=1.0, dtau=0.005)
+    run, mg, mo, (o, f, lnM) = run_pair(oracle_mod, g, eps0, 40)
+    e = errors(mg, mo)
+    assert max(e.values()) < 1e-12, e
+
+    def energy(ff, lm, T):
+        nd, w = o.nodes(), o.weights()
+        c = np.tile(nd["c"], 12 * 8)
+        M4 = np.exp(4 * lm)[:, None] / (2 * math.pi ** 2)
+        return float(np.sum(M4 * ff * w * c * c) + sum(o.eos(t)["B"] for t in T))
+    f0, lnM0 = o.init_state(eps0, NT)
+    E0 = energy(f0, lnM0, o.moments(f0, lnM0, NT)[:, 1])
+    dE_gpu = energy(run.populations().cpu().numpy(), run.lnM().cpu().numpy(), mg[:, 1]) / E0 - 1
+    dE_orc = energy(f, lnM, mo[:, 1]) / E0 - 1
+    print("energy change: GPU %.6e oracle %.6e" % (dE_gpu, dE_orc))
+    assert abs(dE_orc) > 1e-5 and abs(dE_gpu - dE_orc) < 1e-12
+
+
 def test_fp64_0p1d_paper_lattice(oracle_mod):
     # N_xi = N_theta = 5, dtau = 0.2 fm/c (Sec. 4.5), single site
     g = rlb.GridParams(nx=1, ny=1, n_xi=5, n_theta=5, n_phi_half=1, prec=rlb.RLB_F64,

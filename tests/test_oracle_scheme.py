@@ -155,6 +155,101 @@ def test_free_streaming_conserves_energy_momentum(oracle_mod):
     assert np.allclose(lnM, math.log(0.4), rtol=1e-15)
 
 
+def _Ttau_with_bag(o, f, lnM):
+    """sum_x T^{tau nu} including the bag term B g^{mu nu} (g^{tau tau} = 1):
+    (T^{tau tau}_kin + B, T^{tau x}, T^{tau y}), B at each site's matched T."""
+    P = _Ttau(o, f, lnM)
+    T = o.moments(f, lnM)[:, 1]
+    return P + np.array([sum(o.eos(t)["B"] for t in T), 0.0, 0.0])
+
+
+def test_collisions_conserve_energy_momentum_at_constant_mass(oracle_mod):
+    # Minkowski, constant mass (no bag term, no mass-gradient force), collisions on:
+    # streaming and the BGK term with Landau matching conserve sum_x T^{tau nu}
+    # (16 radial nodes: the lattice moments of f_eq then match e(T) to rounding)
+    o = oracle_mod.Oracle(nx=8, ny=7, metric=0, eos_kind=1, eos_m0=0.5, eta_over_s=0.1, n_xi=16,
+                          n_phi_half=8)
+    X, Y = np.meshgrid(np.arange(8) - 3.5, np.arange(7) - 3.0)
+    f, lnM = o.init_state(5.0 + 20.0 * np.exp(-((X - 0.7) ** 2 + Y ** 2) / 4.0))
+    P0 = _Ttau(o, f, lnM)
+    o.step(f, lnM, 1.0, 0.005, 30)
+    P1 = _Ttau(o, f, lnM)
+    assert np.allclose(P1, P0, rtol=0, atol=1e-10 * P0[0]), (P1 - P0) / P0[0]
+
+
+def _bump_run(oracle_mod, dx, eta, n_xi=8):
+    # one Gaussian bump (25 GeV/fm^3, 0.25 fm, off centre) on 10 GeV/fm^3 in a
+    # periodic 1.2 fm box, Minkowski, crossover EOS (grad M != 0), collisions on,
+    # evolved for 0.2 fm/c with dtau = dx / 20
+    from paper_1108_5561_gb300.inputs import coords
+    n = int(round(1.2 / dx))
+    o = oracle_mod.Oracle(nx=n, ny=n, dx=dx, metric=0, eta_over_s=eta, n_xi=n_xi)
+    X, Y = coords(n, n, dx)
+    f, lnM = o.init_state(10.0 + 25.0 * np.exp(-((X - 0.13) ** 2 + (Y + 0.07) ** 2) / (2 * 0.25 ** 2)))
+    P0 = _Ttau_with_bag(o, f, lnM) * dx * dx
+    o.step(f, lnM, 1.0, dx / 20, int(round(4 / dx)))
+    P1 = _Ttau_with_bag(o, f, lnM) * dx * dx
+    return (P1 - P0) / P0[0]
+
+
+def test_energy_with_mass_gradients_converges_with_the_grid(oracle_mod):
+    # The paper's scheme conserves T^{mu nu} + B g^{mu nu} for any EOS obeying the
+    # consistency condition (Sec. 3).  On the lattice, with a position-dependent
+    # mass, sum_x (T^{tau tau}_kin + B) changes by a spatial discretisation error
+    # of the mass-gradient terms: it falls by more than 2.5x when dx halves, and it
+    # does not depend on how far f is from equilibrium (eta/s from 0.03 to 1): the
+    # force applied to the local equilibrium (reading R5) is not its source.
+    d_coarse = _bump_run(oracle_mod, 0.1, 0.03)
+    d_visc = _bump_run(oracle_mod, 0.1, 1.0)
+    d_fine = _bump_run(oracle_mod, 0.05, 0.03)
+    print("energy change: dx 0.1 %.3e (eta/s 1: %.3e), dx 0.05 %.3e" % (d_coarse[0], d_visc[0], d_fine[0]))
+    assert 1e-4 < abs(d_coarse[0]) < 1e-2
+    assert abs(d_fine[0]) < abs(d_coarse[0]) / 2.5
+    assert abs(d_visc[0] - d_coarse[0]) < 0.05 * abs(d_coarse[0])
+    assert np.all(np.abs(d_coarse[1:]) < 1e-4) and np.all(np.abs(d_fine[1:]) < 1e-4)
+
+
+def test_uniform_energy_change_is_the_quadrature_error(oracle_mod):
+    # uniform crossover matter at rest in Minkowski: only the collision term acts,
+    # and it changes the energy at the rate at which the lattice moments of f_eq
+    # miss e(T) (the radial rule is not exact for M/T != z0): about 3e-6 per
+    # relaxation time at T ~ 0.3 GeV with 8 radial nodes, rounding with 16
+    out = {}
+    for n_xi, nph in ((8, 6), (16, 8)):
+        o = oracle_mod.Oracle(nx=2, ny=2, metric=0, eta_over_s=0.1, n_xi=n_xi, n_phi_half=nph)
+        f, lnM = o.init_state(np.full(4, 16.0))
+        P0 = _Ttau_with_bag(o, f, lnM)
+        o.step(f, lnM, 1.0, 0.01, 50)
+        out[n_xi] = (_Ttau_with_bag(o, f, lnM)[0] - P0[0]) / P0[0]
+    print("uniform energy change: 8 radial nodes %.2e, 16 %.2e" % (out[8], out[16]))
+    assert 1e-7 < abs(out[8]) < 1e-4
+    assert abs(out[16]) < 1e-11
+
+
+def test_hotspots_on_a_vacuum_floor_break_the_scheme(oracle_mod):
+    # The hotspot workload as first specified: dx = 0.2 fm and a floor of
+    # eps_EOS(0.10 GeV) = 0.005 GeV/fm^3 between 0.4 fm hotspots (a factor 2e4
+    # between neighbouring cells).  Matter streaming into a near-empty cell
+    # leaves it without a timelike T^{mu nu} (or below the EOS table), and the
+    # oracle stops with a numeric failure in the first steps, as the GPU path
+    # does.  The same window on the 10 GeV/fm^3 background that the benchmark
+    # workloads use runs.
+    from paper_1108_5561_gb300.inputs import hotspots
+    floor = oracle_mod.Oracle(nx=1, ny=1).eos(0.10)["eps"] / oracle_mod.HBARC ** 3
+    assert floor == pytest.approx(0.00503, rel=1e-2)
+    for fl, fails in ((floor, True), (10.0, False)):
+        full, amps, cen = hotspots(256, 256, dx=0.2, n=40, seed=1108, floor=fl)
+        cx, cy = cen[int(np.argmax(amps))]
+        x0, y0 = int(round(cx / 0.2 + 127.5)) - 8, int(round(cy / 0.2 + 127.5)) - 8
+        o = oracle_mod.Oracle(nx=16, ny=16, dx=0.2, eta_over_s=0.16)
+        f, lnM = o.init_state(full[y0:y0 + 16, x0:x0 + 16].copy())
+        if fails:
+            with pytest.raises(RuntimeError, match="status -3"):
+                o.step(f, lnM, 0.4, 0.0036, 5)
+        else:
+            o.step(f, lnM, 0.4, 0.0036, 5)
+
+
 def test_heun_is_second_order(oracle_mod):
     o = oracle_mod.Oracle(nx=1, ny=1, n_xi=6, n_theta=6, n_phi_half=1, eta_over_s=0.1)
     T = []
