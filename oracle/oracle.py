@@ -23,6 +23,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "rlb_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
+# the same source in complex arithmetic (complex-step derivatives, TangentOracle)
+_LIB_CS = os.path.join(_HERE, "_build", "liboracle_cs.so")
 
 HBARC = 0.1973269804  # GeV fm
 Z_QCD = math.pi ** 4 / 180.0 * (4 * (3 * 3 - 1) + 7 * 3 * 3)  # Sec. 3.1, N_c = N_f = 3
@@ -49,24 +51,29 @@ class OracleParams(ctypes.Structure):
         ("T0", ctypes.c_double),
         ("dx", ctypes.c_double),
         ("eta_over_s", ctypes.c_double),
+        ("eta_over_s_im", ctypes.c_double),
     ]
 
 
 DEFAULTS = dict(
     eos_kind=0, family=0, metric=1, nx=32, ny=32, n_xi=8, n_theta=8, n_phi_half=6,
     eos_a=13.9, eos_b=0.5, eos_Tc=0.17, eos_w=0.02, eos_m0=0.5, Z=Z_QCD,
-    z0=1.0, T0=0.3, dx=0.2, eta_over_s=0.08,
+    z0=1.0, T0=0.3, dx=0.2, eta_over_s=0.08, eta_over_s_im=0.0,
 )
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle shared library with gcc (-O2, OpenMP)."""
+    """Compile the oracle shared libraries with gcc (-O2, OpenMP): the FP64
+    oracle and the same source in complex arithmetic (-DOR_COMPLEX_STEP;
+    -fcx-limited-range: plain complex products and quotients, the operands
+    are finite)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + ".tmp%d" % os.getpid()
-        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
-        subprocess.check_call(cmd)
-        os.replace(tmp, _LIB)
+    for lib, extra in ((_LIB, []), (_LIB_CS, ["-DOR_COMPLEX_STEP", "-fcx-limited-range"])):
+        if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+            tmp = lib + ".tmp%d" % os.getpid()
+            cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", *extra, "-o", tmp, _SRC, "-lm"]
+            subprocess.check_call(cmd)
+            os.replace(tmp, lib)
     return _LIB
 
 
@@ -248,6 +255,96 @@ class Oracle:
 
 def _nt(n):
     return int(n) if n and n > 0 else (os.cpu_count() or 1)
+
+
+_lib_cs = None
+
+
+def _load_cs():
+    global _lib_cs
+    if _lib_cs is None:
+        build()
+        lib = ctypes.CDLL(_LIB_CS)
+        vp, d, i = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
+        lib.or_create.argtypes = [ctypes.POINTER(OracleParams), ctypes.POINTER(vp)]
+        lib.or_destroy.argtypes = [vp]
+        lib.or_destroy.restype = None
+        lib.or_num_nodes.argtypes = [vp]
+        lib.or_init_state.argtypes = [vp, vp, vp, vp, i]
+        lib.or_step.argtypes = [vp, vp, vp, d, d, i, i]
+        lib.or_moments.argtypes = [vp, vp, vp, vp, i]
+        lib.or_observables.argtypes = [vp, vp, vp, vp, i]
+        _lib_cs = lib
+    return _lib_cs
+
+
+class TangentOracle:
+    """The oracle's algorithm in complex arithmetic (the complex-step build of
+    rlb_oracle.c): inputs with imaginary parts h d carry, through every step,
+    imaginary parts that are h times the derivatives along d (forward-mode
+    differentiation, exact to rounding for h far below the real parts; no
+    subtraction as in finite differences).  eta_over_s_im is the imaginary
+    part of eta/s.  Arrays are complex128."""
+
+    def __init__(self, **kw):
+        p = dict(DEFAULTS)
+        unknown = set(kw) - set(p)
+        if unknown:
+            raise TypeError("unknown oracle parameters: %s" % sorted(unknown))
+        p.update(kw)
+        self.params = p
+        self._p = OracleParams(**{k: p[k] for k in p})
+        self._lib = _load_cs()
+        h = ctypes.c_void_p()
+        _check(self._lib.or_create(ctypes.byref(self._p), ctypes.byref(h)), "create")
+        self._h = h
+        self.nn = self._lib.or_num_nodes(self._h)
+        self.ns = p["nx"] * p["ny"]
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.or_destroy(h)
+            self._h = None
+
+    def init_state(self, eps0, nthreads: int = 0):
+        eps0 = np.ascontiguousarray(eps0, dtype=np.complex128).reshape(self.ns)
+        f = np.zeros((self.ns, self.nn), dtype=np.complex128)
+        lnM = np.zeros(self.ns, dtype=np.complex128)
+        _check(self._lib.or_init_state(self._h, eps0.ctypes.data, f.ctypes.data, lnM.ctypes.data,
+                                       _nt(nthreads)), "init")
+        return f, lnM
+
+    def step(self, f, lnM, tau, dtau, nsteps=1, nthreads: int = 0):
+        assert f.dtype == np.complex128 and f.flags.c_contiguous and lnM.dtype == np.complex128
+        _check(self._lib.or_step(self._h, f.ctypes.data, lnM.ctypes.data, float(tau), float(dtau),
+                                 int(nsteps), _nt(nthreads)), "step")
+        return f, lnM
+
+    def moments(self, f, lnM, nthreads: int = 0):
+        out = np.zeros((self.ns, 8), dtype=np.complex128)
+        _check(self._lib.or_moments(self._h, f.ctypes.data, lnM.ctypes.data, out.ctypes.data,
+                                    _nt(nthreads)), "moments")
+        return out
+
+    def observables(self, f, lnM, nthreads: int = 0):
+        out = np.zeros(2, dtype=np.complex128)
+        _check(self._lib.or_observables(self._h, f.ctypes.data, lnM.ctypes.data, out.ctypes.data,
+                                        _nt(nthreads)), "observables")
+        return complex(out[0]), complex(out[1])
+
+
+def v2_directional_derivative(eps0, d_eps0, d_eta, steps, tau0, dtau, h=1e-30, nthreads: int = 0, **kw):
+    """(v2, dv2 along (d_eps0, d_eta)) of the oracle run eps0 -> steps Heun
+    steps -> p_perp-weighted v2, by one complex-step run: eps0 + i h d_eps0,
+    eta/s + i h d_eta."""
+    eta = kw.pop("eta_over_s", DEFAULTS["eta_over_s"])
+    o = TangentOracle(eta_over_s=eta, eta_over_s_im=h * d_eta, **kw)
+    f, lnM = o.init_state(np.asarray(eps0, dtype=np.float64) + 1j * h * np.asarray(d_eps0, dtype=np.float64),
+                          nthreads)
+    o.step(f, lnM, tau0, dtau, steps, nthreads)
+    v2 = o.observables(f, lnM, nthreads)[1]
+    return v2.real, v2.imag / h
 
 
 if __name__ == "__main__":  # pragma: no cover

@@ -46,6 +46,37 @@
 #define OR_PI 3.14159265358979323846
 #define OR_HBARC 0.1973269804 /* GeV fm */
 
+/* Scalar of everything that depends on the state or on eta/s (the lattice,
+ * its weights and operators are plain doubles).  The default build uses
+ * double.  Built with -DOR_COMPLEX_STEP the same code runs in C99 double
+ * complex: an input with an imaginary part h * d (h tiny) returns outputs
+ * whose imaginary parts are h times their derivatives along d, exact to
+ * rounding (complex-step differentiation; every operation on the path is
+ * analytic, and comparisons, brackets and convergence tests look at real
+ * parts only).  That build serves as the forward-mode (tangent) oracle for
+ * the adjoint's gradients. */
+#ifdef OR_COMPLEX_STEP
+#include <complex.h>
+#undef I /* the imaginary unit is spelled _Complex_I; I is a variable name here */
+typedef double _Complex real_t;
+#define RE(v) creal(v)
+#define R_EXP cexp
+#define R_SQRT csqrt
+#define R_LOG clog
+#define R_COSH ccosh
+#define R_TANH ctanh
+#define R_POW cpow
+#else
+typedef double real_t;
+#define RE(v) (v)
+#define R_EXP exp
+#define R_SQRT sqrt
+#define R_LOG log
+#define R_COSH cosh
+#define R_TANH tanh
+#define R_POW pow
+#endif
+
 /* ------------------------------------------------------------------------ */
 /* parameters (mirrored by oracle/oracle.py)                                  */
 /* ------------------------------------------------------------------------ */
@@ -63,6 +94,7 @@ typedef struct {
   double T0;         /* conformal momentum scale [GeV] (family 1)          */
   double dx;         /* lattice spacing [fm]                               */
   double eta_over_s; /* INFINITY switches collisions off                   */
+  double eta_over_s_im; /* imaginary part of eta/s (complex-step build only) */
 } or_params;
 
 enum { OR_OK = 0, OR_ERR_ARG = -1, OR_ERR_NUMERIC = -3, OR_ERR_NOMEM = -6 };
@@ -73,35 +105,35 @@ enum { OR_OK = 0, OR_ERR_ARG = -1, OR_ERR_NUMERIC = -3, OR_ERR_NOMEM = -6 };
 /* this analytic, doubly-exponentially decaying integrand converges           */
 /* geometrically in 1/h (error ~ exp(-pi^2/h)); h = 1/16 is far below 1e-16. */
 /* ------------------------------------------------------------------------ */
-static void bessel_k0123(double x, double K[4]) {
+static void bessel_k0123(real_t x, real_t K[4]) {
   const double h = 1.0 / 16.0;
-  double e0 = exp(-x);
-  double s0 = 0.5 * e0, s1 = 0.5 * e0, s2 = 0.5 * e0, s3 = 0.5 * e0;
+  real_t e0 = R_EXP(-x);
+  real_t s0 = 0.5 * e0, s1 = 0.5 * e0, s2 = 0.5 * e0, s3 = 0.5 * e0;
   for (int i = 1; i < 100000; ++i) {
     double t = i * h;
-    double e = exp(-x * cosh(t));
+    real_t e = R_EXP(-x * cosh(t));
     double a1 = cosh(t), a2 = cosh(2 * t), a3 = cosh(3 * t);
     s0 += e;
     s1 += e * a1;
     s2 += e * a2;
     s3 += e * a3;
-    if (e == 0.0 || e * a3 < 1e-22 * s3) break;
+    if (RE(e) == 0.0 || RE(e) * a3 < 1e-22 * RE(s3)) break;
   }
   K[0] = h * s0; K[1] = h * s1; K[2] = h * s2; K[3] = h * s3;
 }
 
 /* J(x) = \int_0^inf sinh^6 t / cosh t exp(-x cosh t) dt, the shear-viscosity
  * integral of Sec. 4.1 after p = M sinh t (same trapezoid argument). */
-static double visc_integral(double x) {
+static real_t visc_integral(real_t x) {
   const double h = 1.0 / 16.0;
-  double s = 0.0;
+  real_t s = 0.0;
   for (int i = 1; i < 100000; ++i) {
     double t = i * h;
     double sh = sinh(t), ch = cosh(t);
-    double e = exp(-x * ch);
-    double term = e * sh * sh * sh * sh * sh * sh / ch;
+    real_t e = R_EXP(-x * ch);
+    real_t term = e * sh * sh * sh * sh * sh * sh / ch;
     s += term;
-    if (e == 0.0 || (t > 1.0 && term < 1e-22 * s)) break;
+    if (RE(e) == 0.0 || (t > 1.0 && RE(term) < 1e-22 * RE(s))) break;
   }
   return h * s;
 }
@@ -142,51 +174,60 @@ static void gauss_legendre(int n, double* x, double* w) {
 /* equation of state (Sec. 2.1, Eq. epsp, Sec. 3.1)                           */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-  double T;     /* GeV                                   */
-  double x;     /* M/T                                   */
-  double M;     /* equilibrium quasiparticle mass M(T)   */
-  double s;     /* entropy density s(T)  [GeV^3]         */
-  double sp;    /* ds/dT                                 */
-  double pkin;  /* Z M^2 T^2 K_2(M/T)/(2 pi^2)           */
-  double e;     /* kinetic equilibrium energy eps - B    */
-  double ep;    /* de/dT                                 */
-  double Bp;    /* dB/dT                                 */
-  double D;     /* dB/deps = B'(T) / (T s'(T))           */
-  double J;     /* \int d^3p/(2pi)^3 p^4/E^2 e^{-E/T}    */
-  double tauR;  /* relaxation time [fm] (Sec. 4.1)       */
+  real_t T;     /* GeV                                   */
+  real_t x;     /* M/T                                   */
+  real_t M;     /* equilibrium quasiparticle mass M(T)   */
+  real_t s;     /* entropy density s(T)  [GeV^3]         */
+  real_t sp;    /* ds/dT                                 */
+  real_t pkin;  /* Z M^2 T^2 K_2(M/T)/(2 pi^2)           */
+  real_t e;     /* kinetic equilibrium energy eps - B    */
+  real_t ep;    /* de/dT                                 */
+  real_t Bp;    /* dB/dT                                 */
+  real_t D;     /* dB/deps = B'(T) / (T s'(T))           */
+  real_t J;     /* \int d^3p/(2pi)^3 p^4/E^2 e^{-E/T}    */
+  real_t tauR;  /* relaxation time [fm] (Sec. 4.1)       */
 } eos_pt;
 
-static double sigma_of(const or_params* P, double T) {
-  return P->eos_a * 0.5 * (1.0 + tanh((T - P->eos_Tc) / P->eos_w)) + P->eos_b;
+static real_t sigma_of(const or_params* P, real_t T) {
+  return P->eos_a * 0.5 * (1.0 + R_TANH((T - P->eos_Tc) / P->eos_w)) + P->eos_b;
 }
-static double sigmap_of(const or_params* P, double T) {
-  double c = cosh((T - P->eos_Tc) / P->eos_w);
+static real_t sigmap_of(const or_params* P, real_t T) {
+  real_t c = R_COSH((T - P->eos_Tc) / P->eos_w);
   return P->eos_a * 0.5 / (P->eos_w * c * c);
 }
 
 /* x^3 K_3(x) decreases monotonically from 8 (x -> 0) to 0; solve
  * x^3 K_3(x) = tgt by Newton (derivative -x^3 K_2) inside a bisection bracket. */
-static double solve_x(double tgt, double guess) {
-  double lo = 1e-9, hi = 200.0, x = guess;
-  if (!(x > lo && x < hi)) x = 2.0;
+static real_t solve_x(real_t tgt, double guess) {
+  double lo = 1e-9, hi = 200.0;
+  real_t x = guess;
+  if (!(RE(x) > lo && RE(x) < hi)) x = 2.0;
   for (int it = 0; it < 300; ++it) {
-    double K[4];
+    real_t K[4];
     bessel_k0123(x, K);
-    double F = x * x * x * K[3] - tgt;
-    if (F > 0) lo = x; else hi = x;
-    double dF = -x * x * x * K[2];
-    double xn = x - F / dF;
-    if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
-    if (fabs(xn - x) <= 1e-16 * x) { x = xn; break; }
+    real_t F = x * x * x * K[3] - tgt;
+    if (RE(F) > 0) lo = RE(x); else hi = RE(x);
+    real_t dF = -x * x * x * K[2];
+    real_t xn = x - F / dF;
+    if (!(RE(xn) > lo && RE(xn) < hi)) xn = 0.5 * (lo + hi);
+    if (fabs(RE(xn) - RE(x)) <= 1e-16 * RE(x)) { x = xn; break; }
     x = xn;
     if (hi - lo <= 2e-16 * hi) break;
   }
+#ifdef OR_COMPLEX_STEP
+  {  /* one Newton step at the converged point sets the imaginary part exactly
+        (a bisection step would have dropped it) */
+    real_t K[4];
+    bessel_k0123(x, K);
+    x = x - (x * x * x * K[3] - tgt) / (-x * x * x * K[2]);
+  }
+#endif
   return x;
 }
 
 /* All local EOS quantities at temperature T (everything except B and p,
  * which need the integral of s). */
-static void eos_eval(const or_params* P, double T, double x_guess, eos_pt* o) {
+static void eos_eval(const or_params* P, real_t T, double x_guess, eos_pt* o) {
   const double Z = P->Z, c2 = 2.0 * OR_PI * OR_PI;
   memset(o, 0, sizeof(*o));
   o->T = T;
@@ -198,9 +239,9 @@ static void eos_eval(const or_params* P, double T, double x_guess, eos_pt* o) {
     o->e = 3.0 * o->pkin;
     o->ep = 4.0 * o->e / T;
     o->Bp = 0.0; o->D = 0.0;
-    o->J = 24.0 * pow(T, 5) / c2;
+    o->J = 24.0 * R_POW(T, 5) / c2;
   } else {
-    double x, K[4];
+    real_t x, K[4];
     if (P->eos_kind == 1) {
       x = P->eos_m0 / T;
       bessel_k0123(x, K);
@@ -208,15 +249,15 @@ static void eos_eval(const or_params* P, double T, double x_guess, eos_pt* o) {
       o->sp = Z * pow(P->eos_m0, 3) * (x * K[2] + 3.0 * K[3]) / (c2 * T);
       o->Bp = 0.0;
     } else {
-      double sg = sigma_of(P, T);
+      real_t sg = sigma_of(P, T);
       x = solve_x(c2 * sg / Z, x_guess);
       bessel_k0123(x, K);
       o->s = T * T * T * sg;
       o->sp = 3.0 * T * T * sg + T * T * T * sigmap_of(P, T);
       /* implicit derivative of x^3 K_3(x) = 2 pi^2 sigma(T)/Z */
-      double xp = -(c2 * sigmap_of(P, T) / Z) / (x * x * x * K[2]);
-      double Mp = x + T * xp;
-      double M = x * T;
+      real_t xp = -(c2 * sigmap_of(P, T) / Z) / (x * x * x * K[2]);
+      real_t Mp = x + T * xp;
+      real_t M = x * T;
       o->Bp = -Z * M * M * T * K[1] * Mp / c2; /* Sec. 3.1 consistency ODE */
     }
     o->x = x;
@@ -225,10 +266,15 @@ static void eos_eval(const or_params* P, double T, double x_guess, eos_pt* o) {
     o->e = T * o->s - o->pkin;     /* = Z M^2 T^2 [3 K_2 + x K_1]/(2 pi^2) */
     o->ep = T * o->sp - o->Bp;
     o->D = o->Bp / (T * o->sp);
-    o->J = pow(o->M, 5) * visc_integral(x) / c2;
+    o->J = R_POW(o->M, 5) * visc_integral(x) / c2;
   }
   /* eta = tau_R Z J / (15 T), eta = (eta/s) s  (Sec. 4.1) */
-  double tauR_GeV = 15.0 * T * P->eta_over_s * o->s / (Z * o->J);
+#ifdef OR_COMPLEX_STEP
+  const real_t eta_s = P->eta_over_s + _Complex_I * P->eta_over_s_im;
+#else
+  const real_t eta_s = P->eta_over_s;
+#endif
+  real_t tauR_GeV = 15.0 * T * eta_s * o->s / (Z * o->J);
   o->tauR = tauR_GeV * OR_HBARC;
 }
 
@@ -253,17 +299,17 @@ typedef struct or_ctx {
  * <= 0.005 GeV; s(T) = T^3 sigma(T) is analytic within pi w/2 of the real axis,
  * so every panel is exact to rounding).  B = p_kin - p is then the solution of
  * the consistency ODE of Sec. 3.1 with B(0) = 0, because dp_kin/dT = s + dB/dT. */
-static double p_of_T(const or_ctx* C, double T, const eos_pt* e) {
+static real_t p_of_T(const or_ctx* C, real_t T, const eos_pt* e) {
   const or_params* P = &C->P;
   if (P->eos_kind == 2) return P->Z * T * T * T * T / (OR_PI * OR_PI);
   if (P->eos_kind == 1) return e->pkin;
-  int npan = (int)ceil(T / 0.005);
+  int npan = (int)ceil(RE(T) / 0.005);
   if (npan < 1) npan = 1;
-  double h = T / npan, sum = 0.0;
+  real_t h = T / npan, sum = 0.0;
   for (int q = 0; q < npan; ++q) {
-    double a = q * h, part = 0.0;
+    real_t a = q * h, part = 0.0;
     for (int i = 0; i < 16; ++i) {
-      double t = a + 0.5 * h * (C->g16x[i] + 1.0);
+      real_t t = a + 0.5 * h * (C->g16x[i] + 1.0);
       part += C->g16w[i] * t * t * t * sigma_of(P, t);
     }
     sum += 0.5 * h * part;
@@ -271,7 +317,7 @@ static double p_of_T(const or_ctx* C, double T, const eos_pt* e) {
   return sum;
 }
 
-static double B_of_T(const or_ctx* C, double T, const eos_pt* e) {
+static real_t B_of_T(const or_ctx* C, real_t T, const eos_pt* e) {
   if (C->P.eos_kind != 0) return 0.0;
   return e->pkin - p_of_T(C, T, e);
 }
@@ -279,27 +325,36 @@ static double B_of_T(const or_ctx* C, double T, const eos_pt* e) {
 /* Solve ln e(T) = ln target for T by Newton in ln T, inside a bisection
  * bracket.  which = 0: e = eps - B (kinetic matching, Eq. sanity with B at its
  * equilibrium value); which = 1: e = eps_EOS(T) = T s - p (initial condition). */
-static int solve_T(const or_ctx* C, double target, int which, double T_guess, double* T_out,
+static int solve_T(const or_ctx* C, real_t target, int which, double T_guess, real_t* T_out,
                    eos_pt* e_out) {
   double ylo = log(1e-3), yhi = log(50.0);
-  double y = (T_guess > 1e-3 && T_guess < 50.0) ? log(T_guess) : log(0.3);
-  double lt = log(target), xg = 2.0;
+  real_t y = (T_guess > 1e-3 && T_guess < 50.0) ? log(T_guess) : log(0.3);
+  real_t lt = R_LOG(target);
+  double xg = 2.0;
   eos_pt e;
   for (int it = 0; it < 400; ++it) {
-    double T = exp(y);
+    real_t T = R_EXP(y);
     eos_eval(&C->P, T, xg, &e);
-    xg = e.x;
-    double val, dval;
+    xg = RE(e.x);
+    real_t val, dval;
     if (which == 0) { val = e.e; dval = e.ep; }
     else { val = T * e.s - p_of_T(C, T, &e); dval = T * e.sp; }
-    double F = log(val) - lt;
-    if (F < 0) ylo = y; else yhi = y;
-    double yn = y - F / (T * dval / val);
-    if (!(yn > ylo && yn < yhi)) yn = 0.5 * (ylo + yhi);
-    if (fabs(yn - y) < 1e-15) {
+    real_t F = R_LOG(val) - lt;
+    if (RE(F) < 0) ylo = RE(y); else yhi = RE(y);
+    real_t yn = y - F / (T * dval / val);
+    if (!(RE(yn) > ylo && RE(yn) < yhi)) yn = 0.5 * (ylo + yhi);
+    if (fabs(RE(yn) - RE(y)) < 1e-15) {
       y = yn;
-      T = exp(y);
+      T = R_EXP(y);
       eos_eval(&C->P, T, xg, &e);
+#ifdef OR_COMPLEX_STEP
+      {  /* one more Newton step: the imaginary part of y is then exact */
+        real_t v2 = which == 0 ? e.e : T * e.s - p_of_T(C, T, &e), d2 = which == 0 ? e.ep : T * e.sp;
+        y = y - (R_LOG(v2) - lt) / (T * d2 / v2);
+        T = R_EXP(y);
+        eos_eval(&C->P, T, xg, &e);
+      }
+#endif
       *T_out = T;
       if (e_out) *e_out = e;
       return OR_OK;
@@ -307,7 +362,7 @@ static int solve_T(const or_ctx* C, double target, int which, double T_guess, do
     y = yn;
     if (yhi - ylo < 1e-15) break;
   }
-  *T_out = exp(y);
+  *T_out = R_EXP(y);
   eos_eval(&C->P, *T_out, xg, &e);
   if (e_out) *e_out = e;
   return (yhi - ylo < 1e-13) ? OR_OK : OR_ERR_NUMERIC;
@@ -503,33 +558,34 @@ static int build_operators(or_ctx* C) {
 /* the eigenvalue of largest modulus is eps (the others are -p_i, |p_i| < eps).*/
 /* Orthonormal Milne frame (tau, x, y, tau*eta_s).                             */
 /* ------------------------------------------------------------------------ */
-static int landau(const double Tk[16], double u[4], double* eps) {
+static int landau(const real_t Tk[16], real_t u[4], real_t* eps) {
   static const double g[4] = {1.0, -1.0, -1.0, -1.0};
-  double v[4] = {1.0, 0.0, 0.0, 0.0};
+  real_t v[4] = {1.0, 0.0, 0.0, 0.0};
   int tail = -1;
   for (int it = 0; it < 20000; ++it) {
-    double w[4], n2 = 0.0;
+    real_t w[4], n2 = 0.0;
     for (int m = 0; m < 4; ++m) {
       w[m] = 0.0;
       for (int nu = 0; nu < 4; ++nu) w[m] += Tk[m * 4 + nu] * g[nu] * v[nu];
       n2 += w[m] * w[m];
     }
-    double nrm = sqrt(n2), d = 0.0;
-    if (!(nrm > 0.0)) return OR_ERR_NUMERIC;
-    if (w[0] < 0) nrm = -nrm;
+    real_t nrm = R_SQRT(n2);
+    double d = 0.0;
+    if (!(RE(nrm) > 0.0)) return OR_ERR_NUMERIC;
+    if (RE(w[0]) < 0) nrm = -nrm;
     for (int m = 0; m < 4; ++m) {
       w[m] /= nrm;
-      d = fmax(d, fabs(w[m] - v[m]));
+      d = fmax(d, fabs(RE(w[m]) - RE(v[m])));
       v[m] = w[m];
     }
     if (tail < 0 && d < 1e-15) tail = 60;
     if (tail >= 0 && tail-- == 0) break;
   }
-  double nn = v[0] * v[0] - v[1] * v[1] - v[2] * v[2] - v[3] * v[3];
-  if (!(nn > 0.0)) return OR_ERR_NUMERIC;
-  double r = 1.0 / sqrt(nn);
+  real_t nn = v[0] * v[0] - v[1] * v[1] - v[2] * v[2] - v[3] * v[3];
+  if (!(RE(nn) > 0.0)) return OR_ERR_NUMERIC;
+  real_t r = 1.0 / R_SQRT(nn);
   for (int m = 0; m < 4; ++m) u[m] = v[m] * r;
-  double e = 0.0;
+  real_t e = 0.0;
   for (int m = 0; m < 4; ++m)
     for (int nu = 0; nu < 4; ++nu) e += g[m] * u[m] * g[nu] * u[nu] * Tk[m * 4 + nu];
   *eps = e;
@@ -593,34 +649,34 @@ int or_operators(const or_ctx* C, double* Dr, double* Dth) {
 }
 
 /* out: x, M, s, s', p_kin, e(=eps-B), e', B', D, J, tauR[fm], p, B, eps, K1, K2 */
-int or_eos(const or_ctx* C, double T, double* out) {
+int or_eos(const or_ctx* C, real_t T, real_t* out) {
   eos_pt e;
   eos_eval(&C->P, T, 2.0, &e);
-  double p = p_of_T(C, T, &e);
-  double K[4] = {0, 0, 0, 0};
+  real_t p = p_of_T(C, T, &e);
+  real_t K[4] = {0, 0, 0, 0};
   if (C->P.eos_kind != 2) bessel_k0123(e.x, K);
-  double v[16] = {e.x, e.M, e.s, e.sp, e.pkin, e.e, e.ep, e.Bp, e.D, e.J, e.tauR, p,
+  real_t v[16] = {e.x, e.M, e.s, e.sp, e.pkin, e.e, e.ep, e.Bp, e.D, e.J, e.tauR, p,
                   B_of_T(C, T, &e), T * e.s - p, K[1], K[2]};
   memcpy(out, v, sizeof(v));
   return OR_OK;
 }
 
-int or_solve_T(const or_ctx* C, double target, int which, double* T) {
+int or_solve_T(const or_ctx* C, real_t target, int which, real_t* T) {
   return solve_T(C, target, which, 0.3, T, NULL);
 }
 
-int or_landau(const double* Tk, double* u, double* eps) { return landau(Tk, u, eps); }
+int or_landau(const real_t* Tk, real_t* u, real_t* eps) { return landau(Tk, u, eps); }
 
-int or_bessel(double x, double* K) { bessel_k0123(x, K); return OR_OK; }
+int or_bessel(real_t x, real_t* K) { bessel_k0123(x, K); return OR_OK; }
 
 /* ------------------------------------------------------------------------ */
 /* one stage of the right-hand side at one site                               */
 /* ------------------------------------------------------------------------ */
-typedef const double* (*or_getf)(void* ud, int site);
-typedef double (*or_getm)(void* ud, int site);
+typedef const real_t* (*or_getf)(void* ud, int site);
+typedef real_t (*or_getm)(void* ud, int site);
 
 typedef struct {
-  double T, u[4], eps_kin, M, Meq, D, tauR, K, B;
+  real_t T, u[4], eps_kin, M, Meq, D, tauR, K, B;
 } or_site;
 
 static int site_index(const or_params* P, int x, int y) {
@@ -632,10 +688,10 @@ static int site_index(const or_params* P, int x, int y) {
 /* matching of one site's populations: T^{mu nu}_kin = M^4/(2 pi^2) sum_n w_n
  * f_n P^_n P^_n (Eq. emtnew, P^ = (cosh xi, v)), Landau u and eps_kin, then T
  * from e(T) = eps_kin and the EOS at T. */
-static int match_site(const or_ctx* C, const double* f, double lnM, double T_guess, or_site* o) {
+static int match_site(const or_ctx* C, const real_t* f, real_t lnM, double T_guess, or_site* o) {
   const int Nx = C->nxi, Nt = C->nth, Np = C->nph;
-  double Tk[16] = {0};
-  double K = 0.0;
+  real_t Tk[16] = {0};
+  real_t K = 0.0;
   for (int l = 0; l < Np; ++l)
     for (int j = 0; j < Nt; ++j)
       for (int k = 0; k < Nx; ++k) {
@@ -647,14 +703,14 @@ static int match_site(const or_ctx* C, const double* f, double lnM, double T_gue
           for (int b = 0; b < 4; ++b) Tk[a * 4 + b] += w * f[n] * Ph[a] * Ph[b];
         K += w * f[n];
       }
-  double M = exp(lnM);
-  double pref = M * M * M * M / (2.0 * OR_PI * OR_PI);
+  real_t M = R_EXP(lnM);
+  real_t pref = M * M * M * M / (2.0 * OR_PI * OR_PI);
   for (int a = 0; a < 16; ++a) Tk[a] *= pref;
   o->K = K * pref;
   o->M = M;
   int rc = landau(Tk, o->u, &o->eps_kin);
   if (rc) return rc;
-  if (!(o->eps_kin > 0.0)) return OR_ERR_NUMERIC;
+  if (!(RE(o->eps_kin) > 0.0)) return OR_ERR_NUMERIC;
   eos_pt e;
   rc = solve_T(C, o->eps_kin, 0, T_guess, &o->T, &e);
   if (rc) return rc;
@@ -677,38 +733,38 @@ static int match_site(const or_ctx* C, const double* f, double lnM, double T_gue
  * eigenvalues of positive real part ~ 9 |a|).  Streaming is second-order upwind
  * per axis, periodic.  `o` is the site's matching.  work: 3 nn doubles. */
 static int stage_site(const or_ctx* C, or_getf gf, or_getm gm, void* ud, int site,
-                      double tau, const or_site* os, double* rhs, double* g_out, double* work) {
+                      double tau, const or_site* os, real_t* rhs, real_t* g_out, real_t* work) {
   const or_params* P = &C->P;
   const int Nx = C->nxi, Nt = C->nth, Np = C->nph, nn = C->nn;
   const int x = site % P->nx, y = site / P->nx;
-  const double* f = gf(ud, site);
+  const real_t* f = gf(ud, site);
   const or_site o = *os;
-  const double M = o.M, T = o.T, invT = 1.0 / T;
-  const double inv_tauR = 1.0 / o.tauR;
-  const double ut = o.u[0], ux = o.u[1], uy = o.u[2], uz = o.u[3];
-  const double* fxm1 = gf(ud, site_index(P, x - 1, y));
-  const double* fxm2 = gf(ud, site_index(P, x - 2, y));
-  const double* fxp1 = gf(ud, site_index(P, x + 1, y));
-  const double* fxp2 = gf(ud, site_index(P, x + 2, y));
-  const double* fym1 = gf(ud, site_index(P, x, y - 1));
-  const double* fym2 = gf(ud, site_index(P, x, y - 2));
-  const double* fyp1 = gf(ud, site_index(P, x, y + 1));
-  const double* fyp2 = gf(ud, site_index(P, x, y + 2));
-  const double ax = (gm(ud, site_index(P, x + 1, y)) - gm(ud, site_index(P, x - 1, y))) / (2.0 * P->dx);
-  const double ay = (gm(ud, site_index(P, x, y + 1)) - gm(ud, site_index(P, x, y - 1))) / (2.0 * P->dx);
-  double* Drf = work;
-  double* Dthf = work + nn;
-  double* R = work + 2 * nn;
+  const real_t M = o.M, T = o.T, invT = 1.0 / T;
+  const real_t inv_tauR = isinf(RE(o.tauR)) ? 0.0 : 1.0 / o.tauR;
+  const real_t ut = o.u[0], ux = o.u[1], uy = o.u[2], uz = o.u[3];
+  const real_t* fxm1 = gf(ud, site_index(P, x - 1, y));
+  const real_t* fxm2 = gf(ud, site_index(P, x - 2, y));
+  const real_t* fxp1 = gf(ud, site_index(P, x + 1, y));
+  const real_t* fxp2 = gf(ud, site_index(P, x + 2, y));
+  const real_t* fym1 = gf(ud, site_index(P, x, y - 1));
+  const real_t* fym2 = gf(ud, site_index(P, x, y - 2));
+  const real_t* fyp1 = gf(ud, site_index(P, x, y + 1));
+  const real_t* fyp2 = gf(ud, site_index(P, x, y + 2));
+  const real_t ax = (gm(ud, site_index(P, x + 1, y)) - gm(ud, site_index(P, x - 1, y))) / (2.0 * P->dx);
+  const real_t ay = (gm(ud, site_index(P, x, y + 1)) - gm(ud, site_index(P, x, y - 1))) / (2.0 * P->dx);
+  real_t* Drf = work;
+  real_t* Dthf = work + nn;
+  real_t* R = work + 2 * nn;
   for (int l = 0; l < Np; ++l)
     for (int j = 0; j < Nt; ++j)
       for (int k = 0; k < Nx; ++k) {
         int n = (l * Nt + j) * Nx + k;
-        double a = 0.0, b = 0.0;
+        real_t a = 0.0, b = 0.0;
         for (int q = 0; q < Nx; ++q) a += C->Dr[k * Nx + q] * f[(l * Nt + j) * Nx + q];
         for (int q = 0; q < Nt; ++q) b += C->Dth[j * Nt + q] * f[(l * Nt + q) * Nx + k];
         Drf[n] = a; Dthf[n] = b;
       }
-  double K = 0.0, E = 0.0, Q = 0.0, A = 0.0;
+  real_t K = 0.0, E = 0.0, Q = 0.0, A = 0.0;
   for (int l = 0; l < Np; ++l)
     for (int j = 0; j < Nt; ++j)
       for (int k = 0; k < Nx; ++k) {
@@ -716,24 +772,24 @@ static int stage_site(const or_ctx* C, or_getf gf, or_getm gm, void* ud, int sit
         const double c = C->c[k], s = C->s[k], st = C->sth[j], mu = C->mu[j];
         const double vx = s * st * C->cph[l], vy = s * st * C->sph[l], vz = s * mu;
         const double Vx = vx / c, Vy = vy / c;
-        double dfx = 0.0, dfy = 0.0;
+        real_t dfx = 0.0, dfy = 0.0;
         if (Vx > 0) dfx = (3.0 * f[n] - 4.0 * fxm1[n] + fxm2[n]) / (2.0 * P->dx);
         else if (Vx < 0) dfx = (-3.0 * f[n] + 4.0 * fxp1[n] - fxp2[n]) / (2.0 * P->dx);
         if (Vy > 0) dfy = (3.0 * f[n] - 4.0 * fym1[n] + fym2[n]) / (2.0 * P->dx);
         else if (Vy < 0) dfy = (-3.0 * f[n] + 4.0 * fyp1[n] - fyp2[n]) / (2.0 * P->dx);
-        const double stream = -Vx * dfx - Vy * dfy;
-        const double milne = P->metric ? (mu * mu * Drf[n] + Dthf[n]) / tau : 0.0;
-        const double Eeq = sqrt(o.Meq * o.Meq + M * M * s * s);
-        const double PeqU = ut * Eeq - M * (vx * ux + vy * uy + vz * uz);
-        const double feq = P->Z * exp(-PeqU * invT);
+        const real_t stream = -Vx * dfx - Vy * dfy;
+        const real_t milne = P->metric ? (mu * mu * Drf[n] + Dthf[n]) / tau : 0.0;
+        const real_t Eeq = R_SQRT(o.Meq * o.Meq + M * M * s * s);
+        const real_t PeqU = ut * Eeq - M * (vx * ux + vy * uy + vz * uz);
+        const real_t feq = P->Z * R_EXP(-PeqU * invT);
         /* d_v f_eq = -(f_eq/T) (u^tau M^2 v/E_eq - M u): node motion (a.v/c) v.d_v and
          * force (a/c).d_v applied to it */
-        const double av = ax * vx + ay * vy;
-        const double vu3 = vx * ux + vy * uy + vz * uz;
-        const double TM = -feq * invT * ((av / c) * (ut * M * M * s * s / Eeq - M * vu3) +
+        const real_t av = ax * vx + ay * vy;
+        const real_t vu3 = vx * ux + vy * uy + vz * uz;
+        const real_t TM = -feq * invT * ((av / c) * (ut * M * M * s * s / Eeq - M * vu3) +
                                          (ut * M * M * av / Eeq - M * (ax * ux + ay * uy)) / c);
-        const double pu = c * ut - (vx * ux + vy * uy + vz * uz);
-        const double coll = -(pu / c) * (f[n] - feq) * inv_tauR;
+        const real_t pu = c * ut - (vx * ux + vy * uy + vz * uz);
+        const real_t coll = -(pu / c) * (f[n] - feq) * inv_tauR;
         R[n] = stream + milne + TM + coll;
         const double w = C->ecw[k] * C->wth[j] / (2.0 * Np);
         K += w * f[n];
@@ -746,26 +802,26 @@ static int stage_site(const or_ctx* C, or_getf gf, or_getm gm, void* ud, int sit
    * (the M^4/(2 pi^2) prefactor cancels).  At u = (1,0) this is the paper's
    * predictor -(dB/deps) sum w cosh^2 R / sum w f, because the discrete
    * integration by parts gives 4 E + Q = K exactly there. */
-  const double D = o.D;
-  const double g = -D * A / (K + D * (4.0 * E + Q - K));
+  const real_t D = o.D;
+  const real_t g = -D * A / (K + D * (4.0 * E + Q - K));
   for (int n = 0; n < nn; ++n) rhs[n] = R[n] + g * Drf[n];
   *g_out = g;
-  if (!isfinite(g)) return OR_ERR_NUMERIC;
+  if (!isfinite(RE(g))) return OR_ERR_NUMERIC;
   return OR_OK;
 }
 
 /* ------------------------------------------------------------------------ */
 /* full-grid accessors and the Heun step (Sec. 4.4 predictor / trapezoid)     */
 /* ------------------------------------------------------------------------ */
-typedef struct { const double* f; const double* lnM; int nn; } or_grid;
-static const double* grid_f(void* ud, int site) {
+typedef struct { const real_t* f; const real_t* lnM; int nn; } or_grid;
+static const real_t* grid_f(void* ud, int site) {
   or_grid* G = (or_grid*)ud; return G->f + (size_t)site * G->nn;
 }
-static double grid_m(void* ud, int site) { return ((or_grid*)ud)->lnM[site]; }
+static real_t grid_m(void* ud, int site) { return ((or_grid*)ud)->lnM[site]; }
 
 /* One stage on the whole grid: match every site, then evaluate the RHS. */
-static int stage_grid(const or_ctx* C, const double* fin, const double* lnMin, double tau,
-                      double* rhs, double* g, double* Tcache, int nthreads) {
+static int stage_grid(const or_ctx* C, const real_t* fin, const real_t* lnMin, double tau,
+                      real_t* rhs, real_t* g, double* Tcache, int nthreads) {
   const int ns = C->P.nx * C->P.ny, nn = C->nn;
   or_site* S = (or_site*)malloc(sizeof(or_site) * ns);
   if (!S) return OR_ERR_NOMEM;
@@ -782,7 +838,7 @@ static int stage_grid(const or_ctx* C, const double* fin, const double* lnMin, d
 #endif
       err = rc;
     } else {
-      Tcache[i] = S[i].T;
+      Tcache[i] = RE(S[i].T);
     }
   }
   if (err) { free(S); return err; }
@@ -790,7 +846,7 @@ static int stage_grid(const or_ctx* C, const double* fin, const double* lnMin, d
 #pragma omp parallel num_threads(nthreads > 0 ? nthreads : 1)
 #endif
   {
-    double* work = (double*)malloc(sizeof(double) * 3 * nn);
+    real_t* work = (real_t*)malloc(sizeof(real_t) * 3 * nn);
 #ifdef _OPENMP
 #pragma omp for schedule(static)
 #endif
@@ -811,14 +867,14 @@ static int stage_grid(const or_ctx* C, const double* fin, const double* lnMin, d
   return err;
 }
 
-int or_step(const or_ctx* C, double* f, double* lnM, double tau, double dtau, int nsteps,
+int or_step(const or_ctx* C, real_t* f, real_t* lnM, double tau, double dtau, int nsteps,
             int nthreads) {
   const int ns = C->P.nx * C->P.ny, nn = C->nn;
   const size_t tot = (size_t)ns * nn;
-  double* fs = (double*)malloc(sizeof(double) * tot);
-  double* rhs = (double*)malloc(sizeof(double) * tot);
-  double* lnMs = (double*)malloc(sizeof(double) * ns);
-  double* g = (double*)malloc(sizeof(double) * ns);
+  real_t* fs = (real_t*)malloc(sizeof(real_t) * tot);
+  real_t* rhs = (real_t*)malloc(sizeof(real_t) * tot);
+  real_t* lnMs = (real_t*)malloc(sizeof(real_t) * ns);
+  real_t* g = (real_t*)malloc(sizeof(real_t) * ns);
   double* Tc = (double*)malloc(sizeof(double) * ns);
   int rc = OR_OK;
   if (!fs || !rhs || !lnMs || !g || !Tc) rc = OR_ERR_NOMEM;
@@ -839,7 +895,7 @@ int or_step(const or_ctx* C, double* f, double* lnM, double tau, double dtau, in
 }
 
 /* the stage right-hand side of the whole grid (for tests) */
-int or_rhs(const or_ctx* C, const double* f, const double* lnM, double tau, double* rhs, double* g,
+int or_rhs(const or_ctx* C, const real_t* f, const real_t* lnM, double tau, real_t* rhs, real_t* g,
            int nthreads) {
   const int ns = C->P.nx * C->P.ny;
   double* Tc = (double*)malloc(sizeof(double) * ns);
@@ -851,7 +907,7 @@ int or_rhs(const or_ctx* C, const double* f, const double* lnM, double tau, doub
 }
 
 /* per site: eps [GeV/fm^3], T [GeV], u^tau, u^x, u^y, M [GeV], P_L [GeV/fm^3], M(T) [GeV] */
-int or_moments(const or_ctx* C, const double* f, const double* lnM, double* out, int nthreads) {
+int or_moments(const or_ctx* C, const real_t* f, const real_t* lnM, real_t* out, int nthreads) {
   const int ns = C->P.nx * C->P.ny, nn = C->nn;
   const double h3 = OR_HBARC * OR_HBARC * OR_HBARC;
   int err = OR_OK;
@@ -860,7 +916,7 @@ int or_moments(const or_ctx* C, const double* f, const double* lnM, double* out,
 #endif
   for (int i = 0; i < ns; ++i) {
     or_site o;
-    const double* fi = f + (size_t)i * nn;
+    const real_t* fi = f + (size_t)i * nn;
     int rc = match_site(C, fi, lnM[i], 0.3, &o);
     if (rc) {
 #ifdef _OPENMP
@@ -870,7 +926,7 @@ int or_moments(const or_ctx* C, const double* f, const double* lnM, double* out,
       continue;
     }
     /* kinetic zz component for the longitudinal pressure */
-    double Tzz = 0.0;
+    real_t Tzz = 0.0;
     for (int l = 0; l < C->nph; ++l)
       for (int j = 0; j < C->nth; ++j)
         for (int k = 0; k < C->nxi; ++k) {
@@ -878,8 +934,8 @@ int or_moments(const or_ctx* C, const double* f, const double* lnM, double* out,
           double vz = C->s[k] * C->mu[j];
           Tzz += w * fi[(l * C->nth + j) * C->nxi + k] * vz * vz;
         }
-    Tzz *= pow(o.M, 4) / (2.0 * OR_PI * OR_PI);
-    double* r = out + (size_t)i * 8;
+    Tzz *= R_POW(o.M, 4) / (2.0 * OR_PI * OR_PI);
+    real_t* r = out + (size_t)i * 8;
     r[0] = (o.eps_kin + o.B) / h3;
     r[1] = o.T;
     r[2] = o.u[0]; r[3] = o.u[1]; r[4] = o.u[2];
@@ -899,9 +955,9 @@ int or_moments(const or_ctx* C, const double* f, const double* lnM, double* out,
  *           W_n = M^2 w_n / (2 pi^2),  p_perp,n = M sinh xi_k sin theta_j.
  * B(T) comes from matching each site.  out[0] = eps_p, out[1] = v2.  The sums
  * over sites run in site order. */
-int or_observables(const or_ctx* C, const double* f, const double* lnM, double* out, int nthreads) {
+int or_observables(const or_ctx* C, const real_t* f, const real_t* lnM, real_t* out, int nthreads) {
   const int ns = C->P.nx * C->P.ny, nn = C->nn;
-  double* part = (double*)malloc(sizeof(double) * 4 * (size_t)ns);
+  real_t* part = (real_t*)malloc(sizeof(real_t) * 4 * (size_t)ns);
   if (!part) return OR_ERR_NUMERIC;
   int err = OR_OK;
 #ifdef _OPENMP
@@ -909,7 +965,7 @@ int or_observables(const or_ctx* C, const double* f, const double* lnM, double* 
 #endif
   for (int i = 0; i < ns; ++i) {
     or_site o;
-    const double* fi = f + (size_t)i * nn;
+    const real_t* fi = f + (size_t)i * nn;
     int rc = match_site(C, fi, lnM[i], 0.3, &o);
     if (rc) {
 #ifdef _OPENMP
@@ -918,12 +974,12 @@ int or_observables(const or_ctx* C, const double* f, const double* lnM, double* 
       err = rc;
       continue;
     }
-    double txx = 0.0, tyy = 0.0, num = 0.0, den = 0.0;
+    real_t txx = 0.0, tyy = 0.0, num = 0.0, den = 0.0;
     for (int l = 0; l < C->nph; ++l)
       for (int j = 0; j < C->nth; ++j)
         for (int k = 0; k < C->nxi; ++k) {
           const double w = C->ecw[k] * C->wth[j] / (2.0 * C->nph);
-          const double fn = fi[(l * C->nth + j) * C->nxi + k];
+          const real_t fn = fi[(l * C->nth + j) * C->nxi + k];
           const double vx = C->s[k] * C->sth[j] * C->cph[l], vy = C->s[k] * C->sth[j] * C->sph[l];
           const double vperp = C->s[k] * C->sth[j];
           const double cos2phi = C->cph[l] * C->cph[l] - C->sph[l] * C->sph[l];
@@ -932,13 +988,13 @@ int or_observables(const or_ctx* C, const double* f, const double* lnM, double* 
           num += w * fn * vperp * cos2phi;
           den += w * fn * vperp;
         }
-    const double M = o.M, m4 = M * M * M * M / (2.0 * OR_PI * OR_PI), m3 = M * M * M / (2.0 * OR_PI * OR_PI);
+    const real_t M = o.M, m4 = M * M * M * M / (2.0 * OR_PI * OR_PI), m3 = M * M * M / (2.0 * OR_PI * OR_PI);
     part[4 * (size_t)i + 0] = m4 * txx - o.B;
     part[4 * (size_t)i + 1] = m4 * tyy - o.B;
     part[4 * (size_t)i + 2] = m3 * num;
     part[4 * (size_t)i + 3] = m3 * den;
   }
-  double sxx = 0.0, syy = 0.0, sn = 0.0, sd = 0.0;
+  real_t sxx = 0.0, syy = 0.0, sn = 0.0, sd = 0.0;
   for (int i = 0; i < ns; ++i) {
     sxx += part[4 * (size_t)i + 0];
     syy += part[4 * (size_t)i + 1];
@@ -952,7 +1008,7 @@ int or_observables(const or_ctx* C, const double* f, const double* lnM, double* 
 }
 
 /* initial state: T from eps_EOS(T) = eps0, M = M(T), u = 0, f = f_eq */
-int or_init_state(const or_ctx* C, const double* eps0, double* f, double* lnM, int nthreads) {
+int or_init_state(const or_ctx* C, const real_t* eps0, real_t* f, real_t* lnM, int nthreads) {
   const int ns = C->P.nx * C->P.ny, nn = C->nn;
   const double h3 = OR_HBARC * OR_HBARC * OR_HBARC;
   int err = OR_OK;
@@ -960,7 +1016,7 @@ int or_init_state(const or_ctx* C, const double* eps0, double* f, double* lnM, i
 #pragma omp parallel for num_threads(nthreads > 0 ? nthreads : 1) schedule(static)
 #endif
   for (int i = 0; i < ns; ++i) {
-    double T;
+    real_t T;
     eos_pt e;
     int rc = solve_T(C, eps0[i] * h3, 1, 0.3, &T, &e);
     if (rc) {
@@ -970,13 +1026,13 @@ int or_init_state(const or_ctx* C, const double* eps0, double* f, double* lnM, i
       err = rc;
       continue;
     }
-    double M = (C->P.family == 1) ? C->P.T0 : e.M;
-    lnM[i] = log(M);
+    real_t M = (C->P.family == 1) ? C->P.T0 : e.M;
+    lnM[i] = R_LOG(M);
     for (int l = 0; l < C->nph; ++l)
       for (int j = 0; j < C->nth; ++j)
         for (int k = 0; k < C->nxi; ++k) {
-          double Eeq = sqrt(e.M * e.M + M * M * C->s[k] * C->s[k]);
-          f[(size_t)i * nn + (l * C->nth + j) * C->nxi + k] = C->P.Z * exp(-Eeq / T);
+          real_t Eeq = R_SQRT(e.M * e.M + M * M * C->s[k] * C->s[k]);
+          f[(size_t)i * nn + (l * C->nth + j) * C->nxi + k] = C->P.Z * R_EXP(-Eeq / T);
         }
   }
   return err;
@@ -987,26 +1043,26 @@ int or_init_state(const or_ctx* C, const double* eps0, double* f, double* lnM, i
  * s+-1, s+-2 along x and y; the predictor at those sites reads the input at
  * their own +-2 neighbours. */
 typedef struct {
-  const or_ctx* C; const double* f; const double* lnM;
-  int np; const int* pid; const double* fs; const double* lnMs; /* predictor patch */
+  const or_ctx* C; const real_t* f; const real_t* lnM;
+  int np; const int* pid; const real_t* fs; const real_t* lnMs; /* predictor patch */
   int use_patch;
 } or_patch;
-static const double* patch_f(void* ud, int site) {
+static const real_t* patch_f(void* ud, int site) {
   or_patch* G = (or_patch*)ud;
   if (!G->use_patch) return G->f + (size_t)site * G->C->nn;
   for (int q = 0; q < G->np; ++q)
     if (G->pid[q] == site) return G->fs + (size_t)q * G->C->nn;
   return NULL;
 }
-static double patch_m(void* ud, int site) {
+static real_t patch_m(void* ud, int site) {
   or_patch* G = (or_patch*)ud;
   if (!G->use_patch) return G->lnM[site];
   for (int q = 0; q < G->np; ++q)
     if (G->pid[q] == site) return G->lnMs[q];
   return NAN;
 }
-int or_step_sites(const or_ctx* C, const double* f, const double* lnM, double tau, double dtau,
-                  const int* sites, int nsel, double* f_out, double* lnM_out, int nthreads) {
+int or_step_sites(const or_ctx* C, const real_t* f, const real_t* lnM, double tau, double dtau,
+                  const int* sites, int nsel, real_t* f_out, real_t* lnM_out, int nthreads) {
   const or_params* P = &C->P;
   const int nn = C->nn;
   int err = OR_OK;
@@ -1022,11 +1078,11 @@ int or_step_sites(const or_ctx* C, const double* f, const double* lnM, double ta
       for (int b = 0; b < np; ++b) dup |= (ids[b] == id);
       if (!dup) ids[np++] = id;
     }
-    double* fs = (double*)malloc(sizeof(double) * (size_t)nn * (9 + 4));
-    double lnMs[9], g;
+    real_t* fs = (real_t*)malloc(sizeof(real_t) * (size_t)nn * (9 + 4));
+    real_t lnMs[9], g;
     int rc = fs ? OR_OK : OR_ERR_NOMEM;
-    double* rhs = fs + (size_t)9 * nn;
-    double* work = rhs + nn;
+    real_t* rhs = fs + (size_t)9 * nn;
+    real_t* work = rhs + nn;
     or_patch G;
     memset(&G, 0, sizeof G);
     G.C = C; G.f = f; G.lnM = lnM;
