@@ -87,7 +87,7 @@ typedef struct {
  *   n_xi, n_theta,        lattice of Sec. 4.3: n_xi radial roots, n_theta
  *   n_phi_half              Gauss-Legendre polar nodes, 2 n_phi_half azimuths.
  *                         Supported (n_xi, n_theta, 2 n_phi_half): (8, 8, 12),
- *                         (16, 8, 16), (5, 5, 2), (8, 8, 2), (8, 16, 2).
+ *                         (16, 8, 16), (5, 5, 2), (6, 4, 6), (8, 8, 2).
  *   family, z0, T0        radial rule: PAPER (weight e^{-z0 cosh xi} sinh^2 xi,
  *                         z0 = M0/T0 of Eq. fansatz) or LAGUERRE (massless limit,
  *                         |p~| = T0 x, weight x e^{-x}; needs the conformal EOS)
@@ -151,7 +151,10 @@ rlb_status rlb_configure_batch(rlb_ctx* ctx, const rlb_grid_params* base, int n_
 
 /* Borrow caller-owned device buffers of at least the rlb_workspace_size bytes,
  * 256-byte aligned; the library never frees them.  Uploads the EOS table and
- * clears the error word on `stream`. */
+ * the lattice line table and clears the error word on `stream`; the first
+ * bind of a context also measures the mean relative error of the device's
+ * hardware 2^x over the exponents of f_eq (one small kernel; the FP32 stage
+ * kernels divide it out of Z) and synchronises `stream`. */
 rlb_status rlb_bind_buffers(rlb_ctx* ctx, void* state, void* scratch, void* stream);
 
 /* Initial condition: local equilibrium at rest with energy density eps0[site]
@@ -185,8 +188,11 @@ rlb_status rlb_step(rlb_ctx* ctx, int nsteps, void* stream);
  * of 24 MiB declared by the library.  It calls no allocating routine: no
  * cudaMalloc, no cudaFree, no library allocator.
  *   - The first call on a device looks up the device address of that array
- *     (cudaGetSymbolAddress) with the context's device current; make this first
- *     call before any stream capture begins.
+ *     (cudaGetSymbolAddress) with the context's device current, and the first
+ *     call of a context that has no bound buffers measures the mean error of
+ *     the device's 2^x approximation (one small kernel using 8 bytes of the
+ *     array, and a synchronisation); make these first calls before any stream
+ *     capture begins.
  *   - Grids whose scratch would exceed 24 MiB are rejected with RLB_ERR_ARG
  *     (about 5,000 sites with FP32 populations on the 8x8x12 lattice, 2,500 with
  *     FP64).
@@ -231,8 +237,10 @@ rlb_status rlb_load_state(rlb_ctx* ctx, const void* host_buf, size_t bytes, void
  * rlb_autotune times every compiled variant of the stage kernel for the
  * configured lattice and precision (packed FP32 kernel with one site per CTA,
  * with and without its register cap; generic kernel; packed kernel with two
- * sites per CTA, with and without its cap; one variant for lattices only the
- * generic kernel takes) on three predictor launches over the current state,
+ * sites per CTA, with and without its cap; for the 8 x 8 x 12 lattice the
+ * mirror-paired kernel, variant 5, the default there: one thread holds the
+ * polar lines theta and pi - theta; one variant for lattices only the generic
+ * kernel takes) on three predictor launches over the current state,
  * and keeps the fastest for later steps.  The state (f, ln M, tau) is
  * unchanged.  Outputs: the chosen variant, optionally the milliseconds per
  * launch of each variant (variant_ms holds at least RLB_MAX_STAGE_VARIANTS

@@ -1,8 +1,10 @@
 """Adjoint of the time evolution (rlb_adjoint_*): gradient of the final
-p_perp-weighted v2 with respect to hotspot amplitudes and eta/s, against
-central finite differences of the GPU forward run (FP64 and FP32 storage),
-against central finite differences of the FP64 oracle, independent of the
-checkpoint interval, and through torch.autograd."""
+p_perp-weighted v2 with respect to hotspot amplitudes and eta/s, against the
+oracle's own forward-mode gradient (complex-step build of the oracle, all 41
+parameters of a 32 x 32, 50-step case), against central finite differences of
+the GPU forward run (FP64 and FP32 storage) and of the FP64 oracle,
+independent of the checkpoint interval, and through torch.autograd."""
+import json
 import os
 
 import numpy as np
@@ -59,6 +61,54 @@ def _fd(prec, amps, basis, rel_h, with_eta=True):
         he = rel_h * ETA
         fde = (_v2(prec, amps, basis, ETA + he) - _v2(prec, amps, basis, ETA - he)) / (2 * he)
     return np.array(fd), fde
+
+
+def _taped():
+    with open(os.path.join(os.path.dirname(__file__), "golden", "adjoint_taped_32x32.json")) as fh:
+        return json.load(fh)
+
+
+@pytest.mark.parametrize("prec,arith,tol", [(rlb.RLB_F64, rlb.RLB_F64, 1e-9), (rlb.RLB_F32, rlb.RLB_F32, 1e-5)])
+def test_adjoint_matches_the_oracle_forward_gradient(prec, arith, tol):
+    # tests/golden/adjoint_taped_32x32.json: dv2/dA_i (40 hotspots) and
+    # dv2/d(eta/s) from the oracle run in complex arithmetic (written by
+    # oracle/taped_gradient.py).  FP64 storage and arithmetic: the same
+    # derivatives to rounding (measured 3e-12); FP32 storage and arithmetic:
+    # the gradient of the FP32 trajectory, within 1e-5 of the largest
+    # component (measured 5e-7).
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    from oracle.taped_gradient import CASE, case_inputs
+    rec = _taped()
+    eps0, amps, basis = case_inputs()
+    assert np.allclose(amps, rec["amplitudes"], rtol=1e-15, atol=0)
+    g = rlb.GridParams(nx=CASE["nx"], ny=CASE["ny"], dx=CASE["dx"], prec=prec, eta_over_s=CASE["eta_over_s"],
+                       tau0=CASE["tau0"], dtau=CASE["dtau"])
+    run = rlb.Run(g)
+    v2, gA, geta = ADJ.v2_gradient(run, torch.as_tensor(eps0.reshape(-1), dtype=torch.float64, device="cuda"),
+                                   torch.as_tensor(basis, dtype=torch.float64, device="cuda"), CASE["steps"], 10,
+                                   arithmetic=arith)
+    ref = np.array(rec["dv2_dA"])
+    scale = np.abs(ref).max()
+    err_A = float(np.abs(np.asarray(gA) - ref).max() / scale)
+    err_eta = float(abs(geta - rec["dv2_deta_over_s"]) / abs(rec["dv2_deta_over_s"]))
+    print("adjoint vs oracle forward gradient (prec %d, arithmetic %d): amplitudes %.2e, eta/s %.2e, v2 %.2e"
+          % (prec, arith, err_A, err_eta, abs(v2 / rec["v2"] - 1)))
+    assert abs(v2 / rec["v2"] - 1) < (1e-12 if prec == rlb.RLB_F64 else 1e-5)
+    assert err_A < tol and err_eta < 10 * tol, (err_A, err_eta)
+
+
+def test_stored_oracle_gradient_is_reproduced(oracle_mod):
+    # one component of the stored gradient recomputed here with the oracle in
+    # complex arithmetic: the file is the oracle's
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    from oracle.taped_gradient import case_inputs, derivative
+    rec = _taped()
+    eps0, _, _ = case_inputs()
+    v2, d = derivative(eps0, np.zeros_like(eps0), 1.0, NT)
+    assert v2 == pytest.approx(rec["v2"], rel=1e-13)
+    assert d == pytest.approx(rec["dv2_deta_over_s"], rel=1e-10)
 
 
 def test_fp64_adjoint_matches_finite_differences():
