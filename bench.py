@@ -96,7 +96,7 @@ def job_rate(units_per_rank: float, world: int, t_max: float) -> float:
 # describes the kernel sources it was taken on (the SHA-1 of the code of the
 # stage-kernel headers, comments removed) and is reported only while they are
 # unchanged.
-STAGE_TRAFFIC = {"sources": ("rlb_stage_mp.cuh", "rlb_stage_x2.cuh"),
+STAGE_TRAFFIC = {"sources": ("rlb_stage_mp.cuh", "rlb_stage_x2.cuh", "rlb_kernels.cuh"),
                  "sha1": "3b6a5c7d9c7d108d336e6b9ec1d53c2c92343c21", "bytes_per_launch": 479.96e6}
 
 

@@ -34,6 +34,19 @@ __device__ __forceinline__ int idx_checked(int v, int n, int* err) {
 #endif
   return v;
 }
+// ln M of f_in at `site` into dst[0] and, in the corrector (mode 1), ln M of
+// f_base into dst[2] (dst in shared memory, 8-byte aligned), by cp.async: the
+// thread that updates ln M after the site's reductions then reads shared
+// memory instead of waiting there for a global load.  The reader calls
+// lnm_wait() first.
+__device__ __forceinline__ void lnm_fetch(double* dst, const double* lnM_in, const double* lnM_base, int site,
+                                          int mode) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(lnM_in + site) : "memory");
+  if (mode == 1) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d + 16), "l"(lnM_base + site) : "memory");
+}
+__device__ __forceinline__ void lnm_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Debug builds: ERR_NONFINITE when one of the n values is not finite.
 template <class R>
 __device__ __forceinline__ void finite_checked(const R* v, int n, int* err) {
@@ -1012,6 +1025,8 @@ __global__ void __launch_bounds__(NTH* NPH)
   __shared__ float redf[2 * kMom * NW];
   __shared__ R gsh;
   __shared__ __align__(16) R Etab[2 * NXI];  // (E_eq, 1/E_eq) per radial node
+  __shared__ double lnm_s[4];                  // ln M of f_in, f_base (lnm_fetch)
+  if (t == 0) lnm_fetch(lnm_s, A.lnM_in, A.lnM_base, site, A.mode);
 
   // 1. own xi-line and the upwind neighbours for streaming
   R f[NXI];
@@ -1147,8 +1162,9 @@ __global__ void __launch_bounds__(NTH* NPH)
     }
     if (!isfinite((double)g)) atomicOr(A.err, (int)ERR_NONFINITE);
     gsh = g;
-    const double lnM = __ldg(A.lnM_in + site), gd = (double)g;
-    A.lnM_out[site] = A.mode == 0 ? lnM + A.dtau * gd : 0.5 * (__ldg(A.lnM_base + site) + lnM + A.dtau * gd);
+    lnm_wait();
+    const double lnM = lnm_s[0], gd = (double)g;
+    A.lnM_out[site] = A.mode == 0 ? lnM + A.dtau * gd : 0.5 * (lnm_s[2] + lnM + A.dtau * gd);
   }
   __syncthreads();
   const R g = gsh;

@@ -120,16 +120,16 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
 // neighbours read are L2 hits.
 template <class S, int NN, int SPC>
 __device__ __forceinline__ void prefetch_ahead_sites(const GridMap& G, const S* f, int ahead) {
-  const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x + ahead;
+  const unsigned b = blockIdx.y * gridDim.x + blockIdx.x + (unsigned)ahead;  // 32-bit division (thread 0 waits on it)
   long long s0, n;
   if (G.n_events == 1) {
-    const long long c = b / gridDim.x, y = b % gridDim.x;
+    const unsigned c = b / gridDim.x, y = b - c * gridDim.x;
     if (c >= gridDim.y) return;
-    s0 = y * G.nx0 + SPC * c;
-    n = G.nx0 - SPC * c;
+    s0 = (long long)y * G.nx0 + SPC * (long long)c;
+    n = G.nx0 - SPC * (long long)c;
   } else {
     if (b >= gridDim.x) return;
-    s0 = SPC * b;
+    s0 = SPC * (long long)b;
     n = G.n_sites - s0;
   }
   n = n < SPC ? n : SPC;
@@ -208,13 +208,15 @@ __device__ __forceinline__ void mp_offsets(const MPSite& m, int l, int jp, float
 // that the neighbour loads overlap the own-line work, keeps them live and
 // measured 3 % slower).  sc holds the site's FP32 matching
 // (four float4); eo is the CTA's polar exchange area (NXI/2 16-byte chunks per
-// thread) and red its per-group partial sums.  Contains one CTA barrier.
+// thread) and red its per-group partial sums; lnm_s[sl] and lnm_s[2 + sl]
+// receive ln M of f_in and f_base at site sl (lnm_fetch at the top of the
+// kernel).  Contains one CTA barrier.
 template <class S, int NXI, int NTH, int NPH, class LD>
 __device__ __forceinline__ void mp_body(const StageArgsMP<S, NXI, NTH, NPH>& A, const MPSite& me,
                                         const size_t (&off)[10], int t, int q, int sl, float milne,
                                         const LineMP<NTH / 2>& lc, float4 la, float4 lb,
                                         const float4 (&sc)[4], LD&& ld, uint4* eo,
-                                        float4* red) {
+                                        float4* red, const double* lnm_s) {
   using Sh = MPShape<NTH, NPH>;
   constexpr int H = Sh::H, G = Sh::G;
   constexpr int NP = NXI / 2;
@@ -393,6 +395,7 @@ __device__ __forceinline__ void mp_body(const StageArgsMP<S, NXI, NTH, NPH>& A, 
     const float s1v = __shfl_down_sync(0xffffffffu, v[0], 4), s2w = __shfl_down_sync(0xffffffffu, v[0], 8);
     if ((lane & 15) == 0) red[sl * G + gi] = make_float4(v[0], s1v, s2w, 0.f);
   }
+  lnm_wait();  // ln M (long arrived)
   __syncthreads();
   float Af = 0.f, Qf = 0.f, Ef = 0.f;
 #pragma unroll
@@ -406,8 +409,8 @@ __device__ __forceinline__ void mp_body(const StageArgsMP<S, NXI, NTH, NPH>& A, 
   const int site = me.site;
   if (q == 0 && me.owner) {
     if (!isfinite(g)) atomicOr(A.err, (int)ERR_NONFINITE);
-    const double lnM = __ldg(A.lnM_in + site), gd = (double)g;
-    A.lnM_out[site] = A.mode == 0 ? lnM + A.dtau * gd : 0.5 * (__ldg(A.lnM_base + site) + lnM + A.dtau * gd);
+    const double lnM = lnm_s[sl], gd = (double)g;
+    A.lnM_out[site] = A.mode == 0 ? lnM + A.dtau * gd : 0.5 * (lnm_s[2 + sl] + lnM + A.dtau * gd);
   }
   const float2 gs = bc2((A.mode == 0 ? A.dtau_r : 0.5f * A.dtau_r) * g);
 #pragma unroll
@@ -478,6 +481,11 @@ __global__ void __launch_bounds__(MPShape<NTH, NPH>::NT, MINB)
   const float4 la = __ldg(&lc.a), lb = __ldg(&lc.b);
   __shared__ uint4 eo[Sh::NT * NP];    // polar exchange: e and o of every thread
   __shared__ float4 red[SPC * Sh::G];  // per-group partial sums for d ln M / d tau
+  // ln M of the site(s), needed after the barrier: copied to shared memory
+  // now, so that the owner thread does not wait there for a global load
+  // (measured 8 % of the stage)
+  __shared__ double lnm_s[4];
+  if (q == 0 && me.owner) lnm_fetch(lnm_s + sl, A.lnM_in, A.lnM_base, me.site, A.mode);
   size_t off[10];
   mp_offsets<NXI, NTH, NPH>(me, l, jp, la.w, lb.x, A.grid.n_sites, A.err, off);
   const float4* scq = reinterpret_cast<const float4*>(A.scf + (size_t)me.site * kSc);
@@ -486,7 +494,7 @@ __global__ void __launch_bounds__(MPShape<NTH, NPH>::NT, MINB)
     if (i < 10) load_pairs<S, NP>(A.f_in + off[i], v);
     else load_pairs<S, NP>(A.f_base + off[i - 10], v);
   };
-  mp_body<S, NXI, NTH, NPH>(A, me, off, t, q, sl, milne, lc, la, lb, sc, ld, eo, red);
+  mp_body<S, NXI, NTH, NPH>(A, me, off, t, q, sl, milne, lc, la, lb, sc, ld, eo, red, lnm_s);
 }
 
 }  // namespace rlbk

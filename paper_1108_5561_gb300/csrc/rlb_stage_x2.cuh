@@ -209,6 +209,12 @@ __global__ void __launch_bounds__(NTH* NPH, MINB)
   __shared__ float2 pth[SPT][NP * LDK];
   __shared__ float4 tab[SPT][NP];  // (E_eq at 2p, 2p+1;  q1/E_eq at 2p, 2p+1)
   __shared__ float4 red[SPT][NW];  // per-warp partial sums for d ln M / d tau
+  __shared__ double lnm_s[4];      // ln M of f_in, f_base per site (lnm_fetch)
+  if (t == 0) {
+#pragma unroll
+    for (int s = 0; s < SPT; ++s)
+      if (s == 0 || has2) lnm_fetch(lnm_s + s, A.lnM_in, A.lnM_base, L[s].site, A.mode);
+  }
 
   // 1. own line and the upwind neighbours (periodic), and the streaming term
   //    right away: the neighbour lines die here instead of staying live across
@@ -404,8 +410,9 @@ __global__ void __launch_bounds__(NTH* NPH, MINB)
     if (t == 0 && (s == 0 || has2)) {
       const int site = L[s].site;
       if (!isfinite(g)) atomicOr(A.err, (int)ERR_NONFINITE);
-      const double lnM = __ldg(A.lnM_in + site), gd = (double)g;
-      A.lnM_out[site] = A.mode == 0 ? lnM + A.dtau * gd : 0.5 * (__ldg(A.lnM_base + site) + lnM + A.dtau * gd);
+      lnm_wait();
+      const double lnM = lnm_s[s], gd = (double)g;
+      A.lnM_out[site] = A.mode == 0 ? lnM + A.dtau * gd : 0.5 * (lnm_s[2 + s] + lnM + A.dtau * gd);
     }
     gb[s] = bc2(g);
   }
