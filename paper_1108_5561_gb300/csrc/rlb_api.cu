@@ -33,7 +33,7 @@ struct rlb_ctx {
   size_t fs_off = 0, lnMs_off = 0, T_off = 0, err_off = 0, tab_off = 0, eps_off = 0;  // scratch
   size_t mom_off = 0, moms_off = 0, sc_off = 0, tabf_off = 0, scf_off = 0;
   size_t ev_off = 0, loc_off = 0, clock_off = 0, lines_off = 0;
-  // per-thread line constants of the mirror-paired stage kernel (rlbk::LineMP)
+  // line constants of the mirror-paired stage kernel (rlbk::LinesMP)
   std::vector<unsigned char> lines_mp;
   // events: one for a single grid, n for a batch (with a per-site locator)
   std::vector<rlbk::EventInfo> events;
@@ -244,33 +244,37 @@ rlbk::OpsX2<NXI, NTH, NPH> make_ops_x2(const rlb::Lattice& L) {
   return o;
 }
 
-// Per-thread line constants of stage_kernel_mp (rlbk::LineMP<H>, H = N_theta/2):
-// thread slot q = l H + j of a site owns the polar lines j and N_theta - 1 - j
-// at azimuth l.  The mirror lines share sin(theta), mu^2 and the polar weight
-// (averaged over the pair, equal up to rounding), and the even and odd blocks
-// of the polar operator come from its rows j < H.
+// Line constants of stage_kernel_mp (rlbk::LinesMP<H, TS>, H = N_theta/2,
+// TS = H N_phi): thread slot q = l H + j of a site owns the polar lines j and
+// N_theta - 1 - j at azimuth l.  The mirror lines share sin(theta), mu^2 and
+// the polar weight (averaged over the pair, equal up to rounding), and the
+// even and odd blocks of the polar operator come from its rows j < H.
 std::vector<unsigned char> make_lines_mp(const rlb::Lattice& L, double dx) {
-  const int nth = L.nth, nph = L.nph, H = nth / 2;
-  const size_t esz = 32 + 16 * (size_t)H;
-  std::vector<unsigned char> out(esz * H * nph, 0);
+  const int nth = L.nth, nph = L.nph, H = nth / 2, TS = H * nph;
+  std::vector<unsigned char> out(32 * (size_t)TS + 16 * (size_t)H * H, 0);
+  float* a = reinterpret_cast<float*>(out.data());
+  float* b = a + 4 * TS;
+  float* ae = b + 4 * TS;
+  float* ao = ae + 2 * H * H;
   for (int l = 0; l < nph; ++l)
     for (int jp = 0; jp < H; ++jp) {
-      float* e = reinterpret_cast<float*>(out.data() + esz * (size_t)(l * H + jp));
-      const int jb = nth - 1 - jp;
+      const int q = l * H + jp, jb = nth - 1 - jp;
       const double st = 0.5 * (L.sth[jp] + L.sth[jb]);
       const double mu2 = 0.5 * (L.mu[jp] * L.mu[jp] + L.mu[jb] * L.mu[jb]);
       const double wj = 0.5 * (L.wth[jp] + L.wth[jb]) / (2.0 * nph);
       const double cp = L.cph[l], sp = L.sph[l];
+      float* e = a + 4 * q;
       e[0] = (float)st; e[1] = (float)mu2; e[2] = (float)wj; e[3] = (float)cp;
-      e[4] = (float)sp; e[5] = (float)(-st * std::fabs(cp) / (2.0 * dx));
-      e[6] = (float)(-st * std::fabs(sp) / (2.0 * dx)); e[7] = 0.f;
-      float* ae = e + 8;
-      float* ao = e + 8 + 2 * H;
-      for (int i = 0; i < H; ++i) {
-        const double d0 = L.Dth[jp * nth + i], d1 = L.Dth[jp * nth + (nth - 1 - i)];
-        ae[2 * i] = ae[2 * i + 1] = (float)(0.5 * (d0 + d1));
-        ao[2 * i] = ao[2 * i + 1] = (float)(0.5 * (d0 - d1));
-      }
+      e = b + 4 * q;
+      e[0] = (float)sp; e[1] = (float)(-st * std::fabs(cp) / (2.0 * dx));
+      e[2] = (float)(-st * std::fabs(sp) / (2.0 * dx)); e[3] = 0.f;
+    }
+  for (int jp = 0; jp < H; ++jp)
+    for (int i = 0; i < H; ++i) {
+      const double d0 = L.Dth[jp * nth + i], d1 = L.Dth[jp * nth + (nth - 1 - i)];
+      const size_t k = 2 * ((size_t)i * H + jp);
+      ae[k] = ae[k + 1] = (float)(0.5 * (d0 + d1));
+      ao[k] = ao[k + 1] = (float)(0.5 * (d0 - d1));
     }
   return out;
 }
@@ -520,7 +524,7 @@ struct Stager {
       b.op = make_ops_x2<NXI, NTH, NPH>(ctx->lat);
       if constexpr (kMP) {
         c.scf = scf; c.err = err; c.grid = gm; c.clock = clock;
-        c.lines = reinterpret_cast<const rlbk::LineMP<NTH / 2>*>(scr + ctx->lines_off);
+        c.lines = reinterpret_cast<const rlbk::LinesMP<NTH / 2, (NTH / 2) * NPH>*>(scr + ctx->lines_off);
         c.milne_on = ctx->gp.metric == RLB_MILNE;
         c.dtau = dtau;
         c.dtau_r = (float)dtau;

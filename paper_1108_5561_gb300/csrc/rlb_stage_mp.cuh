@@ -43,15 +43,18 @@ struct OpsMP {
   float2 s2[NP], q1[NP];                  // sinh^2, sinh (sinh^2 + 1)/cosh
 };
 
-// Per-thread line constants (device memory, one entry per thread slot q =
-// l * (N_theta/2) + j of a site; lanes read different entries):
-//   a = (sin theta_j, mu_j^2, polar weight / (2 N_phi), cos phi_l)
-//   b = (sin phi_l, -sin theta_j |cos phi_l| / (2 dx), -sin theta_j |sin phi_l| / (2 dx), 0)
-//   ae[i], ao[i] = the row j of the even and odd polar blocks, in both halves.
-template <int H>
-struct alignas(16) LineMP {
-  float4 a, b;
-  float2 ae[H], ao[H];
+// Line constants (device memory), stored field by field so that the lanes of
+// a warp read contiguous entries:
+//   a[q] = (sin theta_j, mu_j^2, polar weight / (2 N_phi), cos phi_l)
+//   b[q] = (sin phi_l, -sin theta_j |cos phi_l| / (2 dx), -sin theta_j |sin phi_l| / (2 dx), 0)
+// for the thread slot q = l * (N_theta/2) + j of a site, and the even and odd
+// polar blocks, ae[i * H + j] = (Ae[j][i], Ae[j][i]) (likewise ao), which
+// depend on j only: the lanes of a warp read H distinct entries (one or two
+// sectors) instead of one 96-byte record each.
+template <int H, int TS>
+struct alignas(16) LinesMP {
+  float4 a[TS], b[TS];
+  float2 ae[H * H], ao[H * H];
 };
 
 template <int NTH, int NPH>
@@ -74,7 +77,7 @@ struct StageArgsMP {
   double* lnM_out;
   float* momf_out;        // moments of f_out: one partial sum per 16-lane group
   int* err;
-  const LineMP<NTH / 2>* lines;
+  const LinesMP<NTH / 2, (NTH / 2) * NPH>* lines;
   GridMap grid;
   const Clock* clock;     // proper time of f_in
   int milne_on;           // Milne metric (1/tau terms) or Minkowski
@@ -214,7 +217,7 @@ __device__ __forceinline__ void mp_offsets(const MPSite& m, int l, int jp, float
 template <class S, int NXI, int NTH, int NPH, class LD>
 __device__ __forceinline__ void mp_body(const StageArgsMP<S, NXI, NTH, NPH>& A, const MPSite& me,
                                         const size_t (&off)[10], int t, int q, int sl, float milne,
-                                        const LineMP<NTH / 2>& lc, float4 la, float4 lb,
+                                        const LinesMP<NTH / 2, (NTH / 2) * NPH>& lt, float4 la, float4 lb,
                                         const float4 (&sc)[4], LD&& ld, uint4* eo,
                                         float4* red, const double* lnm_s) {
   using Sh = MPShape<NTH, NPH>;
@@ -301,7 +304,7 @@ __device__ __forceinline__ void mp_body(const StageArgsMP<S, NXI, NTH, NPH>& A, 
     const int g0 = t - jp;  // thread of (l, j = 0)
 #pragma unroll
     for (int i = 0; i < H; ++i) {
-      const float2 ae = __ldg(&lc.ae[i]), ao = __ldg(&lc.ao[i]);
+      const float2 ae = __ldg(&lt.ae[i * H + jp]), ao = __ldg(&lt.ao[i * H + jp]);
 #pragma unroll
       for (int p = 0; p < NP; p += 2) {
         const uint4 ev = eoc(g0 + i, p / 2), ov = eoc(g0 + i, NP / 2 + p / 2);
@@ -477,8 +480,8 @@ __global__ void __launch_bounds__(MPShape<NTH, NPH>::NT, MINB)
     if (A.mode == 1) prefetch_ahead_sites<S, NN, SPC>(A.grid, A.f_base, A.prefetch_ahead);
   }
   const float milne = A.milne_on ? A.clock->inv_tau_f : 0.f;
-  const LineMP<H>& lc = A.lines[q];
-  const float4 la = __ldg(&lc.a), lb = __ldg(&lc.b);
+  const auto& lt = *A.lines;
+  const float4 la = __ldg(&lt.a[q]), lb = __ldg(&lt.b[q]);
   __shared__ uint4 eo[Sh::NT * NP];    // polar exchange: e and o of every thread
   __shared__ float4 red[SPC * Sh::G];  // per-group partial sums for d ln M / d tau
   // ln M of the site(s), needed after the barrier: copied to shared memory
@@ -494,7 +497,7 @@ __global__ void __launch_bounds__(MPShape<NTH, NPH>::NT, MINB)
     if (i < 10) load_pairs<S, NP>(A.f_in + off[i], v);
     else load_pairs<S, NP>(A.f_base + off[i - 10], v);
   };
-  mp_body<S, NXI, NTH, NPH>(A, me, off, t, q, sl, milne, lc, la, lb, sc, ld, eo, red, lnm_s);
+  mp_body<S, NXI, NTH, NPH>(A, me, off, t, q, sl, milne, lt, la, lb, sc, ld, eo, red, lnm_s);
 }
 
 }  // namespace rlbk
