@@ -210,7 +210,7 @@ __device__ __forceinline__ void mp_offsets(const MPSite& m, int l, int jp, float
 // (the neighbour lines die before the site's own work; computing it last, so
 // that the neighbour loads overlap the own-line work, keeps them live and
 // measured 3 % slower).  sc holds the site's FP32 matching
-// (four float4); eo is the CTA's polar exchange area (NXI/2 16-byte chunks per
+// (four float4); eo is the CTA's polar exchange area (NXI/2 + 1 16-byte chunks per
 // thread) and red its per-group partial sums; lnm_s[sl] and lnm_s[2 + sl]
 // receive ln M of f_in and f_base at site sl (lnm_fetch at the top of the
 // kernel).  Contains one CTA barrier.
@@ -223,8 +223,8 @@ __device__ __forceinline__ void mp_body(const StageArgsMP<S, NXI, NTH, NPH>& A, 
   using Sh = MPShape<NTH, NPH>;
   constexpr int H = Sh::H, G = Sh::G;
   constexpr int NP = NXI / 2;
-  constexpr int EOC = NP;  // chunks per thread in eo: e (NP/2), o (NP/2)
-  static_assert(EOC % 4 == 0 || EOC == 2, "eo swizzle");
+  constexpr int EOC = NP + 1;  // 16-byte chunks per thread in eo: e (NP/2), o (NP/2), one of padding
+  static_assert(EOC % 2 == 1, "odd stride: bank-conflict free");
   const auto& op = A.op;
   const int lane = t & 31, jp = q % H;
   const float st = la.x, mu2 = la.y, wj = la.z, cp = la.w, sp = lb.x;
@@ -285,10 +285,14 @@ __device__ __forceinline__ void mp_body(const StageArgsMP<S, NXI, NTH, NPH>& A, 
   }
 
   // 3. polar operator on the even and odd parts, exchanged among the H
-  //    threads of this azimuth (same warp; eo chunk c of thread u at
-  //    c ^ ((u >> 1) & 3), distinct bank groups for 8 consecutive threads)
+  //    threads of this azimuth (same warp).  Thread u's chunks lie EOC = NP + 1
+  //    chunks apart (odd): 8 consecutive threads store to 8 distinct bank
+  //    groups, the two azimuths of a quarter warp read from distinct ones, and
+  //    every address is a constant offset from the thread's or its group's
+  //    base (an XOR swizzle of the unpadded layout cost integer work per
+  //    access; the padded layout measured 2.4 % faster)
   if (milne != 0.f) {
-    auto eoc = [&](int u, int c) -> uint4& { return eo[u * EOC + (c ^ ((u >> 1) & (EOC - 1)))]; };
+    auto eoc = [&](int u, int c) -> uint4& { return eo[u * EOC + c]; };
 #pragma unroll
     for (int p = 0; p < NP; p += 2) {
       const float2 e0 = add2(fA[p], fB[p]), e1 = add2(fA[p + 1], fB[p + 1]);
@@ -482,7 +486,7 @@ __global__ void __launch_bounds__(MPShape<NTH, NPH>::NT, MINB)
   const float milne = A.milne_on ? A.clock->inv_tau_f : 0.f;
   const auto& lt = *A.lines;
   const float4 la = __ldg(&lt.a[q]), lb = __ldg(&lt.b[q]);
-  __shared__ uint4 eo[Sh::NT * NP];    // polar exchange: e and o of every thread
+  __shared__ uint4 eo[Sh::NT * (NP + 1)];  // polar exchange: e and o of every thread
   __shared__ float4 red[SPC * Sh::G];  // per-group partial sums for d ln M / d tau
   // ln M of the site(s), needed after the barrier: copied to shared memory
   // now, so that the owner thread does not wait there for a global load
@@ -491,6 +495,10 @@ __global__ void __launch_bounds__(MPShape<NTH, NPH>::NT, MINB)
   if (q == 0 && me.owner) lnm_fetch(lnm_s + sl, A.lnM_in, A.lnM_base, me.site, A.mode);
   size_t off[10];
   mp_offsets<NXI, NTH, NPH>(me, l, jp, la.w, lb.x, A.grid.n_sites, A.err, off);
+  if (A.mode == 1) {  // the corrector's base lines, read after the site's own work: into L1 now
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(A.f_base + off[0]));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(A.f_base + off[1]));
+  }
   const float4* scq = reinterpret_cast<const float4*>(A.scf + (size_t)me.site * kSc);
   const float4 sc[4] = {__ldg(scq), __ldg(scq + 1), __ldg(scq + 2), __ldg(scq + 3)};
   auto ld = [&](int i, float2 (&v)[NP]) {
