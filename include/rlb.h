@@ -27,7 +27,7 @@
  *     inversion outside the EOS table, non-finite values) set a device error
  *     word that rlb_check, rlb_moments and rlb_sync_error report as
  *     RLB_ERR_NUMERIC.  Bits: 1 Landau, 2 EOS inversion, 4 non-finite, 8 index
- *     check.  The library built with checks (RLB_CHECKS; the Python front end
+ *     check, 16 a bounded device wait expired (reported as RLB_ERR_TIMEOUT).  The library built with checks (RLB_CHECKS; the Python front end
  *     loads it when RLB_CHECKED=1) also range-checks every site index and grid
  *     coordinate the kernels derive (bit 8, the access then goes to site 0)
  *     and the finiteness of every stored population (bit 4).
@@ -239,8 +239,11 @@ rlb_status rlb_load_state(rlb_ctx* ctx, const void* host_buf, size_t bytes, void
  * with and without its register cap; generic kernel; packed kernel with two
  * sites per CTA, with and without its cap; for the 8 x 8 x 12 lattice the
  * mirror-paired kernel, variant 5, the default there: one thread holds the
- * polar lines theta and pi - theta; one variant for lattices only the generic
- * kernel takes) on three predictor launches over the current state,
+ * polar lines theta and pi - theta; with FP32 storage also variant 6, the
+ * mirror-paired kernel reading its own and its upwind neighbours' lines from
+ * shared memory filled by bulk asynchronous copies (one grid with an even nx;
+ * elsewhere variant 6 runs variant 5); one variant for lattices only the
+ * generic kernel takes) on three predictor launches over the current state,
  * and keeps the fastest for later steps.  The state (f, ln M, tau) is
  * unchanged.  Outputs: the chosen variant, optionally the milliseconds per
  * launch of each variant (variant_ms holds at least RLB_MAX_STAGE_VARIANTS
@@ -349,6 +352,17 @@ rlb_status rlb_get_timing(rlb_ctx* ctx, double* stage_ms, long* stage_launches, 
  * helper with no counterpart in the paper.  Synchronises the device's work it
  * launches; no context needed. */
 rlb_status rlb_alu_peaks(int cuda_device, double* tflops);
+
+/* The bounded wait of the halo-staged stage kernel (stage variant 6) on its
+ * own: one CTA sets up the mbarrier its staging completes on, expecting 16
+ * bytes, issues the 16-byte bulk copy of a device value 1.25 only when
+ * `deliver` is nonzero, and waits at most limit_ms (0 < limit_ms <= 2000).
+ * *expired = 1 when the wait ran out (the stage kernel then sets device error
+ * bit 16 and rlb_check returns RLB_ERR_TIMEOUT), 0 when the copy arrived;
+ * *value (optional) = the copied value.  A test helper with no counterpart in
+ * the paper: it shows on a GPU that the wait ends and the context stays
+ * usable, without a fault.  Synchronous; no context needed. */
+rlb_status rlb_wait_selftest(int cuda_device, int deliver, double limit_ms, int* expired, float* value);
 
 /* Synchronise `stream` and report the device error word (RLB_ERR_NUMERIC if set). */
 rlb_status rlb_check(rlb_ctx* ctx, void* stream);

@@ -19,7 +19,8 @@ EXPORTS = ["rlb_create", "rlb_destroy", "rlb_last_error", "rlb_init_eos", "rlb_w
            "rlb_set_timing", "rlb_get_timing", "rlb_step_static_scratch", "rlb_observables",
            "rlb_state_blob_size", "rlb_save_state", "rlb_load_state", "rlb_configure_batch",
            "rlb_init_batch", "rlb_autotune", "rlb_set_stage_variant", "rlb_set_graphs", "rlb_adjoint_set_arithmetic", "rlb_adjoint_workspace_size",
-           "rlb_adjoint_bind", "rlb_adjoint_seed_v2", "rlb_adjoint_seed", "rlb_adjoint_step", "rlb_adjoint_ic", "rlb_alu_peaks"]
+           "rlb_adjoint_bind", "rlb_adjoint_seed_v2", "rlb_adjoint_seed", "rlb_adjoint_step", "rlb_adjoint_ic", "rlb_alu_peaks",
+           "rlb_wait_selftest"]
 
 
 class EosParamsC(ctypes.Structure):
@@ -90,6 +91,8 @@ def load(build_if_missing: bool = True):
     lib.rlb_operators.argtypes = [vp, dp, dp]
     lib.rlb_set_timing.argtypes = [vp, ctypes.c_int]
     lib.rlb_alu_peaks.argtypes = [ctypes.c_int, dp]
+    lib.rlb_wait_selftest.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, P(ctypes.c_int),
+                                      P(ctypes.c_float)]
     lib.rlb_step_static_scratch.argtypes = [vp, vp, ctypes.c_int, vp]
     lib.rlb_get_timing.argtypes = [vp, dp, P(ctypes.c_long), dp, P(ctypes.c_long)]
     lib.rlb_observables.argtypes = [vp, dp, dp, vp]

@@ -11,7 +11,7 @@ LIB = os.path.join(OUT_DIR, "librlb.so")
 # the same library with the device-side range and finiteness checks (RLB_CHECKS)
 LIB_CHECKED = os.path.join(OUT_DIR, "librlb_checked.so")
 SOURCES = ["rlb_api.cu", "rlb_host.cpp"]
-HEADERS = ["rlb_kernels.cuh", "rlb_stage_x2.cuh", "rlb_stage_mp.cuh", "rlb_peaks.cuh", "rlb_adjoint.cuh", "rlb_host.hpp", os.path.join("..", "..", "include", "rlb.h")]
+HEADERS = ["rlb_kernels.cuh", "rlb_stage_x2.cuh", "rlb_stage_mp.cuh", "rlb_stage_mpt.cuh", "rlb_peaks.cuh", "rlb_adjoint.cuh", "rlb_host.hpp", os.path.join("..", "..", "include", "rlb.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

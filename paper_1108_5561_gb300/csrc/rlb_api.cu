@@ -16,7 +16,7 @@
 #include "rlb_host.hpp"
 #include "rlb_kernels.cuh"
 #include "rlb_stage_x2.cuh"
-#include "rlb_stage_mp.cuh"
+#include "rlb_stage_mpt.cuh"
 #include "rlb_adjoint.cuh"
 #include "rlb_peaks.cuh"
 
@@ -267,7 +267,16 @@ std::vector<unsigned char> make_lines_mp(const rlb::Lattice& L, double dx) {
       e[0] = (float)st; e[1] = (float)mu2; e[2] = (float)wj; e[3] = (float)cp;
       e = b + 4 * q;
       e[0] = (float)sp; e[1] = (float)(-st * std::fabs(cp) / (2.0 * dx));
-      e[2] = (float)(-st * std::fabs(sp) / (2.0 * dx)); e[3] = 0.f;
+      e[2] = (float)(-st * std::fabs(sp) / (2.0 * dx));
+      // halo staging (stage_kernel_mpt): bit 0 cos <= 0 (class X-), bit 1
+      // sin <= 0 (Y-), bits 4-11 and 12-19 the index of l in its X and Y class
+      int hx = 0, hy = 0;
+      for (int m = 0; m < l; ++m) {
+        hx += (L.cph[m] > 0) == (cp > 0);
+        hy += (L.sph[m] > 0) == (sp > 0);
+      }
+      const int code = (cp > 0 ? 0 : 1) | (sp > 0 ? 0 : 2) | (hx << 4) | (hy << 12);
+      std::memcpy(&e[3], &code, sizeof code);
     }
   for (int jp = 0; jp < H; ++jp)
     for (int i = 0; i < H; ++i) {
@@ -277,6 +286,29 @@ std::vector<unsigned char> make_lines_mp(const rlb::Lattice& L, double dx) {
       ao[k] = ao[k + 1] = (float)(0.5 * (d0 - d1));
     }
   return out;
+}
+
+// The azimuth classes of the halo-staged kernel (X+: cos > 0, X-, Y+: sin > 0,
+// Y-) as runs of consecutive l; false when a class has more than two runs.
+bool make_halo_runs(const rlb::Lattice& L, rlbk::HaloRuns* R) {
+  std::memset(R, 0, sizeof *R);
+  for (int c = 0; c < 4; ++c) {
+    int runs = 0;
+    for (int l = 0; l < L.nph; ++l) {
+      const double v = c < 2 ? L.cph[l] : L.sph[l];
+      const bool in = (c % 2 == 0) ? v > 0 : !(v > 0);
+      if (!in) continue;
+      ++R->n[c];
+      const double pv = l > 0 ? (c < 2 ? L.cph[l - 1] : L.sph[l - 1]) : 0.0;
+      const bool prev_in = l > 0 && ((c % 2 == 0) ? pv > 0 : !(pv > 0));
+      if (!prev_in) {
+        if (runs == 2) return false;
+        R->start[c][runs++] = l;
+      }
+      R->count[c][runs - 1]++;
+    }
+  }
+  return true;
 }
 
 template <int NXI>
@@ -484,16 +516,24 @@ struct Stager {
   using MPS = rlbk::MPShape<NTH, NPH>;
   static constexpr bool kMP = kX2 && NXI <= 8 && MPS::NT % 32 == 0 && MPS::TS % 16 == 0 && 16 % MPS::H == 0;
   static constexpr int NL = NTH * NPH;
+  // mirror-paired with the halo staged in shared memory by bulk copies: FP32
+  // storage, two sites per CTA, 32-byte lines
+  static constexpr bool kMPT = kMP && std::is_same<S, float>::value && MPS::SPC == 2 && NXI % 8 == 0;
   // variants the autotuner times: packed kernel with the register cap, packed
   // without it, generic kernel, packed with two sites per CTA (capped,
-  // uncapped), mirror-paired kernel (lattices the packed kernel does not take:
-  // generic only)
-  static constexpr int kVariants = kMP ? 6 : (kX2 ? 5 : 1);
+  // uncapped), mirror-paired kernel, mirror-paired with the staged halo (one
+  // grid with an even number of sites per row; otherwise it runs the
+  // mirror-paired kernel) (lattices the packed kernel does not take: generic
+  // only)
+  static constexpr int kVariants = kMPT ? 7 : kMP ? 6 : (kX2 ? 5 : 1);
   static constexpr int kDefault = kMP ? 5 : 0;  // used until rlb_autotune or rlb_set_stage_variant choose
   static_assert(kVariants <= RLB_MAX_STAGE_VARIANTS, "rlb_autotune output size");
   rlbk::StageArgs<S, R, NXI, NTH, NPH> a;
   rlbk::StageArgsX2<S, NXI, NTH, NPH> b;
   rlbk::StageArgsMP<S, NXI, NTH, NPH> c;
+  rlbk::StageArgsMPT<S, NXI, NTH, NPH> d;
+  bool mpt_ok = false;  // variant 6 applies to this grid
+  int mpt_prefetch = 0;
   dim3 grid, grid2;
   int variant = 0;
 
@@ -540,6 +580,13 @@ struct Stager {
                                                           MPS::NT, 0) == cudaSuccess &&
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) == cudaSuccess)
           c.prefetch_ahead = kPrefetchWaves * per_sm * sms;
+        if constexpr (kMPT) {
+          mpt_ok = ctx->events.size() == 1 && ctx->events[0].nx % 2 == 0 && make_halo_runs(ctx->lat, &d.runs);
+          per_sm = 0;
+          if (mpt_ok && cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                            &per_sm, rlbk::stage_kernel_mpt<NXI, NTH, NPH>, MPS::NT, 0) == cudaSuccess)
+            mpt_prefetch = kPrefetchWaves * per_sm * sms;
+        }
       }
     } else {
       a.sc = sc;
@@ -569,6 +616,21 @@ struct Stager {
         c.mode = mode;
         rlbk::stage_kernel_mp<S, NXI, NTH, NPH><<<MPS::SPC == 2 ? grid2 : grid, MPS::NT, 0, st>>>(c);
         return;
+      }
+      if constexpr (kMPT) {
+        if (variant == 6) {
+          c.f_in = f_in; c.lnM_in = lnM_in; c.f_base = f_base; c.lnM_base = lnM_base;
+          c.f_out = f_out; c.lnM_out = lnM_out; c.momf_out = reinterpret_cast<float*>(mom_out);
+          c.mode = mode;
+          if (mpt_ok) {
+            d.m = c;
+            d.m.prefetch_ahead = mpt_prefetch;
+            rlbk::stage_kernel_mpt<NXI, NTH, NPH><<<grid2, MPS::NT, 0, st>>>(d);
+          } else {
+            rlbk::stage_kernel_mp<S, NXI, NTH, NPH><<<grid2, MPS::NT, 0, st>>>(c);
+          }
+          return;
+        }
       }
     }
     if constexpr (kX2) {
@@ -1173,7 +1235,9 @@ rlb_status step_static(rlb_ctx* ctx, char* state, char* scr, int nsteps, cudaStr
   int word = 0;
   RLB_CUDA(cudaMemcpyAsync(&word, err, sizeof(int), cudaMemcpyDeviceToHost, st), "static error word read");
   RLB_CUDA(cudaStreamSynchronize(st), "static step synchronise");
-  if (word) return fail(ctx, RLB_ERR_NUMERIC, "device error word set in the static-scratch step");
+  if (word)
+    return fail(ctx, (word & rlbk::ERR_TIMEOUT) ? RLB_ERR_TIMEOUT : RLB_ERR_NUMERIC,
+                "device error word set in the static-scratch step");
   return RLB_OK;
 }
 
@@ -1470,6 +1534,32 @@ rlb_status rlb_alu_peaks(int cuda_device, double* tflops) {
   return RLB_OK;
 }
 
+rlb_status rlb_wait_selftest(int cuda_device, int deliver, double limit_ms, int* expired, float* value) {
+  if (!expired || !(limit_ms > 0 && limit_ms <= 2000)) return RLB_ERR_ARG;
+  rlb_ctx tmp;  // for the error macro only
+  rlb_ctx* ctx = &tmp;
+  RLB_CUDA(cudaSetDevice(cuda_device), "cudaSetDevice");
+  void* mem = nullptr;
+  RLB_CUDA(cudaMalloc(&mem, 256), "self-test buffer");
+  float* src = static_cast<float*>(mem);
+  int* out = reinterpret_cast<int*>(static_cast<char*>(mem) + 128);
+  const float v[4] = {1.25f, 0.f, 0.f, 0.f};
+  const int init[2] = {-1, 0};
+  cudaError_t e = cudaMemcpy(src, v, sizeof v, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(out, init, sizeof init, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    rlbk::wait_selftest_kernel<<<1, 64>>>(src, deliver, (unsigned long long)(limit_ms * 1e6), out);
+    e = cudaGetLastError();
+  }
+  int res[2] = {-1, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(res, out, sizeof res, cudaMemcpyDeviceToHost);
+  cudaFree(mem);
+  RLB_CUDA(e, "wait self-test");
+  *expired = res[0];
+  if (value) std::memcpy(value, &res[1], sizeof(float));
+  return RLB_OK;
+}
+
 rlb_status rlb_get_tau(const rlb_ctx* ctx, double* tau) {
   if (!ctx || !tau) return RLB_ERR_ARG;
   *tau = ctx->tau;
@@ -1487,10 +1577,12 @@ rlb_status rlb_check(rlb_ctx* ctx, void* stream) {
            "error word read");
   RLB_CUDA(cudaStreamSynchronize(st), "synchronise");
   if (word) {
-    char buf[160];
-    snprintf(buf, sizeof buf, "device error word 0x%x (1: Landau, 2: EOS inversion, 4: non-finite, 8: index check)",
+    char buf[192];
+    snprintf(buf, sizeof buf,
+             "device error word 0x%x (1: Landau, 2: EOS inversion, 4: non-finite, 8: index check, 16: bounded "
+             "wait expired)",
              word);
-    return fail(ctx, RLB_ERR_NUMERIC, buf);
+    return fail(ctx, (word & rlbk::ERR_TIMEOUT) ? RLB_ERR_TIMEOUT : RLB_ERR_NUMERIC, buf);
   }
   return RLB_OK;
 }

@@ -88,6 +88,17 @@ def alu_peaks(device: int = 0) -> dict:
             "fp64_dfma_tflops": float(out[2])}
 
 
+def wait_selftest(device: int = 0, deliver: bool = True, limit_ms: float = 50.0):
+    """The staging wait of stage variant 6 on its own (rlb_wait_selftest):
+    (expired, value); value is 1.25 when the copy was delivered."""
+    lib = L.load()
+    e, v = ctypes.c_int(-1), ctypes.c_float(0.0)
+    rc = lib.rlb_wait_selftest(int(device), int(bool(deliver)), float(limit_ms), ctypes.byref(e), ctypes.byref(v))
+    if rc != 0:
+        raise L.RLBError(rc, "rlb_wait_selftest")
+    return bool(e.value), float(v.value)
+
+
 class Run:
     """One simulation on one GPU: EOS table, grid (or batch of events), device
     buffers, state.  With `events`, the grid's lattice, precision, dx, tau0,

@@ -36,7 +36,7 @@ def record(name, run):
     f = run.populations().double()
     out[name] = [float(f.sum()), float(f.abs().sum()), float(run.lnM().sum())]
 
-for v in range(6):
+for v in range(7):
     g = rlb.GridParams(nx=23, ny=17, dx=0.1, prec=rlb.RLB_F32, eta_over_s=0.16, tau0=0.4, dtau=0.0036)
     r = rlb.Run(g)
     r.set_stage_variant(v)
@@ -44,7 +44,7 @@ for v in range(6):
     r.step(6)
     record("fp32 variant %d" % v, r)
 events = [rlb.Event(7, 5, 0.08), rlb.Event(12, 9, 0.2), rlb.Event(4, 3, 0.3)]
-for v in (0, 3, 5):
+for v in (0, 3, 5, 6):
     g = rlb.GridParams(dx=0.1, prec=rlb.RLB_F32, tau0=0.4, dtau=0.0036)
     r = rlb.Run(g, events=events)
     r.set_stage_variant(v)

@@ -51,7 +51,7 @@ def _sampled(oracle_mod, mg, eps0, picks, nx, ny):
     return {"eps": rel(0), "T": rel(1), "u": du}
 
 
-@pytest.mark.parametrize("variant", [0, 3, 5])
+@pytest.mark.parametrize("variant", [0, 3, 5, 6])
 def test_longest_row_one_step_sampled(oracle_mod, variant):
     nx, ny = NX_MAX, 2
     g = rlb.GridParams(nx=nx, ny=ny, dx=0.1, prec=rlb.RLB_F32, eta_over_s=0.16, tau0=0.4, dtau=0.0036)

@@ -5,7 +5,10 @@ may differ between the instantiations), so the variants agree to FP32
 rounding; so do the generic kernel and the mirror-paired kernel (other
 operation order: the polar operator on even and odd parts, E_eq from a
 reciprocal square root).  Odd row lengths and odd site counts exercise the CTA
-whose second site is missing (it repeats the first and stores nothing)."""
+whose second site is missing (it repeats the first and stores nothing).  The
+halo-staged variant runs the mirror-paired arithmetic on lines read from shared
+memory, so on grids it takes (one grid, even nx) it equals variant 5 bit for
+bit; elsewhere it runs variant 5."""
 import numpy as np
 import pytest
 
@@ -20,7 +23,7 @@ from paper_1108_5561_gb300.inputs import hotspots  # noqa: E402
 
 PACKED = [0, 1, 3, 4]  # one site (capped, uncapped), two sites (capped, uncapped)
 GENERIC = 2
-MIRROR = [5]  # mirror-paired polar lines (8 x 8 x 12 lattice; the default there)
+MIRROR = [5, 6]  # mirror-paired polar lines (8 x 8 x 12 lattice; 5 the default there), 6 with the staged halo
 
 
 def _grid(nx, ny, prec=rlb.RLB_F32, **lat):
@@ -31,7 +34,8 @@ def _grid(nx, ny, prec=rlb.RLB_F32, **lat):
 def _evolve(g, variant, eps, events=None, steps=8):
     r = rlb.Run(g, events=events)
     n = r.set_stage_variant(variant)
-    assert n == (6 if g.n_xi == 8 and g.n_theta == 8 and g.n_phi_half == 6 else 5)
+    mp = g.n_xi == 8 and g.n_theta == 8 and g.n_phi_half == 6
+    assert n == ((7 if g.prec == rlb.RLB_F32 else 6) if mp else 5)
     r.init_grid(eps)
     r.step(steps)
     r.check()
@@ -107,17 +111,40 @@ def test_mirror_paired_variants_on_a_batch_with_an_odd_site_count(variant):
 
 @pytest.mark.parametrize("variant", MIRROR)
 def test_mirror_paired_variants_bf16_and_minkowski(variant):
-    g = _grid(9, 7, prec=rlb.RLB_BF16)
-    eps, _, _ = hotspots(9, 7, n=3, seed=2, spread=0.4)
-    _same(_evolve(g, 0, eps, steps=4), _evolve(g, variant, eps, steps=4), tol=2e-2)
+    if variant == 5:  # the staged variant takes FP32 storage only
+        g = _grid(9, 7, prec=rlb.RLB_BF16)
+        eps, _, _ = hotspots(9, 7, n=3, seed=2, spread=0.4)
+        _same(_evolve(g, 0, eps, steps=4), _evolve(g, variant, eps, steps=4), tol=2e-2)
     g = rlb.GridParams(nx=6, ny=5, dx=0.1, prec=rlb.RLB_F32, metric=rlb.RLB_MINKOWSKI, eta_over_s=0.12,
                        tau0=1.0, dtau=0.0036)
     eps, _, _ = hotspots(6, 5, n=3, seed=4, spread=0.3)
     _same(_evolve(g, 0, eps), _evolve(g, variant, eps), tol=1e-5)
 
 
+@pytest.mark.parametrize("nx,ny", [(24, 16), (2, 3), (2, 1), (4, 5), (160, 150)])
+def test_staged_halo_equals_mirror_paired_bit_for_bit(nx, ny):
+    g = _grid(nx, ny)
+    eps, _, _ = hotspots(nx, ny, n=max(4, nx * ny // 1200), seed=17 + nx, spread=0.4 + nx / 80)
+    a, b = _evolve(g, 5, eps, steps=4), _evolve(g, 6, eps, steps=4)
+    assert torch.equal(a.populations(), b.populations())
+    assert torch.equal(a.lnM(), b.lnM())
+    assert np.array_equal(a.moments(), b.moments())
+
+
+def test_staged_halo_minkowski_bit_for_bit():
+    g = rlb.GridParams(nx=6, ny=5, dx=0.1, prec=rlb.RLB_F32, metric=rlb.RLB_MINKOWSKI, eta_over_s=0.12,
+                       tau0=1.0, dtau=0.0036)
+    eps, _, _ = hotspots(6, 5, n=3, seed=4, spread=0.3)
+    a, b = _evolve(g, 5, eps), _evolve(g, 6, eps)
+    assert torch.equal(a.populations(), b.populations())
+
+
 def test_set_stage_variant_rejects_unknown_numbers():
     r = rlb.Run(_grid(4, 4))
+    assert r.set_stage_variant(-1) == 7
+    with pytest.raises(rlb.RLBError):
+        r.set_stage_variant(7)
+    r = rlb.Run(_grid(4, 4, prec=rlb.RLB_BF16))
     assert r.set_stage_variant(-1) == 6
     with pytest.raises(rlb.RLBError):
         r.set_stage_variant(6)
