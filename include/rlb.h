@@ -214,14 +214,23 @@ rlb_status rlb_step_static_scratch(rlb_ctx* ctx, void* state, int nsteps, void* 
  * restarted from a blob continues bit for bit like the uninterrupted run (same
  * library build, same GPU).  rlb_state_blob_size gives the bytes (configured
  * context).  rlb_save_state copies the current state into `host_buf` (host
- * memory of at least that size; synchronises `stream`); rlb_load_state checks
- * the header against the configured grid (RLB_ERR_ARG on a mismatch or a short
- * buffer, the message says which) and replaces the state, tau included; eta/s,
- * dtau and the EOS are taken from the context, not from the blob.  The paper's
- * scheme needs exactly this state to continue (Sec. 4.4: f, M and T at tau). */
+ * or device memory of at least that size; a host buffer is complete when the
+ * call returns (it synchronises `stream`), a device buffer once `stream`
+ * reaches the copies: the call enqueues them and returns); rlb_load_state
+ * checks the header against the configured grid (RLB_ERR_ARG on a mismatch or
+ * a short buffer, the message says which) and replaces the state, tau
+ * included (it reads the header on the host and synchronises `stream`); eta/s,
+ * dtau and the EOS are taken from the context, not from the blob.
+ * rlb_load_state_async replaces the state from a device blob that
+ * rlb_save_state of this context wrote, without reading its header back: the
+ * caller passes the tau rlb_get_tau reported when the blob was saved, and the
+ * copies are only enqueued on `stream` (RLB_ERR_ARG for a host pointer or a
+ * short buffer).  The paper's scheme needs exactly this state to continue
+ * (Sec. 4.4: f, M and T at tau). */
 rlb_status rlb_state_blob_size(const rlb_ctx* ctx, size_t* bytes);
 rlb_status rlb_save_state(rlb_ctx* ctx, void* host_buf, size_t bytes, void* stream);
 rlb_status rlb_load_state(rlb_ctx* ctx, const void* host_buf, size_t bytes, void* stream);
+rlb_status rlb_load_state_async(rlb_ctx* ctx, const void* dev_buf, size_t bytes, double tau, void* stream);
 
 /* Launch tuning.  rlb_step records one time step (match, predictor stage,
  * match, corrector stage) as a CUDA graph on the context's own stream the first

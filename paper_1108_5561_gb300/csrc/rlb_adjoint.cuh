@@ -188,7 +188,8 @@ __global__ void __launch_bounds__(NTH* NPH, (sizeof(AR) == 4 && NTH * NPH <= 96)
     sums[2] += wp[k] * f[k];
   }
   // site sums and sum_n ob_n (Dr f)_n in one reduction
-  const T* ob = A.ob + (size_t)site * NN + t * NXI;
+  T ob[NXI];
+  load_line<T, T, NXI>(A.ob + (size_t)site * NN + t * NXI, ob);
   T red4[4] = {sums[0], sums[1], sums[2], k0};
 #pragma unroll
   for (int k = 0; k < NXI; ++k) red4[3] += ob[k] * Drf[k];
@@ -287,13 +288,8 @@ __global__ void __launch_bounds__(NTH* NPH, (sizeof(AR) == 4 && NTH * NPH <= 96)
     for (int jj = 0; jj < NTH; ++jj) a += op.Dth[jj * NTH + j] * fs[k * LD + l * NTH + jj];
     fb[k] += a;
   }
-  T* rbo = A.rbar + (size_t)site * NN + t * NXI;
-  T* fbo = A.fbar + (size_t)site * NN + t * NXI;
-#pragma unroll
-  for (int k = 0; k < NXI; ++k) {
-    rbo[k] = rb[k];
-    fbo[k] = fb[k];
-  }
+  store_line<T, T, NXI>(A.rbar + (size_t)site * NN + t * NXI, rb);
+  store_line<T, T, NXI>(A.fbar + (size_t)site * NN + t * NXI, fb);
   // site scalar adjoints
   T s9[9];
 #pragma unroll
@@ -479,6 +475,7 @@ struct AdjAssembleArgs {
   const double* lb;     // adjoint of the stage output ln M
   AR* fout;             // adjoint of f_in
   double* lout;         // adjoint of ln M_in
+  AR acc;               // nonzero: fout, lout += acc x their previous values (in place)
   int* err;             // error word (index checks of debug builds)
   GridMap grid;
   double c, inv2dx;
@@ -518,20 +515,31 @@ __global__ void __launch_bounds__(NTH* NPH)
   const T w3xy = wj * st * st * cp * sp, w3y = wj * st * st * sp * sp;
   // the per-line moment coefficients of the four radial weights
   const T c0 = m[0] * w0, c2 = m[1] * w0, c1 = m[2] * w1 + m[3] * w1y, c3 = m[4] * w3x + m[5] * w3xy + m[6] * w3y;
-  const T* fb = A.fbar + (size_t)site * NN + t * NXI;
-  T* fo = A.fout + (size_t)site * NN + t * NXI;
+  T fb[NXI], r1x[NXI], r2x[NXI], r1y[NXI], r2y[NXI], fo[NXI];
+  load_line<T, T, NXI>(A.fbar + (size_t)site * NN + t * NXI, fb);
+  load_line<T, T, NXI>(A.rbar + d1x * NN + t * NXI, r1x);
+  load_line<T, T, NXI>(A.rbar + d2x * NN + t * NXI, r2x);
+  load_line<T, T, NXI>(A.rbar + d1y * NN + t * NXI, r1y);
+  load_line<T, T, NXI>(A.rbar + d2y * NN + t * NXI, r2y);
   const T m4 = T(-4);
 #pragma unroll
   for (int k = 0; k < NXI; ++k) {
     const T tv = op.tv[k];
     const T a = tv * nsx, b = tv * nsy;
     T v = fb[k];
-    v += a * (m4 * A.rbar[d1x * NN + t * NXI + k] + A.rbar[d2x * NN + t * NXI + k]);
-    v += b * (m4 * A.rbar[d1y * NN + t * NXI + k] + A.rbar[d2y * NN + t * NXI + k]);
+    v += a * (m4 * r1x[k] + r2x[k]);
+    v += b * (m4 * r1y[k] + r2y[k]);
     // moment weights: K, T00, T01, T02, T11, T12, T22 (ecw-scaled radial parts)
     v += c0 * op.w0[k] + c2 * op.w2[k] + c1 * op.w1[k] + c3 * op.w3[k];
     fo[k] = v;
   }
+  if (A.acc != T(0)) {  // the adjoint already there, scaled (the corrector's base term), plus this one
+    T prev[NXI];
+    load_line<T, T, NXI>(A.fout + (size_t)site * NN + t * NXI, prev);
+#pragma unroll
+    for (int k = 0; k < NXI; ++k) fo[k] = A.acc * prev[k] + fo[k];
+  }
+  store_line<T, T, NXI>(A.fout + (size_t)site * NN + t * NXI, fo);
   if (t == 0) {
     const double* sb = A.sbar;
     const int xm = wrap(x - 1, nx), xp = wrap(x + 1, nx), ym = wrap(y - 1, ny), yp = wrap(y + 1, ny);
@@ -541,7 +549,8 @@ __global__ void __launch_bounds__(NTH* NPH)
     const size_t sym = idx_checked(L.base + ym * nx + x, ns_all, A.err), syp = idx_checked(L.base + yp * nx + x, ns_all, A.err);
     const double gx = sb[sxm * kAdjS + AS_AX] - sb[sxp * kAdjS + AS_AX];
     const double gy = sb[sym * kAdjS + AS_AY] - sb[syp * kAdjS + AS_AY];
-    A.lout[site] = A.c * A.lb[site] + A.lbar[site] + A.inv2dx * (gx + gy);
+    const double v = A.c * A.lb[site] + A.lbar[site] + A.inv2dx * (gx + gy);
+    A.lout[site] = A.acc != T(0) ? (double)A.acc * A.lout[site] + v : v;
   }
 }
 
@@ -642,13 +651,6 @@ __global__ void __launch_bounds__(1024) project_kernel(const double* basis, cons
     for (int w = 0; w < 32; ++w) s += red[w];
     out[blockIdx.x] = s;
   }
-}
-
-// out = beta * out + alpha * in (n values)
-template <class T>
-__global__ void axpby_kernel(T* out, const T* in, T alpha, T beta, size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    out[i] = beta * out[i] + (in ? alpha * in[i] : T(0));
 }
 
 // out[i] = (T) in[i]

@@ -433,9 +433,14 @@ rlb_status upload_tables(rlb_ctx* ctx, char* scr, cudaStream_t st) {
   return RLB_OK;
 }
 
+// the clock value travels as a kernel parameter: enqueued on the stream
+// without a host copy that could synchronise it
+__global__ void set_clock_kernel(rlbk::Clock* dst, rlbk::Clock v) { *dst = v; }
+
 rlb_status set_clock(rlb_ctx* ctx, char* scr, double tau, cudaStream_t st) {
-  const rlbk::Clock c{tau, 1.0 / tau, (float)(1.0 / tau), 0.f};  // pageable: copied before return
-  RLB_CUDA(cudaMemcpyAsync(scr + ctx->clock_off, &c, sizeof c, cudaMemcpyHostToDevice, st), "clock upload");
+  const rlbk::Clock c{tau, 1.0 / tau, (float)(1.0 / tau), 0.f};
+  set_clock_kernel<<<1, 1, 0, st>>>(reinterpret_cast<rlbk::Clock*>(scr + ctx->clock_off), c);
+  RLB_CUDA(cudaGetLastError(), "clock upload");
   return RLB_OK;
 }
 
@@ -884,16 +889,28 @@ struct Adjoint {
 
   // adjoint of one stage with input (f_in, lnM_in): from (ob, lb) to (fout, lout);
   // AR: arithmetic of the per-node adjoint work and type of the per-node arrays
+  // acc nonzero: fout, lout += acc x their previous values (instead of overwriting them).
+  // FP32 adjoint on the FP32-arithmetic storage paths: the moments, the
+  // matching and its temperature of f_in may come from the forward recompute
+  // (momf_src, scf_src, T_src), the exact point the forward step used, instead
+  // of being recomputed here.
   template <class AR>
   static rlb_status stage(rlb_ctx* ctx, const S* f_in, const double* lnM_in, double milne, double c,
-                          const AR* ob, const double* lb, AR* fout, double* lout, cudaStream_t st) {
+                          const AR* ob, const double* lb, AR* fout, double* lout, cudaStream_t st,
+                          double acc = 0.0, const float* momf_src = nullptr, const float* scf_src = nullptr,
+                          double* T_src = nullptr) {
     const auto opd = make_ops<double, NXI, NTH, NPH>(ctx->lat);
     const auto opa = make_ops<AR, NXI, NTH, NPH>(ctx->lat);
     const rlbk::GridMap gm = grid_map(ctx, ctx->scratch);
     int* err = reinterpret_cast<int*>(ctx->scratch + ctx->err_off);
     constexpr bool kF32 = std::is_same<AR, float>::value;
     const unsigned nbm = (unsigned)((ctx->ns + kMatchThreads - 1) / kMatchThreads);
-    if constexpr (kF32) {  // FP32 moment partials and the FP32 matching (FP64 final steps) of f_in
+    const bool given = kF32 && scf_src;
+    const float* momf_use = given ? momf_src : P<float>(ctx, ctx->a_momf);
+    const float* scf_use = given ? scf_src : P<float>(ctx, ctx->a_scf);
+    double* T_use = given ? T_src : D(ctx, ctx->a_T);
+    if (given) {
+    } else if constexpr (kF32) {  // FP32 moment partials and the FP32 matching (FP64 final steps) of f_in
       rlbk::MomentsArgs<S, float, NXI, NTH, NPH> a;
       a.f = f_in;
       a.mom = nullptr;
@@ -925,7 +942,7 @@ struct Adjoint {
     }
     {
       rlbk::AdjStageArgs<S, AR, NXI, NTH, NPH> a;
-      a.f_in = f_in; a.sc = D(ctx, ctx->a_sc); a.scf = kF32 ? P<float>(ctx, ctx->a_scf) : nullptr;
+      a.f_in = f_in; a.sc = D(ctx, ctx->a_sc); a.scf = kF32 ? scf_use : nullptr;
       a.ob = ob; a.lb = lb;
       a.rbar = P<AR>(ctx, ctx->a_rb); a.fbar = P<AR>(ctx, ctx->a_fb); a.sbar = D(ctx, ctx->a_sbar);
       a.err = err; a.grid = gm; a.milne = (AR)milne; a.c = (AR)c; a.dtau = (AR)ctx->gp.dtau;
@@ -935,9 +952,9 @@ struct Adjoint {
     }
     {
       rlbk::AdjMatchArgs a;
-      a.mom = D(ctx, ctx->a_mom); a.momf = kF32 ? P<float>(ctx, ctx->a_momf) : nullptr;
-      a.Tstart = D(ctx, ctx->a_T);  // the matching just made: the EOS inversion starts there
-      a.scf = kF32 ? P<float>(ctx, ctx->a_scf) : nullptr;  // FP32: u and T from that matching
+      a.mom = D(ctx, ctx->a_mom); a.momf = kF32 ? momf_use : nullptr;
+      a.Tstart = kF32 ? T_use : D(ctx, ctx->a_T);  // the matching made: the EOS inversion starts there
+      a.scf = kF32 ? scf_use : nullptr;  // FP32: u and T from that matching
       a.lnM = lnM_in; a.sbar = D(ctx, ctx->a_sbar); a.mbar = D(ctx, ctx->a_mbar);
       a.lbar = D(ctx, ctx->a_lbar); a.ebar = D(ctx, ctx->a_ebar); a.err = err; a.eos = eos_view(ctx);
       a.grid = gm; a.ns = (int)ctx->ns;
@@ -950,6 +967,7 @@ struct Adjoint {
       rlbk::AdjAssembleArgs<AR, NXI, NTH, NPH> a;
       a.fbar = P<AR>(ctx, ctx->a_fb); a.rbar = P<AR>(ctx, ctx->a_rb); a.mbar = D(ctx, ctx->a_mbar);
       a.sbar = D(ctx, ctx->a_sbar); a.lbar = D(ctx, ctx->a_lbar); a.lb = lb; a.fout = fout; a.lout = lout;
+      a.acc = (AR)acc;
       a.err = err; a.grid = gm; a.c = c; a.inv2dx = 1.0 / (2.0 * ctx->gp.dx); a.op = opa;
       rlbk::adj_stage3<AR, NXI, NTH, NPH><<<site_grid(ctx), NL, 0, st>>>(a);
       RLB_CUDA(cudaGetLastError(), "adj_stage3 launch");
@@ -957,12 +975,6 @@ struct Adjoint {
     return RLB_OK;
   }
 
-  template <class T>
-  static rlb_status axpby(rlb_ctx* ctx, T* out, const T* in, double a, double b, size_t n, cudaStream_t st) {
-    rlbk::axpby_kernel<T><<<(unsigned)std::min<size_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(out, in, (T)a, (T)b, n);
-    RLB_CUDA(cudaGetLastError(), "axpby launch");
-    return RLB_OK;
-  }
 
   // the adjoint buffers hold the adjoints of a step's output; the context state
   // is that step's input (at ctx->tau): replace them by the adjoints of the input
@@ -988,22 +1000,34 @@ struct Adjoint {
     RLB_CUDA(cudaGetLastError(), "adjoint predictor recompute");
     const double tau = ctx->tau, dt = ctx->gp.dtau;
     const bool milne = ctx->gp.metric == RLB_MILNE;
-    const size_t npop = ctx->ns * ctx->nn;
+    // FP32 adjoint on an FP32-arithmetic storage path: the matchings of f and
+    // f* as the forward step made them (moment partials of the stage kernels,
+    // the same Newton starts), no recomputed moments
+    constexpr bool kReuse = std::is_same<AR, float>::value && std::is_same<R, float>::value;
+    float* scf = reinterpret_cast<float*>(ctx->scratch + ctx->scf_off);
+    double* Tsite = reinterpret_cast<double*>(ctx->scratch + ctx->T_off);
+    if constexpr (kReuse) {  // matching of f* into the adjoint's buffers, from T(f) as the forward did
+      RLB_CUDA(cudaMemcpyAsync(D(ctx, ctx->a_T), Tsite, ctx->ns * sizeof(double), cudaMemcpyDeviceToDevice, st),
+               "adjoint Newton start copy");
+      rlbk::MatchArgs ma = match_args(ctx, moms, ms, nullptr);
+      ma.Tsite = D(ctx, ctx->a_T);
+      ma.sc = nullptr;
+      ma.scf = P<float>(ctx, ctx->a_scf);
+      rlbk::match_kernel<true><<<(unsigned)((ctx->ns + kMatchThreads - 1) / kMatchThreads), kMatchThreads, 0, st>>>(ma);
+      RLB_CUDA(cudaGetLastError(), "adjoint matching launch");
+    }
     // corrector f_new = (f + f* + dtau RHS(f*)) / 2
     r = stage<AR>(ctx, fs, ms, milne ? 1.0 / (tau + dt) : 0.0, 0.5, P<AR>(ctx, ctx->a_f), D(ctx, ctx->a_l),
-                  P<AR>(ctx, ctx->a_fb), D(ctx, ctx->a_lin), st);
+                  P<AR>(ctx, ctx->a_fb), D(ctx, ctx->a_lin), st, 0.0,
+                  kReuse ? reinterpret_cast<const float*>(moms) : nullptr,
+                  kReuse ? P<float>(ctx, ctx->a_scf) : nullptr, kReuse ? D(ctx, ctx->a_T) : nullptr);
     if (r) return r;
-    r = axpby<AR>(ctx, P<AR>(ctx, ctx->a_f), nullptr, 0.0, 0.5, npop, st);  // base terms (1/2) fbar_new
-    if (r) return r;
-    r = axpby<double>(ctx, D(ctx, ctx->a_l), nullptr, 0.0, 0.5, ctx->ns, st);
-    if (r) return r;
-    // predictor f* = f + dtau RHS(f)
-    r = stage<AR>(ctx, f, m, milne ? 1.0 / tau : 0.0, 1.0, P<AR>(ctx, ctx->a_fb), D(ctx, ctx->a_lin),
-                  P<AR>(ctx, ctx->a_fb), D(ctx, ctx->a_lin), st);
-    if (r) return r;
-    r = axpby<AR>(ctx, P<AR>(ctx, ctx->a_f), P<AR>(ctx, ctx->a_fb), 1.0, 1.0, npop, st);
-    if (r) return r;
-    return axpby<double>(ctx, D(ctx, ctx->a_l), D(ctx, ctx->a_lin), 1.0, 1.0, ctx->ns, st);
+    // predictor f* = f + dtau RHS(f); its adjoint adds to the corrector's base
+    // term (1/2) fbar_new, ln M likewise (in the assembly kernel, in place)
+    return stage<AR>(ctx, f, m, milne ? 1.0 / tau : 0.0, 1.0, P<AR>(ctx, ctx->a_fb), D(ctx, ctx->a_lin),
+                     P<AR>(ctx, ctx->a_f), D(ctx, ctx->a_l), st, 0.5,
+                     kReuse ? reinterpret_cast<const float*>(mom) : nullptr, kReuse ? scf : nullptr,
+                     kReuse ? Tsite : nullptr);
   }
 
   // seed: adjoints of v2 (p_perp-weighted) of the current state; out[0] = v2
@@ -1673,6 +1697,19 @@ rlb_status rlb_state_blob_size(const rlb_ctx* ctx, size_t* bytes) {
   return RLB_OK;
 }
 
+// The blob header written on the device by the stream (it travels as a kernel
+// parameter: nothing on the host has to outlive the call).
+__global__ void write_header_kernel(BlobHeader h, BlobHeader* dst) { *dst = h; }
+
+bool is_device_pointer(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice;
+}
+
 rlb_status rlb_save_state(rlb_ctx* ctx, void* host_buf, size_t bytes, void* stream) {
   if (!ctx || !host_buf) return RLB_ERR_ARG;
   if (!ctx->inited) return fail(ctx, RLB_ERR_STATE, "nothing to save: rlb_init_grid or rlb_load_state first");
@@ -1687,8 +1724,14 @@ rlb_status rlb_save_state(rlb_ctx* ctx, void* host_buf, size_t bytes, void* stre
   if (s) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   char* p = static_cast<char*>(host_buf);
-  RLB_CUDA(cudaMemcpyAsync(p, &h, sizeof h, cudaMemcpyDefault, st), "state header");
-  RLB_CUDA(cudaStreamSynchronize(st), "state header synchronise");  // h lives on this stack
+  const bool dev = is_device_pointer(host_buf);
+  if (dev) {  // everything enqueued on the stream: no host synchronisation
+    write_header_kernel<<<1, 1, 0, st>>>(h, reinterpret_cast<BlobHeader*>(p));
+    RLB_CUDA(cudaGetLastError(), "state header");
+  } else {
+    RLB_CUDA(cudaMemcpyAsync(p, &h, sizeof h, cudaMemcpyDefault, st), "state header");
+    RLB_CUDA(cudaStreamSynchronize(st), "state header synchronise");  // h lives on this stack
+  }
   p += sizeof h;
   const struct { const char* src; uint64_t n; } parts[4] = {
       {ctx->state + ctx->f_off, h.f_bytes}, {ctx->state + ctx->lnM_off, h.lnM_bytes},
@@ -1697,7 +1740,33 @@ rlb_status rlb_save_state(rlb_ctx* ctx, void* host_buf, size_t bytes, void* stre
     RLB_CUDA(cudaMemcpyAsync(p, q.src, q.n, cudaMemcpyDefault, st), "state copy");
     p += q.n;
   }
-  RLB_CUDA(cudaStreamSynchronize(st), "state download synchronise");
+  if (!dev) RLB_CUDA(cudaStreamSynchronize(st), "state download synchronise");
+  return RLB_OK;
+}
+
+rlb_status rlb_load_state_async(rlb_ctx* ctx, const void* dev_buf, size_t bytes, double tau, void* stream) {
+  if (!ctx || !dev_buf) return RLB_ERR_ARG;
+  if (!ctx->bound) return fail(ctx, RLB_ERR_STATE, "rlb_bind_buffers must come first");
+  BlobHeader want;
+  blob_parts(ctx, &want);
+  if (bytes < blob_size(want)) return fail(ctx, RLB_ERR_ARG, "state blob is truncated");
+  if (!is_device_pointer(dev_buf)) return fail(ctx, RLB_ERR_ARG, "rlb_load_state_async takes device blobs");
+  rlb_status s = set_device(ctx);
+  if (s) return s;
+  ctx->scf_fresh = false;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const char* p = static_cast<const char*>(dev_buf) + sizeof want;
+  const struct { char* dst; uint64_t n; } parts[4] = {
+      {ctx->state + ctx->f_off, want.f_bytes}, {ctx->state + ctx->lnM_off, want.lnM_bytes},
+      {ctx->scratch + ctx->T_off, want.T_bytes}, {ctx->scratch + ctx->mom_off, want.mom_bytes}};
+  for (const auto& q : parts) {
+    RLB_CUDA(cudaMemcpyAsync(q.dst, p, q.n, cudaMemcpyDeviceToDevice, st), "state copy");
+    p += q.n;
+  }
+  ctx->tau = tau;
+  s = set_clock(ctx, ctx->scratch, ctx->tau, st);
+  if (s) return s;
+  ctx->inited = true;
   return RLB_OK;
 }
 

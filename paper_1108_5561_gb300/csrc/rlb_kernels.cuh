@@ -13,6 +13,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace rlbk {
 
 enum : int { ERR_LANDAU = 1, ERR_EOS = 2, ERR_NONFINITE = 4, ERR_INDEX = 8 };
@@ -108,9 +110,31 @@ template <> __device__ __forceinline__ __nv_bfloat16 st1<__nv_bfloat16, double>(
   return __double2bfloat16(v);
 }
 
+// 8 FP32 values in one 256-bit access (p 32-byte aligned: a line of 8k FP32
+// values at a multiple of 8 elements in a 256-byte aligned array; two 128-bit
+// accesses make every request of the warp touch all 32 sectors of its 1 KB)
+__device__ __forceinline__ void ldg8f(const float* p, float (&v)[8]) {
+  asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+      : "l"(p));
+}
+__device__ __forceinline__ void stg8f(float* p, const float (&v)[8]) {
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(v[0]), "f"(v[1]),
+               "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+               : "memory");
+}
+
 template <class S, class R, int N>
 __device__ __forceinline__ void load_line(const S* __restrict__ p, R (&v)[N]) {
-  if constexpr (sizeof(S) == 4 && N % 4 == 0) {
+  if constexpr (std::is_same<S, float>::value && N % 8 == 0) {
+#pragma unroll
+    for (int i = 0; i < N / 8; ++i) {
+      float a[8];
+      ldg8f(p + 8 * i, a);
+#pragma unroll
+      for (int h = 0; h < 8; ++h) v[8 * i + h] = (R)a[h];
+    }
+  } else if constexpr (sizeof(S) == 4 && N % 4 == 0) {
     const float4* q = reinterpret_cast<const float4*>(p);
 #pragma unroll
     for (int i = 0; i < N / 4; ++i) {
@@ -144,7 +168,15 @@ __device__ __forceinline__ void load_line(const S* __restrict__ p, R (&v)[N]) {
 
 template <class S, class R, int N>
 __device__ __forceinline__ void store_line(S* __restrict__ p, const R (&v)[N]) {
-  if constexpr (sizeof(S) == 4 && N % 4 == 0) {
+  if constexpr (std::is_same<S, float>::value && N % 8 == 0) {
+#pragma unroll
+    for (int i = 0; i < N / 8; ++i) {
+      float a[8];
+#pragma unroll
+      for (int h = 0; h < 8; ++h) a[h] = (float)v[8 * i + h];
+      stg8f(p + 8 * i, a);
+    }
+  } else if constexpr (sizeof(S) == 4 && N % 4 == 0) {
     float4* q = reinterpret_cast<float4*>(p);
 #pragma unroll
     for (int i = 0; i < N / 4; ++i)

@@ -221,13 +221,16 @@ class Run:
         return a.value, b.value
 
     def save_state(self, device: bool = False):
-        """Checkpoint blob of the current state: host bytes, or a CUDA uint8 tensor."""
+        """Checkpoint blob of the current state: host bytes, or a CUDA uint8 tensor
+        (filled in stream order; it carries the tau it was saved at, so that
+        load_state restores it without reading its header back)."""
         n = ctypes.c_size_t()
         self._chk(self.lib.rlb_state_blob_size(self._h, ctypes.byref(n)), "rlb_state_blob_size")
         if device:
             t = self.torch.empty(n.value, dtype=self.torch.uint8, device=self.device)
             self._chk(self.lib.rlb_save_state(self._h, ctypes.c_void_p(t.data_ptr()), n, self._stream()),
                       "rlb_save_state")
+            t._rlb_saved = (self._h.value, self.tau)
             return t
         buf = ctypes.create_string_buffer(n.value)
         self._chk(self.lib.rlb_save_state(self._h, buf, n, self._stream()), "rlb_save_state")
@@ -236,6 +239,12 @@ class Run:
     def load_state(self, blob):
         """Replace the state (and tau) by a blob from save_state of the same grid."""
         if isinstance(blob, self.torch.Tensor):
+            saved = getattr(blob, "_rlb_saved", None)
+            if saved is not None and saved[0] == self._h.value and blob.is_cuda:  # written by this context
+                self._chk(self.lib.rlb_load_state_async(self._h, ctypes.c_void_p(blob.data_ptr()), blob.numel(),
+                                                        ctypes.c_double(saved[1]), self._stream()),
+                          "rlb_load_state_async")
+                return
             self._chk(self.lib.rlb_load_state(self._h, ctypes.c_void_p(blob.data_ptr()), blob.numel(),
                                               self._stream()), "rlb_load_state")
             return
