@@ -174,8 +174,15 @@ __global__ void __launch_bounds__(NTH* NPH, (sizeof(AR) == 4 && NTH * NPH <= 96)
   for (int k = 0; k < NXI; ++k) {
     const T s = op.s[k], c = op.c[k], tv = op.tv[k];
     E[k] = sqrt(Meq * Meq + M2 * op.s2[k]);
-    iE[k] = k1 / E[k];
-    feq[k] = A.Z * exp(-invT * (ut * E[k] - M * vu * s));
+    // FP32 adjoint: the hardware reciprocal and exponential (a few ulp; the
+    // linearisation point needs no more), FP64: the correctly rounded ones
+    if constexpr (std::is_same<T, float>::value) {
+      iE[k] = __frcp_rn(E[k]);
+      feq[k] = A.Z * __expf(-invT * (ut * E[k] - M * vu * s));
+    } else {
+      iE[k] = k1 / E[k];
+      feq[k] = A.Z * exp(-invT * (ut * E[k] - M * vu * s));
+    }
     cc[k] = itr * (ut - tv * vu);
     fc[k] = Gp * op.q1[k] * iE[k] + Hp * op.q2[k] + Jp * op.inv_c[k];
     const T Sx = k3 * f[k] - k4 * fx1[k] + fx2[k], Sy = k3 * f[k] - k4 * fy1[k] + fy2[k];
@@ -479,6 +486,7 @@ struct AdjAssembleArgs {
   int* err;             // error word (index checks of debug builds)
   GridMap grid;
   double c, inv2dx;
+  AR inv2dx_t;          // inv2dx in the arithmetic type
   Ops<AR, NXI, NTH, NPH> op;
 };
 
@@ -494,7 +502,8 @@ __global__ void __launch_bounds__(NTH* NPH)
   const int x = L.x, y = L.y, site = idx_checked(L.site, A.grid.n_sites, A.err), nx = L.nx, ny = L.ny;
   const int t = threadIdx.x, j = t % NTH, l = t / NTH;
   const T cp = op.cph[l], sp = op.sph[l], st = op.sth[j], wj = op.wj[j];
-  const T nsx = -st * fabs(cp) * (T)A.inv2dx, nsy = -st * fabs(sp) * (T)A.inv2dx;
+  const T i2dx = A.inv2dx_t;
+  const T nsx = -st * fabs(cp) * i2dx, nsy = -st * fabs(sp) * i2dx;
   // downwind neighbours: the forward stencil of site i - s uses f(i) with -4,
   // that of i - 2 s with +1 (s = the upwind offset)
   const int sx = (cp > T(0)) ? -1 : 1, sy = (sp > T(0)) ? -1 : 1;
@@ -507,10 +516,14 @@ __global__ void __launch_bounds__(NTH* NPH)
   const size_t d2x = idx_checked(L.base + y * nx + idx_checked(wrap(x - 2 * sx, nx), nx, A.err), ns_all, A.err);
   const size_t d1y = idx_checked(L.base + idx_checked(wrap(y - sy, ny), ny, A.err) * nx + x, ns_all, A.err);
   const size_t d2y = idx_checked(L.base + idx_checked(wrap(y - 2 * sy, ny), ny, A.err) * nx + x, ns_all, A.err);
-  const double* md = A.mbar + (size_t)site * kMom;
+  // the moment adjoints of the site, converted once per CTA (a conversion from
+  // FP64 occupies the FP64 pipe: per thread it dominated the kernel)
+  __shared__ T msh[8];
+  if (t < 7) msh[t] = (T)A.mbar[(size_t)site * kMom + t];
+  __syncthreads();
   T m[7];
 #pragma unroll
-  for (int i = 0; i < 7; ++i) m[i] = (T)md[i];
+  for (int i = 0; i < 7; ++i) m[i] = msh[i];
   const T w0 = wj, w1 = wj * st * cp, w1y = wj * st * sp, w3x = wj * st * st * cp * cp;
   const T w3xy = wj * st * st * cp * sp, w3y = wj * st * st * sp * sp;
   // the per-line moment coefficients of the four radial weights

@@ -958,7 +958,8 @@ struct Adjoint {
       a.lnM = lnM_in; a.sbar = D(ctx, ctx->a_sbar); a.mbar = D(ctx, ctx->a_mbar);
       a.lbar = D(ctx, ctx->a_lbar); a.ebar = D(ctx, ctx->a_ebar); a.err = err; a.eos = eos_view(ctx);
       a.grid = gm; a.ns = (int)ctx->ns;
-      rlbk::adj_match<<<nbm, kMatchThreads, 0, st>>>(a);
+      // one warp per CTA: the FP64-bound per-site work spread over as many SMs as possible
+      rlbk::adj_match<<<(unsigned)((ctx->ns + 31) / 32), 32, 0, st>>>(a);
       RLB_CUDA(cudaGetLastError(), "adj_match launch");
       rlbk::sum_kernel<<<1, 1024, 0, st>>>(D(ctx, ctx->a_ebar), ctx->ns, D(ctx, ctx->a_eta), 1);
       RLB_CUDA(cudaGetLastError(), "adjoint eta sum launch");
@@ -969,6 +970,7 @@ struct Adjoint {
       a.sbar = D(ctx, ctx->a_sbar); a.lbar = D(ctx, ctx->a_lbar); a.lb = lb; a.fout = fout; a.lout = lout;
       a.acc = (AR)acc;
       a.err = err; a.grid = gm; a.c = c; a.inv2dx = 1.0 / (2.0 * ctx->gp.dx); a.op = opa;
+      a.inv2dx_t = (AR)a.inv2dx;
       rlbk::adj_stage3<AR, NXI, NTH, NPH><<<site_grid(ctx), NL, 0, st>>>(a);
       RLB_CUDA(cudaGetLastError(), "adj_stage3 launch");
     }
