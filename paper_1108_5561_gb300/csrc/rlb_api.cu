@@ -146,7 +146,8 @@ void layout(const rlb_grid_params& g, const Shape& sh, size_t table_points, size
   size_t sc_off = off; off += align256(ns * rlbk::kSc * sizeof(double));
   size_t err_off = off; off += 256;
   size_t tab_off = off; off += align256((table_points + 6) * rlb::kFields * sizeof(double));
-  size_t tabf_off = off; off += align256((table_points + 6) * rlb::kFields * sizeof(float));
+  // FP32 table: hi parts, then lo parts (hi + lo = the FP64 table to 2^-48)
+  size_t tabf_off = off; off += align256(2 * (table_points + 6) * rlb::kFields * sizeof(float));
   size_t scf_off = off; off += align256(ns * rlbk::kSc * sizeof(float));
   size_t ev_off = off; off += align256(sh.events * sizeof(rlbk::EventInfo));
   size_t loc_off = off; off += sh.events > 1 ? align256(ns * sizeof(int2)) : 0;
@@ -385,12 +386,26 @@ void eos_geometry(const rlb::EosTable& tab, rlbk::EosView* v) {
   v->c_lo = (float)(c - (double)v->c_hi);
   v->ylo_f = (float)(tab.y0 + 2.0 * tab.h);
   v->yhi_f = (float)(tab.y0 + (tab.n - 4) * tab.h);
+  v->y0_hi = (float)tab.y0;
+  v->y0_lo = (float)(tab.y0 - (double)v->y0_hi);
+}
+
+// The FP32 table in device order: hi parts of every entry, then lo parts.
+std::vector<float> table_hi_lo(const rlb::EosTable& tab) {
+  const size_t n = tab.data.size();
+  std::vector<float> t(2 * n);
+  for (size_t i = 0; i < n; ++i) {
+    t[i] = (float)tab.data[i];
+    t[n + i] = (float)(tab.data[i] - (double)t[i]);
+  }
+  return t;
 }
 
 rlbk::EosView eos_view(const rlb_ctx* c) {
   rlbk::EosView v;
   v.tab = reinterpret_cast<const double*>(c->scratch + c->tab_off);
   v.tabf = reinterpret_cast<const float*>(c->scratch + c->tabf_off);
+  v.tabl = v.tabf + c->tab.data.size();
   eos_geometry(c->tab, &v);
   return v;
 }
@@ -1189,14 +1204,14 @@ rlb_status step_static(rlb_ctx* ctx, char* state, char* scr, int nsteps, cudaStr
   rlbk::EosView ev;
   ev.tab = reinterpret_cast<const double*>(scr + L.tab_off);
   ev.tabf = reinterpret_cast<const float*>(scr + L.tabf_off);
+  ev.tabl = ev.tabf + ctx->tab.data.size();
   eos_geometry(ctx->tab, &ev);
   // contents left by earlier calls are not trusted: EOS tables, Newton starts,
   // error word and the moments of the input are rebuilt here
   RLB_CUDA(cudaMemcpyAsync(scr + L.tab_off, ctx->tab.data.data(), ctx->tab.data.size() * sizeof(double),
                            cudaMemcpyHostToDevice, st), "static EOS table upload");
   {
-    std::vector<float> tf(ctx->tab.data.size());
-    for (size_t i = 0; i < tf.size(); ++i) tf[i] = (float)ctx->tab.data[i];
+    const std::vector<float> tf = table_hi_lo(ctx->tab);
     RLB_CUDA(cudaMemcpyAsync(scr + L.tabf_off, tf.data(), tf.size() * sizeof(float),
                              cudaMemcpyHostToDevice, st), "static FP32 EOS table upload");
     RLB_CUDA(cudaStreamSynchronize(st), "static table upload synchronise");
@@ -1431,8 +1446,7 @@ rlb_status rlb_bind_buffers(rlb_ctx* ctx, void* state, void* scratch, void* stre
                            ctx->tab.data.size() * sizeof(double), cudaMemcpyHostToDevice, st),
            "EOS table upload");
   {
-    std::vector<float> tf(ctx->tab.data.size());
-    for (size_t i = 0; i < tf.size(); ++i) tf[i] = (float)ctx->tab.data[i];
+    const std::vector<float> tf = table_hi_lo(ctx->tab);
     RLB_CUDA(cudaMemcpyAsync(ctx->scratch + ctx->tabf_off, tf.data(), tf.size() * sizeof(float),
                              cudaMemcpyHostToDevice, st),
              "FP32 EOS table upload");

@@ -92,6 +92,10 @@ struct EosView {
   float ih_hi, ih_lo, c_hi, c_lo;
   // the interior of the table in FP32: [y0 + 2h, y0 + (n - 4)h]
   float ylo_f, yhi_f;
+  // double-FP32 form of the table for the FP64-accurate EOS step of the FP32
+  // path: tabf + tabl = tab to 2^-48, y0 = y0_hi + y0_lo
+  const float* tabl;
+  float y0_hi, y0_lo;
 };
 
 
@@ -392,39 +396,90 @@ __device__ bool eos_invert_f(const EosView& E, int field, float target, float y,
   return true;
 }
 
-// One FP64 Newton step of e(y) = target on the FP64 table from an FP32 root
-// (slope from the FP32 table): the EOS inversion of the FP32 storage path.
-// The cell comes from the FP32 location (at a cell edge the two locations may
-// differ by one cell; the offset is then just outside [0, 1), where the same
-// interpolating polynomial still holds to the table's accuracy).
-__device__ __forceinline__ double eos_refine(const EosView& E, int field, double target, float y) {
-  const double yd = (double)y;
-  int i0;
-  float tf;
-  if (!eos_cellf(E, y, &i0, &tf)) return yd;
-  const double t = (yd - E.y0) * E.inv_h - (double)i0;
-  double w[6];
-  lagrange6(t, w);
-  float dw[6];
-  lagrange6f_d(tf, dw);
-  double F = 0.0;
-  float dF = 0.f;
-#pragma unroll
-  for (int m = 0; m < 6; ++m) {
-    F += w[m] * __ldg(E.tab + (size_t)(i0 - 2 + m) * 8 + field);
-    dF += dw[m] * __ldg(E.tabf + (size_t)(i0 - 2 + m) * 8 + field);
-  }
-  dF *= E.ih_hi + E.ih_lo;
-  if (!(dF > 0.f)) return yd;
-  return yd - (F - target) * (double)(1.f / dF);
-}
-
 // a + b = s + e exactly (Knuth's TwoSum)
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
   const float bb = s - a;
   e = (a - (s - bb)) + (b - bb);
 }
+
+// Double-FP32 numbers: the unevaluated sum hi + lo of two FP32 numbers with
+// |lo| <= ulp(hi) / 2 (about 48 significant bits).  Exact sums by TwoSum,
+// exact products by the fused multiply-add (the error of a * b is
+// fma(a, b, -a b)); every multiply-add below is written out, so that no
+// contraction can change an error term.
+struct f2x {
+  float hi, lo;
+};
+__device__ __forceinline__ f2x two_sum_f2x(float a, float b) {
+  f2x r;
+  two_sum(a, b, r.hi, r.lo);
+  return r;
+}
+__device__ __forceinline__ f2x fast_two_sum(float a, float b) {  // |a| >= |b| or a = 0
+  const float s = a + b;
+  return f2x{s, b - (s - a)};
+}
+__device__ __forceinline__ f2x two_prod(float a, float b) {
+  const float p = a * b;
+  return f2x{p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ f2x df_add(f2x a, f2x b) {
+  f2x s = two_sum_f2x(a.hi, b.hi);
+  s.lo += a.lo + b.lo;
+  return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ f2x df_mul(f2x a, f2x b) {
+  f2x p = two_prod(a.hi, b.hi);
+  p.lo = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo));
+  return fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ f2x df_div(f2x a, f2x b) {  // a / b, b != 0
+  const float q1 = a.hi / b.hi;
+  const f2x r = df_add(a, df_mul(b, f2x{-q1, 0.f}));
+  const float q2 = r.hi / b.hi;
+  return fast_two_sum(q1, q2);
+}
+
+// One Newton step of e(y) = target, FP64-accurate, from an FP32 root (slope
+// from the FP32 table): the EOS inversion of the FP32 storage path.  Run on
+// the FP32 pipes in double-FP32 arithmetic (GB300 issues one FP64 warp
+// instruction per 16 cycles per SM):
+//   the offset t in the cell of the FP32 location, from y - y0 and 1/h as
+//   double-FP32 numbers (t to ~1e-9 cells; the FP32 location alone is good to
+//   ~4e-3 cells at u ~ 6.5e4);
+//   the residual sum_m w_m (tab_m - target): sum_m w_m = 1, so the FP32
+//   weights multiply the differences tab_m - target, taken exactly (Sterbenz)
+//   from the double-FP32 table and target, and the sum keeps ~1e-7 of terms of
+//   the size of the step, about 1e-9 in y.
+// The cell comes from the FP32 location (at a cell edge the two locations may
+// differ by one cell; the offset is then just outside [0, 1), where the same
+// interpolating polynomial still holds to the table's accuracy).
+__device__ __forceinline__ float eos_refine_df(const EosView& E, int field, f2x target, float y) {
+  int i0;
+  float tf;
+  if (!eos_cellf(E, y, &i0, &tf)) return y;
+  f2x s = two_sum_f2x(y, -E.y0_hi);
+  s.lo -= E.y0_lo;
+  const f2x u = df_mul(fast_two_sum(s.hi, s.lo), f2x{E.ih_hi, E.ih_lo});
+  const float t = (u.hi - (float)i0) + u.lo;
+  float w[6], dw[6];
+  lagrange6f(t, w);
+  lagrange6f_d(t, dw);
+  float r = 0.f, dF = 0.f;
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    const size_t k = (size_t)(i0 - 2 + m) * 8 + field;
+    const float hi = __ldg(E.tabf + k), lo = __ldg(E.tabl + k);
+    const float d = (hi - target.hi) + (lo - target.lo);
+    r = fmaf(w[m], d, r);
+    dF = fmaf(dw[m], hi, dF);
+  }
+  dF *= E.ih_hi + E.ih_lo;
+  if (!(dF > 0.f)) return y;
+  return y - r / dF;
+}
+
 
 // ---------------------------------------------------------------------------
 // Landau matching on the (tau, x, y) block (Eq. sanity).  Boost invariance and
@@ -436,11 +491,36 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // space of A - eps (largest cross product of two rows), normalised by the
 // Minkowski norm; eps is then the Rayleigh quotient u_mu u_nu T^{mu nu}.
 // ---------------------------------------------------------------------------
-// Mixed version for the FP32 storage path (tm: the same matrix in FP32): Newton
-// from the infinity-norm bound in FP32 on the scaled matrix, then one FP64 Newton step on the FP64 cubic for
-// the eigenvalue (eps = lambda); the eigenvector by the same cross products in
-// FP32 (it is consumed in FP32).
-__device__ bool landau3_mixed(const double tmd[6], const float tm[6], float u[3], double* eps) {
+// Version for the FP32 storage path: tm the matrix in FP32, tmd the same in
+// double-FP32 (the compensated moment sums times the prefactor).  Newton from
+// the infinity-norm bound in FP32 on the scaled matrix gives lambda to FP32
+// precision and the eigenvector u by the cross products; the eigenvalue is
+// then the generalised Rayleigh quotient eps = (w^T T w) / (w^T g w), w = g u
+// (T w = lambda g w for the covariant eigenvector), evaluated in double-FP32:
+// stationary at the eigenvector, its error is second order in the FP32 error
+// of u (~1e-14 relative), as accurate as an FP64 Newton step on the cubic but
+// on the FP32 pipes.  u is recomputed by the cross products at the refined
+// eigenvalue (it is consumed in FP32).
+__device__ __forceinline__ bool null_vector3(float a00, float a01, float a02, float a10, float a11, float a12,
+                                             float a20, float a21, float a22, float lam, float u[3]) {
+  const float r00 = a00 - lam, r11 = a11 - lam, r22 = a22 - lam;
+  const float p0 = a01 * a12 - a02 * r11, p1 = a02 * a10 - r00 * a12, p2 = r00 * r11 - a01 * a10;
+  const float q0 = a01 * r22 - a02 * a21, q1 = a02 * a20 - r00 * r22, q2 = r00 * a21 - a01 * a20;
+  const float s0 = r11 * r22 - a12 * a21, s1 = a12 * a20 - a10 * r22, s2 = a10 * a21 - r11 * a20;
+  const float np = p0 * p0 + p1 * p1 + p2 * p2, nq = q0 * q0 + q1 * q1 + q2 * q2;
+  const float nsq = s0 * s0 + s1 * s1 + s2 * s2;
+  float v0 = s0, v1 = s1, v2 = s2;
+  if (np >= nq && np >= nsq) { v0 = p0; v1 = p1; v2 = p2; }
+  else if (nq >= nsq) { v0 = q0; v1 = q1; v2 = q2; }
+  const float mn = v0 * v0 - v1 * v1 - v2 * v2;
+  if (!(mn > 0.f)) return false;
+  float r = rsqrtf(mn);
+  if (v0 < 0.f) r = -r;
+  u[0] = v0 * r; u[1] = v1 * r; u[2] = v2 * r;
+  return true;
+}
+
+__device__ bool landau3_df(const f2x tmd[6], const float tm[6], float u[3], f2x* eps) {
   const float sc = fmaxf(fabsf(tm[0]) + fabsf(tm[1]) + fabsf(tm[2]),
                          fmaxf(fabsf(tm[1]) + fabsf(tm[3]) + fabsf(tm[4]),
                                fabsf(tm[2]) + fabsf(tm[4]) + fabsf(tm[5])));
@@ -449,52 +529,38 @@ __device__ bool landau3_mixed(const double tmd[6], const float tm[6], float u[3]
   const float a00 = tm[0] * is, a01 = -tm[1] * is, a02 = -tm[2] * is;
   const float a10 = -a01, a11 = -tm[3] * is, a12 = -tm[4] * is;
   const float a20 = -a02, a21 = a12, a22 = -tm[5] * is;
-  {
-    const float c2 = a00 + a11 + a22;
-    const float c1 = a00 * a11 - a01 * a10 + a00 * a22 - a02 * a20 + a11 * a22 - a12 * a21;
-    const float c0 = a00 * (a11 * a22 - a12 * a21) - a01 * (a10 * a22 - a12 * a20) +
-                     a02 * (a10 * a21 - a11 * a20);
-    float lam = 1.f;  // the infinity norm bounds every eigenvalue
-    for (int it = 0; it < 60; ++it) {
-      const float p = ((lam - c2) * lam + c1) * lam - c0;
-      const float dp = (3.f * lam - 2.f * c2) * lam + c1;
-      if (!(dp > 0.f)) break;
-      const float d = p / dp;
-      if (!(d > 0.f)) break;
-      lam -= d;
-      if (d <= 1e-7f * lam) break;
-    }
-    // FP64 Newton step on the unscaled cubic (slope from FP32)
-    const double b00 = tmd[0], b01 = -tmd[1], b02 = -tmd[2];
-    const double b10 = tmd[1], b11 = -tmd[3], b12 = -tmd[4];
-    const double b20 = tmd[2], b21 = -tmd[4], b22 = -tmd[5];
-    const double d2 = b00 + b11 + b22;
-    const double d1 = b00 * b11 - b01 * b10 + b00 * b22 - b02 * b20 + b11 * b22 - b12 * b21;
-    const double d0 = b00 * (b11 * b22 - b12 * b21) - b01 * (b10 * b22 - b12 * b20) +
-                      b02 * (b10 * b21 - b11 * b20);
-    double L = (double)lam * (double)sc;
-    const double pL = ((L - d2) * L + d1) * L - d0;
-    const float dpf = ((3.f * lam - 2.f * c2) * lam + c1) * sc * sc;
-    if (!(dpf > 0.f)) return false;
-    L -= pL * (double)(1.f / dpf);
-    *eps = L;
-    lam = (float)(L * (double)is);
-    const float r00 = a00 - lam, r11 = a11 - lam, r22 = a22 - lam;
-    const float p0 = a01 * a12 - a02 * r11, p1 = a02 * a10 - r00 * a12, p2 = r00 * r11 - a01 * a10;
-    const float q0 = a01 * r22 - a02 * a21, q1 = a02 * a20 - r00 * r22, q2 = r00 * a21 - a01 * a20;
-    const float s0 = r11 * r22 - a12 * a21, s1 = a12 * a20 - a10 * r22, s2 = a10 * a21 - r11 * a20;
-    const float np = p0 * p0 + p1 * p1 + p2 * p2, nq = q0 * q0 + q1 * q1 + q2 * q2;
-    const float nsq = s0 * s0 + s1 * s1 + s2 * s2;
-    float v0 = s0, v1 = s1, v2 = s2;
-    if (np >= nq && np >= nsq) { v0 = p0; v1 = p1; v2 = p2; }
-    else if (nq >= nsq) { v0 = q0; v1 = q1; v2 = q2; }
-    const float mn = v0 * v0 - v1 * v1 - v2 * v2;
-    if (!(mn > 0.f)) return false;
-    float r = rsqrtf(mn);
-    if (v0 < 0.f) r = -r;
-    u[0] = v0 * r; u[1] = v1 * r; u[2] = v2 * r;
+  const float c2 = a00 + a11 + a22;
+  const float c1 = a00 * a11 - a01 * a10 + a00 * a22 - a02 * a20 + a11 * a22 - a12 * a21;
+  const float c0 = a00 * (a11 * a22 - a12 * a21) - a01 * (a10 * a22 - a12 * a20) + a02 * (a10 * a21 - a11 * a20);
+  float lam = 1.f;  // the infinity norm bounds every eigenvalue
+  for (int it = 0; it < 60; ++it) {
+    const float p = ((lam - c2) * lam + c1) * lam - c0;
+    const float dp = (3.f * lam - 2.f * c2) * lam + c1;
+    if (!(dp > 0.f)) break;
+    const float d = p / dp;
+    if (!(d > 0.f)) break;
+    lam -= d;
+    if (d <= 1e-7f * lam) break;
   }
-  return *eps > 0.0;
+  float v[3];
+  if (!null_vector3(a00, a01, a02, a10, a11, a12, a20, a21, a22, lam, v)) return false;
+  // w^T T w and w^T g w with w = (v0, -v1, -v2): the products v_i v_j exact
+  const f2x v00 = two_prod(v[0], v[0]), v01 = two_prod(v[0], v[1]), v02 = two_prod(v[0], v[2]);
+  const f2x v11 = two_prod(v[1], v[1]), v12 = two_prod(v[1], v[2]), v22 = two_prod(v[2], v[2]);
+  const f2x m2{-2.f, 0.f}, p2{2.f, 0.f};
+  f2x num = df_mul(v00, tmd[0]);
+  num = df_add(num, df_mul(df_mul(m2, v01), tmd[1]));
+  num = df_add(num, df_mul(df_mul(m2, v02), tmd[2]));
+  num = df_add(num, df_mul(v11, tmd[3]));
+  num = df_add(num, df_mul(df_mul(p2, v12), tmd[4]));
+  num = df_add(num, df_mul(v22, tmd[5]));
+  f2x den = df_add(v00, f2x{-v11.hi, -v11.lo});
+  den = df_add(den, f2x{-v22.hi, -v22.lo});
+  if (!(den.hi > 0.f)) return false;
+  *eps = df_div(num, den);
+  if (!(eps->hi > 0.f)) return false;
+  const float lam2 = fmaf(eps->hi, is, eps->lo * is);
+  return null_vector3(a00, a01, a02, a10, a11, a12, a20, a21, a22, lam2, u);
 }
 
 __device__ bool landau3(const double tm[6], double u[3], double* eps) {
@@ -721,8 +787,8 @@ __device__ __forceinline__ int match_site_d(const MatchArgs& A, int site, double
 // instruction occupies the pipe for 64 cycles, so the matching keeps FP64 only
 // for the differences of ln M (central differences of nearly equal values).
 __device__ __forceinline__ int match_site_f(const MatchArgs& A, int site, float (&o)[kSc]) {
-  // moments: the kMomParts FP32 partial sums combined with TwoSum, then FP64
-  // (FP64 only for T^{mu nu}, the Landau eigenvalue and the EOS Newton step)
+  // moments: the kMomParts FP32 partial sums combined with TwoSum; T^{mu nu}
+  // in double-FP32 for the FP64-accurate Landau eigenvalue and EOS step
   float m[kMom], mlo[kMom];
   const float4* q = reinterpret_cast<const float4*>(A.momf + (size_t)site * kMom * kMomParts);
 #pragma unroll
@@ -742,23 +808,22 @@ __device__ __forceinline__ int match_site_f(const MatchArgs& A, int site, float 
   const float M = expf(lh) * (1.f + ll);
   const float M2 = M * M;
   const float pref = M2 * M2 * (float)(1.0 / (2.0 * 3.14159265358979323846 * 3.14159265358979323846));
-  const double prefd = (double)pref;
-  double tmd[6];
+  f2x tmd[6];
   float tmf[6];
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
-    tmd[i] = prefd * ((double)m[1 + i] + (double)mlo[1 + i]);
+    tmd[i] = df_mul(f2x{pref, 0.f}, f2x{m[1 + i], mlo[1 + i]});
     tmf[i] = pref * m[1 + i];
   }
   int err = 0;
   float u[3];
-  double epsd;
-  if (!landau3_mixed(tmd, tmf, u, &epsd)) {
+  f2x epsx;
+  if (!landau3_df(tmd, tmf, u, &epsx)) {
     err |= ERR_LANDAU;
     u[0] = 1.f; u[1] = 0.f; u[2] = 0.f;
-    epsd = fmax(tmd[0], 1e-300);
+    epsx = tmd[0].hi > 0.f ? tmd[0] : f2x{1e-30f, 0.f};
   }
-  const float eps = (float)epsd;
+  const float eps = epsx.hi + epsx.lo;
   const float Tg = (float)A.Tsite[site];
   const float yg = (Tg > 0.f) ? logf(Tg) : 0.f;
   float y;
@@ -766,7 +831,7 @@ __device__ __forceinline__ int match_site_f(const MatchArgs& A, int site, float 
     err |= ERR_EOS;
     y = fminf(fmaxf(yg, A.eos.ylo_f), A.eos.yhi_f);
   } else {
-    y = (float)eos_refine(A.eos, EOS_E, epsd, y);
+    y = eos_refine_df(A.eos, EOS_E, epsx, y);
   }
   int i0;
   float t, w[6];
@@ -807,11 +872,11 @@ __device__ __forceinline__ int match_site_f(const MatchArgs& A, int site, float 
   if (A.obs) {
     const double hc = 0.1973269804, h3 = hc * hc * hc;
     double* r = A.obs + (size_t)site * 8;
-    r[0] = (epsd + (double)B) / h3;
+    r[0] = ((double)epsx.hi + (double)epsx.lo + (double)B) / h3;
     r[1] = T;
     r[2] = u[0]; r[3] = u[1]; r[4] = u[2];
     r[5] = M;
-    r[6] = (prefd * ((double)m[7] + (double)mlo[7]) - (double)B) / h3;
+    r[6] = ((double)pref * ((double)m[7] + (double)mlo[7]) - (double)B) / h3;
     r[7] = Meq;
   }
   return err;
