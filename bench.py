@@ -323,7 +323,7 @@ def batch_main(args, rank, world, local):
 def sweep_main(args, rank, world, local):
     """Precision sweep on the 16 x 8 x 16 lattice (2048 populations per site):
     1024 x 1024 grid of 40 hotspots, eta/s 0.16, timed for FP32 and BF16
-    population storage (FP32 arithmetic and moments, FP64 final steps of the
+    population storage (FP32 arithmetic and moments, FP64-accurate final steps of the
     matching), plus the error of both against the FP64 oracle on a 128 x 128
     sub-run.  The JSON line's value is the BF16 rate; both rates and the errors
     are in "sweep"."""

@@ -925,7 +925,7 @@ struct Adjoint {
     const float* scf_use = given ? scf_src : P<float>(ctx, ctx->a_scf);
     double* T_use = given ? T_src : D(ctx, ctx->a_T);
     if (given) {
-    } else if constexpr (kF32) {  // FP32 moment partials and the FP32 matching (FP64 final steps) of f_in
+    } else if constexpr (kF32) {  // FP32 moment partials and the FP32 matching (double-FP32 final steps) of f_in
       rlbk::MomentsArgs<S, float, NXI, NTH, NPH> a;
       a.f = f_in;
       a.mom = nullptr;
