@@ -101,7 +101,10 @@ __global__ void __launch_bounds__(NTH* NPH, (sizeof(AR) == 4 && NTH * NPH <= 96)
   using T = AR;
   constexpr int NL = NTH * NPH;
   constexpr int NN = NL * NXI;
-  constexpr int LD = NL + 1;
+  // polar sums read VEC staged values per shared-memory load when the lines
+  // of one azimuth allow it (rows 16-byte aligned)
+  constexpr int VEC = (NTH % (16 / (int)sizeof(T)) == 0) ? 16 / (int)sizeof(T) : 1;
+  constexpr int LD = NL + (VEC > 1 ? VEC : 1);
   constexpr int NRED = NL < 32 ? NL : (NL + 31) / 32;
   const T k0 = T(0), k1 = T(1), k2 = T(2), k3 = T(3), k4 = T(4);
   const auto& op = A.op;
@@ -109,7 +112,33 @@ __global__ void __launch_bounds__(NTH* NPH, (sizeof(AR) == 4 && NTH * NPH <= 96)
   locate_site(A.grid, blockIdx.x, blockIdx.y, &L);
   const int x = L.x, y = L.y, site = idx_checked(L.site, A.grid.n_sites, A.err), nx = L.nx, ny = L.ny;
   const int t = threadIdx.x, j = t % NTH, l = t / NTH;
-  __shared__ T fs[NXI * LD];
+  __shared__ __align__(16) T fs[NXI * LD];
+  // (D fs)_k along the polar lines of this thread's azimuth: Dth row j (trans
+  // false) or column j (trans true)
+  auto polar = [&](bool trans, T (&out)[NXI]) {
+#pragma unroll
+    for (int k = 0; k < NXI; ++k) {
+      T a = k0;
+      const T* row = fs + k * LD + l * NTH;
+#pragma unroll
+      for (int jj = 0; jj < NTH; jj += VEC) {
+        T v[VEC];
+        if constexpr (VEC == 4) {
+          const float4 q = *reinterpret_cast<const float4*>(row + jj);
+          v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+        } else if constexpr (VEC == 2) {
+          const double2 q = *reinterpret_cast<const double2*>(row + jj);
+          v[0] = q.x; v[1] = q.y;
+        } else {
+          v[0] = row[jj];
+        }
+#pragma unroll
+        for (int h = 0; h < VEC; ++h)
+          a += (trans ? op.Dth[(jj + h) * NTH + j] : op.Dth[j * NTH + jj + h]) * v[h];
+      }
+      out[k] += a;
+    }
+  };
   __shared__ T red[16 * NRED];
 
   // forward recompute
@@ -157,12 +186,8 @@ __global__ void __launch_bounds__(NTH* NPH, (sizeof(AR) == 4 && NTH * NPH <= 96)
   __syncthreads();
   T pth[NXI];  // (Dth f) on the own line
 #pragma unroll
-  for (int k = 0; k < NXI; ++k) {
-    T a = k0;
-#pragma unroll
-    for (int jj = 0; jj < NTH; ++jj) a += op.Dth[j * NTH + jj] * fs[k * LD + l * NTH + jj];
-    pth[k] = a;
-  }
+  for (int k = 0; k < NXI; ++k) pth[k] = k0;
+  polar(false, pth);
   const T st = op.sth[j], mu2 = op.mu2[j], wj = op.wj[j];
   const T vu = st * (cp * ux + sp * uy), A1 = st * (ax * cp + ay * sp), au = ax * ux + ay * uy;
   const T nsx = -st * fabs(cp) * A.inv2dx, nsy = -st * fabs(sp) * A.inv2dx;
@@ -288,13 +313,7 @@ __global__ void __launch_bounds__(NTH* NPH, (sizeof(AR) == 4 && NTH * NPH <= 96)
 #pragma unroll
   for (int k = 0; k < NXI; ++k) fs[k * LD + t] = A.milne * rb[k];  // adjoint of (Dth f)
   __syncthreads();
-#pragma unroll
-  for (int k = 0; k < NXI; ++k) {
-    T a = k0;
-#pragma unroll
-    for (int jj = 0; jj < NTH; ++jj) a += op.Dth[jj * NTH + j] * fs[k * LD + l * NTH + jj];
-    fb[k] += a;
-  }
+  polar(true, fb);
   store_line<T, T, NXI>(A.rbar + (size_t)site * NN + t * NXI, rb);
   store_line<T, T, NXI>(A.fbar + (size_t)site * NN + t * NXI, fb);
   // site scalar adjoints
@@ -324,7 +343,7 @@ struct AdjMatchArgs {
   const double* sbar;
   double* mbar;
   double* lbar;
-  double* ebar;
+  double* ebar;        // per-site eta/s adjoint, accumulated over the stages
   int* err;
   EosView eos;
   GridMap grid;
@@ -425,7 +444,7 @@ __global__ void __launch_bounds__(128) adj_match(const AdjMatchArgs A) {
   // D = D(T), itr = (1/h)(T) / eta (d/dT = (1/T) d/dy)
   const double Tbar = -sb[AS_INVT] / (T * T) + sb[AS_MEQ] * (xv + dx) + sb[AS_D] * dD / T +
                       sb[AS_ITR] * dih / (T * eta);
-  A.ebar[site] = -sb[AS_ITR] * ih / (eta * eta);
+  A.ebar[site] += -sb[AS_ITR] * ih / (eta * eta);  // summed over the stages; over the sites at the end
   const double epsbar = Tbar * T / de;  // de/dT = de/dy / T
   // Landau: F_mu = T^{mu l} (g u)_l - eps u^mu = 0, F_3 = u.g.u - 1 = 0 in
   // z = (u, eps); lambda = J^{-T} zbar, Tbar^{ab} = -lambda_a (g u)_b

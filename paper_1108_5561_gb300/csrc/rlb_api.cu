@@ -976,8 +976,7 @@ struct Adjoint {
       // one warp per CTA: the FP64-bound per-site work spread over as many SMs as possible
       rlbk::adj_match<<<(unsigned)((ctx->ns + 31) / 32), 32, 0, st>>>(a);
       RLB_CUDA(cudaGetLastError(), "adj_match launch");
-      rlbk::sum_kernel<<<1, 1024, 0, st>>>(D(ctx, ctx->a_ebar), ctx->ns, D(ctx, ctx->a_eta), 1);
-      RLB_CUDA(cudaGetLastError(), "adjoint eta sum launch");
+
     }
     {
       rlbk::AdjAssembleArgs<AR, NXI, NTH, NPH> a;
@@ -1066,6 +1065,7 @@ struct Adjoint {
     rlbk::adj_seed_v2<S, AR, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
     RLB_CUDA(cudaGetLastError(), "adjoint seed launch");
     RLB_CUDA(cudaMemsetAsync(D(ctx, ctx->a_eta), 0, sizeof(double), st), "adjoint eta reset");
+    RLB_CUDA(cudaMemsetAsync(D(ctx, ctx->a_ebar), 0, ctx->ns * sizeof(double), st), "adjoint eta reset");
     RLB_CUDA(cudaMemcpyAsync(out, dev + 1, sizeof(double), cudaMemcpyDeviceToHost, st), "v2 download");
     RLB_CUDA(cudaStreamSynchronize(st), "adjoint seed synchronise");
     return RLB_OK;
@@ -1087,6 +1087,9 @@ struct Adjoint {
     a.op = make_ops<double, NXI, NTH, NPH>(ctx->lat);
     rlbk::adj_ic<S, AR, NXI, NTH, NPH><<<(unsigned)ctx->ns, NL, 0, st>>>(a);
     RLB_CUDA(cudaGetLastError(), "adj_ic launch");
+    // the eta/s adjoint: per-site sums over every stage, summed over the sites
+    rlbk::sum_kernel<<<1, 1024, 0, st>>>(D(ctx, ctx->a_ebar), ctx->ns, D(ctx, ctx->a_eta), 0);
+    RLB_CUDA(cudaGetLastError(), "adjoint eta sum launch");
     double* proj = D(ctx, ctx->a_ebar);  // n <= ns doubles (checked by the caller)
     if (n > 0) {
       rlbk::project_kernel<<<(unsigned)n, 1024, 0, st>>>(basis, D(ctx, ctx->a_eps), ctx->ns, proj);
@@ -1885,6 +1888,7 @@ rlb_status rlb_adjoint_seed(rlb_ctx* ctx, const double* fbar, const double* lbar
   RLB_CUDA(cudaMemcpyAsync(ctx->adj + ctx->a_l, lbar, ctx->ns * sizeof(double), cudaMemcpyDefault, st),
            "adjoint seed upload");
   RLB_CUDA(cudaMemsetAsync(ctx->adj + ctx->a_eta, 0, sizeof(double), st), "adjoint eta reset");
+  RLB_CUDA(cudaMemsetAsync(ctx->adj + ctx->a_ebar, 0, ctx->ns * sizeof(double), st), "adjoint eta reset");
   RLB_CUDA(cudaStreamSynchronize(st), "adjoint seed synchronise");
   return RLB_OK;
 }
