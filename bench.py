@@ -32,6 +32,9 @@ sys.path.insert(0, ROOT)
 
 NX = NY = 256
 ETA_S, TAU0, DTAU, DX = 0.16, 0.4, 0.0036, 0.1
+# the time steps of the other workloads, each over tau 0.4 -> 4 fm/c in its
+# stated number of steps: batch 200, adjoint 300, precision sweep 500
+DTAU_BATCH, DTAU_ADJ, DTAU_SWEEP = 3.6 / 200, 3.6 / 300, 3.6 / 500
 WORKLOAD = ("rlb-milne-2+1d 256x256 grid dx 0.1 fm, 768 nodes (8xi x 8theta x 12phi), FP32 "
             "populations, 40 hotspots on 10 GeV/fm^3")
 
@@ -237,7 +240,7 @@ def batch_main(args, rank, world, local):
     evs = batch_events(BATCH_EVENTS, seed=1108)
     events = [rlb.Event(n, n, eta) for n, eta in evs]
     eps = np.concatenate([hotspots(n, n, n=40, seed=1108 + i)[0].reshape(-1) for i, (n, _) in enumerate(evs)])
-    g = rlb.GridParams(dx=DX, prec=rlb.RLB_F32, tau0=TAU0, dtau=DTAU)
+    g = rlb.GridParams(dx=DX, prec=rlb.RLB_F32, tau0=TAU0, dtau=DTAU_BATCH)
     run = rlb.Run(g, device=local, events=events)
     run.init_grid(eps)
     run.step(1)
@@ -305,7 +308,7 @@ def batch_main(args, rank, world, local):
                                    "40 hotspots each, 768 nodes, FP32 populations, %d-step evolution"
                                    % (BATCH_EVENTS, BATCH_EVOLUTION_STEPS),
                        "events": BATCH_EVENTS, "sites": ns, "nodes_per_site": nn, "dx_fm": DX,
-                       "dtau": DTAU, "tau0": TAU0, "stage_variant": chosen, "variant_ms": tune_ms,
+                       "dtau": DTAU_BATCH, "tau0": TAU0, "stage_variant": chosen, "variant_ms": tune_ms,
                        "l2": "inputs larger than L2 (two %.1f GB population arrays)" % (ns * nn * b / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -340,7 +343,7 @@ def sweep_main(args, rank, world, local):
     peak, peak_kind = peaks()
     sampler = ClockSampler(None) if rank == 0 else None
     for name, prec, b in (("fp32", rlb.RLB_F32, 4), ("bf16", rlb.RLB_BF16, 2)):
-        g = rlb.GridParams(nx=side, ny=side, dx=DX, prec=prec, eta_over_s=ETA_S, tau0=TAU0, dtau=DTAU, **lat)
+        g = rlb.GridParams(nx=side, ny=side, dx=DX, prec=prec, eta_over_s=ETA_S, tau0=TAU0, dtau=DTAU_SWEEP, **lat)
         run = rlb.Run(g, device=local)
         run.init_grid(eps0)
         run.step(args.warmup)
@@ -375,10 +378,10 @@ def sweep_main(args, rank, world, local):
         win = eps0[c - sub // 2:c + sub // 2, c - sub // 2:c + sub // 2]
         o = Oracle(nx=sub, ny=sub, dx=DX, eta_over_s=ETA_S, **lat)
         f, lnM = o.init_state(win, os.cpu_count() or 1)
-        o.step(f, lnM, TAU0, DTAU, sub_steps, os.cpu_count() or 1)
+        o.step(f, lnM, TAU0, DTAU_SWEEP, sub_steps, os.cpu_count() or 1)
         mo = o.moments(f, lnM, os.cpu_count() or 1)
         for name, prec in (("fp32", rlb.RLB_F32), ("bf16", rlb.RLB_BF16)):
-            g = rlb.GridParams(nx=sub, ny=sub, dx=DX, prec=prec, eta_over_s=ETA_S, tau0=TAU0, dtau=DTAU, **lat)
+            g = rlb.GridParams(nx=sub, ny=sub, dx=DX, prec=prec, eta_over_s=ETA_S, tau0=TAU0, dtau=DTAU_SWEEP, **lat)
             r = rlb.Run(g, device=local)
             r.init_grid(win)
             r.step(sub_steps)
@@ -396,7 +399,7 @@ def sweep_main(args, rank, world, local):
             "data": "synthetic",
             "config": {"workload": "precision sweep: 1024x1024 grid, 16x8x16 = 2048 populations/site, "
                                    "40 hotspots, BF16 vs FP32 storage",
-                       "grid": [side, side], "nodes_per_site": 2048, "eta_over_s": ETA_S, "dtau": DTAU,
+                       "grid": [side, side], "nodes_per_site": 2048, "eta_over_s": ETA_S, "dtau": DTAU_SWEEP,
                        "tau0": TAU0, "l2": "inputs larger than L2 (4.3 GB BF16 / 8.6 GB FP32 per array)",
                        "parallelism": "single GPU"},
             "roofline": {"bound": "hbm", "achieved": kern["bf16"]["achieved_GBps"], "peak": peak, "unit": "GB/s",
@@ -429,7 +432,7 @@ def adjoint_main(args, rank, world, local):
     _, amps, cen = hotspots(side, side, n=40, seed=1108)
     basis_h = hotspot_basis(side, side, cen, dx=DX)
     floor = 10.0
-    g = rlb.GridParams(nx=side, ny=side, dx=DX, prec=rlb.RLB_F32, eta_over_s=etas, tau0=TAU0, dtau=DTAU)
+    g = rlb.GridParams(nx=side, ny=side, dx=DX, prec=rlb.RLB_F32, eta_over_s=etas, tau0=TAU0, dtau=DTAU_ADJ)
     run = rlb.Run(g, device=local)
     eps0 = torch.as_tensor(floor + amps @ basis_h, dtype=torch.float64, device="cuda")
     basis = torch.as_tensor(basis_h, dtype=torch.float64, device="cuda")
@@ -482,7 +485,7 @@ def adjoint_main(args, rank, world, local):
                                    "%d steps, checkpoint every %d, gradient of final p_perp-weighted v2 wrt "
                                    "40 amplitudes and eta/s (FP32 per-node adjoint arithmetic, FP64 matching "
                                    "adjoint)" % (steps, every),
-                       "grid": [side, side], "forward_s": t_fwd, "gradient_s": t_grad,
+                       "grid": [side, side], "dtau": DTAU_ADJ, "tau0": TAU0, "forward_s": t_fwd, "gradient_s": t_grad,
                        "gradient_fp64_s": t_grad64, "fp64_over_forward": t_grad64 / t_fwd,
                        "fp32_vs_fp64_rel": {
                            "amplitudes": float(np.linalg.norm(gA - gA64) / np.linalg.norm(gA64)),
@@ -705,7 +708,7 @@ def secondary(args, local, torch, rlb):
     evs = batch_events(BATCH_EVENTS, seed=1108)
     events = [rlb.Event(n, n, eta) for n, eta in evs]
     eps = np.concatenate([hotspots(n, n, n=40, seed=1108 + i)[0].reshape(-1) for i, (n, _) in enumerate(evs)])
-    gb = rlb.GridParams(dx=DX, prec=rlb.RLB_F32, tau0=TAU0, dtau=DTAU)
+    gb = rlb.GridParams(dx=DX, prec=rlb.RLB_F32, tau0=TAU0, dtau=DTAU_BATCH)
     run = rlb.Run(gb, device=local, events=events)
     run.init_grid(eps)
     run.step(1)
@@ -724,7 +727,7 @@ def secondary(args, local, torch, rlb):
     side, steps = 128, 300
     _, amps, cen = hotspots(side, side, n=40, seed=1108)
     basis_h = hotspot_basis(side, side, cen, dx=DX)
-    ga = rlb.GridParams(nx=side, ny=side, dx=DX, prec=rlb.RLB_F32, eta_over_s=0.08, tau0=TAU0, dtau=DTAU)
+    ga = rlb.GridParams(nx=side, ny=side, dx=DX, prec=rlb.RLB_F32, eta_over_s=0.08, tau0=TAU0, dtau=DTAU_ADJ)
     run = rlb.Run(ga, device=local)
     eps0 = torch.as_tensor(10.0 + amps @ basis_h, dtype=torch.float64, device="cuda")
     basis = torch.as_tensor(basis_h, dtype=torch.float64, device="cuda")
@@ -739,21 +742,22 @@ def secondary(args, local, torch, rlb):
     torch.cuda.synchronize()
     t_grad = time.perf_counter() - t0
     del run
-    g64 = rlb.GridParams(nx=side, ny=side, dx=DX, prec=rlb.RLB_F64, eta_over_s=0.08, tau0=TAU0, dtau=DTAU)
+    g64 = rlb.GridParams(nx=side, ny=side, dx=DX, prec=rlb.RLB_F64, eta_over_s=0.08, tau0=TAU0, dtau=DTAU_ADJ)
     run = rlb.Run(g64, device=local)
     run.init_grid(eps0)
     run.step(3)
     run.init_grid(eps0)
     t_fwd64 = timed(run, steps)
     del run
-    out["adjoint_128x128"] = {"gradient_s": t_grad, "forward_fp32_s": t_fwd, "over_forward_fp32": t_grad / t_fwd,
+    out["adjoint_128x128"] = {"dtau": DTAU_ADJ, "gradient_s": t_grad, "forward_fp32_s": t_fwd,
+                              "over_forward_fp32": t_grad / t_fwd,
                               "forward_fp64_s": t_fwd64, "over_forward_fp64": t_grad / t_fwd64,
                               "steps": steps, "checkpoint_every": 32}
     # precision sweep: 1024x1024, 16x8x16 lattice
     sweep = {}
     eps0 = hotspots(1024, 1024, n=40, seed=1108)[0]
     for name, prec, b in (("fp32", rlb.RLB_F32, 4), ("bf16", rlb.RLB_BF16, 2)):
-        gs = rlb.GridParams(nx=1024, ny=1024, dx=DX, prec=prec, eta_over_s=ETA_S, tau0=TAU0, dtau=DTAU,
+        gs = rlb.GridParams(nx=1024, ny=1024, dx=DX, prec=prec, eta_over_s=ETA_S, tau0=TAU0, dtau=DTAU_SWEEP,
                             n_xi=16, n_theta=8, n_phi_half=8)
         run = rlb.Run(gs, device=local)
         run.init_grid(eps0)
@@ -778,7 +782,8 @@ def finish(args, rank, world, t, value, achieved, peak, peak_kind, b, nn, launch
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": [NX, NY], "dx_fm": DX, "nodes_per_site": nn,
+            "config": {"workload": WORKLOAD.replace("256x256", "%dx%d" % (NX, NY)), "grid": [NX, NY], "dx_fm": DX,
+                       "nodes_per_site": nn,
                        "eta_over_s": ETA_S, "dtau": DTAU, "tau0": TAU0,
                        "l2": "inputs larger than L2 (two 201 MB population arrays)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
