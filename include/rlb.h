@@ -256,7 +256,8 @@ rlb_status rlb_load_state_async(rlb_ctx* ctx, const void* dev_buf, size_t bytes,
  * and keeps the fastest for later steps.  The state (f, ln M, tau) is
  * unchanged.  Outputs: the chosen variant, optionally the milliseconds per
  * launch of each variant (variant_ms holds at least RLB_MAX_STAGE_VARIANTS
- * doubles) and their number.  Synchronises
+ * doubles; -1 for a variant that would run another variant's kernel on this
+ * configuration, which is never chosen) and their number.  Synchronises
  * `stream`.  Implementation choices, not part of the paper's scheme. */
 #define RLB_MAX_STAGE_VARIANTS 8
 rlb_status rlb_autotune(rlb_ctx* ctx, void* stream, int* chosen, double* variant_ms, int* n_variants);

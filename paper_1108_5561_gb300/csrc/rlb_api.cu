@@ -553,6 +553,8 @@ struct Stager {
   rlbk::StageArgsMP<S, NXI, NTH, NPH> c;
   rlbk::StageArgsMPT<S, NXI, NTH, NPH> d;
   bool mpt_ok = false;  // variant 6 applies to this grid
+  // variant v launches another variant's kernel on this configuration
+  bool runs_elsewhere(int v) const { return kMPT && v == 6 && !mpt_ok; }
   int mpt_prefetch = 0;
   dim3 grid, grid2;
   int variant = 0;
@@ -841,6 +843,10 @@ struct Runner {
       Stager<S, R, NXI, NTH, NPH> sg(ctx, ctx->scratch, reinterpret_cast<const double*>(ctx->scratch + ctx->sc_off),
                                      reinterpret_cast<const float*>(ctx->scratch + ctx->scf_off),
                                      reinterpret_cast<int*>(ctx->scratch + ctx->err_off));
+      if (sg.runs_elsewhere(v)) {  // not a kernel of its own here: never chosen
+        if (ms) ms[v] = -1.0;
+        continue;
+      }
       sg.launch(f, m, f, m, fs, ms_, moms, 0, st);  // warm-up
       cudaEventRecord(e0, st);
       for (int k = 0; k < 3; ++k) sg.launch(f, m, f, m, fs, ms_, moms, 0, st);
