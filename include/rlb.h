@@ -300,13 +300,22 @@ rlb_status rlb_set_graphs(rlb_ctx* ctx, int enable);
  *       that step's input.  Replaces them by the adjoints of the step's input
  *       and adds the step's contribution to d v2/d(eta/s).  The step's
  *       predictor output is recomputed with the forward kernels, bit for bit as
- *       in the forward run; the matchings are recomputed in FP64.
+ *       in the forward run; the matchings are recomputed in FP64 for the FP64
+ *       adjoint arithmetic, and taken as the forward step makes them (FP32
+ *       moment partials, the same Newton starts) by the FP32 adjoint of the
+ *       FP32/BF16 storage paths.
  *   rlb_adjoint_ic
  *       After the last rlb_adjoint_step (the adjoint buffers hold the adjoints
  *       of the initial state rlb_init_grid made from eps0, device FP64,
  *       GeV/fm^3): grad[i] = sum_x basis[i][x] d v2/d eps0(x) for the n_basis
  *       rows of `basis` (device FP64, n_basis x sites, n_basis <= sites), then
  *       grad[n_basis] = d v2/d(eta/s).  `grad` is host memory; synchronises.
+ *   rlb_adjoint_step_from
+ *       The same reversed step with its input state read in place from a
+ *       device blob that rlb_save_state of this context wrote (`bytes` its
+ *       size, `tau` the rlb_get_tau value it was saved at; the header is not
+ *       read back): no copy into the context.  The context's state and tau
+ *       are unchanged; its Newton starting temperatures become the blob's.
  * Checkpointing (which states to keep and recompute) is the caller's choice;
  * the Python module adjoint.py keeps one every k steps. */
 rlb_status rlb_adjoint_set_arithmetic(rlb_ctx* ctx, int prec);
@@ -315,6 +324,7 @@ rlb_status rlb_adjoint_bind(rlb_ctx* ctx, void* workspace);
 rlb_status rlb_adjoint_seed_v2(rlb_ctx* ctx, double* v2, void* stream);
 rlb_status rlb_adjoint_seed(rlb_ctx* ctx, const double* fbar, const double* lbar, void* stream);
 rlb_status rlb_adjoint_step(rlb_ctx* ctx, void* stream);
+rlb_status rlb_adjoint_step_from(rlb_ctx* ctx, const void* state_blob, size_t bytes, double tau, void* stream);
 rlb_status rlb_adjoint_ic(rlb_ctx* ctx, const double* eps0, const double* basis, int n_basis, double* grad,
                           void* stream);
 

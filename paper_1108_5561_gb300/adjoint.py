@@ -8,8 +8,9 @@ checkpoints and wraps the result as a torch.autograd.Function.
 
 Checkpointing: the forward run stores the state every `every` steps; the
 backward sweep reruns each segment from its checkpoint, storing the state of
-every step of the segment, and reverses the steps one by one.  State blobs hold
-the moments and Newton starting values too, so recomputed steps are bit-exact
+every step of the segment (device blobs), and reverses the steps one by one,
+each reading its input state from its blob in place.  State blobs hold the
+moments and Newton starting values too, so recomputed steps are bit-exact
 copies of the forward ones.
 """
 from __future__ import annotations
@@ -53,8 +54,18 @@ class Adjoint:
                                                 ctypes.c_void_p(lb.data_ptr()), self.run._stream()),
                       "rlb_adjoint_seed")
 
-    def step(self):
-        """Reverse one step; the run's state must be that step's input."""
+    def step(self, blob=None):
+        """Reverse one step.  Its input state: the run's state, or a device blob
+        from run.save_state(device=True) of this run, read in place (the run's
+        state is left as it is)."""
+        saved = getattr(blob, "_rlb_saved", None) if blob is not None else None
+        if saved is not None and saved[0] == self.run._h.value and blob.is_cuda:
+            self.run._chk(self.lib.rlb_adjoint_step_from(self.run._h, ctypes.c_void_p(blob.data_ptr()), blob.numel(),
+                                                         ctypes.c_double(saved[1]), self.run._stream()),
+                          "rlb_adjoint_step_from")
+            return
+        if blob is not None:
+            self.run.load_state(blob)
         self.run._chk(self.lib.rlb_adjoint_step(self.run._h, self.run._stream()), "rlb_adjoint_step")
 
     def ic(self, eps0, basis):
@@ -92,8 +103,7 @@ def reverse_sweep(run, adj: Adjoint, cks, steps: int, every: int):
             run.step(1)
             states.append(run.save_state(device=True))
         for s in reversed(range(start, end)):
-            run.load_state(states[s - start])
-            adj.step()
+            adj.step(states[s - start])  # the step's input state read in place
 
 
 def v2_gradient(run, eps0, basis, steps: int, every: int = 32, arithmetic: int = L.RLB_F64):

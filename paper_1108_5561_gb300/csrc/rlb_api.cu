@@ -1000,17 +1000,23 @@ struct Adjoint {
 
   // the adjoint buffers hold the adjoints of a step's output; the context state
   // is that step's input (at ctx->tau): replace them by the adjoints of the input
-  static rlb_status step(rlb_ctx* ctx, cudaStream_t st) {
+  // the step's input state: the context's (null pointers) or a device blob's
+  struct Input {
+    const S* f = nullptr;
+    const double* lnM = nullptr;
+    const double* mom = nullptr;
+  };
+  static rlb_status step(rlb_ctx* ctx, cudaStream_t st, Input in = Input()) {
     ctx->scf_fresh = false;
-    return ctx->adj_prec == RLB_F32 ? step_t<float>(ctx, st) : step_t<double>(ctx, st);
+    return ctx->adj_prec == RLB_F32 ? step_t<float>(ctx, st, in) : step_t<double>(ctx, st, in);
   }
   template <class AR>
-  static rlb_status step_t(rlb_ctx* ctx, cudaStream_t st) {
-    S* f = reinterpret_cast<S*>(ctx->state + ctx->f_off);
+  static rlb_status step_t(rlb_ctx* ctx, cudaStream_t st, Input in) {
+    const S* f = in.f ? in.f : reinterpret_cast<S*>(ctx->state + ctx->f_off);
     S* fs = reinterpret_cast<S*>(ctx->scratch + ctx->fs_off);
-    double* m = reinterpret_cast<double*>(ctx->state + ctx->lnM_off);
+    const double* m = in.lnM ? in.lnM : reinterpret_cast<double*>(ctx->state + ctx->lnM_off);
     double* ms = reinterpret_cast<double*>(ctx->scratch + ctx->lnMs_off);
-    double* mom = reinterpret_cast<double*>(ctx->scratch + ctx->mom_off);
+    const double* mom = in.mom ? in.mom : reinterpret_cast<double*>(ctx->scratch + ctx->mom_off);
     double* moms = reinterpret_cast<double*>(ctx->scratch + ctx->moms_off);
     // the predictor output f*, ln M* exactly as the forward run made it
     rlb_status r = match(ctx, mom, m, nullptr, st);
@@ -1125,7 +1131,17 @@ rlb_status run_op(rlb_ctx* c, Op op, int n, double* p, cudaStream_t st) {
   if (op == OP_INIT) return Rn::init(c, p, st);
   if (op == OP_STEP) return Rn::step(c, n, st);
   if (op == OP_ADJ_SEED) return Adjoint<S, R, NXI, NTH, NPH>::seed(c, p, st);
-  if (op == OP_ADJ_STEP) return Adjoint<S, R, NXI, NTH, NPH>::step(c, st);
+  if (op == OP_ADJ_STEP) {
+    typename Adjoint<S, R, NXI, NTH, NPH>::Input in;
+    if (p) {  // a device state blob: f, ln M and the moments read in place
+      const char* const* b = reinterpret_cast<const char* const*>(p);
+      const uint64_t* o = reinterpret_cast<const uint64_t*>(b + 1);
+      in.f = reinterpret_cast<const S*>(b[0] + o[0]);
+      in.lnM = reinterpret_cast<const double*>(b[0] + o[1]);
+      in.mom = reinterpret_cast<const double*>(b[0] + o[3]);
+    }
+    return Adjoint<S, R, NXI, NTH, NPH>::step(c, st, in);
+  }
   if (op == OP_ADJ_IC) {
     const AdjIcCall* a = reinterpret_cast<const AdjIcCall*>(p);
     return Adjoint<S, R, NXI, NTH, NPH>::ic(c, a->eps0, a->basis, a->n, a->out, st);
@@ -1684,6 +1700,10 @@ rlb_status rlb_observables(rlb_ctx* ctx, double* eps_p, double* v2_pt, void* str
 // ---------------------------------------------------------------------------
 namespace {
 
+// Blob layout (version 2): the header in the first 256 bytes, then f, ln M,
+// T and the moments, each starting at a multiple of 256 bytes (the kernels can
+// read a device blob in place).
+constexpr uint64_t kBlobHead = 256;
 struct BlobHeader {
   char magic[8];  // "RLBSTAT1"
   uint32_t version;
@@ -1696,7 +1716,7 @@ struct BlobHeader {
 void blob_parts(const rlb_ctx* c, BlobHeader* h) {
   std::memset(h, 0, sizeof(*h));
   std::memcpy(h->magic, "RLBSTAT1", 8);
-  h->version = 1;
+  h->version = 2;
   h->prec = c->gp.prec; h->nx = c->gp.nx; h->ny = c->gp.ny;
   h->n_xi = c->gp.n_xi; h->n_theta = c->gp.n_theta; h->n_phi_half = c->gp.n_phi_half;
   h->family = c->gp.family; h->metric = c->gp.metric;
@@ -1708,8 +1728,21 @@ void blob_parts(const rlb_ctx* c, BlobHeader* h) {
   h->mom_bytes = (uint64_t)c->ns * std::max(rlbk::kMom * sizeof(double), rlbk::kMom * rlbk::kMomParts * sizeof(float));
 }
 
+static_assert(sizeof(BlobHeader) <= kBlobHead, "blob header");
+// byte offsets of f, ln M, T, moments in a blob, and its size
+void blob_offsets(const BlobHeader& h, uint64_t (&o)[4], uint64_t* size) {
+  const uint64_t n[4] = {h.f_bytes, h.lnM_bytes, h.T_bytes, h.mom_bytes};
+  uint64_t off = kBlobHead;
+  for (int i = 0; i < 4; ++i) {
+    o[i] = off;
+    off += align256(n[i]);
+  }
+  if (size) *size = off;
+}
 size_t blob_size(const BlobHeader& h) {
-  return sizeof(BlobHeader) + h.f_bytes + h.lnM_bytes + h.T_bytes + h.mom_bytes;
+  uint64_t o[4], n = 0;
+  blob_offsets(h, o, &n);
+  return (size_t)n;
 }
 
 }  // namespace
@@ -1757,14 +1790,13 @@ rlb_status rlb_save_state(rlb_ctx* ctx, void* host_buf, size_t bytes, void* stre
     RLB_CUDA(cudaMemcpyAsync(p, &h, sizeof h, cudaMemcpyDefault, st), "state header");
     RLB_CUDA(cudaStreamSynchronize(st), "state header synchronise");  // h lives on this stack
   }
-  p += sizeof h;
+  uint64_t o[4];
+  blob_offsets(h, o, nullptr);
   const struct { const char* src; uint64_t n; } parts[4] = {
       {ctx->state + ctx->f_off, h.f_bytes}, {ctx->state + ctx->lnM_off, h.lnM_bytes},
       {ctx->scratch + ctx->T_off, h.T_bytes}, {ctx->scratch + ctx->mom_off, h.mom_bytes}};
-  for (const auto& q : parts) {
-    RLB_CUDA(cudaMemcpyAsync(p, q.src, q.n, cudaMemcpyDefault, st), "state copy");
-    p += q.n;
-  }
+  for (int i = 0; i < 4; ++i)
+    RLB_CUDA(cudaMemcpyAsync(p + o[i], parts[i].src, parts[i].n, cudaMemcpyDefault, st), "state copy");
   if (!dev) RLB_CUDA(cudaStreamSynchronize(st), "state download synchronise");
   return RLB_OK;
 }
@@ -1780,14 +1812,14 @@ rlb_status rlb_load_state_async(rlb_ctx* ctx, const void* dev_buf, size_t bytes,
   if (s) return s;
   ctx->scf_fresh = false;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const char* p = static_cast<const char*>(dev_buf) + sizeof want;
+  const char* p = static_cast<const char*>(dev_buf);
+  uint64_t o[4];
+  blob_offsets(want, o, nullptr);
   const struct { char* dst; uint64_t n; } parts[4] = {
       {ctx->state + ctx->f_off, want.f_bytes}, {ctx->state + ctx->lnM_off, want.lnM_bytes},
       {ctx->scratch + ctx->T_off, want.T_bytes}, {ctx->scratch + ctx->mom_off, want.mom_bytes}};
-  for (const auto& q : parts) {
-    RLB_CUDA(cudaMemcpyAsync(q.dst, p, q.n, cudaMemcpyDeviceToDevice, st), "state copy");
-    p += q.n;
-  }
+  for (int i = 0; i < 4; ++i)
+    RLB_CUDA(cudaMemcpyAsync(parts[i].dst, p + o[i], parts[i].n, cudaMemcpyDeviceToDevice, st), "state copy");
   ctx->tau = tau;
   s = set_clock(ctx, ctx->scratch, ctx->tau, st);
   if (s) return s;
@@ -1814,14 +1846,14 @@ rlb_status rlb_load_state(rlb_ctx* ctx, const void* host_buf, size_t bytes, void
   rlb_status s = set_device(ctx);
   if (s) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const char* p = static_cast<const char*>(host_buf) + sizeof got;
+  const char* p = static_cast<const char*>(host_buf);
+  uint64_t o[4];
+  blob_offsets(got, o, nullptr);
   const struct { char* dst; uint64_t n; } parts[4] = {
       {ctx->state + ctx->f_off, got.f_bytes}, {ctx->state + ctx->lnM_off, got.lnM_bytes},
       {ctx->scratch + ctx->T_off, got.T_bytes}, {ctx->scratch + ctx->mom_off, got.mom_bytes}};
-  for (const auto& q : parts) {
-    RLB_CUDA(cudaMemcpyAsync(q.dst, p, q.n, cudaMemcpyDefault, st), "state copy");
-    p += q.n;
-  }
+  for (int i = 0; i < 4; ++i)
+    RLB_CUDA(cudaMemcpyAsync(parts[i].dst, p + o[i], parts[i].n, cudaMemcpyDefault, st), "state copy");
   ctx->tau = got.tau;
   s = set_clock(ctx, ctx->scratch, ctx->tau, st);
   if (s) return s;
@@ -1915,6 +1947,37 @@ rlb_status rlb_adjoint_step(rlb_ctx* ctx, void* stream) {
   rlb_status s = set_device(ctx);
   if (s) return s;
   return dispatch(ctx, OP_ADJ_STEP, 0, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+rlb_status rlb_adjoint_step_from(rlb_ctx* ctx, const void* state_blob, size_t bytes, double tau, void* stream) {
+  if (!ctx || !state_blob) return RLB_ERR_ARG;
+  if (!ctx->inited || !ctx->adj) return fail(ctx, RLB_ERR_STATE, "state and adjoint workspace needed");
+  BlobHeader h;
+  blob_parts(ctx, &h);
+  uint64_t o[4];
+  blob_offsets(h, o, nullptr);
+  if (bytes < blob_size(h)) return fail(ctx, RLB_ERR_ARG, "state blob is truncated");
+  if (!is_device_pointer(state_blob)) return fail(ctx, RLB_ERR_ARG, "rlb_adjoint_step_from takes device blobs");
+  rlb_status s = set_device(ctx);
+  if (s) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const char* b = static_cast<const char*>(state_blob);
+  // the blob's Newton starts and time; the context's own tau comes back after
+  RLB_CUDA(cudaMemcpyAsync(ctx->scratch + ctx->T_off, b + o[2], h.T_bytes, cudaMemcpyDeviceToDevice, st),
+           "adjoint Newton start copy");
+  const double keep = ctx->tau;
+  ctx->tau = tau;
+  s = set_clock(ctx, ctx->scratch, tau, st);
+  if (!s) {
+    struct {
+      const char* blob;
+      uint64_t o[4];
+    } call{b, {o[0], o[1], o[2], o[3]}};
+    s = dispatch(ctx, OP_ADJ_STEP, 0, reinterpret_cast<double*>(&call), st);
+  }
+  ctx->tau = keep;
+  rlb_status s2 = set_clock(ctx, ctx->scratch, keep, st);
+  return s ? s : s2;
 }
 
 rlb_status rlb_adjoint_ic(rlb_ctx* ctx, const double* eps0, const double* basis, int n_basis, double* grad,

@@ -245,3 +245,27 @@ def test_autograd_function():
     # there: rounding-level differences of eps0)
     assert rel.max() < 1e-8
     assert eta.grad.item() == pytest.approx(geta, rel=1e-8)
+
+
+@pytest.mark.parametrize("prec,arith,tol", [(rlb.RLB_F64, rlb.RLB_F64, 1e-10), (rlb.RLB_F32, rlb.RLB_F32, 1e-5)])
+def test_step_from_a_blob_equals_load_then_step(prec, arith, tol):
+    amps, basis_h = _case()
+    run = rlb.Run(_grid(prec))
+    eps0 = torch.as_tensor(FLOOR + amps @ basis_h, dtype=torch.float64, device="cuda")
+    basis = torch.as_tensor(basis_h, dtype=torch.float64, device="cuda")
+    run.init_grid(eps0)
+    blob0 = run.save_state(device=True)
+    run.step(1)
+    f1, l1, tau1 = run.populations().clone(), run.lnM().clone(), run.tau
+    adj = ADJ.Adjoint(run, arith)
+    adj.seed_v2()
+    adj.step(blob0)  # input read in place from the blob; the run's state stays the final one
+    g_blob = adj.ic(eps0, basis)
+    assert torch.equal(run.populations(), f1) and torch.equal(run.lnM(), l1) and run.tau == tau1
+    adj.seed_v2()
+    run.load_state(blob0)
+    adj.step()
+    g_load = adj.ic(eps0, basis)
+    scale = max(np.abs(g_load[0]).max(), 1e-300)
+    assert np.abs(g_blob[0] - g_load[0]).max() / scale < tol
+    assert abs(g_blob[1] - g_load[1]) <= tol * max(abs(g_load[1]), 1e-300)
