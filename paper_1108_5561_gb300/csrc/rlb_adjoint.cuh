@@ -198,13 +198,16 @@ __global__ void __launch_bounds__(NTH* NPH, (sizeof(AR) == 4 && NTH * NPH <= 96)
 #pragma unroll
   for (int k = 0; k < NXI; ++k) {
     const T s = op.s[k], c = op.c[k], tv = op.tv[k];
-    E[k] = sqrt(Meq * Meq + M2 * op.s2[k]);
-    // FP32 adjoint: the hardware reciprocal and exponential (a few ulp; the
-    // linearisation point needs no more), FP64: the correctly rounded ones
+    // FP32 adjoint: the hardware reciprocal square root and exponential (a
+    // few ulp; the linearisation point needs no more), FP64: the correctly
+    // rounded functions
     if constexpr (std::is_same<T, float>::value) {
-      iE[k] = __frcp_rn(E[k]);
+      const float e2 = Meq * Meq + M2 * op.s2[k];
+      iE[k] = rsqrtf(e2);
+      E[k] = e2 * iE[k];
       feq[k] = A.Z * __expf(-invT * (ut * E[k] - M * vu * s));
     } else {
+      E[k] = sqrt(Meq * Meq + M2 * op.s2[k]);
       iE[k] = k1 / E[k];
       feq[k] = A.Z * exp(-invT * (ut * E[k] - M * vu * s));
     }
