@@ -194,7 +194,7 @@ rlb_status rlb_step(rlb_ctx* ctx, int nsteps, void* stream);
  *     array, and a synchronisation); make these first calls before any stream
  *     capture begins.
  *   - Grids whose scratch would exceed 24 MiB are rejected with RLB_ERR_ARG
- *     (about 5,000 sites with FP32 populations on the 8x8x12 lattice, 2,500 with
+ *     (about 4,700 sites with FP32 populations on the 8x8x12 lattice, 2,500 with
  *     FP64).
  *   - Every call in the process shares the array, which keeps whatever the last
  *     call left in it: each call re-uploads the EOS tables, clears the error
