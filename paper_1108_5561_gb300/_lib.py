@@ -20,7 +20,8 @@ EXPORTS = ["rlb_create", "rlb_destroy", "rlb_last_error", "rlb_init_eos", "rlb_w
            "rlb_state_blob_size", "rlb_save_state", "rlb_load_state", "rlb_configure_batch",
            "rlb_init_batch", "rlb_autotune", "rlb_set_stage_variant", "rlb_set_graphs", "rlb_adjoint_set_arithmetic", "rlb_adjoint_workspace_size",
            "rlb_adjoint_bind", "rlb_adjoint_seed_v2", "rlb_adjoint_seed", "rlb_adjoint_step", "rlb_adjoint_ic", "rlb_alu_peaks",
-           "rlb_wait_selftest", "rlb_load_state_async", "rlb_adjoint_step_from"]
+           "rlb_wait_selftest", "rlb_load_state_async", "rlb_adjoint_step_from", "rlb_moments_async",
+           "rlb_moments_wait"]
 
 
 class EosParamsC(ctypes.Structure):
@@ -92,6 +93,8 @@ def load(build_if_missing: bool = True):
     lib.rlb_set_timing.argtypes = [vp, ctypes.c_int]
     lib.rlb_alu_peaks.argtypes = [ctypes.c_int, dp]
     lib.rlb_load_state_async.argtypes = [vp, vp, sz, ctypes.c_double, vp]
+    lib.rlb_moments_async.argtypes = [vp, vp, vp]
+    lib.rlb_moments_wait.argtypes = [vp]
     lib.rlb_adjoint_step_from.argtypes = [vp, vp, sz, ctypes.c_double, vp]
     lib.rlb_wait_selftest.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, P(ctypes.c_int),
                                       P(ctypes.c_float)]

@@ -33,6 +33,13 @@ struct rlb_ctx {
   size_t fs_off = 0, lnMs_off = 0, T_off = 0, err_off = 0, tab_off = 0, eps_off = 0;  // scratch
   size_t mom_off = 0, moms_off = 0, sc_off = 0, tabf_off = 0, scf_off = 0;
   size_t ev_off = 0, loc_off = 0, clock_off = 0, lines_off = 0;
+  // rlb_moments_async: two device staging slots of ns x 8 doubles (allocated
+  // at the first call), a copy stream, per slot the events "observables ready"
+  // and "copy done", the next slot
+  char* mstage = nullptr;
+  cudaStream_t cstream = nullptr;
+  cudaEvent_t cev_ready[2] = {nullptr, nullptr}, cev_done[2] = {nullptr, nullptr};
+  int cslot = 0;
   // line constants of the mirror-paired stage kernel (rlbk::LinesMP)
   std::vector<unsigned char> lines_mp;
   // events: one for a single grid, n for a batch (with a per-site locator)
@@ -1337,6 +1344,12 @@ void rlb_destroy(rlb_ctx* ctx) {
   if (!ctx) return;
   drop_graphs(ctx);
   if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
+  if (ctx->cstream) cudaStreamDestroy(ctx->cstream);
+  if (ctx->mstage) cudaFree(ctx->mstage);
+  for (int i = 0; i < 2; ++i) {
+    if (ctx->cev_ready[i]) cudaEventDestroy(ctx->cev_ready[i]);
+    if (ctx->cev_done[i]) cudaEventDestroy(ctx->cev_done[i]);
+  }
   for (cudaEvent_t e : ctx->gev)
     if (e) cudaEventDestroy(e);
   for (auto& p : ctx->ev_pending) { ctx->ev_pool.push_back(p.second.first); ctx->ev_pool.push_back(p.second.second); }
@@ -1675,6 +1688,55 @@ rlb_status rlb_moments(rlb_ctx* ctx, double* out, int out_on_device, void* strea
   RLB_CUDA(cudaMemcpyAsync(out, dev, ctx->ns * 8 * sizeof(double), cudaMemcpyDeviceToHost, st),
            "moments download");
   return rlb_check(ctx, stream);
+}
+
+rlb_status rlb_moments_async(rlb_ctx* ctx, double* host_out, void* stream) {
+  if (!ctx || !host_out) return RLB_ERR_ARG;
+  if (!ctx->inited) return fail(ctx, RLB_ERR_STATE, "rlb_init_grid must come first");
+  cudaPointerAttributes pa;
+  if (cudaPointerGetAttributes(&pa, host_out) != cudaSuccess || pa.type != cudaMemoryTypeHost) {
+    cudaGetLastError();
+    return fail(ctx, RLB_ERR_ARG, "rlb_moments_async writes page-locked host memory");
+  }
+  rlb_status s = set_device(ctx);
+  if (s) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t slot_b = align256(ctx->ns * 8 * sizeof(double));
+  if (!ctx->cstream) {
+    RLB_CUDA(cudaMalloc(&ctx->mstage, 2 * slot_b), "moments staging slots");
+    RLB_CUDA(cudaStreamCreateWithFlags(&ctx->cstream, cudaStreamNonBlocking), "copy stream");
+    for (int i = 0; i < 2; ++i) {
+      RLB_CUDA(cudaEventCreateWithFlags(&ctx->cev_ready[i], cudaEventDisableTiming), "copy event");
+      RLB_CUDA(cudaEventCreateWithFlags(&ctx->cev_done[i], cudaEventDisableTiming), "copy event");
+      RLB_CUDA(cudaEventRecord(ctx->cev_done[i], ctx->cstream), "copy event");
+    }
+  }
+  const int k = ctx->cslot;
+  ctx->cslot ^= 1;
+  double* dev = reinterpret_cast<double*>(ctx->mstage + (size_t)k * slot_b);
+  // the slot's previous copy has left it; the matching of the current state
+  // writes the observables there (the next step reuses that matching)
+  RLB_CUDA(cudaStreamWaitEvent(st, ctx->cev_done[k], 0), "copy order");
+  const double* mom = reinterpret_cast<const double*>(ctx->scratch + ctx->mom_off);
+  const double* lnM = reinterpret_cast<const double*>(ctx->state + ctx->lnM_off);
+  s = match(ctx, mom, lnM, dev, st);
+  if (s) return s;
+  ctx->scf_fresh = true;
+  RLB_CUDA(cudaEventRecord(ctx->cev_ready[k], st), "copy order");
+  RLB_CUDA(cudaStreamWaitEvent(ctx->cstream, ctx->cev_ready[k], 0), "copy order");
+  RLB_CUDA(cudaMemcpyAsync(host_out, dev, ctx->ns * 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->cstream),
+           "moments download");
+  RLB_CUDA(cudaEventRecord(ctx->cev_done[k], ctx->cstream), "copy order");
+  return RLB_OK;
+}
+
+rlb_status rlb_moments_wait(rlb_ctx* ctx) {
+  if (!ctx) return RLB_ERR_ARG;
+  if (!ctx->cstream) return RLB_OK;
+  rlb_status s = set_device(ctx);
+  if (s) return s;
+  RLB_CUDA(cudaStreamSynchronize(ctx->cstream), "copy synchronise");
+  return rlb_check(ctx, ctx->cstream);
 }
 
 rlb_status rlb_observables(rlb_ctx* ctx, double* eps_p, double* v2_pt, void* stream) {

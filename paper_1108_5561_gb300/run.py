@@ -200,6 +200,19 @@ class Run:
     def check(self):
         self._chk(self.lib.rlb_check(self._h, self._stream()), "rlb_check")
 
+    def moments_async(self, out):
+        """Per-site observables into `out`, a page-locked host float64 tensor
+        (sites x 8), downloaded while the next steps run (rlb_moments_async);
+        read it after moments_wait()."""
+        torch = self.torch
+        assert isinstance(out, torch.Tensor) and out.dtype == torch.float64 and out.is_pinned()
+        assert out.numel() == self.ns * 8 and out.is_contiguous()
+        self._chk(self.lib.rlb_moments_async(self._h, ctypes.c_void_p(out.data_ptr()), self._stream()),
+                  "rlb_moments_async")
+
+    def moments_wait(self):
+        self._chk(self.lib.rlb_moments_wait(self._h), "rlb_moments_wait")
+
     def moments(self, out=None, host: bool = True):
         """Per-site (eps, T, u^tau, u^x, u^y, M, P_L, M(T)); numpy (host) or a device tensor."""
         torch = self.torch
