@@ -360,8 +360,12 @@ __device__ __forceinline__ bool eos_cellf(const EosView& E, float y, int* i0, fl
 
 // Table inversion in FP32 (FP32 storage path): Newton on the interpolant of the
 // FP32 table, safeguarded by a bisection bracket; same failure rules as
-// eos_invert.  The result carries FP32 precision, which is what the FP32
-// kernels consume.
+// eos_invert.  It stops once a step is below kEosStopF in y = ln T: the error
+// left is about C dy^2 with C = e''/(2 e') (2 for e ~ T^4; at most 7.9 for the
+// crossover EOS, at T = 0.145 GeV), at most 2e-6, which the one Newton step
+// of eos_refine_df that follows takes to C (2e-6)^2 ~ 3e-11; stopping at 2e-6
+// instead cost one more table iteration per site.
+constexpr float kEosStopF = 5e-4f;
 __device__ bool eos_invert_f(const EosView& E, int field, float target, float y, float* y_out) {
   const float ih = E.ih_hi + E.ih_lo;
   float lo = E.ylo_f, hi = E.yhi_f;
@@ -389,7 +393,7 @@ __device__ bool eos_invert_f(const EosView& E, int field, float target, float y,
     if (!(yn >= lo && yn <= hi)) yn = 0.5f * (lo + hi);
     const float dy = yn - yf;
     yf = yn;
-    if (fabsf(dy) < 2e-6f || hi - lo < 4e-6f) { ok = true; break; }
+    if (fabsf(dy) < kEosStopF || hi - lo < 4e-6f) { ok = true; break; }
   }
   if (!ok || yf - ymin < 1e-5f || ymax - yf < 1e-5f) return false;
   *y_out = yf;
@@ -532,7 +536,26 @@ __device__ bool landau3_df(const f2x tmd[6], const float tm[6], float u[3], f2x*
   const float c2 = a00 + a11 + a22;
   const float c1 = a00 * a11 - a01 * a10 + a00 * a22 - a02 * a20 + a11 * a22 - a12 * a21;
   const float c0 = a00 * (a11 * a22 - a12 * a21) - a01 * (a10 * a22 - a12 * a20) + a02 * (a10 * a21 - a11 * a20);
-  float lam = 1.f;  // the infinity norm bounds every eigenvalue
+  // Newton start: an upper bound on the largest root.  The infinity norm (1
+  // here) bounds every eigenvalue; closer, where T^{mu nu} satisfies the
+  // energy conditions eps is the minimum of u_mu u_nu T^{mu nu} over timelike
+  // unit u, so the energy in the frame moving with beta = T^{0i} / T^{00}
+  // bounds it from above, with an excess second order in the difference of
+  // the two velocities (a few Newton steps instead of up to a dozen for a
+  // fast-moving cell).  It is taken only where the cubic places it above its
+  // largest root (p >= 0, p' > 0, p'' > 0), raised by 1e-6 against rounding.
+  float lam = 1.f;
+  {
+    const float t0 = tm[0] * is, t1 = tm[1] * is, t2 = tm[2] * is;
+    const float b1 = t1 / t0, b2 = t2 / t0, bb = b1 * b1 + b2 * b2;
+    if (t0 > 0.f && bb < 1.f) {
+      const float e = (t0 - 2.f * (b1 * t1 + b2 * t2) + is * (b1 * b1 * tm[3] + 2.f * b1 * b2 * tm[4] + b2 * b2 * tm[5])) /
+                      (1.f - bb);
+      const float l0 = e * (1.f + 1e-6f);
+      const float p = ((l0 - c2) * l0 + c1) * l0 - c0, dp = (3.f * l0 - 2.f * c2) * l0 + c1;
+      if (l0 < 1.f && p >= 0.f && dp > 0.f && 3.f * l0 > c2) lam = l0;
+    }
+  }
   for (int it = 0; it < 60; ++it) {
     const float p = ((lam - c2) * lam + c1) * lam - c0;
     const float dp = (3.f * lam - 2.f * c2) * lam + c1;
