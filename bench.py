@@ -100,7 +100,7 @@ def job_rate(units_per_rank: float, world: int, t_max: float) -> float:
 # stage-kernel headers, comments removed) and is reported only while they are
 # unchanged.
 STAGE_TRAFFIC = {"sources": ("rlb_stage_mp.cuh", "rlb_stage_x2.cuh", "rlb_kernels.cuh"),
-                 "sha1": "995afac85e3311abdf3bf771261c24bea1ea4e09", "bytes_per_launch": 479.81e6}
+                 "sha1": "58dca9d88d17d4433154fd976ca57735f83fd842", "bytes_per_launch": 479.79e6}
 
 
 def code_digest(files) -> str:
