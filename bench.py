@@ -457,6 +457,10 @@ def adjoint_main(args, rank, world, local):
     _, gA64, geta64 = ADJ.v2_gradient(run, eps0, basis, steps, every, arithmetic=rlb.RLB_F64)
     torch.cuda.synchronize()
     t_grad64 = time.perf_counter() - t0
+    t0 = time.perf_counter()  # every step's state kept in HBM: no recompute
+    ADJ.v2_gradient(run, eps0, basis, steps, 1, arithmetic=rlb.RLB_F32)
+    torch.cuda.synchronize()
+    t_grad1 = time.perf_counter() - t0
     clocks = sampler.stop() if sampler else None
     run.check()
     # finite differences of the forward run for the two largest amplitudes
@@ -487,6 +491,8 @@ def adjoint_main(args, rank, world, local):
                                    "adjoint)" % (steps, every),
                        "grid": [side, side], "dtau": DTAU_ADJ, "tau0": TAU0, "forward_s": t_fwd, "gradient_s": t_grad,
                        "gradient_fp64_s": t_grad64, "fp64_over_forward": t_grad64 / t_fwd,
+                       "every_step_kept": {"gradient_s": t_grad1, "over_forward": t_grad1 / t_fwd,
+                                           "device_bytes": steps * run.state_blob_size()},
                        "fp32_vs_fp64_rel": {
                            "amplitudes": float(np.linalg.norm(gA - gA64) / np.linalg.norm(gA64)),
                            "eta": float(abs(geta - geta64) / abs(geta64))},
@@ -758,6 +764,12 @@ def secondary(args, local, torch, rlb):
     ADJ.v2_gradient(run, eps0, basis, steps, 32, arithmetic=rlb.RLB_F32)
     torch.cuda.synchronize()
     t_grad = time.perf_counter() - t0
+    # the same gradient with every step's state kept in HBM (no recompute)
+    run_blob_bytes = run.state_blob_size()
+    t0 = time.perf_counter()
+    ADJ.v2_gradient(run, eps0, basis, steps, 1, arithmetic=rlb.RLB_F32)
+    torch.cuda.synchronize()
+    t_grad1 = time.perf_counter() - t0
     del run
     g64 = rlb.GridParams(nx=side, ny=side, dx=DX, prec=rlb.RLB_F64, eta_over_s=0.08, tau0=TAU0, dtau=DTAU_ADJ)
     run = rlb.Run(g64, device=local)
@@ -769,7 +781,9 @@ def secondary(args, local, torch, rlb):
     out["adjoint_128x128"] = {"dtau": DTAU_ADJ, "gradient_s": t_grad, "forward_fp32_s": t_fwd,
                               "over_forward_fp32": t_grad / t_fwd,
                               "forward_fp64_s": t_fwd64, "over_forward_fp64": t_grad / t_fwd64,
-                              "steps": steps, "checkpoint_every": 32}
+                              "steps": steps, "checkpoint_every": 32,
+                              "every_step_kept": {"gradient_s": t_grad1, "over_forward_fp32": t_grad1 / t_fwd,
+                                                  "device_bytes": steps * run_blob_bytes}}
     # precision sweep: 1024x1024, 16x8x16 lattice
     sweep = {}
     eps0 = hotspots(1024, 1024, n=40, seed=1108)[0]

@@ -9,7 +9,9 @@ checkpoints and wraps the result as a torch.autograd.Function.
 Checkpointing: the forward run stores the state every `every` steps; the
 backward sweep reruns each segment from its checkpoint, storing the state of
 every step of the segment (device blobs), and reverses the steps one by one,
-each reading its input state from its blob in place.  State blobs hold the
+each reading its input state from its blob in place.  With every = 1 nothing
+is recomputed (one blob per step: 52 MB per step on a 128 x 128 grid of 768
+FP32 populations, 15.6 GB for 300 steps).  State blobs hold the
 moments and Newton starting values too, so recomputed steps are bit-exact
 copies of the forward ones.
 """
@@ -94,10 +96,13 @@ def forward_with_checkpoints(run, eps0, steps: int, every: int):
 
 
 def reverse_sweep(run, adj: Adjoint, cks, steps: int, every: int):
-    """Adjoint of the `steps` steps (the adjoint buffers hold the seed)."""
+    """Adjoint of the `steps` steps (the adjoint buffers hold the seed).  A
+    segment of one step needs no recompute: its adjoint reads the checkpoint
+    in place, so the run's state is not restored for it."""
     for start in reversed(range(0, steps, every)):
         end = min(start + every, steps)
-        run.load_state(cks[start])
+        if end - start > 1:
+            run.load_state(cks[start])
         states = [cks[start]]
         for _ in range(start, end - 1):
             run.step(1)

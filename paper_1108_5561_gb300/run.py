@@ -233,12 +233,16 @@ class Run:
                   "rlb_observables")
         return a.value, b.value
 
+    def state_blob_size(self) -> int:
+        n = ctypes.c_size_t()
+        self._chk(self.lib.rlb_state_blob_size(self._h, ctypes.byref(n)), "rlb_state_blob_size")
+        return n.value
+
     def save_state(self, device: bool = False):
         """Checkpoint blob of the current state: host bytes, or a CUDA uint8 tensor
         (filled in stream order; it carries the tau it was saved at, so that
         load_state restores it without reading its header back)."""
-        n = ctypes.c_size_t()
-        self._chk(self.lib.rlb_state_blob_size(self._h, ctypes.byref(n)), "rlb_state_blob_size")
+        n = ctypes.c_size_t(self.state_blob_size())
         if device:
             t = self.torch.empty(n.value, dtype=self.torch.uint8, device=self.device)
             self._chk(self.lib.rlb_save_state(self._h, ctypes.c_void_p(t.data_ptr()), n, self._stream()),
