@@ -344,10 +344,11 @@ rlb_status rlb_moments(rlb_ctx* ctx, double* out, int out_on_device, void* strea
  * the matching runs on `stream` into one of two device staging slots (sites x 8
  * doubles each, allocated by the context at its first call and freed by
  * rlb_destroy), and the download runs on a copy stream of the context, so
- * that the next rlb_step on `stream` overlaps it.  `host_out` must not be touched until
- * rlb_moments_wait returns (it waits for every download enqueued so far and
- * reports the device error word like rlb_check); a slot's next use waits for
- * its previous download.  RLB_ERR_ARG for pageable host memory. */
+ * that the next rlb_step on `stream` overlaps it.  `host_out` (caller-owned)
+ * must stay allocated and untouched until rlb_moments_wait returns (it waits
+ * for every download enqueued so far and reports the device error word like
+ * rlb_check); a slot's next use waits for its previous download.  RLB_ERR_ARG
+ * for pageable host memory. */
 rlb_status rlb_moments_async(rlb_ctx* ctx, double* host_out, void* stream);
 rlb_status rlb_moments_wait(rlb_ctx* ctx);
 
