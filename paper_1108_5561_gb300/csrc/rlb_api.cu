@@ -1703,13 +1703,26 @@ rlb_status rlb_moments_async(rlb_ctx* ctx, double* host_out, void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t slot_b = align256(ctx->ns * 8 * sizeof(double));
   if (!ctx->cstream) {
-    RLB_CUDA(cudaMalloc(&ctx->mstage, 2 * slot_b), "moments staging slots");
-    RLB_CUDA(cudaStreamCreateWithFlags(&ctx->cstream, cudaStreamNonBlocking), "copy stream");
-    for (int i = 0; i < 2; ++i) {
-      RLB_CUDA(cudaEventCreateWithFlags(&ctx->cev_ready[i], cudaEventDisableTiming), "copy event");
-      RLB_CUDA(cudaEventCreateWithFlags(&ctx->cev_done[i], cudaEventDisableTiming), "copy event");
-      RLB_CUDA(cudaEventRecord(ctx->cev_done[i], ctx->cstream), "copy event");
+    // all or nothing: the context keeps the slots, stream and events only
+    // once every one of them exists
+    char* slots = nullptr;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaError_t e = cudaMalloc(&slots, 2 * slot_b);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventRecord(ev[2 + i], cs);
+    if (e != cudaSuccess) {
+      for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+      if (cs) cudaStreamDestroy(cs);
+      if (slots) cudaFree(slots);
+      return cuda_fail(ctx, e, "moments staging slots, copy stream and events");
     }
+    ctx->mstage = slots;
+    ctx->cstream = cs;
+    ctx->cev_ready[0] = ev[0]; ctx->cev_ready[1] = ev[1];
+    ctx->cev_done[0] = ev[2]; ctx->cev_done[1] = ev[3];
   }
   const int k = ctx->cslot;
   ctx->cslot ^= 1;
