@@ -95,3 +95,30 @@ def test_invalid_arguments_are_rejected(lib):
     assert lib.rlb_configure(h, ctypes.byref(gs)) == 0
     assert lib.rlb_step(h, 1, None) == -5  # before init_grid
     lib.rlb_destroy(h)
+
+
+def test_later_entry_points_check_their_arguments_on_the_host(lib):
+    # argument and state checks that return before any device call
+    from paper_1108_5561_gb300 import EosParams, GridParams
+    buf = np.zeros(64)
+    ptr = buf.ctypes.data_as(ctypes.c_void_p)
+    assert lib.rlb_moments_async(None, ptr, None) == -1
+    assert lib.rlb_moments_wait(None) == -1
+    assert lib.rlb_load_state_async(None, ptr, 64, ctypes.c_double(0.4), None) == -1
+    assert lib.rlb_adjoint_step_from(None, ptr, 64, ctypes.c_double(0.4), None) == -1
+    expired = ctypes.c_int()
+    assert lib.rlb_wait_selftest(0, 1, ctypes.c_double(0.0), ctypes.byref(expired), None) == -1
+    assert lib.rlb_wait_selftest(0, 1, ctypes.c_double(5000.0), ctypes.byref(expired), None) == -1
+    h = ctypes.c_void_p()
+    assert lib.rlb_create(ctypes.byref(h), 0) == 0
+    es = EosParams(table_points=256).c_struct()
+    assert lib.rlb_init_eos(h, ctypes.byref(es)) == 0
+    gs = GridParams().c_struct()
+    assert lib.rlb_configure(h, ctypes.byref(gs)) == 0
+    assert lib.rlb_moments_async(h, None, None) == -1
+    assert lib.rlb_moments_async(h, ptr, None) == -5  # before init_grid
+    assert b"init_grid" in lib.rlb_last_error(h)
+    assert lib.rlb_moments_wait(h) == 0  # nothing enqueued
+    assert lib.rlb_load_state_async(h, ptr, 64, ctypes.c_double(0.4), None) == -5  # no bound buffers
+    assert lib.rlb_adjoint_step_from(h, ptr, 64, ctypes.c_double(0.4), None) == -5
+    lib.rlb_destroy(h)
